@@ -1,0 +1,267 @@
+/* glim_lin.h -- C ABI of the B300 linearization library for GLIM matching-cost factors.
+ *
+ * The library evaluates the voxelized-GICP matching-cost factor of GLIM (Koide et al.,
+ * "GLIM: 3D Range-Inertial Localization and Mapping with GPU-Accelerated Scan Matching
+ * Factors", Sec. III-C) on one CUDA device:
+ *
+ *   e    = sum_l sum_k  w_k d_kl^T Omega_kl d_kl                       Eqs. (2)-(3)
+ *   d_kl = mu~_l(k) - T_rel mu_k,   Omega_kl = (C~_l(k) + R C_k R^T)^-1
+ *   A_k  = [R (mu_k)x, -R],  B_k = [-(T_rel mu_k)x, I]                 Eqs. (4)-(5)
+ *   H    = sum [A B]^T Omega [A B],  b = sum [A B]^T Omega d           Eqs. (6)-(8)
+ *
+ * Conventions (the paper leaves them open or prints them inconsistently):
+ *   - a factor pairs a SOURCE frame s (its points mu_k, covariances C_k) with a TARGET
+ *     frame t (its voxelmap); T_rel = T_t^-1 T_s; poses are perturbed on the right,
+ *     T <- T Exp(xi), xi = [omega; v] (rotation first).  With these, A_k and B_k above are
+ *     the exact derivatives of d_k w.r.t. xi_s and xi_t.
+ *   - H is 12 x 12 over [xi_s; xi_t], b has 12 entries; a unary factor (target fixed)
+ *     uses the top-left 6 x 6 block of H and the first 6 entries of b.  With
+ *     e(xi) ~ e + 2 b^T xi + xi^T H xi, the Gauss-Newton step is xi = -H^-1 b.
+ *   - voxel key = floor(q * inv_r) per axis on the FP32 path: q is formed from the FP32
+ *     rounding of T_rel with one fused multiply-add per term (t, then x, y, z), inv_r is
+ *     the FP32 rounding of 1/r.  Keys must lie in [-2^20, 2^20).
+ *   - a voxel holds the mean of its points and the mean of their covariances
+ *     (Sec. III-C "Preprocessing"); level l uses resolution r_l (e.g. r_0 2^(l-1)).
+ *   - surface validation (Sec. III-C "Correspondence search", Fig. 3): a source point is
+ *     discarded when (mu_k - T_s^-1 t_t) . n_k > 0, evaluated in FP32 as
+ *     s = n_x d_x; s = fma(n_y, d_y, s); s = fma(n_z, d_z, s) with d = mu_k - v.
+ *
+ * Memory and ownership: every array argument documented "device" is a pointer to memory
+ * on the context's device, owned by the caller (for example a PyTorch tensor's storage),
+ * contiguous in the layout stated.  "host" arguments are ordinary host memory.  Objects
+ * returned through out-parameters (contexts, voxelmaps, plans) are owned by the library
+ * and released with the matching destroy/free call.  Work is enqueued on the context's
+ * stream; a call that returns host results synchronizes that stream first.
+ *
+ * Errors: no function throws or aborts.  Every call returns a glim_status; on failure
+ * glim_last_error() describes it.  Device-side conditions (hash table full, key out of
+ * range, non-finite input, bounded waits that gave up) are reported through status
+ * words that the host reads, never by trapping the device.
+ */
+#ifndef GLIM_LIN_H
+#define GLIM_LIN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t glim_status;
+#define GLIM_OK 0
+#define GLIM_EINVAL -1    /* invalid argument or non-finite input */
+#define GLIM_ENOMEM -2    /* device or pinned allocation failed */
+#define GLIM_ECUDA -3     /* a CUDA runtime call failed */
+#define GLIM_EHASHFULL -4 /* voxel hash table could not place a key */
+#define GLIM_ERANGE -5    /* a voxel key lies outside [-2^20, 2^20) */
+#define GLIM_ENOTPD -6    /* a Gauss-Newton system is not positive definite */
+#define GLIM_ETIMEOUT -7  /* a bounded device wait gave up */
+
+#define GLIM_MAX_LEVELS 4
+
+/* Accumulation modes of the per-point sums (precision of the partial sums of H, b, e). */
+#define GLIM_ACC_FP32 0  /* FP32 everywhere, including the cross-block sum (naive) */
+#define GLIM_ACC_KAHAN 1 /* FP32 with compensated (Kahan/Neumaier) per-thread and tree sums,
+                            FP64 across blocks */
+#define GLIM_ACC_FP64 2  /* FP32 per thread and per warp, FP64 across warps and blocks */
+
+typedef struct glim_ctx glim_ctx;
+typedef struct glim_vmap glim_vmap;
+typedef struct glim_plan glim_plan;
+
+/* A frame: n points of one scan or submap in its own coordinates (device pointers).
+ *   pts4    n x float4 (x, y, z, w); w is the point's weight (1 for the paper's cost).
+ *   cov6    n x 6 floats (xx, xy, xz, yy, yz, zz), the point covariance C_k.
+ *   normal3 n x 3 floats, the surface normal n_k; NULL disables surface validation
+ *           for points of this frame.  Each pointer must be 16-byte (pts4) or 8-byte
+ *           (cov6) aligned. */
+typedef struct {
+  const float* pts4;
+  const float* cov6;
+  const float* normal3;
+  int64_t n;
+} glim_frame;
+
+/* A factor: source frame index, target frame index, and the target's voxelmap. */
+typedef struct {
+  int32_t src_frame;
+  int32_t tgt_frame;
+  const glim_vmap* tgt;
+} glim_pair;
+
+/* Launch options of the linearization kernels.  Zero fields take defaults.
+ *   validate_surface  1 = apply the surface-orientation test.
+ *   accum_mode        GLIM_ACC_*.
+ *   block             threads per block (128 or 256; default 256).
+ *   pts_per_thread    points per thread per work item (1, 2, 4 or 8; default 4);
+ *                     a work item (tile) covers block * pts_per_thread points of one pair.
+ *   blocks_per_sm     resident blocks per SM of the persistent kernel (default: occupancy).
+ *   persistent        1 (default) = one persistent kernel over an atomic work queue;
+ *                     2 = one block per work item (hardware scheduling). */
+typedef struct {
+  int32_t validate_surface;
+  int32_t accum_mode;
+  int32_t block;
+  int32_t pts_per_thread;
+  int32_t blocks_per_sm;
+  int32_t persistent;
+  int32_t reserved[2];
+} glim_lin_opts;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`, enqueuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = a new non-blocking stream owned by the context). */
+glim_status glim_create(glim_ctx** out, int device, void* cuda_stream);
+void glim_destroy(glim_ctx* ctx);
+/* Text of the last error on this context (never NULL; empty after success). */
+const char* glim_last_error(const glim_ctx* ctx);
+/* Number of SMs of the context's device. */
+int32_t glim_num_sms(const glim_ctx* ctx);
+/* Number of kernels this context has launched since creation (for accounting). */
+int64_t glim_kernel_launches(const glim_ctx* ctx);
+
+/* ---------------------------------------------------------------- covariances */
+
+/* Per-point covariance from the k nearest neighbours (Sec. III-C "Preprocessing";
+ * Sec. IV-A): exact kNN over the frame, the point itself included, ties broken by
+ * (squared distance in FP64, index); sample covariance with 1/k normalisation; then
+ *   reg_mode 0: C = C_sample + eps I
+ *   reg_mode 1: C = I - (1 - eps) n n^T (GICP plane regularisation), n = eigenvector of
+ *               the smallest eigenvalue, oriented so that n . mu <= 0.
+ * pts4 (device, n x float4), cov6_out (device, n x 6), normal3_out (device, n x 3, or
+ * NULL).  3 <= k <= 32, k <= n. */
+glim_status glim_estimate_covariances(glim_ctx* ctx, const float* pts4, int64_t n, int32_t k,
+                                      int32_t reg_mode, float eps, float* cov6_out,
+                                      float* normal3_out);
+
+/* ---------------------------------------------------------------- voxelmaps */
+
+/* Build the multi-resolution voxelmap of one frame (Sec. III-C "Preprocessing"): for each
+ * level, the occupied voxels with the mean of their points and covariances, in an
+ * open-addressing hash table keyed by the packed voxel key.  pts4 / cov6 are device
+ * arrays (n x float4, n x 6); resolutions is a host array of `levels` voxel sizes.
+ * Returns GLIM_ERANGE if a key is outside [-2^20, 2^20), GLIM_EINVAL on non-finite input.
+ * Synchronizes the stream.  The voxelmap keeps no reference to the input arrays. */
+glim_status glim_build_voxelmap(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n,
+                                const double* resolutions, int32_t levels, glim_vmap** out);
+void glim_vmap_free(glim_vmap* vmap);
+/* Number of occupied voxels, hash capacity and longest probe sequence of a level. */
+glim_status glim_vmap_info(const glim_vmap* vmap, int32_t level, int64_t* n_voxels,
+                           int64_t* capacity, int32_t* max_probe);
+/* Copy a level's voxels to device arrays in canonical order (lexicographic (x, y, z) key
+ * order; the position is the canonical voxel id): keys3 (n_voxels x 3 int32), mean3
+ * (n_voxels x 3), cov6 (n_voxels x 6), count (n_voxels int32).  Any output may be NULL. */
+glim_status glim_vmap_export(glim_ctx* ctx, const glim_vmap* vmap, int32_t level, int32_t* keys3,
+                             float* mean3, float* cov6, int32_t* count);
+
+/* Canonical voxel id of every source point at every level of the target map under the
+ * relative pose T_t^-1 T_s (host poses, 12 doubles [R|t] row-major each), or -1 for a
+ * miss or a point discarded by surface validation.  ids_out: device, n x levels int32. */
+glim_status glim_correspondences(glim_ctx* ctx, const glim_frame* src, const glim_vmap* tgt,
+                                 const double* pose_s12, const double* pose_t12,
+                                 int32_t validate_surface, int32_t* ids_out);
+
+/* Overlap rate (Sec. IV-B): for every pair, the fraction of the source points that fall in
+ * an occupied voxel of the target at `level` (surface validation off).  frames, pairs and
+ * poses12 (nframes x 12 doubles) are host arrays; overlap_out is a device array of npairs
+ * doubles.  One launch for all pairs. */
+glim_status glim_overlap(glim_ctx* ctx, const glim_frame* frames, int32_t nframes,
+                         const glim_pair* pairs, int32_t npairs, const double* poses12,
+                         int32_t level, double* overlap_out);
+
+/* ---------------------------------------------------------------- linearization */
+
+/* Linearize every factor of a batch in one pass (Sec. III-C "Linearization" and
+ * "Implementation"): frames (host array of nframes descriptors), pairs (host array),
+ * poses12 (host, nframes x 12 doubles).  Outputs e_out (npairs), H_out (npairs x 144,
+ * row-major 12 x 12), b_out (npairs x 12), inliers_out (npairs, number of (point, level)
+ * correspondences; may be NULL) are all host or all device arrays; with host outputs the
+ * call synchronizes.  Builds a temporary plan; repeated linearizations of the same batch
+ * should use glim_plan_*. */
+glim_status glim_linearize_factors(glim_ctx* ctx, const glim_frame* frames, int32_t nframes,
+                                   const glim_pair* pairs, int32_t npairs, const double* poses12,
+                                   const glim_lin_opts* opts, double* e_out, double* H_out,
+                                   double* b_out, int64_t* inliers_out);
+
+/* Plain per-factor form, for comparison: one kernel launch per factor followed by a stream
+ * synchronization and a copy of that factor's result, as a for-loop over factors would do.
+ * Same arguments and results as glim_linearize_factors (FP32 accumulation). */
+glim_status glim_linearize_factors_plain(glim_ctx* ctx, const glim_frame* frames, int32_t nframes,
+                                         const glim_pair* pairs, int32_t npairs,
+                                         const double* poses12, const glim_lin_opts* opts,
+                                         double* e_out, double* H_out, double* b_out,
+                                         int64_t* inliers_out);
+
+/* A plan fixes a batch (frames, pairs, options) and owns its device work list, partial-sum
+ * slots, a pinned serialized input block (relative poses) and output block (e, H, b,
+ * inliers), and a CUDA graph of [upload, queue reset, linearize, reduce, download].  The
+ * frames and voxelmaps must stay alive and unchanged while the plan exists. */
+glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames, int32_t nframes,
+                             const glim_pair* pairs, int32_t npairs, const glim_lin_opts* opts,
+                             glim_plan** out);
+void glim_plan_destroy(glim_plan* plan);
+/* Linearize at poses12 (host, nframes x 12 doubles): one upload, one graph launch, one
+ * download.  Outputs as in glim_linearize_factors (host or device). */
+glim_status glim_plan_linearize(glim_plan* plan, const double* poses12, double* e_out,
+                                double* H_out, double* b_out, int64_t* inliers_out);
+/* Device-resident use: glim_plan_set_poses uploads the serialized pose block (async);
+ * glim_plan_launch enqueues queue reset, linearize and reduce (no copies, no sync) and
+ * leaves the results in the plan's device output block, whose arrays
+ * glim_plan_device_outputs returns (e: npairs doubles, H: npairs x 144, b: npairs x 12,
+ * inliers: npairs int64). */
+glim_status glim_plan_set_poses(glim_plan* plan, const double* poses12);
+glim_status glim_plan_launch(glim_plan* plan);
+glim_status glim_plan_device_outputs(glim_plan* plan, double** e, double** H, double** b,
+                                     int64_t** inliers);
+/* Kernels enqueued per glim_plan_launch (queue reset excluded). */
+int32_t glim_plan_kernels_per_launch(const glim_plan* plan);
+/* Timing support: enqueue like glim_plan_launch but with direct launches (no graph), and
+ * record two CUDA events on the context's stream immediately before and after the
+ * linearization kernel, in timing slot `slot` (0 <= slot < 4096). */
+glim_status glim_plan_launch_timed(glim_plan* plan, int32_t slot);
+/* Wait for timing slots [0, nslots) and write each slot's linearization-kernel duration in
+ * milliseconds to ms_out (host array of nslots floats). */
+glim_status glim_plan_kernel_ms(glim_plan* plan, int32_t nslots, float* ms_out);
+/* Autotuner: time every (block, pts_per_thread) candidate of the persistent kernel on this
+ * plan's batch at poses12 with CUDA events (`iters` timed launches each, after one warm-up),
+ * keep the fastest in the plan, and write it to best_out (may be NULL). */
+glim_status glim_plan_autotune(glim_plan* plan, const double* poses12, int32_t iters,
+                               glim_lin_opts* best_out, float* best_ms_out);
+/* The options the plan currently uses. */
+glim_status glim_plan_get_opts(const glim_plan* plan, glim_lin_opts* out);
+
+/* ---------------------------------------------------------------- gradient */
+
+/* Gradient of E = sum over pairs of e (Eq. (2), with the weights w_k) at poses12 (host),
+ * correspondences held fixed (piecewise constant):
+ *   dxi_out   device, nframes x 6 doubles: dE/dxi of every frame pose (right perturbation)
+ *   dmu_out   device, the frames' points concatenated in frame order, 3 floats per point:
+ *             dE/dmu_k
+ *   dw_out    device, same concatenation, 1 float per point: dE/dw_k
+ * omega_grad_full = 1 differentiates Omega = (C~ + R C R^T)^-1 through R as well;
+ * 0 holds Omega fixed (then dE/dxi = 2 b).  dE/dmu_k = -2 w_k sum_l R^T Omega_kl d_kl and
+ * dE/dw_k = sum_l d_kl^T Omega_kl d_kl.  Per-point outputs are written, not accumulated;
+ * points of frames that are never a source get zeros.  Deterministic (no float atomics). */
+glim_status glim_backward(glim_ctx* ctx, const glim_frame* frames, int32_t nframes,
+                          const glim_pair* pairs, int32_t npairs, const double* poses12,
+                          int32_t omega_grad_full, int32_t validate_surface, double* dxi_out,
+                          float* dmu_out, float* dw_out);
+
+/* ---------------------------------------------------------------- Gauss-Newton step */
+
+/* Solve `count` systems H xi = -b by Cholesky in FP64 on the device (Sec. III-C: the
+ * Gauss-Newton step of the quadratic factor).  System i uses the dim x dim block
+ * H[i * stride_H + r * ldh + c] and b[i * stride_b + r]; xi_out is count x dim; status_out
+ * (device, count int32, may be NULL) receives GLIM_OK or GLIM_ENOTPD per system.  All
+ * pointers are device pointers.  1 <= dim <= 12.  Returns GLIM_ENOTPD if any system is not
+ * positive definite (after synchronizing), else GLIM_OK. */
+glim_status glim_gn_solve(glim_ctx* ctx, const double* H, int32_t ldh, int64_t stride_H,
+                          const double* b, int64_t stride_b, int32_t dim, int64_t count,
+                          double* xi_out, int32_t* status_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GLIM_LIN_H */

@@ -445,6 +445,7 @@ struct PairResult {
   long double bL[12] = {};
   int64_t inliers = 0;
   int64_t skipped = 0;
+  double babs = 0;  // sum over terms of |w J^T Omega d|_2, a cancellation-free scale of b
 };
 
 struct PairCtx {
@@ -506,6 +507,7 @@ void accumulate_term(const Pose& T, const float* mu4, const float* cov6, const V
     for (int c = 0; c < 12; ++c) OJ[i][c] = Om[i][0] * J[0][c] + Om[i][1] * J[1][c] + Om[i][2] * J[2][c];
   out.e += w * e;
   out.eL += (long double)(w * e);
+  double gsq = 0;
   for (int r = 0; r < 12; ++r) {
     for (int c = 0; c < 12; ++c) {
       double h = J[0][r] * OJ[0][c] + J[1][r] * OJ[1][c] + J[2][r] * OJ[2][c];
@@ -515,7 +517,9 @@ void accumulate_term(const Pose& T, const float* mu4, const float* cov6, const V
     double g = J[0][r] * Od[0] + J[1][r] * Od[1] + J[2][r] * Od[2];
     out.b[r] += w * g;
     out.bL[r] += (long double)(w * g);
+    gsq += (w * g) * (w * g);
   }
+  out.babs += std::sqrt(gsq);
   out.inliers += 1;
 }
 
@@ -540,7 +544,8 @@ extern "C" {
 // concatenated over pairs in pair order.  ids_in (nullable): same layout; if given, these
 // correspondences are used instead of the lookup (frozen correspondences).
 // comp_out (nullable): per pair 1 + 144 + 12 values accumulated in long double, the
-// oracle's own rounding reference.
+// oracle's own rounding reference, then the cancellation-free scale of b (sum over terms
+// of |w J^T Omega d|_2): 158 values per pair.
 int orc_linearize(const orc_frame* frames, int nframes, void* const* vmaps, const orc_pair* pairs,
                   int npairs, const double* poses12, const orc_opts* opts, double* e_out,
                   double* H_out, double* b_out, int64_t* inliers_out, int64_t* skipped_out,
@@ -586,11 +591,12 @@ int orc_linearize(const orc_frame* frames, int nframes, void* const* vmaps, cons
     if (inliers_out) inliers_out[p] = res.inliers;
     if (skipped_out) skipped_out[p] = res.skipped;
     if (comp_out) {
-      double* o = comp_out + 157 * p;
+      double* o = comp_out + 158 * p;
       o[0] = double(res.eL);
       for (int r = 0; r < 12; ++r)
         for (int c = 0; c < 12; ++c) o[1 + 12 * r + c] = double(res.HL[r][c]);
       for (int r = 0; r < 12; ++r) o[145 + r] = double(res.bL[r]);
+      o[157] = res.babs;
     }
   });
   return ORC_OK;

@@ -198,7 +198,7 @@ def linearize(frames, vmaps, pairs, poses, validate=False, omega_identity=False,
     if ids_in is not None:
         ids_in = np.ascontiguousarray(ids_in, dtype=np.int32)
         assert ids_in.size == nid
-    comp = np.zeros((P, 157)) if want_comp else None
+    comp = np.zeros((P, 158)) if want_comp else None
     opts = _opts(validate, omega_identity, True, nthreads)
     st = lib().orc_linearize(fr, len(frames), _vmaps(vmaps), _pairs(pairs), P, _ptr(poses), C.byref(opts),
                              _ptr(e), _ptr(H), _ptr(b), _ptr(inl), _ptr(skp), _ptr(ids), _ptr(ids_in),
@@ -211,7 +211,8 @@ def linearize(frames, vmaps, pairs, poses, validate=False, omega_identity=False,
     if want_comp:
         out["comp_e"] = comp[:, 0]
         out["comp_H"] = comp[:, 1:145].reshape(P, 12, 12)
-        out["comp_b"] = comp[:, 145:]
+        out["comp_b"] = comp[:, 145:157]
+        out["b_scale"] = comp[:, 157]
     return out
 
 

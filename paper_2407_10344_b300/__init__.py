@@ -1,0 +1,11 @@
+"""B300-native linearization of GLIM matching-cost factors (voxelized GICP, Sec. III-C).
+
+The compute path is the CUDA library ``libglimlin.so`` (C ABI in ``include/glim_lin.h``);
+this package only marshals arguments to it.  See ``api`` for the calls and ``autograd`` for
+the differentiable cost.
+"""
+from .api import (ACC_FP32, ACC_FP64, ACC_KAHAN, Context, FrameData, GlimError, Plan, VoxelMap, backward,
+                  correspondences, estimate_covariances, gn_solve, linearize, overlap, to_pts4)
+
+__all__ = ["ACC_FP32", "ACC_FP64", "ACC_KAHAN", "Context", "FrameData", "GlimError", "Plan", "VoxelMap",
+           "backward", "correspondences", "estimate_covariances", "gn_solve", "linearize", "overlap", "to_pts4"]

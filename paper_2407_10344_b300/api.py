@@ -1,0 +1,363 @@
+"""Python face of the linearization library: thin wrappers over the C ABI that take
+PyTorch CUDA tensors (device memory) and numpy arrays (host poses).
+
+Every computation happens in the CUDA library; this module only checks shapes and
+dtypes, passes pointers and reports errors.  There is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi
+
+ACC_FP32, ACC_KAHAN, ACC_FP64 = _abi.ACC_FP32, _abi.ACC_KAHAN, _abi.ACC_FP64
+
+
+class GlimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_abi.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(t.data_ptr())
+
+
+def _dev(t, dtype, shape1=None, name="tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape1 is not None and (t.dim() != 2 or t.shape[1] != shape1):
+        raise ValueError(f"{name} must have shape (n, {shape1}), got {tuple(t.shape)}")
+    return t
+
+
+def _poses(poses, nframes=None):
+    P = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(-1, 12))
+    if nframes is not None and len(P) != nframes:
+        raise ValueError(f"expected {nframes} poses, got {len(P)}")
+    return P
+
+
+class Context:
+    """A library context on one CUDA device, enqueuing on a torch stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (the library has no CPU path)")
+        self.lib = _abi.load()
+        self.device = device
+        with torch.cuda.device(device):
+            self.stream = stream or torch.cuda.current_stream(device)
+        h = C.c_void_p()
+        st = self.lib.glim_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise GlimError(st, "glim_create failed")
+        self.h = h
+
+    def check(self, st, what):
+        if st != 0:
+            raise GlimError(st, f"{what}: {self.lib.glim_last_error(self.h).decode()}")
+
+    @property
+    def num_sms(self):
+        return int(self.lib.glim_num_sms(self.h))
+
+    @property
+    def kernel_launches(self):
+        return int(self.lib.glim_kernel_launches(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.glim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def to_pts4(points, weights=None, device="cuda"):
+    """(n, 3) points (+ optional (n,) weights) -> contiguous float32 (n, 4) CUDA tensor."""
+    p = torch.as_tensor(np.asarray(points, dtype=np.float32)) if not isinstance(points, torch.Tensor) else points
+    out = torch.ones((p.shape[0], 4), dtype=torch.float32, device=device)
+    out[:, :3] = p[:, :3].to(device=device, dtype=torch.float32)
+    if weights is not None:
+        w = torch.as_tensor(np.asarray(weights, dtype=np.float32)) if not isinstance(weights, torch.Tensor) else weights
+        out[:, 3] = w.to(device=device, dtype=torch.float32)
+    return out
+
+
+def estimate_covariances(ctx: Context, pts4: torch.Tensor, k: int = 10, reg_mode: int = 1, eps: float = 1e-3,
+                         normals: bool = True):
+    """kNN covariances (n, 6) and normals (n, 3) of one frame."""
+    _dev(pts4, torch.float32, 4, "pts4")
+    n = pts4.shape[0]
+    cov = torch.empty((n, 6), dtype=torch.float32, device=pts4.device)
+    nrm = torch.empty((n, 3), dtype=torch.float32, device=pts4.device) if normals else None
+    ctx.check(ctx.lib.glim_estimate_covariances(ctx.h, _ptr(pts4), n, k, reg_mode, eps, _ptr(cov), _ptr(nrm)),
+              "estimate_covariances")
+    return cov, nrm
+
+
+class VoxelMap:
+    """Multi-resolution voxelmap of one frame (library-owned device tables)."""
+
+    def __init__(self, ctx: Context, pts4: torch.Tensor, cov6: torch.Tensor, resolutions):
+        _dev(pts4, torch.float32, 4, "pts4")
+        _dev(cov6, torch.float32, 6, "cov6")
+        if pts4.shape[0] != cov6.shape[0]:
+            raise ValueError("pts4 and cov6 differ in length")
+        self.ctx = ctx
+        self.resolutions = [float(r) for r in resolutions]
+        res = np.ascontiguousarray(self.resolutions, dtype=np.float64)
+        h = C.c_void_p()
+        ctx.check(ctx.lib.glim_build_voxelmap(ctx.h, _ptr(pts4), _ptr(cov6), pts4.shape[0], _ptr(res), len(res),
+                                              C.byref(h)), "build_voxelmap")
+        self.h = h
+
+    @property
+    def levels(self):
+        return len(self.resolutions)
+
+    def info(self, level):
+        n, cap, mp = C.c_int64(), C.c_int64(), C.c_int32()
+        self.ctx.check(self.ctx.lib.glim_vmap_info(self.h, level, C.byref(n), C.byref(cap), C.byref(mp)), "vmap_info")
+        return dict(n_voxels=n.value, capacity=cap.value, max_probe=mp.value)
+
+    def export(self, level):
+        m = self.info(level)["n_voxels"]
+        dev = torch.device("cuda", self.ctx.device)
+        keys = torch.empty((m, 3), dtype=torch.int32, device=dev)
+        mean = torch.empty((m, 3), dtype=torch.float32, device=dev)
+        cov = torch.empty((m, 6), dtype=torch.float32, device=dev)
+        cnt = torch.empty((m,), dtype=torch.int32, device=dev)
+        self.ctx.check(self.ctx.lib.glim_vmap_export(self.ctx.h, self.h, level, _ptr(keys), _ptr(mean), _ptr(cov),
+                                                     _ptr(cnt)), "vmap_export")
+        return dict(keys=keys, mean=mean, cov=cov, count=cnt)
+
+    def free(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.glim_vmap_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class FrameData:
+    """Device arrays of one frame: points (n, 4) with weights in the fourth lane, covariances
+    (n, 6) and optional normals (n, 3)."""
+
+    def __init__(self, pts4, cov6, normal3=None):
+        self.pts4 = _dev(pts4, torch.float32, 4, "pts4")
+        self.cov6 = _dev(cov6, torch.float32, 6, "cov6")
+        self.normal3 = None if normal3 is None else _dev(normal3, torch.float32, 3, "normal3")
+
+    @property
+    def n(self):
+        return self.pts4.shape[0]
+
+    def c(self):
+        return _abi.Frame(self.pts4.data_ptr(), self.cov6.data_ptr(),
+                          None if self.normal3 is None else self.normal3.data_ptr(), self.n)
+
+
+def _frames(frames):
+    arr = (_abi.Frame * max(len(frames), 1))()
+    for i, f in enumerate(frames):
+        arr[i] = f.c()
+    return arr
+
+
+def _pairs(pairs, vmaps):
+    """pairs: (P, 2) (source, target); vmaps: per frame VoxelMap or None (target frames)."""
+    pairs = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+    arr = (_abi.Pair * max(len(pairs), 1))()
+    for i, (s, t) in enumerate(pairs):
+        vm = vmaps[int(t)]
+        if vm is None:
+            raise ValueError(f"pair {i}: target frame {t} has no voxelmap")
+        arr[i] = _abi.Pair(int(s), int(t), vm.h.value)
+    return arr, len(pairs)
+
+
+def _opts(validate_surface=False, accum_mode=ACC_FP64, block=0, pts_per_thread=0, blocks_per_sm=0,
+          persistent=0):
+    o = _abi.LinOpts()
+    o.validate_surface = int(validate_surface)
+    o.accum_mode = int(accum_mode)
+    o.block = int(block)
+    o.pts_per_thread = int(pts_per_thread)
+    o.blocks_per_sm = int(blocks_per_sm)
+    o.persistent = int(persistent)
+    return o
+
+
+def _outputs(npairs, device):
+    if device == "host":
+        return (np.zeros(npairs), np.zeros((npairs, 12, 12)), np.zeros((npairs, 12)),
+                np.zeros(npairs, dtype=np.int64))
+    return (torch.empty(npairs, dtype=torch.float64, device=device),
+            torch.empty((npairs, 12, 12), dtype=torch.float64, device=device),
+            torch.empty((npairs, 12), dtype=torch.float64, device=device),
+            torch.empty(npairs, dtype=torch.int64, device=device))
+
+
+def linearize(ctx: Context, frames, vmaps, pairs, poses, out="host", plain=False, **opts):
+    """e (P,), H (P, 12, 12), b (P, 12), inliers (P,) of every (source, target) pair at poses
+    (nframes, 3, 4).  out = "host" (numpy) or a torch device (CUDA tensors)."""
+    fr = _frames(frames)
+    pr, P = _pairs(pairs, vmaps)
+    Pz = _poses(poses, len(frames))
+    o = _opts(**opts)
+    e, H, b, inl = _outputs(P, out)
+    fn = ctx.lib.glim_linearize_factors_plain if plain else ctx.lib.glim_linearize_factors
+    ctx.check(fn(ctx.h, fr, len(frames), pr, P, _ptr(Pz), C.byref(o), _ptr(e), _ptr(H), _ptr(b), _ptr(inl)),
+              "linearize_factors_plain" if plain else "linearize_factors")
+    return e, H, b, inl
+
+
+class Plan:
+    """A fixed batch of factors: work list, serialized I/O blocks and CUDA graphs."""
+
+    def __init__(self, ctx: Context, frames, vmaps, pairs, **opts):
+        self.ctx = ctx
+        self.frames = list(frames)
+        self.vmaps = list(vmaps)
+        fr = _frames(self.frames)
+        pr, P = _pairs(pairs, self.vmaps)
+        self.npairs = P
+        self.nframes = len(self.frames)
+        o = _opts(**opts)
+        h = C.c_void_p()
+        ctx.check(ctx.lib.glim_plan_create(ctx.h, fr, self.nframes, pr, P, C.byref(o), C.byref(h)), "plan_create")
+        self.h = h
+        self._host = _outputs(P, "host")
+
+    def linearize(self, poses, out=None):
+        """One upload, one graph launch, one download; returns host arrays (e, H, b, inliers)."""
+        Pz = _poses(poses, self.nframes)
+        e, H, b, inl = out if out is not None else self._host
+        self.ctx.check(self.ctx.lib.glim_plan_linearize(self.h, _ptr(Pz), _ptr(e), _ptr(H), _ptr(b), _ptr(inl)),
+                       "plan_linearize")
+        return e, H, b, inl
+
+    def set_poses(self, poses):
+        Pz = _poses(poses, self.nframes)
+        self.ctx.check(self.ctx.lib.glim_plan_set_poses(self.h, _ptr(Pz)), "plan_set_poses")
+
+    def launch(self):
+        self.ctx.check(self.ctx.lib.glim_plan_launch(self.h), "plan_launch")
+
+    def launch_timed(self, slot):
+        """Direct launches with CUDA events around the linearization kernel (timing slot)."""
+        self.ctx.check(self.ctx.lib.glim_plan_launch_timed(self.h, slot), "plan_launch_timed")
+
+    def kernel_ms(self, nslots):
+        out = (C.c_float * max(nslots, 1))()
+        self.ctx.check(self.ctx.lib.glim_plan_kernel_ms(self.h, nslots, out), "plan_kernel_ms")
+        return np.array(out[:nslots], dtype=np.float64)
+
+    @property
+    def kernels_per_launch(self):
+        return int(self.ctx.lib.glim_plan_kernels_per_launch(self.h))
+
+    def device_outputs(self):
+        """Views of the plan's device output block (valid until the next launch)."""
+        e, H, b, inl = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+        self.ctx.check(self.ctx.lib.glim_plan_device_outputs(self.h, C.byref(e), C.byref(H), C.byref(b),
+                                                             C.byref(inl)), "plan_device_outputs")
+        return e.value, H.value, b.value, inl.value
+
+    def autotune(self, poses, iters=5):
+        Pz = _poses(poses, self.nframes)
+        o = _abi.LinOpts()
+        ms = C.c_float()
+        self.ctx.check(self.ctx.lib.glim_plan_autotune(self.h, _ptr(Pz), iters, C.byref(o), C.byref(ms)),
+                       "plan_autotune")
+        return dict(block=o.block, pts_per_thread=o.pts_per_thread, ms=ms.value)
+
+    def opts(self):
+        o = _abi.LinOpts()
+        self.ctx.check(self.ctx.lib.glim_plan_get_opts(self.h, C.byref(o)), "plan_get_opts")
+        return dict(validate_surface=o.validate_surface, accum_mode=o.accum_mode, block=o.block,
+                    pts_per_thread=o.pts_per_thread, blocks_per_sm=o.blocks_per_sm, persistent=o.persistent)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.glim_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def correspondences(ctx: Context, frame: FrameData, vmap: VoxelMap, pose_s, pose_t, validate_surface=False):
+    """Canonical voxel id (n, levels) of every source point, -1 for a miss."""
+    ids = torch.empty((frame.n, vmap.levels), dtype=torch.int32, device=frame.pts4.device)
+    f = frame.c()
+    ps = _poses(pose_s)
+    pt = _poses(pose_t)
+    ctx.check(ctx.lib.glim_correspondences(ctx.h, C.byref(f), vmap.h, _ptr(ps), _ptr(pt), int(validate_surface),
+                                           _ptr(ids)), "correspondences")
+    return ids
+
+
+def overlap(ctx: Context, frames, vmaps, pairs, poses, level=0):
+    fr = _frames(frames)
+    pr, P = _pairs(pairs, vmaps)
+    Pz = _poses(poses, len(frames))
+    out = torch.empty(P, dtype=torch.float64, device=frames[0].pts4.device)
+    ctx.check(ctx.lib.glim_overlap(ctx.h, fr, len(frames), pr, P, _ptr(Pz), level, _ptr(out)), "overlap")
+    return out
+
+
+def backward(ctx: Context, frames, vmaps, pairs, poses, omega_grad_full=True, validate_surface=False):
+    """dE/dxi (nframes, 6) f64, dE/dmu (sum n, 3) f32, dE/dw (sum n,) f32 as CUDA tensors."""
+    fr = _frames(frames)
+    pr, P = _pairs(pairs, vmaps)
+    Pz = _poses(poses, len(frames))
+    dev = frames[0].pts4.device
+    ntot = sum(f.n for f in frames)
+    dxi = torch.empty((len(frames), 6), dtype=torch.float64, device=dev)
+    dmu = torch.empty((ntot, 3), dtype=torch.float32, device=dev)
+    dw = torch.empty((ntot,), dtype=torch.float32, device=dev)
+    ctx.check(ctx.lib.glim_backward(ctx.h, fr, len(frames), pr, P, _ptr(Pz), int(omega_grad_full),
+                                    int(validate_surface), _ptr(dxi), _ptr(dmu), _ptr(dw)), "backward")
+    return dxi, dmu, dw
+
+
+def gn_solve(ctx: Context, H: torch.Tensor, b: torch.Tensor, dim: int = None):
+    """Solve H xi = -b per system; H (count, d, d) or (count, 12, 12) with dim 6 taking the
+    top-left block; b (count, >= dim).  Returns xi (count, dim) and per-system status."""
+    _dev(H, torch.float64, name="H")
+    _dev(b, torch.float64, name="b")
+    count = H.shape[0]
+    ld = H.shape[-1]
+    dim = dim or ld
+    xi = torch.empty((count, dim), dtype=torch.float64, device=H.device)
+    status = torch.empty(count, dtype=torch.int32, device=H.device)
+    st = ctx.lib.glim_gn_solve(ctx.h, _ptr(H), ld, H.shape[-2] * ld, _ptr(b), b.shape[-1], dim, count, _ptr(xi),
+                               _ptr(status))
+    if st not in (0, -6):
+        ctx.check(st, "gn_solve")
+    return xi, status

@@ -1,0 +1,317 @@
+// backward.cu -- gradient of the summed matching cost E = sum_pairs e (Eq. (2) with the
+// per-point weights) for automatic differentiation.  Correspondences are held fixed
+// (piecewise constant); the per-point Jacobians are recomputed rather than stored.
+//
+// For a hit (point k, level l) with y = Omega d, e = d^T y, z = R^T y:
+//   dE/dxi_s, dE/dxi_t (Omega fixed)  = 2 Lift^T g   with g = sum G^T (w y)  (the forward's 2 b)
+//   dE/domega_s (through Omega)      += 2 w (z x C_k z)
+//   dE/domega_t (through Omega)      += -R (2 w (z x C_k z))
+//   dE/dmu_k                          = -2 w R^T sum_l y_l
+//   dE/dw_k                           = sum_l e_l
+// The Omega terms follow from dE/dS = -w y y^T and dS/domega_s,a = R (e_a x C - C e_a x) R^T,
+// dS/domega_t,a = -(e_a x) S' + S' (e_a x) with S' = R C R^T.
+//
+// Pipeline: per work item (pair, tile) the 9 sums (g: 6, a: 3) are block-reduced into the
+// item's slot, and each point writes its (dE/dmu, dE/dw) for that pair into a per-(pair,
+// point) slot; then fixed-order FP64 sums per pair, per frame, and per point.  No float
+// atomics, so the gradient repeats bit for bit.
+#include <algorithm>
+#include <cstring>
+
+#include "plan.cuh"
+
+namespace {
+
+constexpr int BSTRIDE = 12;  // doubles per item slot: g (6), a (3), 3 spare
+
+struct BwdArgs {
+  const Item* items;
+  int32_t nitems;
+  const PairDev* pairs;
+  const FrameDev* frames;
+  const MapDev* maps;
+  const PoseF* pose;
+  int32_t tile;
+  int32_t validate;
+  int32_t full;
+  const int64_t* pair_pt_off;  // npairs: offset of the pair's points in pp
+  float4* pp;                  // per (pair, point): dE/dmu (xyz), dE/dw
+  double* part;                // nitems x BSTRIDE
+};
+
+__global__ void __launch_bounds__(256) k_backward_items(const BwdArgs a) {
+  const int item = blockIdx.x;
+  if (item >= a.nitems) return;
+  const Item it = a.items[item];
+  __shared__ PairView V;
+  __shared__ float s_red[8][9];
+  if (threadIdx.x == 0) {
+    const PairDev pd = a.pairs[it.pair];
+    const PoseF pf = a.pose[it.pair];
+    for (int i = 0; i < 9; ++i) V.R[i] = pf.R[i];
+    for (int i = 0; i < 3; ++i) {
+      V.t[i] = pf.t[i];
+      V.v[i] = pf.v[i];
+    }
+    V.F = a.frames[pd.src];
+    V.M = a.maps[pd.map];
+  }
+  __syncthreads();
+  float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const int64_t k = int64_t(it.start) + threadIdx.x;
+  if (k < V.F.n && threadIdx.x < a.tile) {
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 m = V.F.pts[k];
+    bool visible = true;
+    if (a.validate && V.F.nrm)
+      visible = !behind_surface(m.x, m.y, m.z, V.v, V.F.nrm[3 * k], V.F.nrm[3 * k + 1], V.F.nrm[3 * k + 2]);
+    if (visible) {
+      const float2 ca = V.F.cov[3 * k], cb = V.F.cov[3 * k + 1], cc = V.F.cov[3 * k + 2];
+      const float c00 = ca.x, c01 = ca.y, c02 = cb.x, c11 = cb.y, c12 = cc.x, c22 = cc.y;
+      const float* R = V.R;
+      const float3 q = transform_pinned(R, V.t, m.x, m.y, m.z);
+      const float3 u = make_float3(q.x - V.t[0], q.y - V.t[1], q.z - V.t[2]);
+      // R C R^T
+      float W[3][3], S[3][3];
+      const float C[3][3] = {{c00, c01, c02}, {c01, c11, c12}, {c02, c12, c22}};
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) W[i][j] = R[3 * i] * C[0][j] + R[3 * i + 1] * C[1][j] + R[3 * i + 2] * C[2][j];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) S[i][j] = W[i][0] * R[3 * j] + W[i][1] * R[3 * j + 1] + W[i][2] * R[3 * j + 2];
+      float Y[3] = {0, 0, 0}, E = 0.f, av[3] = {0, 0, 0};
+      for (int l = 0; l < V.M.levels; ++l) {
+        const LevelDev& L = V.M.lv[l];
+        unsigned long long key;
+        if (!level_key(q, L.inv_r, key)) continue;
+        const int s = probe_slot(L, key);
+        if (s < 0) continue;
+        const float4 v0 = L.slots[s].w0, v1 = L.slots[s].w1, v2 = L.slots[s].w2;
+        const float sa = v1.w + S[0][0], sb = v2.x + S[0][1], sc = v2.y + S[0][2], sd = v2.z + S[1][1],
+                    se = v2.w + S[1][2], sf = v0.w + S[2][2];
+        const float A00 = sd * sf - se * se, A01 = sc * se - sb * sf, A02 = sb * se - sc * sd;
+        const float A11 = sa * sf - sc * sc, A12 = sb * sc - sa * se, A22 = sa * sd - sb * sb;
+        const float det = sa * A00 + sb * A01 + sc * A02;
+        if (!(det > 0.f) || !isfinite(det)) continue;
+        const float id = __frcp_rn(det);
+        const float O[3][3] = {{A00 * id, A01 * id, A02 * id}, {A01 * id, A11 * id, A12 * id},
+                               {A02 * id, A12 * id, A22 * id}};
+        const float d[3] = {v1.x - q.x, v1.y - q.y, v1.z - q.z};
+        float y[3];
+        for (int i = 0; i < 3; ++i) y[i] = O[i][0] * d[0] + O[i][1] * d[1] + O[i][2] * d[2];
+        E += d[0] * y[0] + d[1] * y[1] + d[2] * y[2];
+        for (int i = 0; i < 3; ++i) Y[i] += y[i];
+        if (a.full) {
+          float z[3], Cz[3];
+          for (int i = 0; i < 3; ++i) z[i] = R[i] * y[0] + R[3 + i] * y[1] + R[6 + i] * y[2];  // R^T y
+          for (int i = 0; i < 3; ++i) Cz[i] = C[i][0] * z[0] + C[i][1] * z[1] + C[i][2] * z[2];
+          av[0] += z[1] * Cz[2] - z[2] * Cz[1];
+          av[1] += z[2] * Cz[0] - z[0] * Cz[2];
+          av[2] += z[0] * Cz[1] - z[1] * Cz[0];
+        }
+      }
+      const float w = m.w;
+      // dE/dmu = -2 w R^T Y, dE/dw = E
+      out.x = -2.f * w * (R[0] * Y[0] + R[3] * Y[1] + R[6] * Y[2]);
+      out.y = -2.f * w * (R[1] * Y[0] + R[4] * Y[1] + R[7] * Y[2]);
+      out.z = -2.f * w * (R[2] * Y[0] + R[5] * Y[1] + R[8] * Y[2]);
+      out.w = E;
+      const float wy[3] = {w * Y[0], w * Y[1], w * Y[2]};
+      acc[0] = u.y * wy[2] - u.z * wy[1];
+      acc[1] = u.z * wy[0] - u.x * wy[2];
+      acc[2] = u.x * wy[1] - u.y * wy[0];
+      acc[3] = wy[0];
+      acc[4] = wy[1];
+      acc[5] = wy[2];
+      acc[6] = 2.f * w * av[0];
+      acc[7] = 2.f * w * av[1];
+      acc[8] = 2.f * w * av[2];
+    }
+    a.pp[a.pair_pt_off[it.pair] + k] = out;
+  }
+  // block reduction: warp trees in FP32, warps summed in FP64 (fixed order)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    float v = acc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_red[warp][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double t = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += double(s_red[w][threadIdx.x]);
+    a.part[int64_t(item) * BSTRIDE + threadIdx.x] = t;
+  }
+}
+
+// per pair: dxi_pair (12) = 2 Lift^T g + [a; 0; -R a; 0]
+__global__ void k_backward_pairs(const double* __restrict__ part, const int32_t* __restrict__ item_begin,
+                                 const double* __restrict__ pose64, int npairs, double* __restrict__ pair_grad) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = item_begin[p]; i < item_begin[p + 1]; ++i)
+    for (int c = 0; c < 9; ++c) s[c] += part[int64_t(i) * BSTRIDE + c];
+  const double* P = pose64 + 12 * int64_t(p);
+  const double* R = P;
+  const double t[3] = {P[9], P[10], P[11]};
+  const double gr[3] = {s[0], s[1], s[2]}, gt[3] = {s[3], s[4], s[5]}, av[3] = {s[6], s[7], s[8]};
+  double* o = pair_grad + 12 * int64_t(p);
+  for (int i = 0; i < 3; ++i) {
+    // source: 2 b_s = -2 [R^T g_r; R^T g_t]
+    o[i] = -2.0 * (R[i] * gr[0] + R[3 + i] * gr[1] + R[6 + i] * gr[2]) + av[i];
+    o[3 + i] = -2.0 * (R[i] * gt[0] + R[3 + i] * gt[1] + R[6 + i] * gt[2]);
+  }
+  // target: 2 b_t = 2 [g_r + t x g_t; g_t]
+  const double txg[3] = {t[1] * gt[2] - t[2] * gt[1], t[2] * gt[0] - t[0] * gt[2], t[0] * gt[1] - t[1] * gt[0]};
+  for (int i = 0; i < 3; ++i) {
+    o[6 + i] = 2.0 * (gr[i] + txg[i]) - (R[3 * i] * av[0] + R[3 * i + 1] * av[1] + R[3 * i + 2] * av[2]);
+    o[9 + i] = 2.0 * gt[i];
+  }
+}
+
+__global__ void k_backward_frames(const double* __restrict__ pair_grad, const PairDev* __restrict__ pairs,
+                                  const int32_t* __restrict__ tgt, int npairs, int nframes, double* __restrict__ dxi) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nframes) return;
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  for (int p = 0; p < npairs; ++p) {
+    if (pairs[p].src == f)
+      for (int c = 0; c < 6; ++c) s[c] += pair_grad[12 * int64_t(p) + c];
+    if (tgt[p] == f)
+      for (int c = 0; c < 6; ++c) s[c] += pair_grad[12 * int64_t(p) + 6 + c];
+  }
+  for (int c = 0; c < 6; ++c) dxi[6 * int64_t(f) + c] = s[c];
+}
+
+// per point of every frame: sum over the pairs that have the frame as source, in pair order
+__global__ void k_backward_points(const float4* __restrict__ pp, const int64_t* __restrict__ pair_pt_off,
+                                  const int32_t* __restrict__ src_list, const int32_t* __restrict__ src_begin,
+                                  const int64_t* __restrict__ frame_off, const int32_t* __restrict__ point_frame_hint,
+                                  int nframes, int64_t ntot, float* __restrict__ dmu, float* __restrict__ dw) {
+  const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (g >= ntot) return;
+  // frame of global point g (binary search over frame offsets)
+  int lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (frame_off[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  (void)point_frame_hint;
+  const int f = lo;
+  const int64_t k = g - frame_off[f];
+  float sx = 0.f, sy = 0.f, sz = 0.f, sw = 0.f;
+  for (int j = src_begin[f]; j < src_begin[f + 1]; ++j) {
+    const float4 v = pp[pair_pt_off[src_list[j]] + k];
+    sx += v.x;
+    sy += v.y;
+    sz += v.z;
+    sw += v.w;
+  }
+  if (dmu) {
+    dmu[3 * g] = sx;
+    dmu[3 * g + 1] = sy;
+    dmu[3 * g + 2] = sz;
+  }
+  if (dw) dw[g] = sw;
+}
+
+}  // namespace
+
+extern "C" glim_status glim_backward(glim_ctx* ctx, const glim_frame* frames, int32_t nframes, const glim_pair* pairs,
+                                     int32_t npairs, const double* poses12, int32_t omega_grad_full,
+                                     int32_t validate_surface, double* dxi_out, float* dmu_out, float* dw_out) {
+  if (!ctx) return GLIM_EINVAL;
+  if (!poses12 || (nframes > 0 && !dxi_out)) return set_error(ctx, GLIM_EINVAL, "backward: null argument");
+  glim_lin_opts o{};
+  o.block = 256;
+  o.pts_per_thread = 1;
+  o.persistent = 2;
+  o.accum_mode = GLIM_ACC_FP64;
+  o.validate_surface = validate_surface;
+  glim_plan* p = nullptr;
+  glim_status st = glim_plan_create(ctx, frames, nframes, pairs, npairs, &o, &p);
+  if (st != GLIM_OK) return st;
+  auto done = [&](glim_status s) {
+    glim_plan_destroy(p);
+    return s;
+  };
+  plan_pack_poses(p, poses12);
+  if (cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+    return done(set_error(ctx, GLIM_ECUDA, "backward: upload failed"));
+  // host-side tables
+  std::vector<int64_t> pair_off(std::max(npairs, 1), 0), frame_off(nframes + 1, 0);
+  int64_t npp = 0;
+  for (int q = 0; q < npairs; ++q) {
+    pair_off[q] = npp;
+    npp += frames[pairs[q].src_frame].n;
+  }
+  for (int f = 0; f < nframes; ++f) frame_off[f + 1] = frame_off[f] + frames[f].n;
+  const int64_t ntot = frame_off[nframes];
+  std::vector<int32_t> src_begin(nframes + 1, 0), src_list, tgt(std::max(npairs, 1), 0);
+  for (int f = 0; f < nframes; ++f) {
+    src_begin[f] = int32_t(src_list.size());
+    for (int q = 0; q < npairs; ++q)
+      if (pairs[q].src_frame == f) src_list.push_back(q);
+  }
+  src_begin[nframes] = int32_t(src_list.size());
+  for (int q = 0; q < npairs; ++q) tgt[q] = pairs[q].tgt_frame;
+  if (src_list.empty()) src_list.push_back(0);
+  DevBuf<int64_t> d_pair_off, d_frame_off;
+  DevBuf<int32_t> d_src_begin, d_src_list, d_tgt;
+  DevBuf<float4> d_pp;
+  DevBuf<double> d_part, d_pair_grad;
+  if (d_pair_off.alloc(pair_off.size(), ctx->stream) != cudaSuccess ||
+      d_frame_off.alloc(frame_off.size(), ctx->stream) != cudaSuccess ||
+      d_src_begin.alloc(src_begin.size(), ctx->stream) != cudaSuccess ||
+      d_src_list.alloc(src_list.size(), ctx->stream) != cudaSuccess ||
+      d_tgt.alloc(tgt.size(), ctx->stream) != cudaSuccess ||
+      d_pp.alloc(std::max<int64_t>(npp, 1), ctx->stream) != cudaSuccess ||
+      d_part.alloc(size_t(std::max(p->nitems, 1)) * BSTRIDE, ctx->stream) != cudaSuccess ||
+      d_pair_grad.alloc(size_t(std::max(npairs, 1)) * 12, ctx->stream) != cudaSuccess)
+    return done(set_error(ctx, GLIM_ENOMEM, "backward: scratch allocation failed"));
+  cudaMemcpyAsync(d_pair_off.p, pair_off.data(), pair_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream);
+  cudaMemcpyAsync(d_frame_off.p, frame_off.data(), frame_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream);
+  cudaMemcpyAsync(d_src_begin.p, src_begin.data(), src_begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream);
+  cudaMemcpyAsync(d_src_list.p, src_list.data(), src_list.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream);
+  cudaMemcpyAsync(d_tgt.p, tgt.data(), tgt.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream);
+  if (p->nitems > 0) {
+    BwdArgs a;
+    a.items = p->d_items;
+    a.nitems = p->nitems;
+    a.pairs = p->d_pairs;
+    a.frames = p->d_frames;
+    a.maps = p->d_maps;
+    a.pose = p->in_pose32();
+    a.tile = p->tile;
+    a.validate = validate_surface;
+    a.full = omega_grad_full;
+    a.pair_pt_off = d_pair_off.p;
+    a.pp = d_pp.p;
+    a.part = d_part.p;
+    k_backward_items<<<p->nitems, 256, 0, ctx->stream>>>(a);
+    ctx->launches++;
+  }
+  if (npairs > 0) {
+    k_backward_pairs<<<ceil_div_i(npairs, 64), 64, 0, ctx->stream>>>(d_part.p, p->d_item_begin, p->in_pose64(),
+                                                                     npairs, d_pair_grad.p);
+    ctx->launches++;
+  }
+  if (nframes > 0) {
+    k_backward_frames<<<ceil_div_i(nframes, 64), 64, 0, ctx->stream>>>(d_pair_grad.p, p->d_pairs, d_tgt.p, npairs,
+                                                                       nframes, dxi_out);
+    ctx->launches++;
+  }
+  if (ntot > 0 && (dmu_out || dw_out)) {
+    k_backward_points<<<ceil_div_i(ntot, 256), 256, 0, ctx->stream>>>(
+        d_pp.p, d_pair_off.p, d_src_list.p, d_src_begin.p, d_frame_off.p, nullptr, nframes, ntot, dmu_out, dw_out);
+    ctx->launches++;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return done(cuda_check(ctx, e, "backward launch"));
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return done(set_error(ctx, GLIM_ECUDA, "backward: sync failed"));
+  ctx->err.clear();
+  return done(GLIM_OK);
+}

@@ -1,0 +1,186 @@
+// common.cuh -- shared internals of the linearization library (context, status words,
+// voxel keys, hash slots).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/glim_lin.h"
+
+// ------------------------------------------------------------------ context
+struct glim_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  int64_t launches = 0;
+  unsigned int* d_status = nullptr;  // device status word (bit flags below)
+};
+
+// device status bits (set with atomicOr; read by the host after a synchronize)
+#define GLIM_DS_RANGE 1u      // a build key was outside [-2^20, 2^20)
+#define GLIM_DS_NONFINITE 2u  // a non-finite input value
+#define GLIM_DS_HASHFULL 4u   // the hash insert exhausted its probe bound
+#define GLIM_DS_TIMEOUT 8u    // a bounded wait gave up
+
+glim_status set_error(glim_ctx* ctx, glim_status st, const char* fmt, ...);
+glim_status cuda_check(glim_ctx* ctx, cudaError_t e, const char* what);
+#define GLIM_CUDA(ctx, call)                                   \
+  do {                                                         \
+    cudaError_t _e = (call);                                   \
+    if (_e != cudaSuccess) return cuda_check((ctx), _e, #call); \
+  } while (0)
+// after a kernel launch: count it and check the launch
+#define GLIM_LAUNCHED(ctx)                                                   \
+  do {                                                                       \
+    (ctx)->launches++;                                                       \
+    cudaError_t _e = cudaGetLastError();                                     \
+    if (_e != cudaSuccess) return cuda_check((ctx), _e, "kernel launch");    \
+  } while (0)
+
+// read and clear the device status word; map to a status code
+glim_status take_device_status(glim_ctx* ctx, const char* where);
+
+// stream-ordered temporary device buffer
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  cudaError_t alloc(size_t count, cudaStream_t stream) {
+    release();
+    s = stream;
+    n = count;
+    if (count == 0) return cudaSuccess;
+    return cudaMallocAsync((void**)&p, count * sizeof(T), stream);
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+// ------------------------------------------------------------------ voxel keys
+// A voxel key (kx, ky, kz) with every component in [-2^20, 2^20) packs into 63 bits as
+// ((kx + 2^20) << 42) | ((ky + 2^20) << 21) | (kz + 2^20); unsigned order of packed keys
+// equals lexicographic (x, y, z) order of the keys.
+#define GLIM_KEY_BIAS (1 << 20)
+#define GLIM_EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
+
+__host__ __device__ inline unsigned long long pack_key(int kx, int ky, int kz) {
+  return ((unsigned long long)(kx + GLIM_KEY_BIAS) << 42) |
+         ((unsigned long long)(ky + GLIM_KEY_BIAS) << 21) | (unsigned long long)(kz + GLIM_KEY_BIAS);
+}
+__host__ __device__ inline int unpack_x(unsigned long long k) { return int((k >> 42) & 0x1FFFFF) - GLIM_KEY_BIAS; }
+__host__ __device__ inline int unpack_y(unsigned long long k) { return int((k >> 21) & 0x1FFFFF) - GLIM_KEY_BIAS; }
+__host__ __device__ inline int unpack_z(unsigned long long k) { return int(k & 0x1FFFFF) - GLIM_KEY_BIAS; }
+
+// Fibonacci hashing of the packed key into a power-of-two table.
+__host__ __device__ inline uint32_t hash_slot(unsigned long long key, int log2cap) {
+  return uint32_t((key * 0x9E3779B97F4A7C15ull) >> (64 - log2cap));
+}
+
+// floor(c * inv_r) as an int in [-2^20, 2^20), or false.  One FP32 multiply, rounded to
+// nearest (explicit so that the compiler cannot fuse it with anything).
+__device__ __forceinline__ bool voxel_coord(float c, float inv_r, int& k) {
+  float f = floorf(__fmul_rn(c, inv_r));
+  if (!(f >= -1048576.0f && f < 1048576.0f)) return false;  // also rejects NaN
+  k = __float2int_rz(f);
+  return true;
+}
+
+// ------------------------------------------------------------------ hash slot (48 bytes)
+// One open-addressing slot holds the key and the voxel statistics, so a single probe that
+// matches returns the voxel:  w0 = {key lo, key hi, count (int bits), c22},
+// w1 = {mean x, mean y, mean z, c00}, w2 = {c01, c02, c11, c12}.
+struct __align__(16) VoxSlot {
+  float4 w0, w1, w2;
+};
+
+struct LevelDev {
+  const VoxSlot* slots;
+  const int32_t* slot_id;  // canonical voxel id of each slot (-1 = empty)
+  uint32_t mask;           // capacity - 1
+  int32_t log2cap;
+  int32_t max_probe;       // longest probe sequence of any stored key
+  float inv_r;
+};
+
+// host-side voxelmap
+struct glim_vmap {
+  int device = 0;
+  int levels = 0;
+  double res[GLIM_MAX_LEVELS] = {0};
+  float inv_r[GLIM_MAX_LEVELS] = {0};
+  int64_t n_vox[GLIM_MAX_LEVELS] = {0};
+  int64_t cap[GLIM_MAX_LEVELS] = {0};
+  int32_t log2cap[GLIM_MAX_LEVELS] = {0};
+  int32_t max_probe[GLIM_MAX_LEVELS] = {0};
+  VoxSlot* slots[GLIM_MAX_LEVELS] = {nullptr};
+  int32_t* slot_id[GLIM_MAX_LEVELS] = {nullptr};
+  unsigned long long* vkey[GLIM_MAX_LEVELS] = {nullptr};  // canonical order
+  float* vmean[GLIM_MAX_LEVELS] = {nullptr};              // n_vox x 3
+  float* vcov[GLIM_MAX_LEVELS] = {nullptr};               // n_vox x 6
+  int32_t* vcount[GLIM_MAX_LEVELS] = {nullptr};
+  LevelDev dev(int l) const {
+    LevelDev d;
+    d.slots = slots[l];
+    d.slot_id = slot_id[l];
+    d.mask = uint32_t(cap[l] - 1);
+    d.log2cap = log2cap[l];
+    d.max_probe = max_probe[l];
+    d.inv_r = inv_r[l];
+    return d;
+  }
+};
+
+// per-pair relative pose in FP32 as used by the point loop
+struct __align__(16) PoseF {
+  float R[9];
+  float t[3];
+  float v[3];  // target viewpoint in the source frame, -R^T t
+  float pad;
+};
+
+// host helpers shared by the linearize / backward / correspondence paths
+struct RelPose {
+  double R[9], t[3];
+};
+RelPose relative_pose(const double* pose_s12, const double* pose_t12);
+PoseF pose_to_f32(const RelPose& T);
+
+// ------------------------------------------------------------------ primitives (sort.cu)
+// Exclusive prefix sum of n uint32 values (in may equal out).  tmp is managed internally.
+glim_status scan_exclusive_u32(glim_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n);
+// Stable LSD radix sort of (key, value) pairs by the key bits in `varying` (bits that are
+// not set in `varying` are equal in all keys).  Results in keys_out / vals_out.
+glim_status radix_sort_pairs(glim_ctx* ctx, const unsigned long long* keys_in, const uint32_t* vals_in,
+                             unsigned long long* keys_out, uint32_t* vals_out, int64_t n,
+                             unsigned long long varying);
+// OR over (k ^ k[0]) of all keys: the bits that vary.
+glim_status key_varying_bits(glim_ctx* ctx, const unsigned long long* keys, int64_t n,
+                             unsigned long long* varying_host);
+
+// builds a sorted grid (keys of points at inv_r, their sorted order, unique cells)
+struct SortedCells {
+  DevBuf<unsigned long long> key_sorted;  // n
+  DevBuf<uint32_t> idx_sorted;            // n
+  DevBuf<uint32_t> cell_start;            // m + 1
+  DevBuf<unsigned long long> cell_key;    // m
+  int64_t m = 0;
+};
+glim_status sort_into_cells(glim_ctx* ctx, const float* pts4, int64_t n, float inv_r, SortedCells& out,
+                            bool range_is_error);
+
+inline int ceil_div_i(int64_t a, int64_t b) { return int((a + b - 1) / b); }

@@ -1,0 +1,936 @@
+// linearize.cu -- batched linearization of matching-cost factors (Sec. III-C "Linearization"
+// and "Implementation"), the hot path of the library.
+//
+// Work decomposition: every factor (pair) is cut into tiles of block * pts_per_thread source
+// points; a work item is (pair, tile).  A persistent kernel with one resident wave of blocks
+// takes items from an atomic queue; each block reduces its item to 28 partial sums plus an
+// inlier count and writes them to the item's own slot (no float atomics, so results repeat
+// bit for bit).  A second kernel sums each pair's slots in a fixed order in FP64 and expands
+// them into e, H (12 x 12) and b (12).
+//
+// Per point (FP32): the pinned transform q = R mu + t, u = R mu, the rotated covariance
+// R C R^T once for all levels, then per level the voxel key, one hash probe sequence and, on
+// a hit, S = C~ + R C R^T, Omega = S^-1 (adjugate / determinant), d = mu~ - q, e = d^T Omega d.
+// Across levels the point keeps Omega_sum = sum w Omega, g_sum = sum w Omega d, e_sum.
+//
+// Per-point quadratic factor in 28 numbers: with G = [-(u)x, I] (3 x 6), which is the same
+// for every level of a point,
+//     A_k = -G diag(R, R),   B_k = G S_t,   S_t = [[I, 0], [-(t)x, I]]
+// (Eqs. (4)-(5); u x R = R (mu)x and q = u + t).  Hence with Lift = [-diag(R,R), S_t] (6 x 12)
+//     H = Lift^T M Lift,  b = Lift^T g,   M = sum G^T Omega_sum G,   g = sum G^T g_sum,
+// so a point accumulates the 21 unique entries of M (blocks -u x Omega u x, u x Omega, Omega),
+// the 6 entries of g ([u x g_sum; g_sum]) and e: 28 accumulators instead of the 91 of H and b.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "plan.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------- accumulation policies
+// Plain FP32 running sums.
+struct AccPlain {
+  float s[NACC];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NACC; ++i) s[i] = 0.f;
+  }
+  __device__ __forceinline__ void add(int i, float x) { s[i] += x; }
+};
+
+// Neumaier-compensated FP32 running sums (Neumaier 1974): c collects the rounding error of
+// every addition.
+struct AccComp {
+  float s[NACC], c[NACC];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NACC; ++i) s[i] = c[i] = 0.f;
+  }
+  __device__ __forceinline__ void add(int i, float x) {
+    const float t = s[i] + x;
+    c[i] += (fabsf(s[i]) >= fabsf(x)) ? ((s[i] - t) + x) : ((x - t) + s[i]);
+    s[i] = t;
+  }
+};
+
+template <int ACC>
+struct AccOf {
+  using type = AccPlain;
+};
+template <>
+struct AccOf<GLIM_ACC_KAHAN> {
+  using type = AccComp;
+};
+
+// ---------------------------------------------------------------- per-point term
+template <class A>
+__device__ __forceinline__ void point_term(const PairView& P, int64_t k, int validate, A& acc, int& inl) {
+  const float4 m = ldg4(&P.F.pts[k]);
+  if (validate && P.F.nrm) {
+    const float* nk = P.F.nrm + 3 * k;
+    if (behind_surface(m.x, m.y, m.z, P.v, __ldg(nk), __ldg(nk + 1), __ldg(nk + 2))) return;
+  }
+  const float2 ca = __ldg(&P.F.cov[3 * k]), cb = __ldg(&P.F.cov[3 * k + 1]), cc = __ldg(&P.F.cov[3 * k + 2]);
+  // C (xx xy xz / yy yz / zz)
+  const float c00 = ca.x, c01 = ca.y, c02 = cb.x, c11 = cb.y, c12 = cc.x, c22 = cc.y;
+  const float* R = P.R;
+  const float3 q = transform_pinned(R, P.t, m.x, m.y, m.z);
+  const float3 u = make_float3(q.x - P.t[0], q.y - P.t[1], q.z - P.t[2]);
+  // W = R C, then RCR^T (symmetric: 6 entries)
+  const float w00 = R[0] * c00 + R[1] * c01 + R[2] * c02;
+  const float w01 = R[0] * c01 + R[1] * c11 + R[2] * c12;
+  const float w02 = R[0] * c02 + R[1] * c12 + R[2] * c22;
+  const float w10 = R[3] * c00 + R[4] * c01 + R[5] * c02;
+  const float w11 = R[3] * c01 + R[4] * c11 + R[5] * c12;
+  const float w12 = R[3] * c02 + R[4] * c12 + R[5] * c22;
+  const float w20 = R[6] * c00 + R[7] * c01 + R[8] * c02;
+  const float w21 = R[6] * c01 + R[7] * c11 + R[8] * c12;
+  const float w22 = R[6] * c02 + R[7] * c12 + R[8] * c22;
+  const float r00 = w00 * R[0] + w01 * R[1] + w02 * R[2];
+  const float r01 = w00 * R[3] + w01 * R[4] + w02 * R[5];
+  const float r02 = w00 * R[6] + w01 * R[7] + w02 * R[8];
+  const float r11 = w10 * R[3] + w11 * R[4] + w12 * R[5];
+  const float r12 = w10 * R[6] + w11 * R[7] + w12 * R[8];
+  const float r22 = w20 * R[6] + w21 * R[7] + w22 * R[8];
+
+  float o00 = 0.f, o01 = 0.f, o02 = 0.f, o11 = 0.f, o12 = 0.f, o22 = 0.f;  // sum Omega
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f;                                      // sum Omega d
+  float es = 0.f;
+  int hits = 0;
+#pragma unroll
+  for (int l = 0; l < GLIM_MAX_LEVELS; ++l) {
+    if (l >= P.M.levels) break;
+    const LevelDev& L = P.M.lv[l];
+    unsigned long long key;
+    if (!level_key(q, L.inv_r, key)) continue;
+    const int s = probe_slot(L, key);
+    if (s < 0) continue;
+    const float4 v0 = ldg4(&L.slots[s].w0), v1 = ldg4(&L.slots[s].w1), v2 = ldg4(&L.slots[s].w2);
+    // S = C~ + R C R^T
+    const float a = v1.w + r00, b = v2.x + r01, c = v2.y + r02, d = v2.z + r11, e = v2.w + r12, f = v0.w + r22;
+    const float A00 = d * f - e * e, A01 = c * e - b * f, A02 = b * e - c * d;
+    const float A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
+    const float det = a * A00 + b * A01 + c * A02;
+    if (!(det > 0.f) || !isfinite(det)) continue;  // S not positive definite: skip the term
+    const float id = __frcp_rn(det);
+    const float O00 = A00 * id, O01 = A01 * id, O02 = A02 * id, O11 = A11 * id, O12 = A12 * id, O22 = A22 * id;
+    const float dx = v1.x - q.x, dy = v1.y - q.y, dz = v1.z - q.z;
+    const float y0 = O00 * dx + O01 * dy + O02 * dz;
+    const float y1 = O01 * dx + O11 * dy + O12 * dz;
+    const float y2 = O02 * dx + O12 * dy + O22 * dz;
+    es += dx * y0 + dy * y1 + dz * y2;
+    o00 += O00; o01 += O01; o02 += O02; o11 += O11; o12 += O12; o22 += O22;
+    g0 += y0; g1 += y1; g2 += y2;
+    ++hits;
+  }
+  if (hits == 0) return;
+  inl += hits;
+  const float wk = m.w;
+  o00 *= wk; o01 *= wk; o02 *= wk; o11 *= wk; o12 *= wk; o22 *= wk;
+  g0 *= wk; g1 *= wk; g2 *= wk;
+  es *= wk;
+  // W = (u)x Omega_sum
+  const float W00 = -u.z * o01 + u.y * o02, W01 = -u.z * o11 + u.y * o12, W02 = -u.z * o12 + u.y * o22;
+  const float W10 = u.z * o00 - u.x * o02, W11 = u.z * o01 - u.x * o12, W12 = u.z * o02 - u.x * o22;
+  const float W20 = -u.y * o00 + u.x * o01, W21 = -u.y * o01 + u.x * o11, W22 = -u.y * o02 + u.x * o12;
+  // M_rr = -(u)x Omega (u)x = W (u)x^T  (symmetric)
+  acc.add(0, -u.z * W01 + u.y * W02);
+  acc.add(1, u.z * W00 - u.x * W02);
+  acc.add(2, -u.y * W00 + u.x * W01);
+  acc.add(3, u.z * W10 - u.x * W12);
+  acc.add(4, -u.y * W10 + u.x * W11);
+  acc.add(5, -u.y * W20 + u.x * W21);
+  // M_rt = (u)x Omega
+  acc.add(6, W00); acc.add(7, W01); acc.add(8, W02);
+  acc.add(9, W10); acc.add(10, W11); acc.add(11, W12);
+  acc.add(12, W20); acc.add(13, W21); acc.add(14, W22);
+  // M_tt = Omega
+  acc.add(15, o00); acc.add(16, o01); acc.add(17, o02); acc.add(18, o11); acc.add(19, o12); acc.add(20, o22);
+  // g = [u x g_sum; g_sum]
+  acc.add(21, u.y * g2 - u.z * g1);
+  acc.add(22, u.z * g0 - u.x * g2);
+  acc.add(23, u.x * g1 - u.y * g0);
+  acc.add(24, g0); acc.add(25, g1); acc.add(26, g2);
+  acc.add(27, es);
+}
+
+// ---------------------------------------------------------------- block reduction
+// Warp transpose-reduction: 32 values per lane -> lane l holds the warp total of value l
+// (31 shuffles instead of 5 per value).
+__device__ __forceinline__ void warp_transpose_reduce(float (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16, c = 16; o >= 1; o >>= 1, c >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < c; ++j) {
+      const float send = upper ? v[j] : v[j + c];
+      const float keep = upper ? v[j + c] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+}
+
+// Same with error-free two-sum of the hi parts, collecting the rounding errors in lo.
+__device__ __forceinline__ void warp_transpose_reduce_comp(float (&hi)[32], float (&lo)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16, c = 16; o >= 1; o >>= 1, c >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < c; ++j) {
+      const float sh = upper ? hi[j] : hi[j + c], sl = upper ? lo[j] : lo[j + c];
+      const float kh = upper ? hi[j + c] : hi[j], kl = upper ? lo[j + c] : lo[j];
+      const float rh = __shfl_xor_sync(0xffffffffu, sh, o), rl = __shfl_xor_sync(0xffffffffu, sl, o);
+      const float s = kh + rh;
+      const float bp = s - kh;
+      const float err = (kh - (s - bp)) + (rh - bp);  // two-sum (Knuth)
+      hi[j] = s;
+      lo[j] = kl + rl + err;
+    }
+  }
+}
+
+template <int BLOCK, int ACC>
+__device__ __forceinline__ void block_reduce_store(const typename AccOf<ACC>::type& acc, int inl, double* out) {
+  constexpr int NW = BLOCK / 32;
+  __shared__ float s_hi[NW][32];
+  __shared__ float s_lo[NW][32];
+  __shared__ int s_inl[NW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float hi[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) hi[i] = (i < NACC) ? acc.s[i] : 0.f;
+  if constexpr (ACC == GLIM_ACC_KAHAN) {
+    float lo[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) lo[i] = (i < NACC) ? acc.c[i] : 0.f;
+    warp_transpose_reduce_comp(hi, lo);
+    s_lo[warp][lane] = lo[0];
+  } else {
+    warp_transpose_reduce(hi);
+  }
+  s_hi[warp][lane] = hi[0];
+  const int wi = __reduce_add_sync(0xffffffffu, unsigned(inl));
+  if (lane == 0) s_inl[warp] = wi;
+  __syncthreads();
+  if (threadIdx.x < NACC) {
+    const int i = threadIdx.x;
+    if constexpr (ACC == GLIM_ACC_FP32) {
+      float t = 0.f;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) t += s_hi[w][i];
+      out[i] = double(t);
+    } else if constexpr (ACC == GLIM_ACC_KAHAN) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) t += double(s_hi[w][i]) + double(s_lo[w][i]);
+      out[i] = t;
+    } else {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) t += double(s_hi[w][i]);
+      out[i] = t;
+    }
+  } else if (threadIdx.x == NACC) {
+    int t = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) t += s_inl[w];
+    out[NACC] = double(t);
+  }
+  __syncthreads();  // shared buffers are reused by the next item
+}
+
+// ---------------------------------------------------------------- item processing
+template <int BLOCK, int PPT, int ACC>
+__device__ __forceinline__ void process_item(const LinArgs& a, int item) {
+  const Item it = a.items[item];
+  // stage the pair's constants (pose, frame, map) in shared memory once per item; every
+  // thread reads them from there (uniform addresses, broadcast)
+  __shared__ PairView s_view;
+  if (threadIdx.x == 0) {
+    const PairDev pd = a.pairs[it.pair];
+    const PoseF pf = a.pose[it.pair];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) s_view.R[i] = pf.R[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      s_view.t[i] = pf.t[i];
+      s_view.v[i] = pf.v[i];
+    }
+    s_view.F = a.frames[pd.src];
+    s_view.M = a.maps[pd.map];
+  }
+  __syncthreads();
+  typename AccOf<ACC>::type acc;
+  acc.zero();
+  int inl = 0;
+  const int64_t end = min(int64_t(it.start) + a.tile, s_view.F.n);
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    const int64_t k = int64_t(it.start) + j * BLOCK + threadIdx.x;
+    if (k < end) point_term(s_view, k, a.validate, acc, inl);
+  }
+  // the reduction ends with a barrier, so s_view is free for the next item afterwards
+  block_reduce_store<BLOCK, ACC>(acc, inl, a.part + int64_t(item) * PSTRIDE);
+}
+
+// Persistent kernel: blocks take items from the atomic queue until it is exhausted.
+template <int BLOCK, int PPT, int ACC>
+__global__ void __launch_bounds__(BLOCK) k_linearize_queue(const LinArgs a) {
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.head, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= a.nitems) break;
+    process_item<BLOCK, PPT, ACC>(a, item);
+  }
+}
+
+// One block per item (hardware scheduling; also the per-factor launches of the plain form).
+template <int BLOCK, int PPT, int ACC>
+__global__ void __launch_bounds__(BLOCK) k_linearize_grid(const LinArgs a) {
+  const int item = a.item_base + blockIdx.x;
+  if (item >= a.nitems) return;
+  process_item<BLOCK, PPT, ACC>(a, item);
+}
+
+// ---------------------------------------------------------------- FP64 reduce + expand
+struct ReduceArgs {
+  const double* part;
+  const int32_t* item_begin;  // npairs + 1 (items of pair p are item_begin[p] .. item_begin[p+1]-1)
+  const double* pose64;       // per pair: R (9), t (3) of T_rel in FP64
+  int32_t pair_base;
+  int32_t npairs;
+  int32_t fp32_sum;           // 1: sum the partials in FP32 (naive mode)
+  double* e;
+  double* H;
+  double* b;
+  long long* inl;
+};
+
+__global__ void __launch_bounds__(128) k_reduce_expand(const ReduceArgs a) {
+  const int p = a.pair_base + blockIdx.x;
+  if (p >= a.npairs) return;
+  __shared__ double s[PSTRIDE];
+  __shared__ double M[6][6], g[6], L[6][12], T[6][12];
+  const int tid = threadIdx.x;
+  const int ib = a.item_begin[p], ie = a.item_begin[p + 1];
+  if (tid <= NACC) {
+    if (a.fp32_sum) {
+      float t = 0.f;
+      for (int i = ib; i < ie; ++i) t += float(a.part[int64_t(i) * PSTRIDE + tid]);
+      s[tid] = double(t);
+    } else {
+      double t = 0.0;
+      for (int i = ib; i < ie; ++i) t += a.part[int64_t(i) * PSTRIDE + tid];
+      s[tid] = t;
+    }
+  }
+  // Lift = [-diag(R, R), S_t],  S_t = [[I, 0], [-(t)x, I]]
+  const double* P = a.pose64 + 12 * int64_t(p);
+  if (tid < 72) {
+    const int r = tid / 12, c = tid % 12;
+    double v = 0.0;
+    if (c < 6) {
+      if ((r < 3) == (c < 3)) v = -P[3 * (r % 3) + (c % 3)];
+    } else {
+      const int cc = c - 6;
+      if (r == cc) v = 1.0;
+      else if (r >= 3 && cc < 3) {
+        const double tx = P[9], ty = P[10], tz = P[11];
+        // -(t)x = [[0, tz, -ty], [-tz, 0, tx], [ty, -tx, 0]]
+        const double neg_hat[3][3] = {{0.0, tz, -ty}, {-tz, 0.0, tx}, {ty, -tx, 0.0}};
+        v = neg_hat[r - 3][cc];
+      }
+    }
+    L[r][c] = v;
+  }
+  __syncthreads();
+  if (tid < 36) {
+    // M from the 21 unique sums: [[M_rr, M_rt], [M_rt^T, M_tt]]
+    const int r = tid / 6, c = tid % 6;
+    const int sym[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+    double v;
+    if (r < 3 && c < 3) v = s[sym[r][c]];
+    else if (r < 3) v = s[6 + 3 * r + (c - 3)];
+    else if (c < 3) v = s[6 + 3 * c + (r - 3)];
+    else v = s[15 + sym[r - 3][c - 3]];
+    M[r][c] = v;
+  } else if (tid < 42) {
+    g[tid - 36] = s[21 + (tid - 36)];
+  }
+  __syncthreads();
+  if (tid < 72) {  // T = M Lift
+    const int r = tid / 12, c = tid % 12;
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v += M[r][k] * L[k][c];
+    T[r][c] = v;
+  }
+  __syncthreads();
+  for (int i = tid; i < 144; i += blockDim.x) {  // H = Lift^T T
+    const int r = i / 12, c = i % 12;
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v += L[k][r] * T[k][c];
+    a.H[int64_t(p) * 144 + i] = v;
+  }
+  if (tid < 12) {  // b = Lift^T g
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v += L[k][tid] * g[k];
+    a.b[int64_t(p) * 12 + tid] = v;
+  }
+  if (tid == 0) {
+    a.e[p] = s[27];
+    if (a.inl) a.inl[p] = (long long)(s[NACC] + 0.5);
+  }
+}
+
+// ---------------------------------------------------------------- kernel table
+template <int BLOCK, int ACC>
+LinKernel pick_ppt(int ppt, bool persistent) {
+  switch (ppt) {
+    case 1: return persistent ? k_linearize_queue<BLOCK, 1, ACC> : k_linearize_grid<BLOCK, 1, ACC>;
+    case 2: return persistent ? k_linearize_queue<BLOCK, 2, ACC> : k_linearize_grid<BLOCK, 2, ACC>;
+    case 4: return persistent ? k_linearize_queue<BLOCK, 4, ACC> : k_linearize_grid<BLOCK, 4, ACC>;
+    case 8: return persistent ? k_linearize_queue<BLOCK, 8, ACC> : k_linearize_grid<BLOCK, 8, ACC>;
+  }
+  return nullptr;
+}
+
+template <int BLOCK>
+LinKernel pick_acc(int acc, int ppt, bool persistent) {
+  switch (acc) {
+    case GLIM_ACC_FP32: return pick_ppt<BLOCK, GLIM_ACC_FP32>(ppt, persistent);
+    case GLIM_ACC_KAHAN: return pick_ppt<BLOCK, GLIM_ACC_KAHAN>(ppt, persistent);
+    case GLIM_ACC_FP64: return pick_ppt<BLOCK, GLIM_ACC_FP64>(ppt, persistent);
+  }
+  return nullptr;
+}
+
+LinKernel pick_kernel(int block, int acc, int ppt, bool persistent) {
+  switch (block) {
+    case 128: return pick_acc<128>(acc, ppt, persistent);
+    case 256: return pick_acc<256>(acc, ppt, persistent);
+  }
+  return nullptr;
+}
+
+void fill_defaults(glim_lin_opts& o) {
+  if (o.block == 0) o.block = 256;
+  if (o.pts_per_thread == 0) o.pts_per_thread = 4;
+  if (o.persistent == 0) o.persistent = 1;
+}
+
+bool opts_valid(const glim_lin_opts& o) {
+  return (o.block == 128 || o.block == 256) &&
+         (o.pts_per_thread == 1 || o.pts_per_thread == 2 || o.pts_per_thread == 4 || o.pts_per_thread == 8) &&
+         (o.accum_mode >= 0 && o.accum_mode <= 2) && (o.persistent == 1 || o.persistent == 2) &&
+         o.blocks_per_sm >= 0 && o.blocks_per_sm <= 32;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+namespace {
+
+void drop_graphs(glim_plan* p) {
+  if (p->g_full) cudaGraphExecDestroy(p->g_full);
+  if (p->g_dev) cudaGraphExecDestroy(p->g_dev);
+  p->g_full = p->g_dev = nullptr;
+}
+
+}  // namespace
+
+glim_status plan_configure(glim_plan* p, const glim_lin_opts& o) {
+  glim_ctx* ctx = p->ctx;
+  drop_graphs(p);
+  cudaFree(p->d_items);
+  cudaFree(p->d_item_begin);
+  cudaFree(p->d_part);
+  p->d_items = nullptr;
+  p->d_item_begin = nullptr;
+  p->d_part = nullptr;
+  p->opts = o;
+  p->tile = o.block * o.pts_per_thread;
+  std::vector<Item> items;
+  std::vector<int32_t> begin(p->npairs + 1, 0);
+  for (int q = 0; q < p->npairs; ++q) {
+    begin[q] = int32_t(items.size());
+    const int64_t n = p->frames[p->pairs[q].src_frame].n;
+    for (int64_t s = 0; s < n; s += p->tile) items.push_back(Item{q, int32_t(s)});
+  }
+  begin[p->npairs] = int32_t(items.size());
+  p->nitems = int(items.size());
+  const size_t ni = std::max<size_t>(items.size(), 1);
+  GLIM_CUDA(ctx, cudaMalloc(&p->d_items, ni * sizeof(Item)));
+  GLIM_CUDA(ctx, cudaMalloc(&p->d_item_begin, begin.size() * sizeof(int32_t)));
+  GLIM_CUDA(ctx, cudaMalloc(&p->d_part, ni * PSTRIDE * sizeof(double)));
+  if (!items.empty())
+    GLIM_CUDA(ctx, cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice));
+  GLIM_CUDA(ctx, cudaMemcpy(p->d_item_begin, begin.data(), begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  p->kernel = pick_kernel(o.block, o.accum_mode, o.pts_per_thread, o.persistent == 1);
+  if (!p->kernel) return set_error(ctx, GLIM_EINVAL, "no kernel for block=%d ppt=%d acc=%d", o.block, o.pts_per_thread, o.accum_mode);
+  if (o.persistent == 1) {
+    int per_sm = o.blocks_per_sm;
+    if (per_sm == 0) {
+      GLIM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kernel, o.block, 0));
+      per_sm = std::max(per_sm, 1);
+    }
+    p->grid = std::max(1, std::min(per_sm * ctx->num_sms, p->nitems));
+  } else {
+    p->grid = std::max(1, p->nitems);
+  }
+  return GLIM_OK;
+}
+
+namespace {
+
+// Enqueue queue reset + linearize + reduce on the ctx stream (no sync); with slot >= 0,
+// record that timing slot's events around the linearization kernel.
+glim_status plan_enqueue_kernels(glim_plan* p, int slot = -1) {
+  glim_ctx* ctx = p->ctx;
+  if (p->nitems > 0) {
+    LinArgs a;
+    a.items = p->d_items;
+    a.nitems = p->nitems;
+    a.item_base = 0;
+    a.pairs = p->d_pairs;
+    a.frames = p->d_frames;
+    a.maps = p->d_maps;
+    a.pose = p->in_pose32();
+    a.head = p->d_head;
+    a.part = p->d_part;
+    a.tile = p->tile;
+    a.validate = p->opts.validate_surface;
+    if (p->opts.persistent == 1) GLIM_CUDA(ctx, cudaMemsetAsync(p->d_head, 0, sizeof(int), ctx->stream));
+    if (slot >= 0) GLIM_CUDA(ctx, cudaEventRecord(p->ev[2 * slot], ctx->stream));
+    p->kernel<<<p->grid, p->opts.block, 0, ctx->stream>>>(a);
+    GLIM_LAUNCHED(ctx);
+    if (slot >= 0) GLIM_CUDA(ctx, cudaEventRecord(p->ev[2 * slot + 1], ctx->stream));
+  }
+  ReduceArgs r;
+  r.part = p->d_part;
+  r.item_begin = p->d_item_begin;
+  r.pose64 = p->in_pose64();
+  r.pair_base = 0;
+  r.npairs = p->npairs;
+  r.fp32_sum = p->opts.accum_mode == GLIM_ACC_FP32 ? 1 : 0;
+  r.e = p->out_e();
+  r.H = p->out_H();
+  r.b = p->out_b();
+  r.inl = p->out_inl();
+  if (p->npairs > 0) {
+    k_reduce_expand<<<p->npairs, 128, 0, ctx->stream>>>(r);
+    GLIM_LAUNCHED(ctx);
+  }
+  return GLIM_OK;
+}
+
+}  // namespace
+
+void plan_pack_poses(glim_plan* p, const double* poses12) {
+  PoseF* pf = reinterpret_cast<PoseF*>(p->h_in);
+  double* pd = reinterpret_cast<double*>(reinterpret_cast<char*>(p->h_in) + sizeof(PoseF) * p->npairs);
+  for (int q = 0; q < p->npairs; ++q) {
+    const RelPose T = relative_pose(poses12 + 12 * p->pairs[q].src_frame, poses12 + 12 * p->pairs[q].tgt_frame);
+    pf[q] = pose_to_f32(T);
+    std::memcpy(pd + 12 * q, T.R, 9 * sizeof(double));
+    std::memcpy(pd + 12 * q + 9, T.t, 3 * sizeof(double));
+  }
+}
+
+namespace {
+
+glim_status capture(glim_plan* p, bool full, cudaGraphExec_t* out) {
+  glim_ctx* ctx = p->ctx;
+  cudaGraph_t g = nullptr;
+  GLIM_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  glim_status st = GLIM_OK;
+  if (full && cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+    st = GLIM_ECUDA;
+  if (st == GLIM_OK) st = plan_enqueue_kernels(p);
+  if (st == GLIM_OK && full &&
+      cudaMemcpyAsync(p->h_out, p->d_out, p->out_bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+    st = GLIM_ECUDA;
+  cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+  if (st != GLIM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st == GLIM_ECUDA ? set_error(ctx, st, "graph capture failed") : st;
+  }
+  if (ce != cudaSuccess) return cuda_check(ctx, ce, "cudaStreamEndCapture");
+  ce = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ce != cudaSuccess) return cuda_check(ctx, ce, "cudaGraphInstantiate");
+  return GLIM_OK;
+}
+
+glim_status copy_outputs(glim_plan* p, double* e_out, double* H_out, double* b_out, int64_t* inl_out, bool from_host) {
+  glim_ctx* ctx = p->ctx;
+  const int P = p->npairs;
+  if (from_host) {
+    const char* base = reinterpret_cast<const char*>(p->h_out);
+    std::memcpy(e_out, base, P * sizeof(double));
+    std::memcpy(H_out, base + P * sizeof(double), size_t(P) * 144 * sizeof(double));
+    std::memcpy(b_out, base + size_t(P) * 145 * sizeof(double), size_t(P) * 12 * sizeof(double));
+    if (inl_out) std::memcpy(inl_out, base + size_t(P) * 157 * sizeof(double), P * sizeof(int64_t));
+    return GLIM_OK;
+  }
+  GLIM_CUDA(ctx, cudaMemcpyAsync(e_out, p->out_e(), P * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  GLIM_CUDA(ctx, cudaMemcpyAsync(H_out, p->out_H(), size_t(P) * 144 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  GLIM_CUDA(ctx, cudaMemcpyAsync(b_out, p->out_b(), size_t(P) * 12 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  if (inl_out)
+    GLIM_CUDA(ctx, cudaMemcpyAsync(inl_out, p->out_inl(), P * sizeof(int64_t), cudaMemcpyDeviceToDevice, ctx->stream));
+  return GLIM_OK;
+}
+
+glim_status validate_batch(glim_ctx* ctx, const glim_frame* frames, int32_t nframes, const glim_pair* pairs,
+                           int32_t npairs) {
+  if (nframes < 0 || npairs < 0 || (nframes > 0 && !frames) || (npairs > 0 && !pairs))
+    return set_error(ctx, GLIM_EINVAL, "linearize: bad batch sizes");
+  for (int f = 0; f < nframes; ++f) {
+    const glim_frame& F = frames[f];
+    if (F.n < 0 || F.n > 0x7FFFFFFFll || (F.n > 0 && (!F.pts4 || !F.cov6)))
+      return set_error(ctx, GLIM_EINVAL, "linearize: frame %d has bad size or null arrays", f);
+    if ((reinterpret_cast<uintptr_t>(F.pts4) & 15) || (reinterpret_cast<uintptr_t>(F.cov6) & 7))
+      return set_error(ctx, GLIM_EINVAL, "linearize: frame %d arrays misaligned", f);
+  }
+  for (int q = 0; q < npairs; ++q) {
+    const glim_pair& P = pairs[q];
+    if (P.src_frame < 0 || P.src_frame >= nframes || P.tgt_frame < 0 || P.tgt_frame >= nframes || !P.tgt)
+      return set_error(ctx, GLIM_EINVAL, "linearize: pair %d is invalid", q);
+    if (P.tgt->device != ctx->device) return set_error(ctx, GLIM_EINVAL, "linearize: pair %d map on another device", q);
+  }
+  return GLIM_OK;
+}
+
+}  // namespace
+
+extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames, int32_t nframes,
+                                        const glim_pair* pairs, int32_t npairs, const glim_lin_opts* opts,
+                                        glim_plan** out) {
+  if (!ctx || !out) return GLIM_EINVAL;
+  *out = nullptr;
+  glim_status st = validate_batch(ctx, frames, nframes, pairs, npairs);
+  if (st != GLIM_OK) return st;
+  glim_lin_opts o{};
+  if (opts) o = *opts;
+  fill_defaults(o);
+  if (!opts_valid(o)) return set_error(ctx, GLIM_EINVAL, "linearize: invalid options");
+  GLIM_CUDA(ctx, cudaSetDevice(ctx->device));
+  glim_plan* p = new glim_plan;
+  p->ctx = ctx;
+  p->nframes = nframes;
+  p->npairs = npairs;
+  p->frames.assign(frames, frames + nframes);
+  p->pairs.assign(pairs, pairs + npairs);
+  // frames and maps
+  std::vector<FrameDev> fd(std::max(nframes, 1));
+  for (int f = 0; f < nframes; ++f) {
+    fd[f].pts = reinterpret_cast<const float4*>(frames[f].pts4);
+    fd[f].cov = reinterpret_cast<const float2*>(frames[f].cov6);
+    fd[f].nrm = frames[f].normal3;
+    fd[f].n = frames[f].n;
+  }
+  std::vector<const glim_vmap*> maps;
+  std::vector<PairDev> pd(std::max(npairs, 1));
+  for (int q = 0; q < npairs; ++q) {
+    auto it = std::find(maps.begin(), maps.end(), pairs[q].tgt);
+    if (it == maps.end()) {
+      maps.push_back(pairs[q].tgt);
+      it = maps.end() - 1;
+    }
+    pd[q].src = pairs[q].src_frame;
+    pd[q].map = int32_t(it - maps.begin());
+  }
+  std::vector<MapDev> md(std::max<size_t>(maps.size(), 1));
+  for (size_t i = 0; i < maps.size(); ++i) {
+    std::memset(&md[i], 0, sizeof(MapDev));
+    md[i].levels = maps[i]->levels;
+    for (int l = 0; l < maps[i]->levels; ++l) md[i].lv[l] = maps[i]->dev(l);
+  }
+  p->nmaps = int(maps.size());
+  auto fail = [&](glim_status s) {
+    glim_plan_destroy(p);
+    return s;
+  };
+  if (cudaMalloc(&p->d_frames, fd.size() * sizeof(FrameDev)) != cudaSuccess ||
+      cudaMalloc(&p->d_pairs, pd.size() * sizeof(PairDev)) != cudaSuccess ||
+      cudaMalloc(&p->d_maps, md.size() * sizeof(MapDev)) != cudaSuccess ||
+      cudaMalloc(&p->d_head, sizeof(int)) != cudaSuccess)
+    return fail(set_error(ctx, GLIM_ENOMEM, "plan: device allocation failed"));
+  cudaMemcpy(p->d_frames, fd.data(), fd.size() * sizeof(FrameDev), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_pairs, pd.data(), pd.size() * sizeof(PairDev), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_maps, md.data(), md.size() * sizeof(MapDev), cudaMemcpyHostToDevice);
+  p->in_bytes = std::max<size_t>(size_t(npairs) * (sizeof(PoseF) + 12 * sizeof(double)), 16);
+  p->out_bytes = std::max<size_t>(size_t(npairs) * (157 * sizeof(double) + sizeof(int64_t)), 16);
+  if (cudaMalloc(&p->d_in, p->in_bytes) != cudaSuccess || cudaMalloc(&p->d_out, p->out_bytes) != cudaSuccess ||
+      cudaMallocHost(&p->h_in, p->in_bytes) != cudaSuccess || cudaMallocHost(&p->h_out, p->out_bytes) != cudaSuccess)
+    return fail(set_error(ctx, GLIM_ENOMEM, "plan: serialized block allocation failed"));
+  st = plan_configure(p, o);
+  if (st != GLIM_OK) return fail(st);
+  *out = p;
+  ctx->err.clear();
+  return GLIM_OK;
+}
+
+extern "C" void glim_plan_destroy(glim_plan* p) {
+  if (!p) return;
+  cudaSetDevice(p->ctx->device);
+  cudaStreamSynchronize(p->ctx->stream);
+  drop_graphs(p);
+  for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+  cudaFree(p->d_frames);
+  cudaFree(p->d_pairs);
+  cudaFree(p->d_maps);
+  cudaFree(p->d_items);
+  cudaFree(p->d_item_begin);
+  cudaFree(p->d_part);
+  cudaFree(p->d_head);
+  cudaFree(p->d_in);
+  cudaFree(p->d_out);
+  if (p->h_in) cudaFreeHost(p->h_in);
+  if (p->h_out) cudaFreeHost(p->h_out);
+  delete p;
+}
+
+extern "C" glim_status glim_plan_set_poses(glim_plan* p, const double* poses12) {
+  if (!p || !poses12) return GLIM_EINVAL;
+  glim_ctx* ctx = p->ctx;
+  // the pinned block may still be read by an earlier upload
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  plan_pack_poses(p, poses12);
+  GLIM_CUDA(ctx, cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream));
+  return GLIM_OK;
+}
+
+extern "C" glim_status glim_plan_launch(glim_plan* p) {
+  if (!p) return GLIM_EINVAL;
+  glim_ctx* ctx = p->ctx;
+  if (!p->use_graph) return plan_enqueue_kernels(p);
+  if (!p->g_dev) {
+    glim_status st = capture(p, false, &p->g_dev);
+    if (st != GLIM_OK) return st;
+  }
+  GLIM_CUDA(ctx, cudaGraphLaunch(p->g_dev, ctx->stream));
+  ctx->launches += glim_plan_kernels_per_launch(p);
+  return GLIM_OK;
+}
+
+extern "C" glim_status glim_plan_launch_timed(glim_plan* p, int32_t slot) {
+  if (!p || slot < 0 || slot >= 4096) return GLIM_EINVAL;
+  glim_ctx* ctx = p->ctx;
+  while (int(p->ev.size()) < 2 * (slot + 1)) {
+    cudaEvent_t e;
+    GLIM_CUDA(ctx, cudaEventCreate(&e));
+    p->ev.push_back(e);
+  }
+  return plan_enqueue_kernels(p, slot);
+}
+
+extern "C" glim_status glim_plan_kernel_ms(glim_plan* p, int32_t nslots, float* ms_out) {
+  if (!p || nslots < 0 || 2 * nslots > int(p->ev.size()) || (nslots > 0 && !ms_out)) return GLIM_EINVAL;
+  glim_ctx* ctx = p->ctx;
+  for (int s = 0; s < nslots; ++s) {
+    GLIM_CUDA(ctx, cudaEventSynchronize(p->ev[2 * s + 1]));
+    GLIM_CUDA(ctx, cudaEventElapsedTime(&ms_out[s], p->ev[2 * s], p->ev[2 * s + 1]));
+  }
+  return GLIM_OK;
+}
+
+extern "C" int32_t glim_plan_kernels_per_launch(const glim_plan* p) {
+  if (!p) return 0;
+  return (p->nitems > 0 ? 1 : 0) + (p->npairs > 0 ? 1 : 0);
+}
+
+extern "C" glim_status glim_plan_device_outputs(glim_plan* p, double** e, double** H, double** b, int64_t** inl) {
+  if (!p) return GLIM_EINVAL;
+  if (e) *e = p->out_e();
+  if (H) *H = p->out_H();
+  if (b) *b = p->out_b();
+  if (inl) *inl = reinterpret_cast<int64_t*>(p->out_inl());
+  return GLIM_OK;
+}
+
+extern "C" glim_status glim_plan_linearize(glim_plan* p, const double* poses12, double* e_out, double* H_out,
+                                           double* b_out, int64_t* inliers_out) {
+  if (!p || !poses12) return GLIM_EINVAL;
+  glim_ctx* ctx = p->ctx;
+  if (p->npairs > 0 && (!e_out || !H_out || !b_out))
+    return set_error(ctx, GLIM_EINVAL, "plan_linearize: null output");
+  const bool dev_out = p->npairs > 0 && is_device_ptr(e_out);
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  plan_pack_poses(p, poses12);
+  if (dev_out || !p->use_graph) {
+    GLIM_CUDA(ctx, cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream));
+    glim_status st = plan_enqueue_kernels(p);
+    if (st != GLIM_OK) return st;
+    if (dev_out) return copy_outputs(p, e_out, H_out, b_out, inliers_out, false);
+    GLIM_CUDA(ctx, cudaMemcpyAsync(p->h_out, p->d_out, p->out_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  } else {
+    if (!p->g_full) {
+      glim_status st = capture(p, true, &p->g_full);
+      if (st != GLIM_OK) return st;
+    }
+    GLIM_CUDA(ctx, cudaGraphLaunch(p->g_full, ctx->stream));
+    ctx->launches += glim_plan_kernels_per_launch(p);
+  }
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return copy_outputs(p, e_out, H_out, b_out, inliers_out, true);
+}
+
+extern "C" glim_status glim_plan_get_opts(const glim_plan* p, glim_lin_opts* out) {
+  if (!p || !out) return GLIM_EINVAL;
+  *out = p->opts;
+  return GLIM_OK;
+}
+
+extern "C" glim_status glim_plan_autotune(glim_plan* p, const double* poses12, int32_t iters, glim_lin_opts* best_out,
+                                          float* best_ms_out) {
+  if (!p || !poses12 || iters < 1) return GLIM_EINVAL;
+  glim_ctx* ctx = p->ctx;
+  glim_status st = glim_plan_set_poses(p, poses12);
+  if (st != GLIM_OK) return st;
+  const glim_lin_opts base = p->opts;
+  glim_lin_opts best = base;
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  GLIM_CUDA(ctx, cudaEventCreate(&e0));
+  GLIM_CUDA(ctx, cudaEventCreate(&e1));
+  const int blocks[] = {128, 256};
+  const int ppts[] = {1, 2, 4, 8};
+  for (int bl : blocks)
+    for (int pp : ppts) {
+      glim_lin_opts o = base;
+      o.block = bl;
+      o.pts_per_thread = pp;
+      o.persistent = 1;
+      o.blocks_per_sm = 0;
+      st = plan_configure(p, o);
+      if (st != GLIM_OK) break;
+      st = plan_enqueue_kernels(p);  // warm-up
+      if (st != GLIM_OK) break;
+      cudaEventRecord(e0, ctx->stream);
+      for (int i = 0; i < iters && st == GLIM_OK; ++i) st = plan_enqueue_kernels(p);
+      cudaEventRecord(e1, ctx->stream);
+      if (st != GLIM_OK) break;
+      GLIM_CUDA(ctx, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= iters;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = o;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != GLIM_OK) return st;
+  st = plan_configure(p, best);
+  if (st != GLIM_OK) return st;
+  if (best_out) *best_out = best;
+  if (best_ms_out) *best_ms_out = best_ms;
+  return GLIM_OK;
+}
+
+extern "C" glim_status glim_linearize_factors(glim_ctx* ctx, const glim_frame* frames, int32_t nframes,
+                                              const glim_pair* pairs, int32_t npairs, const double* poses12,
+                                              const glim_lin_opts* opts, double* e_out, double* H_out,
+                                              double* b_out, int64_t* inliers_out) {
+  if (!ctx) return GLIM_EINVAL;
+  if (!poses12 && nframes > 0) return set_error(ctx, GLIM_EINVAL, "linearize: null poses");
+  glim_plan* p = nullptr;
+  glim_status st = glim_plan_create(ctx, frames, nframes, pairs, npairs, opts, &p);
+  if (st != GLIM_OK) return st;
+  p->use_graph = false;
+  st = glim_plan_linearize(p, poses12, e_out, H_out, b_out, inliers_out);
+  if (st == GLIM_OK) cudaStreamSynchronize(ctx->stream);
+  glim_plan_destroy(p);
+  return st;
+}
+
+extern "C" glim_status glim_linearize_factors_plain(glim_ctx* ctx, const glim_frame* frames, int32_t nframes,
+                                                    const glim_pair* pairs, int32_t npairs, const double* poses12,
+                                                    const glim_lin_opts* opts, double* e_out, double* H_out,
+                                                    double* b_out, int64_t* inliers_out) {
+  if (!ctx) return GLIM_EINVAL;
+  glim_lin_opts o{};
+  if (opts) o = *opts;
+  o.accum_mode = GLIM_ACC_FP32;
+  o.persistent = 2;
+  glim_plan* p = nullptr;
+  glim_status st = glim_plan_create(ctx, frames, nframes, pairs, npairs, &o, &p);
+  if (st != GLIM_OK) return st;
+  const bool dev_out = npairs > 0 && is_device_ptr(e_out);
+  plan_pack_poses(p, poses12);
+  GLIM_CUDA(ctx, cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<int32_t> begin(npairs + 1);
+  cudaMemcpy(begin.data(), p->d_item_begin, (npairs + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  double* h = reinterpret_cast<double*>(p->h_out);
+  for (int q = 0; q < npairs && st == GLIM_OK; ++q) {
+    // one factor: its items, its reduction, its download, and a synchronization
+    LinArgs a;
+    a.items = p->d_items;
+    a.nitems = begin[q + 1];
+    a.item_base = begin[q];
+    a.pairs = p->d_pairs;
+    a.frames = p->d_frames;
+    a.maps = p->d_maps;
+    a.pose = p->in_pose32();
+    a.head = p->d_head;
+    a.part = p->d_part;
+    a.tile = p->tile;
+    a.validate = o.validate_surface;
+    const int nb = begin[q + 1] - begin[q];
+    if (nb > 0) {
+      p->kernel<<<nb, o.block, 0, ctx->stream>>>(a);
+      ctx->launches++;
+      if (cudaGetLastError() != cudaSuccess) { st = set_error(ctx, GLIM_ECUDA, "plain: launch failed"); break; }
+    }
+    ReduceArgs r;
+    r.part = p->d_part;
+    r.item_begin = p->d_item_begin;
+    r.pose64 = p->in_pose64();
+    r.pair_base = q;
+    r.npairs = q + 1;
+    r.fp32_sum = 1;
+    r.e = p->out_e();
+    r.H = p->out_H();
+    r.b = p->out_b();
+    r.inl = p->out_inl();
+    k_reduce_expand<<<1, 128, 0, ctx->stream>>>(r);
+    ctx->launches++;
+    if (cudaGetLastError() != cudaSuccess) { st = set_error(ctx, GLIM_ECUDA, "plain: reduce launch failed"); break; }
+    cudaMemcpyAsync(h + q, p->out_e() + q, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(h + npairs + size_t(q) * 144, p->out_H() + size_t(q) * 144, 144 * sizeof(double),
+                    cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(h + size_t(npairs) * 145 + size_t(q) * 12, p->out_b() + size_t(q) * 12, 12 * sizeof(double),
+                    cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(reinterpret_cast<long long*>(h + size_t(npairs) * 157) + q, p->out_inl() + q, sizeof(long long),
+                    cudaMemcpyDeviceToHost, ctx->stream);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = set_error(ctx, GLIM_ECUDA, "plain: sync failed");
+  }
+  if (st == GLIM_OK) {
+    if (dev_out) {
+      st = copy_outputs(p, e_out, H_out, b_out, inliers_out, false);
+      cudaStreamSynchronize(ctx->stream);
+    } else {
+      st = copy_outputs(p, e_out, H_out, b_out, inliers_out, true);
+    }
+  }
+  glim_plan_destroy(p);
+  return st;
+}

@@ -1,0 +1,106 @@
+// plan.cuh -- device descriptions of a factor batch (frames, voxelmaps, pairs, work items)
+// and the plan object that owns them; shared by the forward and backward kernels.
+#pragma once
+#include <vector>
+
+#include "lookup.cuh"
+
+namespace glim_detail {
+
+constexpr int NACC = 28;    // accumulators per point (forward)
+constexpr int PSTRIDE = 32; // doubles per partial slot: 28 sums, inliers, 3 spare
+
+struct FrameDev {
+  const float4* pts;
+  const float2* cov;  // 3 float2 per point
+  const float* nrm;   // 3 floats per point or null
+  int64_t n;
+};
+
+struct MapDev {
+  LevelDev lv[GLIM_MAX_LEVELS];
+  int32_t levels;
+  int32_t pad[3];
+};
+
+struct PairDev {
+  int32_t src;
+  int32_t map;
+};
+
+struct Item {
+  int32_t pair;
+  int32_t start;
+};
+
+struct LinArgs {
+  const Item* items;
+  int32_t nitems;
+  int32_t item_base;   // first item (non-persistent launches)
+  const PairDev* pairs;
+  const FrameDev* frames;
+  const MapDev* maps;
+  const PoseF* pose;   // per pair
+  int* head;           // work-queue head (persistent)
+  double* part;        // nitems x PSTRIDE
+  int32_t tile;
+  int32_t validate;
+};
+
+struct PairView {
+  float R[9], t[3], v[3];
+  FrameDev F;
+  MapDev M;
+};
+
+using LinKernel = void (*)(const LinArgs);
+
+}  // namespace glim_detail
+
+using namespace glim_detail;
+
+struct glim_plan {
+  glim_ctx* ctx = nullptr;
+  int nframes = 0, npairs = 0;
+  glim_lin_opts opts{};
+  std::vector<glim_frame> frames;
+  std::vector<glim_pair> pairs;
+  // static device data
+  FrameDev* d_frames = nullptr;
+  MapDev* d_maps = nullptr;
+  PairDev* d_pairs = nullptr;
+  int nmaps = 0;
+  // work list (depends on the tile size)
+  Item* d_items = nullptr;
+  int32_t* d_item_begin = nullptr;
+  int nitems = 0;
+  int tile = 0;
+  double* d_part = nullptr;
+  int* d_head = nullptr;
+  int grid = 0;
+  LinKernel kernel = nullptr;
+  // serialized input block: PoseF[npairs] then double[npairs * 12]
+  size_t in_bytes = 0;
+  void* d_in = nullptr;
+  void* h_in = nullptr;
+  // serialized output block: e[npairs], H[npairs*144], b[npairs*12], inliers[npairs]
+  size_t out_bytes = 0;
+  void* d_out = nullptr;
+  void* h_out = nullptr;
+  std::vector<cudaEvent_t> ev;       // timing slots: ev[2 s], ev[2 s + 1]
+  bool use_graph = true;
+  cudaGraphExec_t g_full = nullptr;  // upload + kernels + download
+  cudaGraphExec_t g_dev = nullptr;   // kernels only
+
+  PoseF* in_pose32() const { return reinterpret_cast<PoseF*>(d_in); }
+  double* in_pose64() const { return reinterpret_cast<double*>(reinterpret_cast<char*>(d_in) + sizeof(PoseF) * npairs); }
+  double* out_e() const { return reinterpret_cast<double*>(d_out); }
+  double* out_H() const { return out_e() + npairs; }
+  double* out_b() const { return out_H() + size_t(npairs) * 144; }
+  long long* out_inl() const { return reinterpret_cast<long long*>(out_b() + size_t(npairs) * 12); }
+};
+
+
+// shared host helpers (linearize.cu)
+void plan_pack_poses(glim_plan* p, const double* poses12);
+glim_status plan_configure(glim_plan* p, const glim_lin_opts& o);

@@ -1,0 +1,317 @@
+// voxelmap.cu -- multi-resolution voxelmap build (Sec. III-C "Preprocessing"), export,
+// per-point correspondences and the overlap rate (Sec. IV-B).
+//
+// Build of one level:
+//   1. voxel key of every point (FP32 floor(x * inv_r)), sorted with its point index by a
+//      stable radix sort, so the members of a voxel are contiguous and in point order;
+//   2. one thread per voxel sums its members' means and covariances in FP64 in that order
+//      and stores the averages (canonical id = rank of the key = position in sorted order);
+//   3. the voxels are inserted into an open-addressing table (linear probing, load <= 1/2)
+//      whose 48-byte slots carry the key and the statistics together.
+#include "lookup.cuh"
+
+namespace {
+
+__global__ void k_voxel_stats(const float4* __restrict__ pts, const float* __restrict__ cov6,
+                              const uint32_t* __restrict__ idx_sorted, const uint32_t* __restrict__ cell_start,
+                              const unsigned long long* __restrict__ cell_key, int64_t m,
+                              unsigned long long* __restrict__ vkey, float* __restrict__ vmean,
+                              float* __restrict__ vcov, int32_t* __restrict__ vcount,
+                              unsigned int* __restrict__ status) {
+  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v >= m) return;
+  const uint32_t b = cell_start[v], e = cell_start[v + 1];
+  double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (uint32_t j = b; j < e; ++j) {
+    const uint32_t i = idx_sorted[j];
+    const float4 p = pts[i];
+    s[0] += p.x;
+    s[1] += p.y;
+    s[2] += p.z;
+    const float2* c = reinterpret_cast<const float2*>(cov6 + 6 * int64_t(i));
+    const float2 c0 = c[0], c1 = c[1], c2 = c[2];
+    if (!(isfinite(c0.x) && isfinite(c0.y) && isfinite(c1.x) && isfinite(c1.y) && isfinite(c2.x) && isfinite(c2.y)))
+      atomicOr(status, GLIM_DS_NONFINITE);
+    s[3] += c0.x;
+    s[4] += c0.y;
+    s[5] += c1.x;
+    s[6] += c1.y;
+    s[7] += c2.x;
+    s[8] += c2.y;
+  }
+  const double inv = 1.0 / double(e - b);
+  vkey[v] = cell_key[v];
+  for (int c = 0; c < 3; ++c) vmean[3 * v + c] = float(s[c] * inv);
+  for (int c = 0; c < 6; ++c) vcov[6 * v + c] = float(s[3 + c] * inv);
+  vcount[v] = int32_t(e - b);
+}
+
+__global__ void k_hash_insert(const unsigned long long* __restrict__ vkey, const float* __restrict__ vmean,
+                              const float* __restrict__ vcov, const int32_t* __restrict__ vcount, int64_t m,
+                              VoxSlot* __restrict__ slots, int32_t* __restrict__ slot_id, int log2cap,
+                              uint32_t mask, int* __restrict__ max_probe, unsigned int* __restrict__ status) {
+  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v >= m) return;
+  const unsigned long long key = vkey[v];
+  uint32_t h = hash_slot(key, log2cap);
+  for (uint32_t p = 0; p <= mask; ++p) {
+    unsigned long long* kp = reinterpret_cast<unsigned long long*>(&slots[h].w0);
+    const unsigned long long old = atomicCAS(kp, GLIM_EMPTY_KEY, key);
+    if (old == GLIM_EMPTY_KEY) {
+      float* w = reinterpret_cast<float*>(&slots[h]);
+      w[2] = __int_as_float(vcount[v]);
+      w[3] = vcov[6 * v + 5];                                    // c22
+      w[4] = vmean[3 * v];
+      w[5] = vmean[3 * v + 1];
+      w[6] = vmean[3 * v + 2];
+      w[7] = vcov[6 * v + 0];                                    // c00
+      w[8] = vcov[6 * v + 1];                                    // c01
+      w[9] = vcov[6 * v + 2];                                    // c02
+      w[10] = vcov[6 * v + 3];                                   // c11
+      w[11] = vcov[6 * v + 4];                                   // c12
+      slot_id[h] = int32_t(v);
+      atomicMax(max_probe, int(p + 1));
+      return;
+    }
+    h = (h + 1u) & mask;
+  }
+  atomicOr(status, GLIM_DS_HASHFULL);
+}
+
+__global__ void k_export(const unsigned long long* __restrict__ vkey, const float* __restrict__ vmean,
+                         const float* __restrict__ vcov, const int32_t* __restrict__ vcount, int64_t m,
+                         int32_t* keys3, float* mean3, float* cov6, int32_t* count) {
+  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v >= m) return;
+  const unsigned long long k = vkey[v];
+  if (keys3) {
+    keys3[3 * v] = unpack_x(k);
+    keys3[3 * v + 1] = unpack_y(k);
+    keys3[3 * v + 2] = unpack_z(k);
+  }
+  if (mean3)
+    for (int c = 0; c < 3; ++c) mean3[3 * v + c] = vmean[3 * v + c];
+  if (cov6)
+    for (int c = 0; c < 6; ++c) cov6[6 * v + c] = vcov[6 * v + c];
+  if (count) count[v] = vcount[v];
+}
+
+struct CorrArgs {
+  const float4* pts;
+  const float* nrm;
+  int64_t n;
+  PoseF pose;
+  LevelDev lv[GLIM_MAX_LEVELS];
+  int levels;
+  int validate;
+};
+
+__global__ void k_correspondences(const CorrArgs a, int32_t* __restrict__ ids) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= a.n) return;
+  const float4 m = a.pts[k];
+  bool visible = true;
+  if (a.validate && a.nrm)
+    visible = !behind_surface(m.x, m.y, m.z, a.pose.v, a.nrm[3 * k], a.nrm[3 * k + 1], a.nrm[3 * k + 2]);
+  const float3 q = transform_pinned(a.pose.R, a.pose.t, m.x, m.y, m.z);
+  for (int l = 0; l < a.levels; ++l) {
+    int32_t id = -1;
+    unsigned long long key;
+    if (visible && level_key(q, a.lv[l].inv_r, key)) {
+      int s = probe_slot(a.lv[l], key);
+      if (s >= 0) id = a.lv[l].slot_id[s];
+    }
+    ids[k * a.levels + l] = id;
+  }
+}
+
+struct OverlapPair {
+  const float4* pts;
+  int64_t n;
+  LevelDev lv;
+  PoseF pose;
+};
+
+__global__ void k_overlap(const OverlapPair* __restrict__ pairs, double* __restrict__ out) {
+  const OverlapPair P = pairs[blockIdx.x];
+  int64_t hits = 0;
+  for (int64_t k = threadIdx.x; k < P.n; k += blockDim.x) {
+    const float4 m = ldg4(&P.pts[k]);
+    const float3 q = transform_pinned(P.pose.R, P.pose.t, m.x, m.y, m.z);
+    unsigned long long key;
+    if (level_key(q, P.lv.inv_r, key) && probe_slot(P.lv, key) >= 0) ++hits;
+  }
+  __shared__ unsigned long long s[8];
+  unsigned long long h = __reduce_add_sync(0xffffffffu, unsigned(hits));
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = h;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += s[w];
+    out[blockIdx.x] = P.n > 0 ? double(t) / double(P.n) : 0.0;
+  }
+}
+
+int log2_ceil(int64_t x) {
+  int l = 0;
+  while ((int64_t(1) << l) < x) ++l;
+  return l;
+}
+
+void free_levels(glim_vmap* vm) {
+  for (int l = 0; l < GLIM_MAX_LEVELS; ++l) {
+    cudaFree(vm->slots[l]);
+    cudaFree(vm->slot_id[l]);
+    cudaFree(vm->vkey[l]);
+    cudaFree(vm->vmean[l]);
+    cudaFree(vm->vcov[l]);
+    cudaFree(vm->vcount[l]);
+  }
+}
+
+glim_status build_level(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n, glim_vmap* vm, int l) {
+  SortedCells cells;
+  glim_status st = sort_into_cells(ctx, pts4, n, vm->inv_r[l], cells, true);
+  if (st != GLIM_OK) return st;
+  st = take_device_status(ctx, "voxel keys");
+  if (st != GLIM_OK) return st;
+  const int64_t m = cells.m;
+  vm->n_vox[l] = m;
+  const int64_t cap = std::max<int64_t>(16, int64_t(1) << log2_ceil(2 * m));
+  vm->cap[l] = cap;
+  vm->log2cap[l] = log2_ceil(cap);
+  GLIM_CUDA(ctx, cudaMalloc(&vm->slots[l], cap * sizeof(VoxSlot)));
+  GLIM_CUDA(ctx, cudaMalloc(&vm->slot_id[l], cap * sizeof(int32_t)));
+  GLIM_CUDA(ctx, cudaMalloc(&vm->vkey[l], std::max<int64_t>(m, 1) * sizeof(unsigned long long)));
+  GLIM_CUDA(ctx, cudaMalloc(&vm->vmean[l], std::max<int64_t>(m, 1) * 3 * sizeof(float)));
+  GLIM_CUDA(ctx, cudaMalloc(&vm->vcov[l], std::max<int64_t>(m, 1) * 6 * sizeof(float)));
+  GLIM_CUDA(ctx, cudaMalloc(&vm->vcount[l], std::max<int64_t>(m, 1) * sizeof(int32_t)));
+  GLIM_CUDA(ctx, cudaMemsetAsync(vm->slots[l], 0xFF, cap * sizeof(VoxSlot), ctx->stream));
+  GLIM_CUDA(ctx, cudaMemsetAsync(vm->slot_id[l], 0xFF, cap * sizeof(int32_t), ctx->stream));
+  if (m == 0) {
+    vm->max_probe[l] = 0;
+    return GLIM_OK;
+  }
+  k_voxel_stats<<<ceil_div_i(m, 128), 128, 0, ctx->stream>>>(
+      reinterpret_cast<const float4*>(pts4), cov6, cells.idx_sorted.p, cells.cell_start.p, cells.cell_key.p, m,
+      vm->vkey[l], vm->vmean[l], vm->vcov[l], vm->vcount[l], ctx->d_status);
+  GLIM_LAUNCHED(ctx);
+  DevBuf<int> maxp;
+  GLIM_CUDA(ctx, maxp.alloc(1, ctx->stream));
+  GLIM_CUDA(ctx, cudaMemsetAsync(maxp.p, 0, sizeof(int), ctx->stream));
+  k_hash_insert<<<ceil_div_i(m, 256), 256, 0, ctx->stream>>>(vm->vkey[l], vm->vmean[l], vm->vcov[l], vm->vcount[l],
+                                                             m, vm->slots[l], vm->slot_id[l], vm->log2cap[l],
+                                                             uint32_t(cap - 1), maxp.p, ctx->d_status);
+  GLIM_LAUNCHED(ctx);
+  int mp = 0;
+  GLIM_CUDA(ctx, cudaMemcpyAsync(&mp, maxp.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  vm->max_probe[l] = mp;
+  return take_device_status(ctx, "voxel statistics / hash insert");
+}
+
+}  // namespace
+
+extern "C" glim_status glim_build_voxelmap(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n,
+                                           const double* resolutions, int32_t levels, glim_vmap** out) {
+  if (!ctx || !out) return GLIM_EINVAL;
+  *out = nullptr;
+  if (n < 0 || (n > 0 && (!pts4 || !cov6)) || !resolutions || levels < 1 || levels > GLIM_MAX_LEVELS)
+    return set_error(ctx, GLIM_EINVAL, "build_voxelmap: bad arguments (n=%lld levels=%d)", (long long)n, levels);
+  if (n > 0x7FFFFFFFll) return set_error(ctx, GLIM_EINVAL, "build_voxelmap: n too large");
+  if ((reinterpret_cast<uintptr_t>(pts4) & 15) || (reinterpret_cast<uintptr_t>(cov6) & 7))
+    return set_error(ctx, GLIM_EINVAL, "build_voxelmap: pts4 must be 16-byte and cov6 8-byte aligned");
+  for (int l = 0; l < levels; ++l)
+    if (!(resolutions[l] > 0.0) || !std::isfinite(resolutions[l]))
+      return set_error(ctx, GLIM_EINVAL, "build_voxelmap: resolution %d is not positive", l);
+  GLIM_CUDA(ctx, cudaSetDevice(ctx->device));
+  glim_vmap* vm = new glim_vmap;
+  vm->device = ctx->device;
+  vm->levels = levels;
+  for (int l = 0; l < levels; ++l) {
+    vm->res[l] = resolutions[l];
+    vm->inv_r[l] = float(1.0 / resolutions[l]);
+    glim_status st = build_level(ctx, pts4, cov6, n, vm, l);
+    if (st != GLIM_OK) {
+      cudaStreamSynchronize(ctx->stream);
+      free_levels(vm);
+      delete vm;
+      return st;
+    }
+  }
+  *out = vm;
+  ctx->err.clear();
+  return GLIM_OK;
+}
+
+extern "C" void glim_vmap_free(glim_vmap* vm) {
+  if (!vm) return;
+  cudaSetDevice(vm->device);
+  free_levels(vm);
+  delete vm;
+}
+
+extern "C" glim_status glim_vmap_info(const glim_vmap* vm, int32_t level, int64_t* n_voxels, int64_t* capacity,
+                                      int32_t* max_probe) {
+  if (!vm || level < 0 || level >= vm->levels) return GLIM_EINVAL;
+  if (n_voxels) *n_voxels = vm->n_vox[level];
+  if (capacity) *capacity = vm->cap[level];
+  if (max_probe) *max_probe = vm->max_probe[level];
+  return GLIM_OK;
+}
+
+extern "C" glim_status glim_vmap_export(glim_ctx* ctx, const glim_vmap* vm, int32_t level, int32_t* keys3,
+                                        float* mean3, float* cov6, int32_t* count) {
+  if (!ctx || !vm || level < 0 || level >= vm->levels)
+    return ctx ? set_error(ctx, GLIM_EINVAL, "vmap_export: bad level") : GLIM_EINVAL;
+  const int64_t m = vm->n_vox[level];
+  if (m == 0) return GLIM_OK;
+  k_export<<<ceil_div_i(m, 256), 256, 0, ctx->stream>>>(vm->vkey[level], vm->vmean[level], vm->vcov[level],
+                                                        vm->vcount[level], m, keys3, mean3, cov6, count);
+  GLIM_LAUNCHED(ctx);
+  return GLIM_OK;
+}
+
+extern "C" glim_status glim_correspondences(glim_ctx* ctx, const glim_frame* src, const glim_vmap* tgt,
+                                            const double* pose_s12, const double* pose_t12,
+                                            int32_t validate_surface, int32_t* ids_out) {
+  if (!ctx || !src || !tgt || !pose_s12 || !pose_t12 || (src->n > 0 && !ids_out))
+    return ctx ? set_error(ctx, GLIM_EINVAL, "correspondences: null argument") : GLIM_EINVAL;
+  if (src->n <= 0) return GLIM_OK;
+  CorrArgs a;
+  a.pts = reinterpret_cast<const float4*>(src->pts4);
+  a.nrm = src->normal3;
+  a.n = src->n;
+  a.pose = pose_to_f32(relative_pose(pose_s12, pose_t12));
+  a.levels = tgt->levels;
+  for (int l = 0; l < tgt->levels; ++l) a.lv[l] = tgt->dev(l);
+  a.validate = validate_surface;
+  k_correspondences<<<ceil_div_i(src->n, 256), 256, 0, ctx->stream>>>(a, ids_out);
+  GLIM_LAUNCHED(ctx);
+  return GLIM_OK;
+}
+
+extern "C" glim_status glim_overlap(glim_ctx* ctx, const glim_frame* frames, int32_t nframes, const glim_pair* pairs,
+                                    int32_t npairs, const double* poses12, int32_t level, double* overlap_out) {
+  if (!ctx || !frames || !pairs || !poses12 || !overlap_out || npairs < 0)
+    return ctx ? set_error(ctx, GLIM_EINVAL, "overlap: null argument") : GLIM_EINVAL;
+  if (npairs == 0) return GLIM_OK;
+  std::vector<OverlapPair> hp(npairs);
+  for (int p = 0; p < npairs; ++p) {
+    const glim_pair& q = pairs[p];
+    if (q.src_frame < 0 || q.src_frame >= nframes || q.tgt_frame < 0 || q.tgt_frame >= nframes || !q.tgt ||
+        level < 0 || level >= q.tgt->levels)
+      return set_error(ctx, GLIM_EINVAL, "overlap: bad pair %d", p);
+    hp[p].pts = reinterpret_cast<const float4*>(frames[q.src_frame].pts4);
+    hp[p].n = frames[q.src_frame].n;
+    hp[p].lv = q.tgt->dev(level);
+    hp[p].pose = pose_to_f32(relative_pose(poses12 + 12 * q.src_frame, poses12 + 12 * q.tgt_frame));
+  }
+  DevBuf<OverlapPair> dp;
+  GLIM_CUDA(ctx, dp.alloc(npairs, ctx->stream));
+  GLIM_CUDA(ctx, cudaMemcpyAsync(dp.p, hp.data(), npairs * sizeof(OverlapPair), cudaMemcpyHostToDevice, ctx->stream));
+  k_overlap<<<npairs, 256, 0, ctx->stream>>>(dp.p, overlap_out);
+  GLIM_LAUNCHED(ctx);
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // hp must outlive the copy
+  return GLIM_OK;
+}

@@ -1,0 +1,299 @@
+"""Parity of the CUDA path against the FP64 oracle (element by element on the same seeded
+inputs): voxel keys and correspondence ids bit-exact, e / H / b within 1e-4 relative
+(norm-wise, see gpu_helpers.rel_errors), covariances within 1e-4, gradients, the
+Gauss-Newton step, the overlap rate, determinism and edge cases."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def G():
+    import paper_2407_10344_b300 as G
+    return G
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    return G.Context(0)
+
+
+@pytest.fixture(scope="module")
+def room(ctx):
+    from gpu_helpers import Prepared
+    w = synth.box_room()
+    w.resolutions = [0.5, 1.0, 2.0]
+    return Prepared(ctx, w)
+
+
+@pytest.fixture(scope="module")
+def corridor(ctx):
+    from gpu_helpers import Prepared
+    return Prepared(ctx, synth.corridor())
+
+
+@pytest.fixture(scope="module")
+def urban_small(ctx):
+    from gpu_helpers import Prepared
+    return Prepared(ctx, synth.urban(n_submaps=12, neighbours=3, point_scale=0.2))
+
+
+def _check(res, ref, tol=TOL):
+    from gpu_helpers import numpy_of, rel_errors
+    e, H, b, inl = [numpy_of(x) for x in res]
+    ee, eH, eb = rel_errors(e, H, b, ref)
+    assert (inl == ref["inliers"]).all(), (inl, ref["inliers"])
+    assert ee.max() <= tol and eH.max() <= tol and eb.max() <= tol, (ee.max(), eH.max(), eb.max())
+    return ee.max(), eH.max(), eb.max()
+
+
+# ---------------------------------------------------------------------------- voxelmap
+def test_voxelmap_matches_oracle(room):
+    gm, om = room.gmaps[1], room.omaps[1]
+    for l in range(om.levels):
+        g = {k: v.cpu().numpy() for k, v in gm.export(l).items()}
+        o = om.export(l)
+        assert np.array_equal(g["keys"], o["keys"])          # canonical order, bit-exact keys
+        assert np.array_equal(g["count"], o["count"])
+        np.testing.assert_allclose(g["mean"], o["mean"], rtol=0, atol=2e-6 * max(1.0, np.abs(o["mean"]).max()))
+        np.testing.assert_allclose(g["cov"], o["cov"], rtol=0, atol=2e-6 * np.abs(o["cov"]).max())
+        info = gm.info(l)
+        assert info["capacity"] >= 2 * info["n_voxels"] and info["max_probe"] >= 1
+
+
+def test_voxelmap_face_points_and_negative_coordinates(G, ctx):
+    g = O.as_pts4(np.array([[0.25, 0.25, 0.25], [0.75, 0.5, 0.25], [-0.5, 0.125, 0.0], [-1.0, 0.0, -0.0],
+                            [-1e-30, 2.0, -2.0]]))
+    cov = np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (len(g), 1))
+    gm = G.VoxelMap(ctx, torch.as_tensor(g, device="cuda"), torch.as_tensor(cov, device="cuda"), [1.0, 0.5])
+    om = O.VMap(g, cov, [1.0, 0.5])
+    for l in range(2):
+        assert np.array_equal(gm.export(l)["keys"].cpu().numpy(), om.export(l)["keys"])
+
+
+def test_voxelmap_errors(G, ctx):
+    cov = torch.tensor([[1, 0, 0, 1, 0, 1]] * 2, dtype=torch.float32, device="cuda")
+    far = torch.tensor([[0, 0, 0, 1], [2.0 ** 21, 0, 0, 1]], dtype=torch.float32, device="cuda")
+    with pytest.raises(G.GlimError, match="ERANGE"):
+        G.VoxelMap(ctx, far, cov, [1.0])
+    bad = torch.tensor([[0, 0, 0, 1], [float("nan"), 0, 0, 1]], dtype=torch.float32, device="cuda")
+    with pytest.raises(G.GlimError, match="EINVAL"):
+        G.VoxelMap(ctx, bad, cov, [1.0])
+    # the context stays usable after the errors
+    ok = G.VoxelMap(ctx, far[:1].clone(), cov[:1].clone(), [1.0])
+    assert ok.info(0)["n_voxels"] == 1
+
+
+# ---------------------------------------------------------------------------- correspondences
+@pytest.mark.parametrize("validate", [False, True])
+def test_correspondence_ids_bit_exact(G, ctx, room, validate):
+    w = room.w
+    gid = G.correspondences(ctx, room.gframes[0], room.gmaps[1], w.poses[0], w.poses[1], validate).cpu().numpy()
+    ref = room.oracle(validate=validate, want_ids=True)
+    assert np.array_equal(gid.reshape(-1), ref["ids"])
+    assert (gid >= 0).mean() > 0.5
+
+
+def test_correspondences_face_points(G, ctx):
+    """Points whose transformed coordinates sit within an ulp of a voxel face."""
+    res = 0.5
+    Ts = synth.make_pose(synth.rot_axis_angle([0.6, -0.2, 0.7], 0.9), [1.3, -0.7, 0.4])
+    Tt = np.eye(3, 4)
+    s = synth.Stream(14, "faces")
+    n = 5000
+    face = np.stack([np.round(s.uniform(n, -4, 4) / res) * res, s.uniform(n, -4, 4), s.uniform(n, -4, 4)], 1)
+    mu = ((face - Ts[:, 3]) @ Ts[:, :3]).astype(np.float32)
+    tgt = np.concatenate([face, face + [res / 2, 0, 0], face - [res / 2, 0, 0]]).astype(np.float32)
+    cov = np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (len(tgt), 1))
+    om = O.VMap(O.as_pts4(tgt), cov, [res])
+    gm = G.VoxelMap(ctx, torch.as_tensor(O.as_pts4(tgt), device="cuda"), torch.as_tensor(cov, device="cuda"), [res])
+    src4 = O.as_pts4(mu)
+    scov = cov[:n]
+    fr = G.FrameData(torch.as_tensor(src4, device="cuda"), torch.as_tensor(scov, device="cuda"))
+    gid = G.correspondences(ctx, fr, gm, Ts, Tt).cpu().numpy().reshape(-1)
+    ref = O.linearize([O.Frame(src4, scov), O.Frame(O.as_pts4(tgt), cov)], [None, om], [[0, 1]],
+                      np.stack([Ts, Tt]), want_ids=True)
+    assert np.array_equal(gid, ref["ids"])
+
+
+# ---------------------------------------------------------------------------- linearization
+@pytest.mark.parametrize("acc", [0, 1, 2])
+def test_linearize_room_all_accum_modes(G, ctx, room, acc):
+    ref = room.oracle()
+    res = G.linearize(ctx, room.gframes, room.gmaps, room.w.pairs, room.w.poses, accum_mode=acc)
+    _check(res, ref)
+
+
+@pytest.mark.parametrize("validate", [False, True])
+def test_linearize_corridor_batched_plan(G, ctx, corridor, validate):
+    ref = corridor.oracle(validate=validate)
+    plan = G.Plan(ctx, corridor.gframes, corridor.gmaps, corridor.w.pairs, validate_surface=validate)
+    for _ in range(2):  # first call captures the graph, second replays it
+        res = plan.linearize(corridor.w.poses)
+        _check(res, ref)
+    plan.close()
+
+
+def test_linearize_device_outputs_and_plain(G, ctx, corridor):
+    ref = corridor.oracle()
+    res_dev = G.linearize(ctx, corridor.gframes, corridor.gmaps, corridor.w.pairs, corridor.w.poses, out="cuda")
+    _check(res_dev, ref)
+    res_plain = G.linearize(ctx, corridor.gframes, corridor.gmaps, corridor.w.pairs, corridor.w.poses, plain=True)
+    _check(res_plain, ref)
+
+
+@pytest.mark.parametrize("block,ppt", [(128, 1), (128, 8), (256, 2), (256, 4)])
+def test_linearize_urban_multilevel_tiles(G, ctx, urban_small, block, ppt):
+    ref = urban_small.oracle(validate=True)
+    res = G.linearize(ctx, urban_small.gframes, urban_small.gmaps, urban_small.w.pairs, urban_small.w.poses,
+                      validate_surface=True, block=block, pts_per_thread=ppt)
+    _check(res, ref)
+
+
+def test_linearize_grid_variant_and_autotune(G, ctx, urban_small):
+    w = urban_small.w
+    ref = urban_small.oracle()
+    res = G.linearize(ctx, urban_small.gframes, urban_small.gmaps, w.pairs, w.poses, persistent=2)
+    _check(res, ref)
+    plan = G.Plan(ctx, urban_small.gframes, urban_small.gmaps, w.pairs)
+    best = plan.autotune(w.poses, iters=2)
+    assert best["block"] in (128, 256) and best["pts_per_thread"] in (1, 2, 4, 8) and best["ms"] > 0
+    _check(plan.linearize(w.poses), ref)
+
+
+def test_deterministic_and_partitioned(G, ctx, urban_small):
+    """Two runs are bit-identical, and splitting the pair list into parts run one after the
+    other reproduces the full run bit for bit (the multi-GPU partitioning)."""
+    w = urban_small.w
+    r1 = G.linearize(ctx, urban_small.gframes, urban_small.gmaps, w.pairs, w.poses)
+    r2 = G.linearize(ctx, urban_small.gframes, urban_small.gmaps, w.pairs, w.poses)
+    for a, b in zip(r1, r2):
+        assert np.array_equal(a, b)
+    parts = np.array_split(np.arange(len(w.pairs)), 3)
+    cat = [G.linearize(ctx, urban_small.gframes, urban_small.gmaps, w.pairs[idx], w.poses) for idx in parts]
+    for j in range(4):
+        assert np.array_equal(np.concatenate([c[j] for c in cat]), r1[j])
+
+
+def test_edge_cases_empty_ragged_and_misses(G, ctx, room):
+    """Empty source frame, a source smaller than one tile, a ragged tail, and a pair whose
+    points all miss (poses far apart)."""
+    dev = torch.device("cuda")
+    src = room.gframes[0]
+    empty = G.FrameData(torch.zeros((0, 4), device=dev), torch.zeros((0, 6), device=dev))
+    tiny = G.FrameData(src.pts4[:37].clone(), src.cov6[:37].clone())
+    ragged = G.FrameData(src.pts4[:1025 + 3].clone(), src.cov6[:1025 + 3].clone())
+    frames = [empty, tiny, ragged, room.gframes[1]]
+    oframes = [O.Frame(f.pts4.cpu().numpy(), f.cov6.cpu().numpy()) for f in frames]
+    gmaps = [None, None, None, room.gmaps[1]]
+    omaps = [None, None, None, room.omaps[1]]
+    pairs = np.array([[0, 3], [1, 3], [2, 3], [2, 3]], np.int32)
+    poses = np.stack([room.w.poses[0]] * 3 + [room.w.poses[1]])
+    far = poses.copy()
+    far[2, :, 3] += 500.0
+    for P in (poses, far):
+        ref = O.linearize(oframes, omaps, pairs, P, want_comp=True)
+        res = G.linearize(ctx, frames, gmaps, pairs, P)
+        assert res[0][0] == 0 and not res[1][0].any() and res[3][0] == 0
+        if P is far:
+            assert res[3][2] == 0 and res[0][2] == 0
+        ok = ref["e"] > 0
+        from gpu_helpers import rel_errors
+        ee, eH, eb = rel_errors(res[0][ok], res[1][ok], res[2][ok], {k: v[ok] for k, v in ref.items()})
+        assert ee.max() <= TOL and eH.max() <= TOL and eb.max() <= TOL
+        assert np.array_equal(res[3], ref["inliers"])
+
+
+def test_invalid_arguments(G, ctx, room):
+    with pytest.raises(G.GlimError, match="EINVAL"):
+        G.linearize(ctx, room.gframes, room.gmaps, [[0, 1]], room.w.poses, block=96)
+    with pytest.raises(ValueError):
+        G.linearize(ctx, room.gframes, room.gmaps, [[0, 0]], room.w.poses)  # frame 0 has no voxelmap
+
+
+# ---------------------------------------------------------------------------- covariances
+def test_covariances_match_bruteforce_oracle(G, ctx):
+    w = synth.corridor(n_cur=6000, kf_range=(5000, 5001), n_kf=1)
+    for pts in w.points:
+        p4 = G.to_pts4(pts, device="cuda")
+        cov, nrm = G.estimate_covariances(ctx, p4, k=10)
+        c64, n64, _, tie = O.estimate_covariances(pts, k=10)
+        cov, nrm = cov.cpu().numpy().astype(np.float64), nrm.cpu().numpy().astype(np.float64)
+        ok = ~tie
+        Cg = cov[:, [0, 1, 2, 1, 3, 4, 2, 4, 5]].reshape(-1, 3, 3)
+        Co = c64[:, [0, 1, 2, 1, 3, 4, 2, 4, 5]].reshape(-1, 3, 3)
+        rel = np.linalg.norm((Cg - Co).reshape(len(Cg), -1), axis=1) / np.linalg.norm(Co.reshape(len(Co), -1), axis=1)
+        assert rel[ok].max() <= 1e-4
+        assert np.abs(nrm[ok] - n64[ok]).max() <= 1e-4
+        # raw covariance mode
+        cov0, _ = G.estimate_covariances(ctx, p4, k=7, reg_mode=0, eps=1e-6)
+        c0, _, _, _ = O.estimate_covariances(pts, k=7, reg_mode=0, eps=1e-6)
+        np.testing.assert_allclose(cov0.cpu().numpy(), c0, rtol=1e-4, atol=1e-6 * np.abs(c0).max())
+
+
+def test_covariances_small_cloud_bruteforce_path(G, ctx):
+    pts = synth.box_room(n_src=300, n_tgt=300).points[0]
+    cov, _ = G.estimate_covariances(ctx, G.to_pts4(pts, device="cuda"), k=5, reg_mode=0, eps=0.0)
+    c0, _, _, _ = O.estimate_covariances(pts, k=5, reg_mode=0, eps=0.0)
+    np.testing.assert_allclose(cov.cpu().numpy(), c0, rtol=1e-4, atol=1e-7 * np.abs(c0).max())
+
+
+# ---------------------------------------------------------------------------- gradient
+@pytest.mark.parametrize("full", [False, True])
+def test_backward_matches_oracle_gradient(G, ctx, full):
+    from gpu_helpers import Prepared
+    P = Prepared(ctx, synth.corridor(n_cur=4000, kf_range=(3000, 5000), n_kf=3, weights=True))
+    w = P.w
+    dxi, dmu, dw = G.backward(ctx, P.gframes, P.gmaps, w.pairs, w.poses, omega_grad_full=full)
+    odxi, odmu, odw = O.gradient(P.oframes, P.omaps, w.pairs, w.poses, omega_grad_full=full)
+    dxi = dxi.cpu().numpy()
+    assert np.linalg.norm(dxi - odxi) <= 1e-4 * np.linalg.norm(odxi)
+    odmu_all = np.concatenate(odmu)
+    odw_all = np.concatenate(odw)
+    assert np.linalg.norm(dmu.cpu().numpy() - odmu_all) <= 1e-4 * np.linalg.norm(odmu_all)
+    assert np.linalg.norm(dw.cpu().numpy() - odw_all) <= 1e-4 * np.linalg.norm(odw_all)
+
+
+# ---------------------------------------------------------------------------- Gauss-Newton
+def test_gn_solve_matches_oracle_and_flags_singular(G, ctx, room):
+    res = G.linearize(ctx, room.gframes, room.gmaps, room.w.pairs, room.w.poses, out="cuda")
+    xi, st = G.gn_solve(ctx, res[1], res[2], dim=6)
+    H, b = res[1].cpu().numpy()[0], res[2].cpu().numpy()[0]
+    np.testing.assert_allclose(xi.cpu().numpy()[0], O.gn_solve(H[:6, :6], b[:6]), rtol=1e-9, atol=1e-12)
+    assert st.cpu().numpy()[0] == 0
+    # the full 12 x 12 binary H has the 6-dimensional gauge null space: not positive definite
+    _, st12 = G.gn_solve(ctx, res[1], res[2], dim=12)
+    assert st12.cpu().numpy()[0] == -6
+
+
+def test_gauss_newton_recovers_pose(G, ctx):
+    from gpu_helpers import Prepared
+    P = Prepared(ctx, synth.box_room(sigma=0.0))
+    poses = P.w.poses.copy()
+    plan = G.Plan(ctx, P.gframes, P.gmaps, P.w.pairs)
+    for _ in range(10):
+        e, H, b, _ = plan.linearize(poses)
+        xi, st = G.gn_solve(ctx, torch.as_tensor(H, device="cuda"), torch.as_tensor(b, device="cuda"), dim=6)
+        poses[0] = O.retract(poses[0], xi.cpu().numpy()[0])
+    D = O.compose(O.inverse(P.w.poses_true[0]), poses[0])
+    ang = math.degrees(math.acos(min(1.0, (np.trace(D[:, :3]) - 1) / 2)))
+    assert ang < 0.05 and np.linalg.norm(D[:, 3]) < 0.005
+
+
+# ---------------------------------------------------------------------------- overlap
+def test_overlap_matches_oracle(G, ctx, corridor):
+    w = corridor.w
+    for level in range(len(w.resolutions)):
+        ov = G.overlap(ctx, corridor.gframes, corridor.gmaps, w.pairs, w.poses, level=level).cpu().numpy()
+        for p, (s, t) in enumerate(w.pairs):
+            ref = O.overlap(corridor.oframes[s], corridor.omaps[t], w.poses[s], w.poses[t], level=level)
+            assert ov[p] == pytest.approx(ref, abs=0)
