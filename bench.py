@@ -113,7 +113,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------- CPU oracle leg
-def oracle_sample(w, budget_s=15.0, nthreads=None, target_points=6_000_000):
+def oracle_sample(w, budget_s=15.0, nthreads=None, target_points=30_000_000):
     """Time the FP64 oracle on the first pairs of the workload (about budget_s of CPU work).
     Covariances here are a plain stand-in (identity-plane) since only linearization is timed."""
     from oracle import oracle as O

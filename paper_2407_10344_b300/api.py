@@ -58,7 +58,8 @@ class Context:
         self.lib = _abi.load()
         self.device = device
         with torch.cuda.device(device):
-            self.stream = stream or torch.cuda.current_stream(device)
+            # the library works on its own stream; call() orders it against torch's current stream
+            self.stream = stream or torch.cuda.Stream(device)
         h = C.c_void_p()
         st = self.lib.glim_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream))
         if st != 0:
@@ -68,6 +69,20 @@ class Context:
     def check(self, st, what):
         if st != 0:
             raise GlimError(st, f"{what}: {self.lib.glim_last_error(self.h).decode()}")
+
+    def call(self, what, fn, *args, ok=(0,)):
+        """Run a library call on the context stream, after the work already queued on torch's
+        current stream, and make torch's current stream wait for it."""
+        cur = torch.cuda.current_stream(self.device)
+        same = cur.cuda_stream == self.stream.cuda_stream
+        if not same:
+            self.stream.wait_stream(cur)
+        st = fn(*args)
+        if not same:
+            cur.wait_stream(self.stream)
+        if st not in ok:
+            self.check(st, what)
+        return st
 
     @property
     def num_sms(self):
@@ -107,8 +122,7 @@ def estimate_covariances(ctx: Context, pts4: torch.Tensor, k: int = 10, reg_mode
     n = pts4.shape[0]
     cov = torch.empty((n, 6), dtype=torch.float32, device=pts4.device)
     nrm = torch.empty((n, 3), dtype=torch.float32, device=pts4.device) if normals else None
-    ctx.check(ctx.lib.glim_estimate_covariances(ctx.h, _ptr(pts4), n, k, reg_mode, eps, _ptr(cov), _ptr(nrm)),
-              "estimate_covariances")
+    ctx.call("estimate_covariances", ctx.lib.glim_estimate_covariances, ctx.h, _ptr(pts4), n, k, reg_mode, eps, _ptr(cov), _ptr(nrm))
     return cov, nrm
 
 
@@ -124,8 +138,8 @@ class VoxelMap:
         self.resolutions = [float(r) for r in resolutions]
         res = np.ascontiguousarray(self.resolutions, dtype=np.float64)
         h = C.c_void_p()
-        ctx.check(ctx.lib.glim_build_voxelmap(ctx.h, _ptr(pts4), _ptr(cov6), pts4.shape[0], _ptr(res), len(res),
-                                              C.byref(h)), "build_voxelmap")
+        ctx.call("build_voxelmap", ctx.lib.glim_build_voxelmap, ctx.h, _ptr(pts4), _ptr(cov6), pts4.shape[0], _ptr(res), len(res),
+                                              C.byref(h))
         self.h = h
 
     @property
@@ -134,7 +148,7 @@ class VoxelMap:
 
     def info(self, level):
         n, cap, mp = C.c_int64(), C.c_int64(), C.c_int32()
-        self.ctx.check(self.ctx.lib.glim_vmap_info(self.h, level, C.byref(n), C.byref(cap), C.byref(mp)), "vmap_info")
+        self.ctx.call("vmap_info", self.ctx.lib.glim_vmap_info, self.h, level, C.byref(n), C.byref(cap), C.byref(mp))
         return dict(n_voxels=n.value, capacity=cap.value, max_probe=mp.value)
 
     def export(self, level):
@@ -144,8 +158,8 @@ class VoxelMap:
         mean = torch.empty((m, 3), dtype=torch.float32, device=dev)
         cov = torch.empty((m, 6), dtype=torch.float32, device=dev)
         cnt = torch.empty((m,), dtype=torch.int32, device=dev)
-        self.ctx.check(self.ctx.lib.glim_vmap_export(self.ctx.h, self.h, level, _ptr(keys), _ptr(mean), _ptr(cov),
-                                                     _ptr(cnt)), "vmap_export")
+        self.ctx.call("vmap_export", self.ctx.lib.glim_vmap_export, self.ctx.h, self.h, level, _ptr(keys), _ptr(mean), _ptr(cov),
+                                                     _ptr(cnt))
         return dict(keys=keys, mean=mean, cov=cov, count=cnt)
 
     def free(self):
@@ -228,8 +242,8 @@ def linearize(ctx: Context, frames, vmaps, pairs, poses, out="host", plain=False
     o = _opts(**opts)
     e, H, b, inl = _outputs(P, out)
     fn = ctx.lib.glim_linearize_factors_plain if plain else ctx.lib.glim_linearize_factors
-    ctx.check(fn(ctx.h, fr, len(frames), pr, P, _ptr(Pz), C.byref(o), _ptr(e), _ptr(H), _ptr(b), _ptr(inl)),
-              "linearize_factors_plain" if plain else "linearize_factors")
+    ctx.call("linearize_factors_plain" if plain else "linearize_factors", fn, ctx.h, fr, len(frames), pr, P,
+             _ptr(Pz), C.byref(o), _ptr(e), _ptr(H), _ptr(b), _ptr(inl))
     return e, H, b, inl
 
 
@@ -246,7 +260,7 @@ class Plan:
         self.nframes = len(self.frames)
         o = _opts(**opts)
         h = C.c_void_p()
-        ctx.check(ctx.lib.glim_plan_create(ctx.h, fr, self.nframes, pr, P, C.byref(o), C.byref(h)), "plan_create")
+        ctx.call("plan_create", ctx.lib.glim_plan_create, ctx.h, fr, self.nframes, pr, P, C.byref(o), C.byref(h))
         self.h = h
         self._host = _outputs(P, "host")
 
@@ -254,24 +268,23 @@ class Plan:
         """One upload, one graph launch, one download; returns host arrays (e, H, b, inliers)."""
         Pz = _poses(poses, self.nframes)
         e, H, b, inl = out if out is not None else self._host
-        self.ctx.check(self.ctx.lib.glim_plan_linearize(self.h, _ptr(Pz), _ptr(e), _ptr(H), _ptr(b), _ptr(inl)),
-                       "plan_linearize")
+        self.ctx.call("plan_linearize", self.ctx.lib.glim_plan_linearize, self.h, _ptr(Pz), _ptr(e), _ptr(H), _ptr(b), _ptr(inl))
         return e, H, b, inl
 
     def set_poses(self, poses):
         Pz = _poses(poses, self.nframes)
-        self.ctx.check(self.ctx.lib.glim_plan_set_poses(self.h, _ptr(Pz)), "plan_set_poses")
+        self.ctx.call("plan_set_poses", self.ctx.lib.glim_plan_set_poses, self.h, _ptr(Pz))
 
     def launch(self):
-        self.ctx.check(self.ctx.lib.glim_plan_launch(self.h), "plan_launch")
+        self.ctx.call("plan_launch", self.ctx.lib.glim_plan_launch, self.h)
 
     def launch_timed(self, slot):
         """Direct launches with CUDA events around the linearization kernel (timing slot)."""
-        self.ctx.check(self.ctx.lib.glim_plan_launch_timed(self.h, slot), "plan_launch_timed")
+        self.ctx.call("plan_launch_timed", self.ctx.lib.glim_plan_launch_timed, self.h, slot)
 
     def kernel_ms(self, nslots):
         out = (C.c_float * max(nslots, 1))()
-        self.ctx.check(self.ctx.lib.glim_plan_kernel_ms(self.h, nslots, out), "plan_kernel_ms")
+        self.ctx.call("plan_kernel_ms", self.ctx.lib.glim_plan_kernel_ms, self.h, nslots, out)
         return np.array(out[:nslots], dtype=np.float64)
 
     @property
@@ -281,21 +294,20 @@ class Plan:
     def device_outputs(self):
         """Views of the plan's device output block (valid until the next launch)."""
         e, H, b, inl = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
-        self.ctx.check(self.ctx.lib.glim_plan_device_outputs(self.h, C.byref(e), C.byref(H), C.byref(b),
-                                                             C.byref(inl)), "plan_device_outputs")
+        self.ctx.call("plan_device_outputs", self.ctx.lib.glim_plan_device_outputs, self.h, C.byref(e), C.byref(H), C.byref(b),
+                                                             C.byref(inl))
         return e.value, H.value, b.value, inl.value
 
     def autotune(self, poses, iters=5):
         Pz = _poses(poses, self.nframes)
         o = _abi.LinOpts()
         ms = C.c_float()
-        self.ctx.check(self.ctx.lib.glim_plan_autotune(self.h, _ptr(Pz), iters, C.byref(o), C.byref(ms)),
-                       "plan_autotune")
+        self.ctx.call("plan_autotune", self.ctx.lib.glim_plan_autotune, self.h, _ptr(Pz), iters, C.byref(o), C.byref(ms))
         return dict(block=o.block, pts_per_thread=o.pts_per_thread, ms=ms.value)
 
     def opts(self):
         o = _abi.LinOpts()
-        self.ctx.check(self.ctx.lib.glim_plan_get_opts(self.h, C.byref(o)), "plan_get_opts")
+        self.ctx.call("plan_get_opts", self.ctx.lib.glim_plan_get_opts, self.h, C.byref(o))
         return dict(validate_surface=o.validate_surface, accum_mode=o.accum_mode, block=o.block,
                     pts_per_thread=o.pts_per_thread, blocks_per_sm=o.blocks_per_sm, persistent=o.persistent)
 
@@ -317,8 +329,8 @@ def correspondences(ctx: Context, frame: FrameData, vmap: VoxelMap, pose_s, pose
     f = frame.c()
     ps = _poses(pose_s)
     pt = _poses(pose_t)
-    ctx.check(ctx.lib.glim_correspondences(ctx.h, C.byref(f), vmap.h, _ptr(ps), _ptr(pt), int(validate_surface),
-                                           _ptr(ids)), "correspondences")
+    ctx.call("correspondences", ctx.lib.glim_correspondences, ctx.h, C.byref(f), vmap.h, _ptr(ps), _ptr(pt), int(validate_surface),
+                                           _ptr(ids))
     return ids
 
 
@@ -327,7 +339,7 @@ def overlap(ctx: Context, frames, vmaps, pairs, poses, level=0):
     pr, P = _pairs(pairs, vmaps)
     Pz = _poses(poses, len(frames))
     out = torch.empty(P, dtype=torch.float64, device=frames[0].pts4.device)
-    ctx.check(ctx.lib.glim_overlap(ctx.h, fr, len(frames), pr, P, _ptr(Pz), level, _ptr(out)), "overlap")
+    ctx.call("overlap", ctx.lib.glim_overlap, ctx.h, fr, len(frames), pr, P, _ptr(Pz), level, _ptr(out))
     return out
 
 
@@ -341,8 +353,8 @@ def backward(ctx: Context, frames, vmaps, pairs, poses, omega_grad_full=True, va
     dxi = torch.empty((len(frames), 6), dtype=torch.float64, device=dev)
     dmu = torch.empty((ntot, 3), dtype=torch.float32, device=dev)
     dw = torch.empty((ntot,), dtype=torch.float32, device=dev)
-    ctx.check(ctx.lib.glim_backward(ctx.h, fr, len(frames), pr, P, _ptr(Pz), int(omega_grad_full),
-                                    int(validate_surface), _ptr(dxi), _ptr(dmu), _ptr(dw)), "backward")
+    ctx.call("backward", ctx.lib.glim_backward, ctx.h, fr, len(frames), pr, P, _ptr(Pz), int(omega_grad_full),
+                                    int(validate_surface), _ptr(dxi), _ptr(dmu), _ptr(dw))
     return dxi, dmu, dw
 
 
@@ -356,8 +368,6 @@ def gn_solve(ctx: Context, H: torch.Tensor, b: torch.Tensor, dim: int = None):
     dim = dim or ld
     xi = torch.empty((count, dim), dtype=torch.float64, device=H.device)
     status = torch.empty(count, dtype=torch.int32, device=H.device)
-    st = ctx.lib.glim_gn_solve(ctx.h, _ptr(H), ld, H.shape[-2] * ld, _ptr(b), b.shape[-1], dim, count, _ptr(xi),
-                               _ptr(status))
-    if st not in (0, -6):
-        ctx.check(st, "gn_solve")
+    ctx.call("gn_solve", ctx.lib.glim_gn_solve, ctx.h, _ptr(H), ld, H.shape[-2] * ld, _ptr(b), b.shape[-1], dim,
+             count, _ptr(xi), _ptr(status), ok=(0, -6))
     return xi, status

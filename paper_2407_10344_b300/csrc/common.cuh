@@ -86,10 +86,22 @@ __host__ __device__ inline int unpack_x(unsigned long long k) { return int((k >>
 __host__ __device__ inline int unpack_y(unsigned long long k) { return int((k >> 21) & 0x1FFFFF) - GLIM_KEY_BIAS; }
 __host__ __device__ inline int unpack_z(unsigned long long k) { return int(k & 0x1FFFFF) - GLIM_KEY_BIAS; }
 
-// Fibonacci hashing of the packed key into a power-of-two table.
+// Fibonacci hashing of a packed key into a power-of-two table (grid cells of the kNN search).
 __host__ __device__ inline uint32_t hash_slot(unsigned long long key, int log2cap) {
   return uint32_t((key * 0x9E3779B97F4A7C15ull) >> (64 - log2cap));
 }
+
+// Voxel-table hash of an integer key: the spatial hash of Teschner et al. (2003), as used by
+// voxel hashing (Niessner et al. 2013), followed by a Fibonacci multiply whose top bits index
+// the power-of-two table.
+__host__ __device__ inline uint32_t hash3(int kx, int ky, int kz, int log2cap) {
+  const uint32_t h = (uint32_t(kx) * 73856093u) ^ (uint32_t(ky) * 19349663u) ^ (uint32_t(kz) * 83492791u);
+  return (h * 2654435761u) >> (32 - log2cap);
+}
+
+// Coordinate value marking an empty slot (every byte 0x80, outside [-2^20, 2^20)).
+#define GLIM_EMPTY_COORD int(0x80808080)
+#define GLIM_EMPTY_XY 0x8080808080808080ull
 
 // floor(c * inv_r) as an int in [-2^20, 2^20), or false.  One FP32 multiply, rounded to
 // nearest (explicit so that the compiler cannot fuse it with anything).
@@ -101,9 +113,10 @@ __device__ __forceinline__ bool voxel_coord(float c, float inv_r, int& k) {
 }
 
 // ------------------------------------------------------------------ hash slot (48 bytes)
-// One open-addressing slot holds the key and the voxel statistics, so a single probe that
-// matches returns the voxel:  w0 = {key lo, key hi, count (int bits), c22},
-// w1 = {mean x, mean y, mean z, c00}, w2 = {c01, c02, c11, c12}.
+// One open-addressing slot holds the key and the voxel statistics, so a probe that matches
+// returns the voxel with the same 48-byte read:  w0 = {kx, ky, kz (int bits), c22},
+// w1 = {mean x, mean y, mean z, c00}, w2 = {c01, c02, c11, c12}.  Empty slots have every
+// byte 0x80.
 struct __align__(16) VoxSlot {
   float4 w0, w1, w2;
 };

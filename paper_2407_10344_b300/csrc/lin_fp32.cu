@@ -1,0 +1,7 @@
+// lin_fp32.cu -- instantiations of the linearization kernel for accumulation mode GLIM_ACC_FP32
+// (one translation unit per mode so that they compile in parallel).
+#include "lin_kernel.cuh"
+
+namespace glim_detail {
+LinKernel pick_lin_fp32(int block, int ppt, int lmax) { return pick_lin<GLIM_ACC_FP32>(block, ppt, lmax); }
+}  // namespace glim_detail

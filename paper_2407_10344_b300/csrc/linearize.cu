@@ -24,279 +24,9 @@
 #include <cmath>
 #include <cstring>
 
-#include "plan.cuh"
+#include "lin_kernel.cuh"
 
 namespace {
-
-// ---------------------------------------------------------------- accumulation policies
-// Plain FP32 running sums.
-struct AccPlain {
-  float s[NACC];
-  __device__ __forceinline__ void zero() {
-#pragma unroll
-    for (int i = 0; i < NACC; ++i) s[i] = 0.f;
-  }
-  __device__ __forceinline__ void add(int i, float x) { s[i] += x; }
-};
-
-// Neumaier-compensated FP32 running sums (Neumaier 1974): c collects the rounding error of
-// every addition.
-struct AccComp {
-  float s[NACC], c[NACC];
-  __device__ __forceinline__ void zero() {
-#pragma unroll
-    for (int i = 0; i < NACC; ++i) s[i] = c[i] = 0.f;
-  }
-  __device__ __forceinline__ void add(int i, float x) {
-    const float t = s[i] + x;
-    c[i] += (fabsf(s[i]) >= fabsf(x)) ? ((s[i] - t) + x) : ((x - t) + s[i]);
-    s[i] = t;
-  }
-};
-
-template <int ACC>
-struct AccOf {
-  using type = AccPlain;
-};
-template <>
-struct AccOf<GLIM_ACC_KAHAN> {
-  using type = AccComp;
-};
-
-// ---------------------------------------------------------------- per-point term
-template <class A>
-__device__ __forceinline__ void point_term(const PairView& P, int64_t k, int validate, A& acc, int& inl) {
-  const float4 m = ldg4(&P.F.pts[k]);
-  if (validate && P.F.nrm) {
-    const float* nk = P.F.nrm + 3 * k;
-    if (behind_surface(m.x, m.y, m.z, P.v, __ldg(nk), __ldg(nk + 1), __ldg(nk + 2))) return;
-  }
-  const float2 ca = __ldg(&P.F.cov[3 * k]), cb = __ldg(&P.F.cov[3 * k + 1]), cc = __ldg(&P.F.cov[3 * k + 2]);
-  // C (xx xy xz / yy yz / zz)
-  const float c00 = ca.x, c01 = ca.y, c02 = cb.x, c11 = cb.y, c12 = cc.x, c22 = cc.y;
-  const float* R = P.R;
-  const float3 q = transform_pinned(R, P.t, m.x, m.y, m.z);
-  const float3 u = make_float3(q.x - P.t[0], q.y - P.t[1], q.z - P.t[2]);
-  // W = R C, then RCR^T (symmetric: 6 entries)
-  const float w00 = R[0] * c00 + R[1] * c01 + R[2] * c02;
-  const float w01 = R[0] * c01 + R[1] * c11 + R[2] * c12;
-  const float w02 = R[0] * c02 + R[1] * c12 + R[2] * c22;
-  const float w10 = R[3] * c00 + R[4] * c01 + R[5] * c02;
-  const float w11 = R[3] * c01 + R[4] * c11 + R[5] * c12;
-  const float w12 = R[3] * c02 + R[4] * c12 + R[5] * c22;
-  const float w20 = R[6] * c00 + R[7] * c01 + R[8] * c02;
-  const float w21 = R[6] * c01 + R[7] * c11 + R[8] * c12;
-  const float w22 = R[6] * c02 + R[7] * c12 + R[8] * c22;
-  const float r00 = w00 * R[0] + w01 * R[1] + w02 * R[2];
-  const float r01 = w00 * R[3] + w01 * R[4] + w02 * R[5];
-  const float r02 = w00 * R[6] + w01 * R[7] + w02 * R[8];
-  const float r11 = w10 * R[3] + w11 * R[4] + w12 * R[5];
-  const float r12 = w10 * R[6] + w11 * R[7] + w12 * R[8];
-  const float r22 = w20 * R[6] + w21 * R[7] + w22 * R[8];
-
-  float o00 = 0.f, o01 = 0.f, o02 = 0.f, o11 = 0.f, o12 = 0.f, o22 = 0.f;  // sum Omega
-  float g0 = 0.f, g1 = 0.f, g2 = 0.f;                                      // sum Omega d
-  float es = 0.f;
-  int hits = 0;
-#pragma unroll
-  for (int l = 0; l < GLIM_MAX_LEVELS; ++l) {
-    if (l >= P.M.levels) break;
-    const LevelDev& L = P.M.lv[l];
-    unsigned long long key;
-    if (!level_key(q, L.inv_r, key)) continue;
-    const int s = probe_slot(L, key);
-    if (s < 0) continue;
-    const float4 v0 = ldg4(&L.slots[s].w0), v1 = ldg4(&L.slots[s].w1), v2 = ldg4(&L.slots[s].w2);
-    // S = C~ + R C R^T
-    const float a = v1.w + r00, b = v2.x + r01, c = v2.y + r02, d = v2.z + r11, e = v2.w + r12, f = v0.w + r22;
-    const float A00 = d * f - e * e, A01 = c * e - b * f, A02 = b * e - c * d;
-    const float A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
-    const float det = a * A00 + b * A01 + c * A02;
-    if (!(det > 0.f) || !isfinite(det)) continue;  // S not positive definite: skip the term
-    const float id = __frcp_rn(det);
-    const float O00 = A00 * id, O01 = A01 * id, O02 = A02 * id, O11 = A11 * id, O12 = A12 * id, O22 = A22 * id;
-    const float dx = v1.x - q.x, dy = v1.y - q.y, dz = v1.z - q.z;
-    const float y0 = O00 * dx + O01 * dy + O02 * dz;
-    const float y1 = O01 * dx + O11 * dy + O12 * dz;
-    const float y2 = O02 * dx + O12 * dy + O22 * dz;
-    es += dx * y0 + dy * y1 + dz * y2;
-    o00 += O00; o01 += O01; o02 += O02; o11 += O11; o12 += O12; o22 += O22;
-    g0 += y0; g1 += y1; g2 += y2;
-    ++hits;
-  }
-  if (hits == 0) return;
-  inl += hits;
-  const float wk = m.w;
-  o00 *= wk; o01 *= wk; o02 *= wk; o11 *= wk; o12 *= wk; o22 *= wk;
-  g0 *= wk; g1 *= wk; g2 *= wk;
-  es *= wk;
-  // W = (u)x Omega_sum
-  const float W00 = -u.z * o01 + u.y * o02, W01 = -u.z * o11 + u.y * o12, W02 = -u.z * o12 + u.y * o22;
-  const float W10 = u.z * o00 - u.x * o02, W11 = u.z * o01 - u.x * o12, W12 = u.z * o02 - u.x * o22;
-  const float W20 = -u.y * o00 + u.x * o01, W21 = -u.y * o01 + u.x * o11, W22 = -u.y * o02 + u.x * o12;
-  // M_rr = -(u)x Omega (u)x = W (u)x^T  (symmetric)
-  acc.add(0, -u.z * W01 + u.y * W02);
-  acc.add(1, u.z * W00 - u.x * W02);
-  acc.add(2, -u.y * W00 + u.x * W01);
-  acc.add(3, u.z * W10 - u.x * W12);
-  acc.add(4, -u.y * W10 + u.x * W11);
-  acc.add(5, -u.y * W20 + u.x * W21);
-  // M_rt = (u)x Omega
-  acc.add(6, W00); acc.add(7, W01); acc.add(8, W02);
-  acc.add(9, W10); acc.add(10, W11); acc.add(11, W12);
-  acc.add(12, W20); acc.add(13, W21); acc.add(14, W22);
-  // M_tt = Omega
-  acc.add(15, o00); acc.add(16, o01); acc.add(17, o02); acc.add(18, o11); acc.add(19, o12); acc.add(20, o22);
-  // g = [u x g_sum; g_sum]
-  acc.add(21, u.y * g2 - u.z * g1);
-  acc.add(22, u.z * g0 - u.x * g2);
-  acc.add(23, u.x * g1 - u.y * g0);
-  acc.add(24, g0); acc.add(25, g1); acc.add(26, g2);
-  acc.add(27, es);
-}
-
-// ---------------------------------------------------------------- block reduction
-// Warp transpose-reduction: 32 values per lane -> lane l holds the warp total of value l
-// (31 shuffles instead of 5 per value).
-__device__ __forceinline__ void warp_transpose_reduce(float (&v)[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int o = 16, c = 16; o >= 1; o >>= 1, c >>= 1) {
-    const bool upper = (lane & o) != 0;
-#pragma unroll
-    for (int j = 0; j < c; ++j) {
-      const float send = upper ? v[j] : v[j + c];
-      const float keep = upper ? v[j + c] : v[j];
-      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-  }
-}
-
-// Same with error-free two-sum of the hi parts, collecting the rounding errors in lo.
-__device__ __forceinline__ void warp_transpose_reduce_comp(float (&hi)[32], float (&lo)[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int o = 16, c = 16; o >= 1; o >>= 1, c >>= 1) {
-    const bool upper = (lane & o) != 0;
-#pragma unroll
-    for (int j = 0; j < c; ++j) {
-      const float sh = upper ? hi[j] : hi[j + c], sl = upper ? lo[j] : lo[j + c];
-      const float kh = upper ? hi[j + c] : hi[j], kl = upper ? lo[j + c] : lo[j];
-      const float rh = __shfl_xor_sync(0xffffffffu, sh, o), rl = __shfl_xor_sync(0xffffffffu, sl, o);
-      const float s = kh + rh;
-      const float bp = s - kh;
-      const float err = (kh - (s - bp)) + (rh - bp);  // two-sum (Knuth)
-      hi[j] = s;
-      lo[j] = kl + rl + err;
-    }
-  }
-}
-
-template <int BLOCK, int ACC>
-__device__ __forceinline__ void block_reduce_store(const typename AccOf<ACC>::type& acc, int inl, double* out) {
-  constexpr int NW = BLOCK / 32;
-  __shared__ float s_hi[NW][32];
-  __shared__ float s_lo[NW][32];
-  __shared__ int s_inl[NW];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float hi[32];
-#pragma unroll
-  for (int i = 0; i < 32; ++i) hi[i] = (i < NACC) ? acc.s[i] : 0.f;
-  if constexpr (ACC == GLIM_ACC_KAHAN) {
-    float lo[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) lo[i] = (i < NACC) ? acc.c[i] : 0.f;
-    warp_transpose_reduce_comp(hi, lo);
-    s_lo[warp][lane] = lo[0];
-  } else {
-    warp_transpose_reduce(hi);
-  }
-  s_hi[warp][lane] = hi[0];
-  const int wi = __reduce_add_sync(0xffffffffu, unsigned(inl));
-  if (lane == 0) s_inl[warp] = wi;
-  __syncthreads();
-  if (threadIdx.x < NACC) {
-    const int i = threadIdx.x;
-    if constexpr (ACC == GLIM_ACC_FP32) {
-      float t = 0.f;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) t += s_hi[w][i];
-      out[i] = double(t);
-    } else if constexpr (ACC == GLIM_ACC_KAHAN) {
-      double t = 0.0;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) t += double(s_hi[w][i]) + double(s_lo[w][i]);
-      out[i] = t;
-    } else {
-      double t = 0.0;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) t += double(s_hi[w][i]);
-      out[i] = t;
-    }
-  } else if (threadIdx.x == NACC) {
-    int t = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) t += s_inl[w];
-    out[NACC] = double(t);
-  }
-  __syncthreads();  // shared buffers are reused by the next item
-}
-
-// ---------------------------------------------------------------- item processing
-template <int BLOCK, int PPT, int ACC>
-__device__ __forceinline__ void process_item(const LinArgs& a, int item) {
-  const Item it = a.items[item];
-  // stage the pair's constants (pose, frame, map) in shared memory once per item; every
-  // thread reads them from there (uniform addresses, broadcast)
-  __shared__ PairView s_view;
-  if (threadIdx.x == 0) {
-    const PairDev pd = a.pairs[it.pair];
-    const PoseF pf = a.pose[it.pair];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) s_view.R[i] = pf.R[i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      s_view.t[i] = pf.t[i];
-      s_view.v[i] = pf.v[i];
-    }
-    s_view.F = a.frames[pd.src];
-    s_view.M = a.maps[pd.map];
-  }
-  __syncthreads();
-  typename AccOf<ACC>::type acc;
-  acc.zero();
-  int inl = 0;
-  const int64_t end = min(int64_t(it.start) + a.tile, s_view.F.n);
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    const int64_t k = int64_t(it.start) + j * BLOCK + threadIdx.x;
-    if (k < end) point_term(s_view, k, a.validate, acc, inl);
-  }
-  // the reduction ends with a barrier, so s_view is free for the next item afterwards
-  block_reduce_store<BLOCK, ACC>(acc, inl, a.part + int64_t(item) * PSTRIDE);
-}
-
-// Persistent kernel: blocks take items from the atomic queue until it is exhausted.
-template <int BLOCK, int PPT, int ACC>
-__global__ void __launch_bounds__(BLOCK) k_linearize_queue(const LinArgs a) {
-  __shared__ int s_item;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(a.head, 1);
-    __syncthreads();
-    const int item = s_item;
-    __syncthreads();
-    if (item >= a.nitems) break;
-    process_item<BLOCK, PPT, ACC>(a, item);
-  }
-}
-
-// One block per item (hardware scheduling; also the per-factor launches of the plain form).
-template <int BLOCK, int PPT, int ACC>
-__global__ void __launch_bounds__(BLOCK) k_linearize_grid(const LinArgs a) {
-  const int item = a.item_base + blockIdx.x;
-  if (item >= a.nitems) return;
-  process_item<BLOCK, PPT, ACC>(a, item);
-}
 
 // ---------------------------------------------------------------- FP64 reduce + expand
 struct ReduceArgs {
@@ -392,31 +122,11 @@ __global__ void __launch_bounds__(128) k_reduce_expand(const ReduceArgs a) {
 }
 
 // ---------------------------------------------------------------- kernel table
-template <int BLOCK, int ACC>
-LinKernel pick_ppt(int ppt, bool persistent) {
-  switch (ppt) {
-    case 1: return persistent ? k_linearize_queue<BLOCK, 1, ACC> : k_linearize_grid<BLOCK, 1, ACC>;
-    case 2: return persistent ? k_linearize_queue<BLOCK, 2, ACC> : k_linearize_grid<BLOCK, 2, ACC>;
-    case 4: return persistent ? k_linearize_queue<BLOCK, 4, ACC> : k_linearize_grid<BLOCK, 4, ACC>;
-    case 8: return persistent ? k_linearize_queue<BLOCK, 8, ACC> : k_linearize_grid<BLOCK, 8, ACC>;
-  }
-  return nullptr;
-}
-
-template <int BLOCK>
-LinKernel pick_acc(int acc, int ppt, bool persistent) {
+LinKernel pick_kernel(int block, int acc, int ppt, int lmax) {
   switch (acc) {
-    case GLIM_ACC_FP32: return pick_ppt<BLOCK, GLIM_ACC_FP32>(ppt, persistent);
-    case GLIM_ACC_KAHAN: return pick_ppt<BLOCK, GLIM_ACC_KAHAN>(ppt, persistent);
-    case GLIM_ACC_FP64: return pick_ppt<BLOCK, GLIM_ACC_FP64>(ppt, persistent);
-  }
-  return nullptr;
-}
-
-LinKernel pick_kernel(int block, int acc, int ppt, bool persistent) {
-  switch (block) {
-    case 128: return pick_acc<128>(acc, ppt, persistent);
-    case 256: return pick_acc<256>(acc, ppt, persistent);
+    case GLIM_ACC_FP32: return pick_lin_fp32(block, ppt, lmax);
+    case GLIM_ACC_KAHAN: return pick_lin_kahan(block, ppt, lmax);
+    case GLIM_ACC_FP64: return pick_lin_fp64(block, ppt, lmax);
   }
   return nullptr;
 }
@@ -482,7 +192,7 @@ glim_status plan_configure(glim_plan* p, const glim_lin_opts& o) {
   if (!items.empty())
     GLIM_CUDA(ctx, cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice));
   GLIM_CUDA(ctx, cudaMemcpy(p->d_item_begin, begin.data(), begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  p->kernel = pick_kernel(o.block, o.accum_mode, o.pts_per_thread, o.persistent == 1);
+  p->kernel = pick_kernel(o.block, o.accum_mode, o.pts_per_thread, p->lmax);
   if (!p->kernel) return set_error(ctx, GLIM_EINVAL, "no kernel for block=%d ppt=%d acc=%d", o.block, o.pts_per_thread, o.accum_mode);
   if (o.persistent == 1) {
     int per_sm = o.blocks_per_sm;
@@ -512,7 +222,7 @@ glim_status plan_enqueue_kernels(glim_plan* p, int slot = -1) {
     a.frames = p->d_frames;
     a.maps = p->d_maps;
     a.pose = p->in_pose32();
-    a.head = p->d_head;
+    a.head = p->opts.persistent == 1 ? p->d_head : nullptr;
     a.part = p->d_part;
     a.tile = p->tile;
     a.validate = p->opts.validate_surface;
@@ -663,6 +373,8 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
     for (int l = 0; l < maps[i]->levels; ++l) md[i].lv[l] = maps[i]->dev(l);
   }
   p->nmaps = int(maps.size());
+  p->lmax = 1;
+  for (const glim_vmap* m : maps) p->lmax = std::max(p->lmax, m->levels);
   auto fail = [&](glim_status s) {
     glim_plan_destroy(p);
     return s;
@@ -874,6 +586,7 @@ extern "C" glim_status glim_linearize_factors_plain(glim_ctx* ctx, const glim_fr
   glim_plan* p = nullptr;
   glim_status st = glim_plan_create(ctx, frames, nframes, pairs, npairs, &o, &p);
   if (st != GLIM_OK) return st;
+  o = p->opts;  // with the defaults filled in
   const bool dev_out = npairs > 0 && is_device_ptr(e_out);
   plan_pack_poses(p, poses12);
   GLIM_CUDA(ctx, cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream));
@@ -890,7 +603,7 @@ extern "C" glim_status glim_linearize_factors_plain(glim_ctx* ctx, const glim_fr
     a.frames = p->d_frames;
     a.maps = p->d_maps;
     a.pose = p->in_pose32();
-    a.head = p->d_head;
+    a.head = nullptr;  // one block per item of this factor
     a.part = p->d_part;
     a.tile = p->tile;
     a.validate = o.validate_surface;
@@ -898,7 +611,8 @@ extern "C" glim_status glim_linearize_factors_plain(glim_ctx* ctx, const glim_fr
     if (nb > 0) {
       p->kernel<<<nb, o.block, 0, ctx->stream>>>(a);
       ctx->launches++;
-      if (cudaGetLastError() != cudaSuccess) { st = set_error(ctx, GLIM_ECUDA, "plain: launch failed"); break; }
+      const cudaError_t le = cudaGetLastError();
+      if (le != cudaSuccess) { st = cuda_check(ctx, le, "plain: linearize launch"); break; }
     }
     ReduceArgs r;
     r.part = p->d_part;
@@ -913,7 +627,8 @@ extern "C" glim_status glim_linearize_factors_plain(glim_ctx* ctx, const glim_fr
     r.inl = p->out_inl();
     k_reduce_expand<<<1, 128, 0, ctx->stream>>>(r);
     ctx->launches++;
-    if (cudaGetLastError() != cudaSuccess) { st = set_error(ctx, GLIM_ECUDA, "plain: reduce launch failed"); break; }
+    const cudaError_t re = cudaGetLastError();
+    if (re != cudaSuccess) { st = cuda_check(ctx, re, "plain: reduce launch"); break; }
     cudaMemcpyAsync(h + q, p->out_e() + q, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     cudaMemcpyAsync(h + npairs + size_t(q) * 144, p->out_H() + size_t(q) * 144, 144 * sizeof(double),
                     cudaMemcpyDeviceToHost, ctx->stream);

@@ -3,13 +3,7 @@
 #pragma once
 #include "common.cuh"
 
-// Read-only loads through the non-coherent path; the voxel tables and source frames are not
-// written while a linearization kernel runs.
 __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
-
-__device__ __forceinline__ unsigned long long slot_key(const float4& w0) {
-  return (unsigned long long)__float_as_uint(w0.x) | ((unsigned long long)__float_as_uint(w0.y) << 32);
-}
 
 // q = R mu + t on the FP32 path: one fused multiply-add per term, starting from t and adding
 // the x, y, z terms in that order (R row-major).
@@ -32,24 +26,35 @@ __device__ __forceinline__ bool behind_surface(float mx, float my, float mz, con
   return s > 0.0f;
 }
 
-// Packed voxel key of q at a level, or false when a component is outside [-2^20, 2^20).
-__device__ __forceinline__ bool level_key(const float3& q, float inv_r, unsigned long long& key) {
-  int kx, ky, kz;
-  if (!voxel_coord(q.x, inv_r, kx) || !voxel_coord(q.y, inv_r, ky) || !voxel_coord(q.z, inv_r, kz)) return false;
-  key = pack_key(kx, ky, kz);
-  return true;
+// floor(c * inv_r) with one round-to-nearest FP32 multiply; false (a miss) when the product
+// is outside [-2^20, 2^20) or not a number.  Then floor(product) lies in the same range and
+// the conversion rounding down is exact.
+__device__ __forceinline__ bool key_coord(float c, float inv_r, int& k) {
+  const float p = __fmul_rn(c, inv_r);
+  k = __float2int_rd(p);
+  return p >= -1048576.0f && p < 1048576.0f;
 }
 
-// Linear probe for `key`; returns the slot index or -1.  The loop is bounded by the longest
-// probe sequence recorded when the table was built.
-__device__ __forceinline__ int probe_slot(const LevelDev& L, unsigned long long key) {
-  uint32_t h = hash_slot(key, L.log2cap);
-  for (int p = 0; p < L.max_probe; ++p) {
+__device__ __forceinline__ bool level_key3(const float3& q, float inv_r, int& kx, int& ky, int& kz) {
+  const bool a = key_coord(q.x, inv_r, kx);
+  const bool b = key_coord(q.y, inv_r, ky);
+  const bool c = key_coord(q.z, inv_r, kz);
+  return a && b && c;
+}
+
+// Linear probe for key (kx, ky, kz) starting at slot h; returns the slot index or -1.  The
+// loop is bounded by the longest probe sequence recorded when the table was built.
+__device__ __forceinline__ int probe_from(const LevelDev& L, int kx, int ky, int kz, uint32_t h, int first) {
+  for (int p = first; p < L.max_probe; ++p) {
     const float4 w0 = ldg4(&L.slots[h].w0);
-    const unsigned long long k = slot_key(w0);
-    if (k == key) return int(h);
-    if (k == GLIM_EMPTY_KEY) return -1;
+    const int sx = __float_as_int(w0.x);
+    if (sx == kx && __float_as_int(w0.y) == ky && __float_as_int(w0.z) == kz) return int(h);
+    if (sx == GLIM_EMPTY_COORD) return -1;
     h = (h + 1u) & L.mask;
   }
   return -1;
+}
+
+__device__ __forceinline__ int probe_slot3(const LevelDev& L, int kx, int ky, int kz) {
+  return probe_from(L, kx, ky, kz, hash3(kx, ky, kz, L.log2cap), 0);
 }

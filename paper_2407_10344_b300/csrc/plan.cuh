@@ -70,6 +70,7 @@ struct glim_plan {
   MapDev* d_maps = nullptr;
   PairDev* d_pairs = nullptr;
   int nmaps = 0;
+  int lmax = 1;  // most levels of any target map (kernel template parameter)
   // work list (depends on the tile size)
   Item* d_items = nullptr;
   int32_t* d_item_begin = nullptr;

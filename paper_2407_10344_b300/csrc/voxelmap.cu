@@ -53,13 +53,17 @@ __global__ void k_hash_insert(const unsigned long long* __restrict__ vkey, const
   const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (v >= m) return;
   const unsigned long long key = vkey[v];
-  uint32_t h = hash_slot(key, log2cap);
+  const int kx = unpack_x(key), ky = unpack_y(key), kz = unpack_z(key);
+  // claim the slot through its first 8 bytes (kx, ky); keys are unique, so a claimed slot is
+  // never claimed again
+  const unsigned long long xy = (unsigned long long)(uint32_t)kx | ((unsigned long long)(uint32_t)ky << 32);
+  uint32_t h = hash3(kx, ky, kz, log2cap);
   for (uint32_t p = 0; p <= mask; ++p) {
     unsigned long long* kp = reinterpret_cast<unsigned long long*>(&slots[h].w0);
-    const unsigned long long old = atomicCAS(kp, GLIM_EMPTY_KEY, key);
-    if (old == GLIM_EMPTY_KEY) {
+    const unsigned long long old = atomicCAS(kp, GLIM_EMPTY_XY, xy);
+    if (old == GLIM_EMPTY_XY) {
       float* w = reinterpret_cast<float*>(&slots[h]);
-      w[2] = __int_as_float(vcount[v]);
+      w[2] = __int_as_float(kz);
       w[3] = vcov[6 * v + 5];                                    // c22
       w[4] = vmean[3 * v];
       w[5] = vmean[3 * v + 1];
@@ -116,9 +120,9 @@ __global__ void k_correspondences(const CorrArgs a, int32_t* __restrict__ ids) {
   const float3 q = transform_pinned(a.pose.R, a.pose.t, m.x, m.y, m.z);
   for (int l = 0; l < a.levels; ++l) {
     int32_t id = -1;
-    unsigned long long key;
-    if (visible && level_key(q, a.lv[l].inv_r, key)) {
-      int s = probe_slot(a.lv[l], key);
+    int kx, ky, kz;
+    if (visible && level_key3(q, a.lv[l].inv_r, kx, ky, kz)) {
+      int s = probe_slot3(a.lv[l], kx, ky, kz);
       if (s >= 0) id = a.lv[l].slot_id[s];
     }
     ids[k * a.levels + l] = id;
@@ -138,8 +142,8 @@ __global__ void k_overlap(const OverlapPair* __restrict__ pairs, double* __restr
   for (int64_t k = threadIdx.x; k < P.n; k += blockDim.x) {
     const float4 m = ldg4(&P.pts[k]);
     const float3 q = transform_pinned(P.pose.R, P.pose.t, m.x, m.y, m.z);
-    unsigned long long key;
-    if (level_key(q, P.lv.inv_r, key) && probe_slot(P.lv, key) >= 0) ++hits;
+    int kx, ky, kz;
+    if (level_key3(q, P.lv.inv_r, kx, ky, kz) && probe_slot3(P.lv, kx, ky, kz) >= 0) ++hits;
   }
   __shared__ unsigned long long s[8];
   unsigned long long h = __reduce_add_sync(0xffffffffu, unsigned(hits));
@@ -186,7 +190,7 @@ glim_status build_level(glim_ctx* ctx, const float* pts4, const float* cov6, int
   GLIM_CUDA(ctx, cudaMalloc(&vm->vmean[l], std::max<int64_t>(m, 1) * 3 * sizeof(float)));
   GLIM_CUDA(ctx, cudaMalloc(&vm->vcov[l], std::max<int64_t>(m, 1) * 6 * sizeof(float)));
   GLIM_CUDA(ctx, cudaMalloc(&vm->vcount[l], std::max<int64_t>(m, 1) * sizeof(int32_t)));
-  GLIM_CUDA(ctx, cudaMemsetAsync(vm->slots[l], 0xFF, cap * sizeof(VoxSlot), ctx->stream));
+  GLIM_CUDA(ctx, cudaMemsetAsync(vm->slots[l], 0x80, cap * sizeof(VoxSlot), ctx->stream));
   GLIM_CUDA(ctx, cudaMemsetAsync(vm->slot_id[l], 0xFF, cap * sizeof(int32_t), ctx->stream));
   if (m == 0) {
     vm->max_probe[l] = 0;
