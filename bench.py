@@ -49,7 +49,7 @@ def dist_env():
 def make_workload(args, rank):
     import synth
     if args.workload == "urban":
-        return synth.urban(seed=3 + 1000 * rank, n_submaps=args.submaps)
+        return synth.urban(seed=3 + 1000 * rank, n_submaps=args.submaps, keep=args.keep)
     if args.workload == "corridor":
         return synth.corridor(seed=2 + 1000 * rank)
     raise ValueError(args.workload)
@@ -57,7 +57,8 @@ def make_workload(args, rank):
 
 def workload_desc(w, args):
     if args.workload == "urban":
-        return (f"urban global step: {len(w.points)} submaps of log-U[50k,200k] pts, {len(w.pairs)} pairs "
+        sub = f" (first {len(w.points)} of a {args.submaps}-submap trajectory)" if args.keep else ""
+        return (f"urban global step: {len(w.points)} submaps of log-U[50k,200k] pts{sub}, {len(w.pairs)} pairs "
                 f"(10 nearest), voxels 0.5/1/2 m")
     return "corridor odometry window: 30k-pt frame vs 10 keyframes of 15k-40k pts, 0.5 m voxels"
 
@@ -164,17 +165,23 @@ def run_ours(args):
     gen_s = time.perf_counter() - t_gen
     ctx = G.Context(local)
     # inputs resident in HBM: points, kNN covariances and normals, voxelmaps of every target
-    frames, maps = [], [None] * len(w.points)
+    # Frames in Z-order of 0.5 m cells (the spatially coherent order that voxel-grid
+    # downsampling or a scan-line order gives); the synthetic generator's own order is random.
+    frames, frames_random, maps = [], [], [None] * len(w.points)
     targets = set(int(t) for t in w.pairs[:, 1])
     for i, p in enumerate(w.points):
         p4 = G.to_pts4(p, device=dev)
         cov, nrm = G.estimate_covariances(ctx, p4, k=10)
+        frames_random.append(G.FrameData(p4, cov, nrm))
+        if args.order == "morton":
+            perm = G.spatial_order(ctx, p4, 0.5)
+            p4, cov, nrm = p4[perm].contiguous(), cov[perm].contiguous(), nrm[perm].contiguous()
         frames.append(G.FrameData(p4, cov, nrm))
         if i in targets:
             maps[i] = G.VoxelMap(ctx, p4, cov, w.resolutions)
     torch.cuda.synchronize()
     acc = {"fp32": G.ACC_FP32, "kahan": G.ACC_KAHAN, "fp64": G.ACC_FP64}[args.accum]
-    plan = G.Plan(ctx, frames, maps, w.pairs, accum_mode=acc)
+    plan = G.Plan(ctx, frames, maps, w.pairs, accum_mode=acc, block=args.block, pts_per_thread=args.ppt)
     tuned = plan.autotune(w.poses, iters=2) if args.autotune else None
     opts = plan.opts()
     plan.set_poses(w.poses)
@@ -234,6 +241,16 @@ def run_ours(args):
     t0 = time.perf_counter()
     plan.linearize(w.poses)
     batched_ms = (time.perf_counter() - t0) * 1e3
+    # the same batch with the frames in the generator's random point order
+    random_ms = None
+    if args.order == "morton":
+        plan_r = G.Plan(ctx, frames_random, maps, w.pairs, accum_mode=acc, block=opts["block"],
+                        pts_per_thread=opts["pts_per_thread"])
+        plan_r.set_poses(w.poses)
+        for i in range(W + 3):
+            plan_r.launch_timed(i)
+        random_ms = float(np.median(plan_r.kernel_ms(W + 3)[W:]))
+        plan_r.close()
     pk = peaks()
     hbm_peak = pk.get("hbm_gbs", 6400.0)
     kavg_ms = float(np.mean(kern_ms))
@@ -246,6 +263,7 @@ def run_ours(args):
                    "pair_points_per_step": n_pp, "levels": len(w.resolutions), "resolutions_m": w.resolutions,
                    "accum_mode": args.accum, "block": opts["block"], "pts_per_thread": opts["pts_per_thread"],
                    "autotuned": tuned, "surface_validation": False,
+                   "point_order": "Z-order of 0.5 m cells" if args.order == "morton" else "generator (random)",
                    "l2": "inputs larger than L2: %.2f GB source stream per step (L2 126 MB)" % (BYTES_PER_POINT * n_pp / 1e9),
                    "parallelism": f"replicas x{ws} (independent batches per GPU, no collective)",
                    "generation_s": round(gen_s, 1)},
@@ -260,6 +278,8 @@ def run_ours(args):
                         "clouds and voxelmaps resident"},
         "plain": {"ms_per_batch": plain_ms, "batched_ms_per_batch": batched_ms,
                   "speedup": plain_ms / batched_ms if batched_ms > 0 else None},
+        "random_point_order": None if random_ms is None else {
+            "kernel_ms": random_ms, "value": n_pp / (random_ms / 1e3), "unit": UNIT},
         "gpu_launches": gpu_launches,
         "clocks": clk,
     }
@@ -302,8 +322,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="urban", choices=["urban", "corridor"])
     ap.add_argument("--submaps", type=int, default=400)
+    ap.add_argument("--keep", type=int, default=None, help="keep only the first N submaps (profiling cases)")
     ap.add_argument("--accum", default="fp64", choices=["fp32", "kahan", "fp64"])
+    ap.add_argument("--order", default="morton", choices=["morton", "random"],
+                    help="source point order of the frames")
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--block", type=int, default=0, help="threads per block (0: default; autotune overrides)")
+    ap.add_argument("--ppt", type=int, default=0, help="points per thread (0: default; autotune overrides)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-points", type=int, default=3_000_000)

@@ -93,7 +93,7 @@ typedef struct {
  *   validate_surface  1 = apply the surface-orientation test.
  *   accum_mode        GLIM_ACC_*.
  *   block             threads per block (128 or 256; default 256).
- *   pts_per_thread    points per thread per work item (1, 2, 4 or 8; default 4);
+ *   pts_per_thread    points per thread per work item (1..256; default 16);
  *                     a work item (tile) covers block * pts_per_thread points of one pair.
  *   blocks_per_sm     resident blocks per SM of the persistent kernel (default: occupancy).
  *   persistent        1 (default) = one persistent kernel over an atomic work queue;
@@ -135,6 +135,18 @@ glim_status glim_estimate_covariances(glim_ctx* ctx, const float* pts4, int64_t 
                                       int32_t reg_mode, float eps, float* cov6_out,
                                       float* normal3_out);
 
+/* ---------------------------------------------------------------- point order */
+
+/* Permutation that orders a frame's points along a Z-order (Morton) curve of cubic cells of
+ * size `cell` (metres): perm_out[i] is the index of the point placed at position i (device,
+ * n int32).  Points with equal cells keep their relative order.  Applying it to a frame (as
+ * voxel-grid downsampling or a scan-line order would) keeps neighbouring points together, so
+ * the lanes of a warp read the same voxel records.  The linearization result does not depend
+ * on the point order beyond floating-point rounding.  GLIM_ERANGE if a cell coordinate is
+ * outside [-2^20, 2^20). */
+glim_status glim_spatial_order(glim_ctx* ctx, const float* pts4, int64_t n, float cell,
+                               int32_t* perm_out);
+
 /* ---------------------------------------------------------------- voxelmaps */
 
 /* Build the multi-resolution voxelmap of one frame (Sec. III-C "Preprocessing"): for each
@@ -145,10 +157,25 @@ glim_status glim_estimate_covariances(glim_ctx* ctx, const float* pts4, int64_t 
  * Synchronizes the stream.  The voxelmap keeps no reference to the input arrays. */
 glim_status glim_build_voxelmap(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n,
                                 const double* resolutions, int32_t levels, glim_vmap** out);
+/* As glim_build_voxelmap, choosing the table layout of every level:
+ *   layout 0 (default): a dense grid over the bounding box of the occupied keys whose cells
+ *            hold the voxel records (48 bytes per cell) when the box has at most 256 cells
+ *            per voxel plus 2^22 cells and needs at most 32 GiB, else an open-addressing hash
+ *            table (linear probing, load <= 1/2);
+ *   layout 1: dense grid (GLIM_EINVAL if the bounding box exceeds the limit);
+ *   layout 2: hash table.
+ * Both layouts give identical correspondences and results; the dense grid resolves every
+ * lookup, hit or miss, with one 48-byte read, the hash table with one read per probe. */
+glim_status glim_build_voxelmap_ex(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n,
+                                   const double* resolutions, int32_t levels, int32_t layout,
+                                   glim_vmap** out);
 void glim_vmap_free(glim_vmap* vmap);
-/* Number of occupied voxels, hash capacity and longest probe sequence of a level. */
+/* Number of occupied voxels, table capacity (hash slots, or grid cells for a dense level)
+ * and longest probe sequence (1 for a dense level) of a level. */
 glim_status glim_vmap_info(const glim_vmap* vmap, int32_t level, int64_t* n_voxels,
                            int64_t* capacity, int32_t* max_probe);
+/* 1 if the level uses a dense index grid, 0 for a hash table, -1 for a bad argument. */
+int32_t glim_vmap_is_dense(const glim_vmap* vmap, int32_t level);
 /* Copy a level's voxels to device arrays in canonical order (lexicographic (x, y, z) key
  * order; the position is the canonical voxel id): keys3 (n_voxels x 3 int32), mean3
  * (n_voxels x 3), cov6 (n_voxels x 6), count (n_voxels int32).  Any output may be NULL. */

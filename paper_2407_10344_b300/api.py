@@ -126,10 +126,20 @@ def estimate_covariances(ctx: Context, pts4: torch.Tensor, k: int = 10, reg_mode
     return cov, nrm
 
 
+def spatial_order(ctx: Context, pts4: torch.Tensor, cell: float = 0.5) -> torch.Tensor:
+    """Permutation (int64 CUDA tensor) ordering the points along a Z-order curve of cells."""
+    _dev(pts4, torch.float32, 4, "pts4")
+    perm = torch.empty(pts4.shape[0], dtype=torch.int32, device=pts4.device)
+    ctx.call("spatial_order", ctx.lib.glim_spatial_order, ctx.h, _ptr(pts4), pts4.shape[0], float(cell), _ptr(perm))
+    return perm.long()
+
+
 class VoxelMap:
     """Multi-resolution voxelmap of one frame (library-owned device tables)."""
 
-    def __init__(self, ctx: Context, pts4: torch.Tensor, cov6: torch.Tensor, resolutions):
+    def __init__(self, ctx: Context, pts4: torch.Tensor, cov6: torch.Tensor, resolutions, layout: str = "auto"):
+        """layout: "auto" (dense index grid when its box is small enough, else hash table),
+        "dense" or "hash"."""
         _dev(pts4, torch.float32, 4, "pts4")
         _dev(cov6, torch.float32, 6, "cov6")
         if pts4.shape[0] != cov6.shape[0]:
@@ -138,8 +148,9 @@ class VoxelMap:
         self.resolutions = [float(r) for r in resolutions]
         res = np.ascontiguousarray(self.resolutions, dtype=np.float64)
         h = C.c_void_p()
-        ctx.call("build_voxelmap", ctx.lib.glim_build_voxelmap, ctx.h, _ptr(pts4), _ptr(cov6), pts4.shape[0], _ptr(res), len(res),
-                                              C.byref(h))
+        lay = {"auto": 0, "dense": 1, "hash": 2}[layout]
+        ctx.call("build_voxelmap", ctx.lib.glim_build_voxelmap_ex, ctx.h, _ptr(pts4), _ptr(cov6), pts4.shape[0],
+                 _ptr(res), len(res), lay, C.byref(h))
         self.h = h
 
     @property
@@ -150,6 +161,9 @@ class VoxelMap:
         n, cap, mp = C.c_int64(), C.c_int64(), C.c_int32()
         self.ctx.call("vmap_info", self.ctx.lib.glim_vmap_info, self.h, level, C.byref(n), C.byref(cap), C.byref(mp))
         return dict(n_voxels=n.value, capacity=cap.value, max_probe=mp.value)
+
+    def is_dense(self, level):
+        return bool(self.ctx.lib.glim_vmap_is_dense(self.h, level))
 
     def export(self, level):
         m = self.info(level)["n_voxels"]

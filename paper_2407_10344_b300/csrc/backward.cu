@@ -83,7 +83,8 @@ __global__ void __launch_bounds__(256) k_backward_items(const BwdArgs a) {
         const LevelDev& L = V.M.lv[l];
         int kx, ky, kz;
         if (!level_key3(q, L.inv_r, kx, ky, kz)) continue;
-        const int s = probe_slot3(L, kx, ky, kz);
+        int vid;
+        const int s = find_voxel(L, kx, ky, kz, &vid);
         if (s < 0) continue;
         const float4 v0 = L.slots[s].w0, v1 = L.slots[s].w1, v2 = L.slots[s].w2;
         const float sa = v1.w + S[0][0], sb = v2.x + S[0][1], sc = v2.y + S[0][2], sd = v2.z + S[1][1],

@@ -121,13 +121,21 @@ struct __align__(16) VoxSlot {
   float4 w0, w1, w2;
 };
 
+// One resolution level of a voxelmap as the kernels see it.  Either a dense grid over the
+// bounding box of the occupied keys whose cells hold the voxel records directly (empty cells
+// have every byte 0x80; an occupied cell has w0 = {canonical id, kx, ky, c22}), or, when
+// that box is too large, an open-addressing hash table whose slots carry key and statistics.
 struct LevelDev {
-  const VoxSlot* slots;
-  const int32_t* slot_id;  // canonical voxel id of each slot (-1 = empty)
-  uint32_t mask;           // capacity - 1
+  const VoxSlot* slots;    // hash: table slots; dense: nx * ny * nz cells, z fastest
+  const int32_t* slot_id;  // hash: canonical voxel id of each slot (-1 = empty)
+  const int32_t* grid;     // unused (kept for layout stability)
+  uint32_t mask;           // hash: capacity - 1
   int32_t log2cap;
-  int32_t max_probe;       // longest probe sequence of any stored key
+  int32_t max_probe;       // hash: longest probe sequence of any stored key
   float inv_r;
+  int32_t dense;
+  int32_t ox, oy, oz;      // dense: key of grid cell (0, 0, 0)
+  uint32_t nx, ny, nz;     // dense: grid dimensions
 };
 
 // host-side voxelmap
@@ -142,6 +150,10 @@ struct glim_vmap {
   int32_t max_probe[GLIM_MAX_LEVELS] = {0};
   VoxSlot* slots[GLIM_MAX_LEVELS] = {nullptr};
   int32_t* slot_id[GLIM_MAX_LEVELS] = {nullptr};
+  int32_t dense[GLIM_MAX_LEVELS] = {0};
+  int32_t* grid[GLIM_MAX_LEVELS] = {nullptr};
+  int32_t org[GLIM_MAX_LEVELS][3] = {};
+  uint32_t dim[GLIM_MAX_LEVELS][3] = {};
   unsigned long long* vkey[GLIM_MAX_LEVELS] = {nullptr};  // canonical order
   float* vmean[GLIM_MAX_LEVELS] = {nullptr};              // n_vox x 3
   float* vcov[GLIM_MAX_LEVELS] = {nullptr};               // n_vox x 6
@@ -154,6 +166,14 @@ struct glim_vmap {
     d.log2cap = log2cap[l];
     d.max_probe = max_probe[l];
     d.inv_r = inv_r[l];
+    d.dense = dense[l];
+    d.grid = grid[l];
+    d.ox = org[l][0];
+    d.oy = org[l][1];
+    d.oz = org[l][2];
+    d.nx = dim[l][0];
+    d.ny = dim[l][1];
+    d.nz = dim[l][2];
     return d;
   }
 };

@@ -3,5 +3,5 @@
 #include "lin_kernel.cuh"
 
 namespace glim_detail {
-LinKernel pick_lin_fp64(int block, int ppt, int lmax) { return pick_lin<GLIM_ACC_FP64>(block, ppt, lmax); }
+LinKernelInfo pick_lin_fp64(int block, int lmax) { return pick_lin<GLIM_ACC_FP64>(block, lmax); }
 }  // namespace glim_detail

@@ -3,5 +3,5 @@
 #include "lin_kernel.cuh"
 
 namespace glim_detail {
-LinKernel pick_lin_kahan(int block, int ppt, int lmax) { return pick_lin<GLIM_ACC_KAHAN>(block, ppt, lmax); }
+LinKernelInfo pick_lin_kahan(int block, int lmax) { return pick_lin<GLIM_ACC_KAHAN>(block, lmax); }
 }  // namespace glim_detail

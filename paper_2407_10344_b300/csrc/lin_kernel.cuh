@@ -67,119 +67,164 @@ __device__ __forceinline__ PointIn load_point(const FrameDev& F, int64_t k) {
   return p;
 }
 
+// Per-warp staging of one round (one point per lane): the lanes' point data and the compacted
+// list of (point, level) hits with their voxel statistics.  Records have an odd stride, so
+// lanes reading consecutive records hit distinct shared-memory banks.
+// Both records are three float4 (48 bytes): eight lanes of a quarter warp reading consecutive
+// records touch distinct banks.
+//   point: {q.x, q.y, q.z, u.x} {u.y, u.z, S'00, S'01} {S'02, S'11, S'12, S'22}, S' = R C R^T
+//   term:  {mean.x, mean.y, mean.z, C~00} {C~01, C~02, C~11, C~12} {C~22, w, source lane, 0}
+template <int LMAX>
+struct WarpStage {
+  float4 pt[32 * 3];
+  float4 term[32 * LMAX * 3];
+};
+
+// One round for the warp.  Phase 1 (every lane, its own point): transform, keys and the first
+// probe of every level in flight together, collision fallback, then the hits are compacted
+// into the warp's term list (level-major, lane order within a level).  Phase 2 (the lanes
+// share the term list): per hit S = C~ + R C R^T, Omega = adj(S)/det(S), d = mu~ - q,
+// y = Omega d, e = d^T y, and the point's G-form contribution w [G^T Omega G, G^T y, e] with
+// G = [-(u)x, I] is accumulated.  Misses and discarded points cost no phase-2 lanes.
 template <int LMAX, class A>
-__device__ __forceinline__ void point_term(const PairView& P, const PointIn& in, int64_t k, int validate, A& acc,
-                                           int& inl) {
+__device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in, bool live, int64_t k, int validate,
+                                           WarpStage<LMAX>& ws, A& acc, int& inl) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   const float4 m = in.m;
-  if (validate && P.F.nrm) {
+  if (live && validate && P.F.nrm) {
     const float* nk = P.F.nrm + 3 * k;
-    if (behind_surface(m.x, m.y, m.z, P.v, __ldg(nk), __ldg(nk + 1), __ldg(nk + 2))) return;
+    live = !behind_surface(m.x, m.y, m.z, P.v, __ldg(nk), __ldg(nk + 1), __ldg(nk + 2));
   }
   const float* R = P.R;
   const float3 q = transform_pinned(R, P.t, m.x, m.y, m.z);
 
-  // first probe of every level, all reads in flight together
   int kx[LMAX], ky[LMAX], kz[LMAX];
-  bool ok[LMAX];
-  uint32_t hh[LMAX];
+  bool hit[LMAX];
+  uint32_t hh[LMAX];  // hash level: first slot
   float4 s0[LMAX], s1[LMAX], s2[LMAX];
+  // one read of every level, all in flight together: a dense level reads its grid cell (the
+  // record itself), a hash level its first slot (key and statistics)
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
     const LevelDev& L = P.M.lv[l];
-    ok[l] = (l < P.M.levels) && level_key3(q, L.inv_r, kx[l], ky[l], kz[l]);
-    if (ok[l]) {
-      hh[l] = hash3(kx[l], ky[l], kz[l], L.log2cap);
-      const VoxSlot* sl = L.slots + hh[l];
-      s0[l] = ldg4(&sl->w0);
-      s1[l] = ldg4(&sl->w1);
-      s2[l] = ldg4(&sl->w2);
+    hit[l] = live && (l < P.M.levels) && level_key3(q, L.inv_r, kx[l], ky[l], kz[l]);
+    if (hit[l]) {
+      int64_t c;
+      if (L.dense) {
+        c = dense_cell(L, kx[l], ky[l], kz[l]);
+        hit[l] = c >= 0;
+      } else {
+        hh[l] = hash3(kx[l], ky[l], kz[l], L.log2cap);
+        c = hh[l];
+      }
+      if (hit[l]) {
+        const VoxSlot* sl = L.slots + c;
+        s0[l] = ldg4(&sl->w0);
+        s1[l] = ldg4(&sl->w1);
+        s2[l] = ldg4(&sl->w2);
+      }
     }
   }
-
-  // R C R^T while the probes are in flight (W = R C, then the 6 entries of W R^T)
-  const float c00 = in.ca.x, c01 = in.ca.y, c02 = in.cb.x, c11 = in.cb.y, c12 = in.cc.x, c22 = in.cc.y;
-  const float w00 = R[0] * c00 + R[1] * c01 + R[2] * c02;
-  const float w01 = R[0] * c01 + R[1] * c11 + R[2] * c12;
-  const float w02 = R[0] * c02 + R[1] * c12 + R[2] * c22;
-  const float w10 = R[3] * c00 + R[4] * c01 + R[5] * c02;
-  const float w11 = R[3] * c01 + R[4] * c11 + R[5] * c12;
-  const float w12 = R[3] * c02 + R[4] * c12 + R[5] * c22;
-  const float w20 = R[6] * c00 + R[7] * c01 + R[8] * c02;
-  const float w21 = R[6] * c01 + R[7] * c11 + R[8] * c12;
-  const float w22 = R[6] * c02 + R[7] * c12 + R[8] * c22;
-  const float r00 = w00 * R[0] + w01 * R[1] + w02 * R[2];
-  const float r01 = w00 * R[3] + w01 * R[4] + w02 * R[5];
-  const float r02 = w00 * R[6] + w01 * R[7] + w02 * R[8];
-  const float r11 = w10 * R[3] + w11 * R[4] + w12 * R[5];
-  const float r12 = w10 * R[6] + w11 * R[7] + w12 * R[8];
-  const float r22 = w20 * R[6] + w21 * R[7] + w22 * R[8];
-
-  float o00 = 0.f, o01 = 0.f, o02 = 0.f, o11 = 0.f, o12 = 0.f, o22 = 0.f;  // sum Omega
-  float g0 = 0.f, g1 = 0.f, g2 = 0.f;                                      // sum Omega d
-  float es = 0.f;
-  int hits = 0;
+  int nh = 0;
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
-    if (!ok[l]) continue;
-    float4 v0 = s0[l], v1 = s1[l], v2 = s2[l];
-    const int sx = __float_as_int(v0.x);
-    if (!(sx == kx[l] && __float_as_int(v0.y) == ky[l] && __float_as_int(v0.z) == kz[l])) {
-      if (sx == GLIM_EMPTY_COORD) continue;
-      // collision: continue the probe sequence (rare at load factor <= 1/2)
-      const LevelDev& L = P.M.lv[l];
-      const int s = probe_from(L, kx[l], ky[l], kz[l], (hh[l] + 1u) & L.mask, 1);
-      if (s < 0) continue;
-      v0 = ldg4(&L.slots[s].w0);
-      v1 = ldg4(&L.slots[s].w1);
-      v2 = ldg4(&L.slots[s].w2);
+    if (hit[l] && P.M.lv[l].dense) hit[l] = __float_as_int(s0[l].x) >= 0;  // occupied cell
+    if (hit[l] && !P.M.lv[l].dense) {
+      const int sx = __float_as_int(s0[l].x);
+      if (!(sx == kx[l] && __float_as_int(s0[l].y) == ky[l] && __float_as_int(s0[l].z) == kz[l])) {
+        hit[l] = false;
+        if (sx != GLIM_EMPTY_COORD) {  // collision: continue the probe sequence
+          const LevelDev& L = P.M.lv[l];
+          const int s = probe_from(L, kx[l], ky[l], kz[l], (hh[l] + 1u) & L.mask, 1);
+          if (s >= 0) {
+            hit[l] = true;
+            s0[l] = ldg4(&L.slots[s].w0);
+            s1[l] = ldg4(&L.slots[s].w1);
+            s2[l] = ldg4(&L.slots[s].w2);
+          }
+        }
+      }
     }
-    // S = C~ + R C R^T, Omega = adj(S) / det(S)
-    const float a = v1.w + r00, b = v2.x + r01, c = v2.y + r02, d = v2.z + r11, e = v2.w + r12, f = v0.w + r22;
+    nh += hit[l] ? 1 : 0;
+  }
+  if (nh > 0) {  // stage this lane's point: q, u, R C R^T, w
+    const float c00 = in.ca.x, c01 = in.ca.y, c02 = in.cb.x, c11 = in.cb.y, c12 = in.cc.x, c22 = in.cc.y;
+    const float w00 = R[0] * c00 + R[1] * c01 + R[2] * c02;
+    const float w01 = R[0] * c01 + R[1] * c11 + R[2] * c12;
+    const float w02 = R[0] * c02 + R[1] * c12 + R[2] * c22;
+    const float w10 = R[3] * c00 + R[4] * c01 + R[5] * c02;
+    const float w11 = R[3] * c01 + R[4] * c11 + R[5] * c12;
+    const float w12 = R[3] * c02 + R[4] * c12 + R[5] * c22;
+    const float w20 = R[6] * c00 + R[7] * c01 + R[8] * c02;
+    const float w21 = R[6] * c01 + R[7] * c11 + R[8] * c12;
+    const float w22 = R[6] * c02 + R[7] * c12 + R[8] * c22;
+    float4* pp = ws.pt + lane * 3;
+    pp[0] = make_float4(q.x, q.y, q.z, q.x - P.t[0]);
+    pp[1] = make_float4(q.y - P.t[1], q.z - P.t[2], w00 * R[0] + w01 * R[1] + w02 * R[2],
+                        w00 * R[3] + w01 * R[4] + w02 * R[5]);
+    pp[2] = make_float4(w00 * R[6] + w01 * R[7] + w02 * R[8], w10 * R[3] + w11 * R[4] + w12 * R[5],
+                        w10 * R[6] + w11 * R[7] + w12 * R[8], w20 * R[6] + w21 * R[7] + w22 * R[8]);
+    inl += nh;
+  }
+  // compaction of the hits: level-major, lane order within a level
+  int base = 0;
+#pragma unroll
+  for (int l = 0; l < LMAX; ++l) {
+    const unsigned mask = __ballot_sync(0xffffffffu, hit[l]);
+    if (hit[l]) {
+      float4* t = ws.term + (base + __popc(mask & lt)) * 3;
+      t[0] = s1[l];                                                     // voxel mean, C~00
+      t[1] = s2[l];                                                     // C~ 01 02 11 12
+      t[2] = make_float4(s0[l].w, m.w, __int_as_float(lane), 0.f);     // C~22, w, lane
+    }
+    base += __popc(mask);
+  }
+  __syncwarp();
+  for (int i = lane; i < base; i += 32) {
+    const float4 t0 = ws.term[3 * i], t1 = ws.term[3 * i + 1], t2 = ws.term[3 * i + 2];
+    const float4* pp = ws.pt + 3 * __float_as_int(t2.z);
+    const float4 p0 = pp[0], p1 = pp[1], p2 = pp[2];
+    // S = C~ + R C R^T
+    const float a = t0.w + p1.z, b = t1.x + p1.w, c = t1.y + p2.x;
+    const float d = t1.z + p2.y, e = t1.w + p2.z, f = t2.x + p2.w;
     const float A00 = d * f - e * e, A01 = c * e - b * f, A02 = b * e - c * d;
     const float A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
     const float det = a * A00 + b * A01 + c * A02;
     if (!(det > 0.f) || !(det < INFINITY)) continue;  // S not positive definite: skip the term
-    const float id = __fdividef(1.0f, det);
-    const float O00 = A00 * id, O01 = A01 * id, O02 = A02 * id, O11 = A11 * id, O12 = A12 * id, O22 = A22 * id;
-    const float dx = v1.x - q.x, dy = v1.y - q.y, dz = v1.z - q.z;
-    const float y0 = O00 * dx + O01 * dy + O02 * dz;
-    const float y1 = O01 * dx + O11 * dy + O12 * dz;
-    const float y2 = O02 * dx + O12 * dy + O22 * dz;
-    es += dx * y0 + dy * y1 + dz * y2;
-    o00 += O00; o01 += O01; o02 += O02; o11 += O11; o12 += O12; o22 += O22;
-    g0 += y0; g1 += y1; g2 += y2;
-    ++hits;
+    const float id = __fdividef(t2.y, det);          // w / det
+    const float o00 = A00 * id, o01 = A01 * id, o02 = A02 * id, o11 = A11 * id, o12 = A12 * id, o22 = A22 * id;
+    const float dx = t0.x - p0.x, dy = t0.y - p0.y, dz = t0.z - p0.z;
+    const float g0 = o00 * dx + o01 * dy + o02 * dz;  // w Omega d
+    const float g1 = o01 * dx + o11 * dy + o12 * dz;
+    const float g2 = o02 * dx + o12 * dy + o22 * dz;
+    const float es = dx * g0 + dy * g1 + dz * g2;     // w d^T Omega d
+    const float ux = p0.w, uy = p1.x, uz = p1.y;
+    // W = (u)x (w Omega)
+    const float W00 = -uz * o01 + uy * o02, W01 = -uz * o11 + uy * o12, W02 = -uz * o12 + uy * o22;
+    const float W10 = uz * o00 - ux * o02, W11 = uz * o01 - ux * o12, W12 = uz * o02 - ux * o22;
+    const float W20 = -uy * o00 + ux * o01, W21 = -uy * o01 + ux * o11, W22 = -uy * o02 + ux * o12;
+    // M_rr = -(u)x Omega (u)x = W (u)x^T  (symmetric)
+    acc.add(0, -uz * W01 + uy * W02);
+    acc.add(1, uz * W00 - ux * W02);
+    acc.add(2, -uy * W00 + ux * W01);
+    acc.add(3, uz * W10 - ux * W12);
+    acc.add(4, -uy * W10 + ux * W11);
+    acc.add(5, -uy * W20 + ux * W21);
+    // M_rt = (u)x Omega
+    acc.add(6, W00); acc.add(7, W01); acc.add(8, W02);
+    acc.add(9, W10); acc.add(10, W11); acc.add(11, W12);
+    acc.add(12, W20); acc.add(13, W21); acc.add(14, W22);
+    // M_tt = Omega
+    acc.add(15, o00); acc.add(16, o01); acc.add(17, o02); acc.add(18, o11); acc.add(19, o12); acc.add(20, o22);
+    // g = [u x (w Omega d); w Omega d]
+    acc.add(21, uy * g2 - uz * g1);
+    acc.add(22, uz * g0 - ux * g2);
+    acc.add(23, ux * g1 - uy * g0);
+    acc.add(24, g0); acc.add(25, g1); acc.add(26, g2);
+    acc.add(27, es);
   }
-  if (hits == 0) return;
-  inl += hits;
-  const float wk = m.w;
-  o00 *= wk; o01 *= wk; o02 *= wk; o11 *= wk; o12 *= wk; o22 *= wk;
-  g0 *= wk; g1 *= wk; g2 *= wk;
-  es *= wk;
-  const float3 u = make_float3(q.x - P.t[0], q.y - P.t[1], q.z - P.t[2]);
-  // W = (u)x Omega_sum
-  const float W00 = -u.z * o01 + u.y * o02, W01 = -u.z * o11 + u.y * o12, W02 = -u.z * o12 + u.y * o22;
-  const float W10 = u.z * o00 - u.x * o02, W11 = u.z * o01 - u.x * o12, W12 = u.z * o02 - u.x * o22;
-  const float W20 = -u.y * o00 + u.x * o01, W21 = -u.y * o01 + u.x * o11, W22 = -u.y * o02 + u.x * o12;
-  // M_rr = -(u)x Omega (u)x = W (u)x^T  (symmetric)
-  acc.add(0, -u.z * W01 + u.y * W02);
-  acc.add(1, u.z * W00 - u.x * W02);
-  acc.add(2, -u.y * W00 + u.x * W01);
-  acc.add(3, u.z * W10 - u.x * W12);
-  acc.add(4, -u.y * W10 + u.x * W11);
-  acc.add(5, -u.y * W20 + u.x * W21);
-  // M_rt = (u)x Omega
-  acc.add(6, W00); acc.add(7, W01); acc.add(8, W02);
-  acc.add(9, W10); acc.add(10, W11); acc.add(11, W12);
-  acc.add(12, W20); acc.add(13, W21); acc.add(14, W22);
-  // M_tt = Omega
-  acc.add(15, o00); acc.add(16, o01); acc.add(17, o02); acc.add(18, o11); acc.add(19, o12); acc.add(20, o22);
-  // g = [u x g_sum; g_sum]
-  acc.add(21, u.y * g2 - u.z * g1);
-  acc.add(22, u.z * g0 - u.x * g2);
-  acc.add(23, u.x * g1 - u.y * g0);
-  acc.add(24, g0); acc.add(25, g1); acc.add(26, g2);
-  acc.add(27, es);
+  __syncwarp();  // the stage is rewritten by the next round
 }
 
 // ---------------------------------------------------------------- block reduction
@@ -270,8 +315,8 @@ __device__ __forceinline__ void block_reduce_store(const typename AccOf<ACC>::ty
 }
 
 // ---------------------------------------------------------------- items and the kernel
-template <int BLOCK, int PPT, int ACC, int LMAX>
-__device__ __forceinline__ void process_item(const LinArgs& a, int item, PairView& V) {
+template <int BLOCK, int ACC, int LMAX>
+__device__ __forceinline__ void process_item(const LinArgs& a, int item, PairView& V, WarpStage<LMAX>& ws) {
   const Item it = a.items[item];
   if (threadIdx.x == 0) {
     const PairDev pd = a.pairs[it.pair];
@@ -293,16 +338,18 @@ __device__ __forceinline__ void process_item(const LinArgs& a, int item, PairVie
   const int64_t n = V.F.n;
   const int64_t base = int64_t(it.start) + threadIdx.x;
   const int64_t end = min(int64_t(it.start) + a.tile, n);
-  // software pipeline: the next point's data is read while the current one is processed
+  // software pipeline: the next round's point is read while the current round is processed
   PointIn cur;
   if (base < end) cur = load_point(V.F, base);
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) {
+  const int rounds = a.ppt;
+#pragma unroll 1
+  for (int j = 0; j < rounds; ++j) {
     const int64_t k = base + int64_t(j) * BLOCK;
     PointIn nxt;
-    if (j + 1 < PPT && k + BLOCK < end) nxt = load_point(V.F, k + BLOCK);
-    if (k < end) point_term<LMAX>(V, cur, k, a.validate, acc, inl);
-    if (j + 1 < PPT) cur = nxt;
+    const bool more = (j + 1 < rounds) && (k + BLOCK < end);
+    if (more) nxt = load_point(V.F, k + BLOCK);
+    warp_round<LMAX>(V, cur, k < end, k, a.validate, ws, acc, inl);
+    if (more) cur = nxt;
   }
   // the reduction ends with a barrier, so V is free for the next item afterwards
   block_reduce_store<BLOCK, ACC>(acc, inl, a.part + int64_t(item) * PSTRIDE);
@@ -310,13 +357,20 @@ __device__ __forceinline__ void process_item(const LinArgs& a, int item, PairVie
 
 // With a.head set: persistent blocks take items from the atomic queue until it is exhausted.
 // With a.head null: one block per item, item = a.item_base + blockIdx.x.
-template <int BLOCK, int PPT, int ACC, int LMAX>
+template <int BLOCK, int LMAX>
+constexpr size_t lin_dyn_smem() {
+  return size_t(BLOCK / 32) * sizeof(WarpStage<LMAX>);
+}
+
+template <int BLOCK, int ACC, int LMAX>
 __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize(const LinArgs a) {
   __shared__ PairView V;
   __shared__ int s_item[2];
+  extern __shared__ float4 dyn_smem[];
+  WarpStage<LMAX>& ws = reinterpret_cast<WarpStage<LMAX>*>(dyn_smem)[threadIdx.x >> 5];
   if (a.head == nullptr) {
     const int item = a.item_base + blockIdx.x;
-    if (item < a.nitems) process_item<BLOCK, PPT, ACC, LMAX>(a, item, V);
+    if (item < a.nitems) process_item<BLOCK, ACC, LMAX>(a, item, V, ws);
     return;
   }
   // the next item index is fetched one item ahead, so the queue's atomic latency overlaps work
@@ -326,40 +380,41 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize(const LinArgs 
   for (int b = 1;; b ^= 1) {
     if (cur >= a.nitems) break;
     if (threadIdx.x == 0) s_item[b] = atomicAdd(a.head, 1);
-    process_item<BLOCK, PPT, ACC, LMAX>(a, cur, V);  // ends with a barrier
+    process_item<BLOCK, ACC, LMAX>(a, cur, V, ws);  // ends with a barrier
     cur = s_item[b];
   }
 }
 
+// Kernel and its dynamic shared memory (bytes) for a configuration; the attribute allowing
+// that much dynamic shared memory is set on first use.
+template <int B, int ACC, int L>
+LinKernelInfo lin_info() {
+  LinKernelInfo k;
+  k.fn = k_linearize<B, ACC, L>;
+  k.smem = lin_dyn_smem<B, L>();
+  return k;
+}
+
 template <int ACC>
-LinKernel pick_lin(int block, int ppt, int lmax) {
-#define GLIM_PICK_L(B, P)                                 \
-  switch (lmax) {                                         \
-    case 1: return k_linearize<B, P, ACC, 1>;             \
-    case 2: return k_linearize<B, P, ACC, 2>;             \
-    case 3: return k_linearize<B, P, ACC, 3>;             \
-    case 4: return k_linearize<B, P, ACC, 4>;             \
-  }                                                       \
-  return nullptr;
-#define GLIM_PICK_P(B)                 \
-  switch (ppt) {                       \
-    case 1: { GLIM_PICK_L(B, 1) }      \
-    case 2: { GLIM_PICK_L(B, 2) }      \
-    case 4: { GLIM_PICK_L(B, 4) }      \
-    case 8: { GLIM_PICK_L(B, 8) }      \
-  }                                    \
-  return nullptr;
+LinKernelInfo pick_lin(int block, int lmax) {
+#define GLIM_PICK_L(B)                            \
+  switch (lmax) {                                 \
+    case 1: return lin_info<B, ACC, 1>();         \
+    case 2: return lin_info<B, ACC, 2>();         \
+    case 3: return lin_info<B, ACC, 3>();         \
+    case 4: return lin_info<B, ACC, 4>();         \
+  }                                               \
+  return LinKernelInfo{};
   switch (block) {
-    case 128: { GLIM_PICK_P(128) }
-    case 256: { GLIM_PICK_P(256) }
+    case 128: { GLIM_PICK_L(128) }
+    case 256: { GLIM_PICK_L(256) }
   }
-  return nullptr;
-#undef GLIM_PICK_P
+  return LinKernelInfo{};
 #undef GLIM_PICK_L
 }
 
-LinKernel pick_lin_fp32(int block, int ppt, int lmax);
-LinKernel pick_lin_kahan(int block, int ppt, int lmax);
-LinKernel pick_lin_fp64(int block, int ppt, int lmax);
+LinKernelInfo pick_lin_fp32(int block, int lmax);
+LinKernelInfo pick_lin_kahan(int block, int lmax);
+LinKernelInfo pick_lin_fp64(int block, int lmax);
 
 }  // namespace glim_detail

@@ -122,24 +122,24 @@ __global__ void __launch_bounds__(128) k_reduce_expand(const ReduceArgs a) {
 }
 
 // ---------------------------------------------------------------- kernel table
-LinKernel pick_kernel(int block, int acc, int ppt, int lmax) {
+LinKernelInfo pick_kernel(int block, int acc, int lmax) {
   switch (acc) {
-    case GLIM_ACC_FP32: return pick_lin_fp32(block, ppt, lmax);
-    case GLIM_ACC_KAHAN: return pick_lin_kahan(block, ppt, lmax);
-    case GLIM_ACC_FP64: return pick_lin_fp64(block, ppt, lmax);
+    case GLIM_ACC_FP32: return pick_lin_fp32(block, lmax);
+    case GLIM_ACC_KAHAN: return pick_lin_kahan(block, lmax);
+    case GLIM_ACC_FP64: return pick_lin_fp64(block, lmax);
   }
-  return nullptr;
+  return LinKernelInfo{};
 }
 
 void fill_defaults(glim_lin_opts& o) {
   if (o.block == 0) o.block = 256;
-  if (o.pts_per_thread == 0) o.pts_per_thread = 4;
+  if (o.pts_per_thread == 0) o.pts_per_thread = 16;
   if (o.persistent == 0) o.persistent = 1;
 }
 
 bool opts_valid(const glim_lin_opts& o) {
   return (o.block == 128 || o.block == 256) &&
-         (o.pts_per_thread == 1 || o.pts_per_thread == 2 || o.pts_per_thread == 4 || o.pts_per_thread == 8) &&
+         (o.pts_per_thread >= 1 && o.pts_per_thread <= 256) &&
          (o.accum_mode >= 0 && o.accum_mode <= 2) && (o.persistent == 1 || o.persistent == 2) &&
          o.blocks_per_sm >= 0 && o.blocks_per_sm <= 32;
 }
@@ -192,12 +192,16 @@ glim_status plan_configure(glim_plan* p, const glim_lin_opts& o) {
   if (!items.empty())
     GLIM_CUDA(ctx, cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice));
   GLIM_CUDA(ctx, cudaMemcpy(p->d_item_begin, begin.data(), begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  p->kernel = pick_kernel(o.block, o.accum_mode, o.pts_per_thread, p->lmax);
+  const LinKernelInfo ki = pick_kernel(o.block, o.accum_mode, p->lmax);
+  p->kernel = ki.fn;
+  p->kernel_smem = ki.smem;
   if (!p->kernel) return set_error(ctx, GLIM_EINVAL, "no kernel for block=%d ppt=%d acc=%d", o.block, o.pts_per_thread, o.accum_mode);
+  GLIM_CUDA(ctx, cudaFuncSetAttribute(reinterpret_cast<const void*>(p->kernel),
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(p->kernel_smem)));
   if (o.persistent == 1) {
     int per_sm = o.blocks_per_sm;
     if (per_sm == 0) {
-      GLIM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kernel, o.block, 0));
+      GLIM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kernel, o.block, p->kernel_smem));
       per_sm = std::max(per_sm, 1);
     }
     p->grid = std::max(1, std::min(per_sm * ctx->num_sms, p->nitems));
@@ -225,10 +229,11 @@ glim_status plan_enqueue_kernels(glim_plan* p, int slot = -1) {
     a.head = p->opts.persistent == 1 ? p->d_head : nullptr;
     a.part = p->d_part;
     a.tile = p->tile;
+    a.ppt = p->opts.pts_per_thread;
     a.validate = p->opts.validate_surface;
     if (p->opts.persistent == 1) GLIM_CUDA(ctx, cudaMemsetAsync(p->d_head, 0, sizeof(int), ctx->stream));
     if (slot >= 0) GLIM_CUDA(ctx, cudaEventRecord(p->ev[2 * slot], ctx->stream));
-    p->kernel<<<p->grid, p->opts.block, 0, ctx->stream>>>(a);
+    p->kernel<<<p->grid, p->opts.block, p->kernel_smem, ctx->stream>>>(a);
     GLIM_LAUNCHED(ctx);
     if (slot >= 0) GLIM_CUDA(ctx, cudaEventRecord(p->ev[2 * slot + 1], ctx->stream));
   }
@@ -523,7 +528,7 @@ extern "C" glim_status glim_plan_autotune(glim_plan* p, const double* poses12, i
   GLIM_CUDA(ctx, cudaEventCreate(&e0));
   GLIM_CUDA(ctx, cudaEventCreate(&e1));
   const int blocks[] = {128, 256};
-  const int ppts[] = {1, 2, 4, 8};
+  const int ppts[] = {8, 16, 32, 64};
   for (int bl : blocks)
     for (int pp : ppts) {
       glim_lin_opts o = base;
@@ -606,10 +611,11 @@ extern "C" glim_status glim_linearize_factors_plain(glim_ctx* ctx, const glim_fr
     a.head = nullptr;  // one block per item of this factor
     a.part = p->d_part;
     a.tile = p->tile;
+    a.ppt = o.pts_per_thread;
     a.validate = o.validate_surface;
     const int nb = begin[q + 1] - begin[q];
     if (nb > 0) {
-      p->kernel<<<nb, o.block, 0, ctx->stream>>>(a);
+      p->kernel<<<nb, o.block, p->kernel_smem, ctx->stream>>>(a);
       ctx->launches++;
       const cudaError_t le = cudaGetLastError();
       if (le != cudaSuccess) { st = cuda_check(ctx, le, "plain: linearize launch"); break; }

@@ -58,3 +58,24 @@ __device__ __forceinline__ int probe_from(const LevelDev& L, int kx, int ky, int
 __device__ __forceinline__ int probe_slot3(const LevelDev& L, int kx, int ky, int kz) {
   return probe_from(L, kx, ky, kz, hash3(kx, ky, kz, L.log2cap), 0);
 }
+
+// Dense grid cell of key (kx, ky, kz), or -1 outside the grid.
+__device__ __forceinline__ int64_t dense_cell(const LevelDev& L, int kx, int ky, int kz) {
+  const uint32_t x = uint32_t(kx - L.ox), y = uint32_t(ky - L.oy), z = uint32_t(kz - L.oz);
+  if (x >= L.nx || y >= L.ny || z >= L.nz) return -1;
+  return (int64_t(x) * L.ny + y) * L.nz + z;
+}
+
+// Voxel of key (kx, ky, kz) at a level: the index of its record in L.slots (dense: grid cell;
+// hash: slot) or -1, and the canonical id through *id.
+__device__ __forceinline__ int find_voxel(const LevelDev& L, int kx, int ky, int kz, int* id) {
+  if (L.dense) {
+    const int64_t c = dense_cell(L, kx, ky, kz);
+    const int v = c < 0 ? -1 : __float_as_int(ldg4(&L.slots[c].w0).x);
+    *id = v < 0 ? -1 : v;
+    return v < 0 ? -1 : int(c);
+  }
+  const int s = probe_slot3(L, kx, ky, kz);
+  *id = s < 0 ? -1 : L.slot_id[s];
+  return s;
+}

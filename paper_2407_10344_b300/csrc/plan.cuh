@@ -43,7 +43,8 @@ struct LinArgs {
   const PoseF* pose;   // per pair
   int* head;           // work-queue head (persistent)
   double* part;        // nitems x PSTRIDE
-  int32_t tile;
+  int32_t tile;      // points per item = blockDim.x * ppt
+  int32_t ppt;       // rounds per item (points per thread)
   int32_t validate;
 };
 
@@ -54,6 +55,10 @@ struct PairView {
 };
 
 using LinKernel = void (*)(const LinArgs);
+struct LinKernelInfo {
+  LinKernel fn = nullptr;
+  size_t smem = 0;  // dynamic shared memory per block
+};
 
 }  // namespace glim_detail
 
@@ -80,6 +85,7 @@ struct glim_plan {
   int* d_head = nullptr;
   int grid = 0;
   LinKernel kernel = nullptr;
+  size_t kernel_smem = 0;
   // serialized input block: PoseF[npairs] then double[npairs * 12]
   size_t in_bytes = 0;
   void* d_in = nullptr;

@@ -192,7 +192,63 @@ __global__ void k_cell_end(const unsigned long long* __restrict__ ks, int64_t n,
   if (i == n - 1 && ks[i] != GLIM_EMPTY_KEY) cell_start[m] = uint32_t(n);
 }
 
+// spread the low 21 bits of v so that bit i moves to bit 3 i (Morton interleave)
+__device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
+  v &= 0x1FFFFFull;
+  v = (v | (v << 32)) & 0x1F00000000FFFFull;
+  v = (v | (v << 16)) & 0x1F0000FF0000FFull;
+  v = (v | (v << 8)) & 0x100F00F00F00F00Full;
+  v = (v | (v << 4)) & 0x10C30C30C30C30C3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+__global__ void k_morton_keys(const float4* __restrict__ pts, int64_t n, float inv_cell,
+                              unsigned long long* __restrict__ keys, uint32_t* __restrict__ idx,
+                              unsigned int* __restrict__ status) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 p = pts[i];
+  idx[i] = uint32_t(i);
+  int kx, ky, kz;
+  if (!voxel_coord(p.x, inv_cell, kx) || !voxel_coord(p.y, inv_cell, ky) || !voxel_coord(p.z, inv_cell, kz)) {
+    atomicOr(status, isfinite(p.x) && isfinite(p.y) && isfinite(p.z) ? GLIM_DS_RANGE : GLIM_DS_NONFINITE);
+    keys[i] = 0;
+    return;
+  }
+  keys[i] = (spread3(unsigned(kx + GLIM_KEY_BIAS)) << 2) | (spread3(unsigned(ky + GLIM_KEY_BIAS)) << 1) |
+            spread3(unsigned(kz + GLIM_KEY_BIAS));
+}
+
 }  // namespace
+
+extern "C" glim_status glim_spatial_order(glim_ctx* ctx, const float* pts4, int64_t n, float cell,
+                                          int32_t* perm_out) {
+  if (!ctx) return GLIM_EINVAL;
+  if (n < 0 || n > 0x7FFFFFFFll || !(cell > 0.f) || (n > 0 && (!pts4 || !perm_out)))
+    return set_error(ctx, GLIM_EINVAL, "spatial_order: bad arguments");
+  if (reinterpret_cast<uintptr_t>(pts4) & 15) return set_error(ctx, GLIM_EINVAL, "spatial_order: pts4 misaligned");
+  if (n == 0) return GLIM_OK;
+  GLIM_CUDA(ctx, cudaSetDevice(ctx->device));
+  DevBuf<unsigned long long> keys, ks;
+  DevBuf<uint32_t> idx;
+  GLIM_CUDA(ctx, keys.alloc(n, ctx->stream));
+  GLIM_CUDA(ctx, ks.alloc(n, ctx->stream));
+  GLIM_CUDA(ctx, idx.alloc(n, ctx->stream));
+  k_morton_keys<<<ceil_div_i(n, 256), 256, 0, ctx->stream>>>(reinterpret_cast<const float4*>(pts4), n,
+                                                            float(1.0 / double(cell)), keys.p, idx.p, ctx->d_status);
+  GLIM_LAUNCHED(ctx);
+  glim_status st = take_device_status(ctx, "spatial_order");
+  if (st != GLIM_OK) return st;
+  unsigned long long varying = 0;
+  st = key_varying_bits(ctx, keys.p, n, &varying);
+  if (st != GLIM_OK) return st;
+  st = radix_sort_pairs(ctx, keys.p, idx.p, ks.p, reinterpret_cast<uint32_t*>(perm_out), n, varying);
+  if (st != GLIM_OK) return st;
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->err.clear();
+  return GLIM_OK;
+}
 
 glim_status scan_exclusive_u32(glim_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n) {
   if (n <= 0) return GLIM_OK;

@@ -8,6 +8,8 @@
 //      and stores the averages (canonical id = rank of the key = position in sorted order);
 //   3. the voxels are inserted into an open-addressing table (linear probing, load <= 1/2)
 //      whose 48-byte slots carry the key and the statistics together.
+#include <climits>
+
 #include "lookup.cuh"
 
 namespace {
@@ -82,6 +84,37 @@ __global__ void k_hash_insert(const unsigned long long* __restrict__ vkey, const
   atomicOr(status, GLIM_DS_HASHFULL);
 }
 
+__global__ void k_key_bbox(const unsigned long long* __restrict__ vkey, int64_t m, int* __restrict__ bb) {
+  int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
+  for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < m; v += int64_t(gridDim.x) * blockDim.x) {
+    const unsigned long long k = vkey[v];
+    const int c[3] = {unpack_x(k), unpack_y(k), unpack_z(k)};
+    for (int a = 0; a < 3; ++a) {
+      mn[a] = min(mn[a], c[a]);
+      mx[a] = max(mx[a], c[a]);
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    atomicMin(&bb[a], mn[a]);
+    atomicMax(&bb[3 + a], mx[a]);
+  }
+}
+
+// dense layout: the voxel record stored in its grid cell, w0 = {canonical id, kx, ky, c22}
+__global__ void k_dense_build(const unsigned long long* __restrict__ vkey, const float* __restrict__ vmean,
+                              const float* __restrict__ vcov, int64_t m, VoxSlot* __restrict__ cells,
+                              int ox, int oy, int oz, uint32_t ny, uint32_t nz) {
+  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v >= m) return;
+  const unsigned long long key = vkey[v];
+  const int kx = unpack_x(key), ky = unpack_y(key), kz = unpack_z(key);
+  VoxSlot r;
+  r.w0 = make_float4(__int_as_float(int(v)), __int_as_float(kx), __int_as_float(ky), vcov[6 * v + 5]);
+  r.w1 = make_float4(vmean[3 * v], vmean[3 * v + 1], vmean[3 * v + 2], vcov[6 * v + 0]);
+  r.w2 = make_float4(vcov[6 * v + 1], vcov[6 * v + 2], vcov[6 * v + 3], vcov[6 * v + 4]);
+  cells[(int64_t(kx - ox) * ny + (ky - oy)) * nz + (kz - oz)] = r;
+}
+
 __global__ void k_export(const unsigned long long* __restrict__ vkey, const float* __restrict__ vmean,
                          const float* __restrict__ vcov, const int32_t* __restrict__ vcount, int64_t m,
                          int32_t* keys3, float* mean3, float* cov6, int32_t* count) {
@@ -121,10 +154,7 @@ __global__ void k_correspondences(const CorrArgs a, int32_t* __restrict__ ids) {
   for (int l = 0; l < a.levels; ++l) {
     int32_t id = -1;
     int kx, ky, kz;
-    if (visible && level_key3(q, a.lv[l].inv_r, kx, ky, kz)) {
-      int s = probe_slot3(a.lv[l], kx, ky, kz);
-      if (s >= 0) id = a.lv[l].slot_id[s];
-    }
+    if (visible && level_key3(q, a.lv[l].inv_r, kx, ky, kz)) find_voxel(a.lv[l], kx, ky, kz, &id);
     ids[k * a.levels + l] = id;
   }
 }
@@ -142,8 +172,8 @@ __global__ void k_overlap(const OverlapPair* __restrict__ pairs, double* __restr
   for (int64_t k = threadIdx.x; k < P.n; k += blockDim.x) {
     const float4 m = ldg4(&P.pts[k]);
     const float3 q = transform_pinned(P.pose.R, P.pose.t, m.x, m.y, m.z);
-    int kx, ky, kz;
-    if (level_key3(q, P.lv.inv_r, kx, ky, kz) && probe_slot3(P.lv, kx, ky, kz) >= 0) ++hits;
+    int kx, ky, kz, id;
+    if (level_key3(q, P.lv.inv_r, kx, ky, kz) && find_voxel(P.lv, kx, ky, kz, &id) >= 0) ++hits;
   }
   __shared__ unsigned long long s[8];
   unsigned long long h = __reduce_add_sync(0xffffffffu, unsigned(hits));
@@ -164,6 +194,7 @@ int log2_ceil(int64_t x) {
 
 void free_levels(glim_vmap* vm) {
   for (int l = 0; l < GLIM_MAX_LEVELS; ++l) {
+    cudaFree(vm->grid[l]);
     cudaFree(vm->slots[l]);
     cudaFree(vm->slot_id[l]);
     cudaFree(vm->vkey[l]);
@@ -173,7 +204,14 @@ void free_levels(glim_vmap* vm) {
   }
 }
 
-glim_status build_level(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n, glim_vmap* vm, int l) {
+// Dense grids (48 bytes per cell) are used when the key bounding box has at most this many
+// cells per occupied voxel plus a fixed allowance, and at most DENSE_MAX_BYTES per level.
+constexpr int64_t DENSE_CELLS_PER_VOXEL = 256;
+constexpr int64_t DENSE_CELLS_ALLOWANCE = int64_t(1) << 22;
+constexpr int64_t DENSE_MAX_BYTES = int64_t(32) << 30;
+
+glim_status build_level(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n, glim_vmap* vm, int l,
+                        int layout) {
   SortedCells cells;
   glim_status st = sort_into_cells(ctx, pts4, n, vm->inv_r[l], cells, true);
   if (st != GLIM_OK) return st;
@@ -181,25 +219,65 @@ glim_status build_level(glim_ctx* ctx, const float* pts4, const float* cov6, int
   if (st != GLIM_OK) return st;
   const int64_t m = cells.m;
   vm->n_vox[l] = m;
+  GLIM_CUDA(ctx, cudaMalloc(&vm->vkey[l], std::max<int64_t>(m, 1) * sizeof(unsigned long long)));
+  GLIM_CUDA(ctx, cudaMalloc(&vm->vmean[l], std::max<int64_t>(m, 1) * 3 * sizeof(float)));
+  GLIM_CUDA(ctx, cudaMalloc(&vm->vcov[l], std::max<int64_t>(m, 1) * 6 * sizeof(float)));
+  GLIM_CUDA(ctx, cudaMalloc(&vm->vcount[l], std::max<int64_t>(m, 1) * sizeof(int32_t)));
+  if (m > 0) {
+    k_voxel_stats<<<ceil_div_i(m, 128), 128, 0, ctx->stream>>>(
+        reinterpret_cast<const float4*>(pts4), cov6, cells.idx_sorted.p, cells.cell_start.p, cells.cell_key.p, m,
+        vm->vkey[l], vm->vmean[l], vm->vcov[l], vm->vcount[l], ctx->d_status);
+    GLIM_LAUNCHED(ctx);
+  }
+  // dense grid over the key bounding box when it is small enough (or requested)
+  int bb[6] = {0, 0, 0, -1, -1, -1};
+  if (m > 0) {
+    DevBuf<int> dbb;
+    GLIM_CUDA(ctx, dbb.alloc(6, ctx->stream));
+    const int init[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
+    GLIM_CUDA(ctx, cudaMemcpyAsync(dbb.p, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+    k_key_bbox<<<std::min(ceil_div_i(m, 256), 4 * ctx->num_sms), 256, 0, ctx->stream>>>(vm->vkey[l], m, dbb.p);
+    GLIM_LAUNCHED(ctx);
+    GLIM_CUDA(ctx, cudaMemcpyAsync(bb, dbb.p, sizeof(bb), cudaMemcpyDeviceToHost, ctx->stream));
+    GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  const int64_t nx = int64_t(bb[3]) - bb[0] + 1, ny = int64_t(bb[4]) - bb[1] + 1, nz = int64_t(bb[5]) - bb[2] + 1;
+  const int64_t ncell = m > 0 ? nx * ny * nz : 0;
+  const bool fits = ncell < (int64_t(1) << 31) && ncell <= DENSE_CELLS_PER_VOXEL * m + DENSE_CELLS_ALLOWANCE &&
+                    ncell * int64_t(sizeof(VoxSlot)) <= DENSE_MAX_BYTES;
+  if (layout == 1 && !fits)
+    return set_error(ctx, GLIM_EINVAL, "build_voxelmap: dense layout requested but the grid has %lld cells",
+                     (long long)ncell);
+  if (m > 0 && (layout == 1 || (layout == 0 && fits))) {
+    vm->dense[l] = 1;
+    vm->org[l][0] = bb[0];
+    vm->org[l][1] = bb[1];
+    vm->org[l][2] = bb[2];
+    vm->dim[l][0] = uint32_t(nx);
+    vm->dim[l][1] = uint32_t(ny);
+    vm->dim[l][2] = uint32_t(nz);
+    vm->cap[l] = ncell;
+    vm->log2cap[l] = 0;
+    vm->max_probe[l] = 1;
+    GLIM_CUDA(ctx, cudaMalloc(&vm->slots[l], ncell * sizeof(VoxSlot)));
+    GLIM_CUDA(ctx, cudaMemsetAsync(vm->slots[l], 0x80, ncell * sizeof(VoxSlot), ctx->stream));
+    k_dense_build<<<ceil_div_i(m, 256), 256, 0, ctx->stream>>>(vm->vkey[l], vm->vmean[l], vm->vcov[l], m,
+                                                               vm->slots[l], bb[0], bb[1], bb[2], uint32_t(ny),
+                                                               uint32_t(nz));
+    GLIM_LAUNCHED(ctx);
+    return take_device_status(ctx, "voxel statistics / dense grid");
+  }
   const int64_t cap = std::max<int64_t>(16, int64_t(1) << log2_ceil(2 * m));
   vm->cap[l] = cap;
   vm->log2cap[l] = log2_ceil(cap);
   GLIM_CUDA(ctx, cudaMalloc(&vm->slots[l], cap * sizeof(VoxSlot)));
   GLIM_CUDA(ctx, cudaMalloc(&vm->slot_id[l], cap * sizeof(int32_t)));
-  GLIM_CUDA(ctx, cudaMalloc(&vm->vkey[l], std::max<int64_t>(m, 1) * sizeof(unsigned long long)));
-  GLIM_CUDA(ctx, cudaMalloc(&vm->vmean[l], std::max<int64_t>(m, 1) * 3 * sizeof(float)));
-  GLIM_CUDA(ctx, cudaMalloc(&vm->vcov[l], std::max<int64_t>(m, 1) * 6 * sizeof(float)));
-  GLIM_CUDA(ctx, cudaMalloc(&vm->vcount[l], std::max<int64_t>(m, 1) * sizeof(int32_t)));
   GLIM_CUDA(ctx, cudaMemsetAsync(vm->slots[l], 0x80, cap * sizeof(VoxSlot), ctx->stream));
   GLIM_CUDA(ctx, cudaMemsetAsync(vm->slot_id[l], 0xFF, cap * sizeof(int32_t), ctx->stream));
   if (m == 0) {
     vm->max_probe[l] = 0;
     return GLIM_OK;
   }
-  k_voxel_stats<<<ceil_div_i(m, 128), 128, 0, ctx->stream>>>(
-      reinterpret_cast<const float4*>(pts4), cov6, cells.idx_sorted.p, cells.cell_start.p, cells.cell_key.p, m,
-      vm->vkey[l], vm->vmean[l], vm->vcov[l], vm->vcount[l], ctx->d_status);
-  GLIM_LAUNCHED(ctx);
   DevBuf<int> maxp;
   GLIM_CUDA(ctx, maxp.alloc(1, ctx->stream));
   GLIM_CUDA(ctx, cudaMemsetAsync(maxp.p, 0, sizeof(int), ctx->stream));
@@ -218,7 +296,14 @@ glim_status build_level(glim_ctx* ctx, const float* pts4, const float* cov6, int
 
 extern "C" glim_status glim_build_voxelmap(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n,
                                            const double* resolutions, int32_t levels, glim_vmap** out) {
+  return glim_build_voxelmap_ex(ctx, pts4, cov6, n, resolutions, levels, 0, out);
+}
+
+extern "C" glim_status glim_build_voxelmap_ex(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n,
+                                              const double* resolutions, int32_t levels, int32_t layout,
+                                              glim_vmap** out) {
   if (!ctx || !out) return GLIM_EINVAL;
+  if (layout < 0 || layout > 2) return set_error(ctx, GLIM_EINVAL, "build_voxelmap: layout must be 0, 1 or 2");
   *out = nullptr;
   if (n < 0 || (n > 0 && (!pts4 || !cov6)) || !resolutions || levels < 1 || levels > GLIM_MAX_LEVELS)
     return set_error(ctx, GLIM_EINVAL, "build_voxelmap: bad arguments (n=%lld levels=%d)", (long long)n, levels);
@@ -235,7 +320,7 @@ extern "C" glim_status glim_build_voxelmap(glim_ctx* ctx, const float* pts4, con
   for (int l = 0; l < levels; ++l) {
     vm->res[l] = resolutions[l];
     vm->inv_r[l] = float(1.0 / resolutions[l]);
-    glim_status st = build_level(ctx, pts4, cov6, n, vm, l);
+    glim_status st = build_level(ctx, pts4, cov6, n, vm, l, layout);
     if (st != GLIM_OK) {
       cudaStreamSynchronize(ctx->stream);
       free_levels(vm);
@@ -318,4 +403,9 @@ extern "C" glim_status glim_overlap(glim_ctx* ctx, const glim_frame* frames, int
   GLIM_LAUNCHED(ctx);
   GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // hp must outlive the copy
   return GLIM_OK;
+}
+
+extern "C" int32_t glim_vmap_is_dense(const glim_vmap* vm, int32_t level) {
+  if (!vm || level < 0 || level >= vm->levels) return -1;
+  return vm->dense[level];
 }

@@ -332,19 +332,23 @@ def urban_trajectory(n: int, nx: int = 5, ny: int = 4, block: float = 60.0):
 
 def urban(seed: int = 3, n_submaps: int = 400, n_range=(50000, 200000), neighbours: int = 10,
           sigma: float = 0.03, sensor_range: float = 35.0, resolutions=(0.5, 1.0, 2.0),
-          point_scale: float = 1.0) -> Workload:
+          point_scale: float = 1.0, keep: int = None) -> Workload:
     """Global step: submaps along a street trajectory, each paired with its nearest submaps.
 
     Submap sizes are log-uniform in ``n_range`` (times ``point_scale``); each submap is paired
     as source with its ``neighbours`` nearest submaps (by centre distance) as targets.  The
     linearization poses are the truth perturbed by 0.5 degree / 0.05 m, as in a global
-    optimisation step that has not converged yet.
+    optimisation step that has not converged yet.  ``keep`` = N keeps only the first N submaps
+    of the trajectory (same spacing, same sizes), paired among themselves: a smaller batch
+    with the overlap statistics of the full one.
     """
     s = Stream(seed, "urban")
     prims, _, _ = urban_prims(seed)
     traj = urban_trajectory(n_submaps)
     lo, hi = math.log(n_range[0]), math.log(n_range[1])
     sizes = np.floor(np.exp(s.uniform(n_submaps, lo, hi)) * point_scale).astype(np.int64)
+    if keep is not None:
+        traj, sizes, n_submaps = traj[:keep], sizes[:keep], keep
     pts, poses_true = [], []
     for (x, y, yaw), n in zip(traj, sizes):
         T = make_pose(rot_axis_angle([0, 0, 1], yaw), [x, y, 1.8])

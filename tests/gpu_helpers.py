@@ -15,7 +15,7 @@ from oracle import oracle as O
 
 
 class Prepared:
-    def __init__(self, ctx, w, k=10, validate_normals=True, cov_source="gpu"):
+    def __init__(self, ctx, w, k=10, validate_normals=True, cov_source="gpu", layout="auto"):
         self.ctx = ctx
         self.w = w
         dev = torch.device("cuda", ctx.device)
@@ -39,7 +39,7 @@ class Prepared:
             self.oframes.append(O.Frame(p4.cpu().numpy(), cov.cpu().numpy(),
                                         None if nrm is None else nrm.cpu().numpy()))
             if i in targets:
-                self.gmaps[i] = G.VoxelMap(ctx, p4, cov, w.resolutions)
+                self.gmaps[i] = G.VoxelMap(ctx, p4, cov, w.resolutions, layout=layout)
                 self.omaps[i] = O.VMap(self.oframes[i].pts4, self.oframes[i].cov6, w.resolutions)
 
     def oracle(self, pairs=None, poses=None, validate=False, want_ids=False, nthreads=8):

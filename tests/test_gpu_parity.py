@@ -41,10 +41,16 @@ def corridor(ctx):
     return Prepared(ctx, synth.corridor())
 
 
-@pytest.fixture(scope="module")
-def urban_small(ctx):
+@pytest.fixture(scope="module", params=["auto", "hash"])
+def urban_small(ctx, request):
+    """Urban submaps at realistic spacing (the first 12 submaps of the 400-submap trajectory,
+    at a fifth of the point density), with dense-grid and with hash-table voxelmaps."""
     from gpu_helpers import Prepared
-    return Prepared(ctx, synth.urban(n_submaps=12, neighbours=3, point_scale=0.2))
+    w = synth.urban(n_submaps=400, neighbours=3, point_scale=0.2, keep=12)
+    P = Prepared(ctx, w, layout=request.param)
+    t = int(w.pairs[0, 1])
+    assert all(P.gmaps[t].is_dense(l) == (request.param == "auto") for l in range(3))
+    return P
 
 
 def _check(res, ref, tol=TOL):
@@ -57,8 +63,10 @@ def _check(res, ref, tol=TOL):
 
 
 # ---------------------------------------------------------------------------- voxelmap
-def test_voxelmap_matches_oracle(room):
-    gm, om = room.gmaps[1], room.omaps[1]
+@pytest.mark.parametrize("layout", ["dense", "hash"])
+def test_voxelmap_matches_oracle(G, ctx, room, layout):
+    g = room.gframes[1]
+    gm, om = G.VoxelMap(ctx, g.pts4, g.cov6, room.w.resolutions, layout=layout), room.omaps[1]
     for l in range(om.levels):
         g = {k: v.cpu().numpy() for k, v in gm.export(l).items()}
         o = om.export(l)
@@ -67,7 +75,8 @@ def test_voxelmap_matches_oracle(room):
         np.testing.assert_allclose(g["mean"], o["mean"], rtol=0, atol=2e-6 * max(1.0, np.abs(o["mean"]).max()))
         np.testing.assert_allclose(g["cov"], o["cov"], rtol=0, atol=2e-6 * np.abs(o["cov"]).max())
         info = gm.info(l)
-        assert info["capacity"] >= 2 * info["n_voxels"] and info["max_probe"] >= 1
+        assert gm.is_dense(l) == (layout == "dense")
+        assert info["capacity"] >= (1 if layout == "dense" else 2) * info["n_voxels"] and info["max_probe"] >= 1
 
 
 def test_voxelmap_face_points_and_negative_coordinates(G, ctx):
@@ -95,9 +104,12 @@ def test_voxelmap_errors(G, ctx):
 
 # ---------------------------------------------------------------------------- correspondences
 @pytest.mark.parametrize("validate", [False, True])
-def test_correspondence_ids_bit_exact(G, ctx, room, validate):
+@pytest.mark.parametrize("layout", ["dense", "hash"])
+def test_correspondence_ids_bit_exact(G, ctx, room, validate, layout):
     w = room.w
-    gid = G.correspondences(ctx, room.gframes[0], room.gmaps[1], w.poses[0], w.poses[1], validate).cpu().numpy()
+    g = room.gframes[1]
+    vm = G.VoxelMap(ctx, g.pts4, g.cov6, w.resolutions, layout=layout)
+    gid = G.correspondences(ctx, room.gframes[0], vm, w.poses[0], w.poses[1], validate).cpu().numpy()
     ref = room.oracle(validate=validate, want_ids=True)
     assert np.array_equal(gid.reshape(-1), ref["ids"])
     assert (gid >= 0).mean() > 0.5
@@ -115,14 +127,16 @@ def test_correspondences_face_points(G, ctx):
     tgt = np.concatenate([face, face + [res / 2, 0, 0], face - [res / 2, 0, 0]]).astype(np.float32)
     cov = np.tile(np.array([1, 0, 0, 1, 0, 1], np.float32), (len(tgt), 1))
     om = O.VMap(O.as_pts4(tgt), cov, [res])
-    gm = G.VoxelMap(ctx, torch.as_tensor(O.as_pts4(tgt), device="cuda"), torch.as_tensor(cov, device="cuda"), [res])
     src4 = O.as_pts4(mu)
     scov = cov[:n]
     fr = G.FrameData(torch.as_tensor(src4, device="cuda"), torch.as_tensor(scov, device="cuda"))
-    gid = G.correspondences(ctx, fr, gm, Ts, Tt).cpu().numpy().reshape(-1)
     ref = O.linearize([O.Frame(src4, scov), O.Frame(O.as_pts4(tgt), cov)], [None, om], [[0, 1]],
                       np.stack([Ts, Tt]), want_ids=True)
-    assert np.array_equal(gid, ref["ids"])
+    for layout in ("dense", "hash"):
+        gm = G.VoxelMap(ctx, torch.as_tensor(O.as_pts4(tgt), device="cuda"), torch.as_tensor(cov, device="cuda"),
+                        [res], layout=layout)
+        gid = G.correspondences(ctx, fr, gm, Ts, Tt).cpu().numpy().reshape(-1)
+        assert np.array_equal(gid, ref["ids"])
 
 
 # ---------------------------------------------------------------------------- linearization
@@ -297,3 +311,34 @@ def test_overlap_matches_oracle(G, ctx, corridor):
         for p, (s, t) in enumerate(w.pairs):
             ref = O.overlap(corridor.oframes[s], corridor.omaps[t], w.poses[s], w.poses[t], level=level)
             assert ov[p] == pytest.approx(ref, abs=0)
+
+
+# ---------------------------------------------------------------------------- point order
+def test_spatial_order_is_a_stable_morton_sort(G, ctx):
+    pts = synth.corridor(n_cur=5000, kf_range=(100, 101), n_kf=1).points[0]
+    p4 = G.to_pts4(pts, device="cuda")
+    perm = G.spatial_order(ctx, p4, 0.5).cpu().numpy()
+    assert np.array_equal(np.sort(perm), np.arange(len(pts)))
+    k = np.floor(pts.astype(np.float32) * np.float32(2.0)).astype(np.int64) + (1 << 20)
+
+    def spread(v):
+        out = np.zeros_like(v)
+        for b in range(21):
+            out |= ((v >> b) & 1) << (3 * b)
+        return out
+
+    code = (spread(k[:, 0]) << 2) | (spread(k[:, 1]) << 1) | spread(k[:, 2])
+    c = code[perm]
+    assert (np.diff(c) >= 0).all()
+    ties = np.diff(c) == 0
+    assert (np.diff(perm)[ties] > 0).all()  # stable within a cell
+
+
+def test_linearize_independent_of_point_order(G, ctx, corridor):
+    """Reordering the source points changes e, H, b only by rounding."""
+    ref = corridor.oracle()
+    src = corridor.gframes[0]
+    perm = G.spatial_order(ctx, src.pts4, 0.5)
+    fr = [G.FrameData(src.pts4[perm].contiguous(), src.cov6[perm].contiguous(),
+                      src.normal3[perm].contiguous())] + corridor.gframes[1:]
+    _check(G.linearize(ctx, fr, corridor.gmaps, corridor.w.pairs, corridor.w.poses), ref)
