@@ -220,6 +220,27 @@ glim_status glim_linearize_factors_plain(glim_ctx* ctx, const glim_frame* frames
                                          double* e_out, double* H_out, double* b_out,
                                          int64_t* inliers_out);
 
+/* For callers that cannot allocate device memory while they linearize: processes whose device
+ * memory is reserved up front by another allocator, so that a cudaMalloc may fail or wait, and
+ * real-time loops that must not block in the driver (cudaFree synchronizes the device).  The
+ * paper has no counterpart; this is a service of the library.
+ *
+ * Same computation and arguments as glim_linearize_factors, except that e_out, H_out, b_out
+ * and inliers_out (may be NULL) must be device arrays, and that the call allocates nothing:
+ * its scratch (descriptors, work list, queue head, partial sums) is one statically sized array
+ * of about 4.5 MB that every device loading this library holds until the process exits.
+ * Limits: at most 256 frames, 256 pairs and 16384 work items of block * pts_per_thread points
+ * (GLIM_EINVAL with a message naming the limit otherwise).  The first call on a device looks
+ * up that array's device address; make that first call before any stream capture.  Every call
+ * shares the array and overwrites it (the queue head is cleared on each call), so calls that
+ * overlap on the GPU, from any stream or thread, race: issue them one after another.  The work
+ * is enqueued on the context's stream; the call does not synchronize. */
+glim_status glim_linearize_factors_noalloc(glim_ctx* ctx, const glim_frame* frames, int32_t nframes,
+                                           const glim_pair* pairs, int32_t npairs,
+                                           const double* poses12, const glim_lin_opts* opts,
+                                           double* e_out, double* H_out, double* b_out,
+                                           int64_t* inliers_out);
+
 /* A plan fixes a batch (frames, pairs, options) and owns its device work list, partial-sum
  * slots, a pinned serialized input block (relative poses) and output block (e, H, b,
  * inliers), and a CUDA graph of [upload, queue reset, linearize, reduce, download].  The

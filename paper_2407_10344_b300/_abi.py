@@ -54,6 +54,8 @@ SIGNATURES = {
                                       C.POINTER(LinOpts), _vp, _vp, _vp, _vp]),
     "glim_linearize_factors_plain": (_i32, [_vp, C.POINTER(Frame), _i32, C.POINTER(Pair), _i32, _vp,
                                             C.POINTER(LinOpts), _vp, _vp, _vp, _vp]),
+    "glim_linearize_factors_noalloc": (_i32, [_vp, C.POINTER(Frame), _i32, C.POINTER(Pair), _i32, _vp,
+                                              C.POINTER(LinOpts), _vp, _vp, _vp, _vp]),
     "glim_plan_create": (_i32, [_vp, C.POINTER(Frame), _i32, C.POINTER(Pair), _i32, C.POINTER(LinOpts),
                                 C.POINTER(_vp)]),
     "glim_plan_destroy": (None, [_vp]),

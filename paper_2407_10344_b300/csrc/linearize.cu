@@ -655,3 +655,25 @@ extern "C" glim_status glim_linearize_factors_plain(glim_ctx* ctx, const glim_fr
   glim_plan_destroy(p);
   return st;
 }
+
+// Enqueue the FP64 reduce-and-expand kernel of pairs [0, npairs) on `stream` (used by the
+// entry point that works without device allocations).
+glim_status enqueue_reduce_expand(glim_ctx* ctx, const double* part, const int32_t* item_begin,
+                                  const double* pose64, int32_t npairs, int32_t fp32_sum, double* e, double* H,
+                                  double* b, long long* inl) {
+  if (npairs <= 0) return GLIM_OK;
+  ReduceArgs r;
+  r.part = part;
+  r.item_begin = item_begin;
+  r.pose64 = pose64;
+  r.pair_base = 0;
+  r.npairs = npairs;
+  r.fp32_sum = fp32_sum;
+  r.e = e;
+  r.H = H;
+  r.b = b;
+  r.inl = inl;
+  k_reduce_expand<<<npairs, 128, 0, ctx->stream>>>(r);
+  GLIM_LAUNCHED(ctx);
+  return GLIM_OK;
+}

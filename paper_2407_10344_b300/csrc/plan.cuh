@@ -111,3 +111,6 @@ struct glim_plan {
 // shared host helpers (linearize.cu)
 void plan_pack_poses(glim_plan* p, const double* poses12);
 glim_status plan_configure(glim_plan* p, const glim_lin_opts& o);
+glim_status enqueue_reduce_expand(glim_ctx* ctx, const double* part, const int32_t* item_begin,
+                                  const double* pose64, int32_t npairs, int32_t fp32_sum, double* e, double* H,
+                                  double* b, long long* inl);
