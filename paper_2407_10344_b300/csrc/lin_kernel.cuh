@@ -67,25 +67,24 @@ __device__ __forceinline__ PointIn load_point(const FrameDev& F, int64_t k) {
   return p;
 }
 
-// Per-warp staging of one round (one point per lane): the lanes' point data and the compacted
-// list of (point, level) hits with their voxel statistics.  Records have an odd stride, so
-// lanes reading consecutive records hit distinct shared-memory banks.
-// Both records are three float4 (48 bytes): eight lanes of a quarter warp reading consecutive
-// records touch distinct banks.
-//   point: {q.x, q.y, q.z, u.x} {u.y, u.z, S'00, S'01} {S'02, S'11, S'12, S'22}, S' = R C R^T
-//   term:  {mean.x, mean.y, mean.z, C~00} {C~01, C~02, C~11, C~12} {C~22, w, source lane, 0}
+// Per-warp staging of one round: the compacted list of (point, level) hits.  A term record is
+// three float4 (48 bytes), self-contained, so phase 2 reads only its own record and lanes
+// reading consecutive records touch distinct banks:
+//   {S'00, S'01, S'02, S'11} {S'12, S'22, d.x, d.y} {d.z, u.x, u.y, u.z}
+// with S' = (C~ + R C R^T) / w, d = mu~ - q, u = R mu.  Dividing S by the point weight w > 0
+// makes adj(S')/det(S') = w Omega, so every later product already carries the weight.
 template <int LMAX>
 struct WarpStage {
-  float4 pt[32 * 3];
   float4 term[32 * LMAX * 3];
 };
 
-// One round for the warp.  Phase 1 (every lane, its own point): transform, keys and the first
-// probe of every level in flight together, collision fallback, then the hits are compacted
-// into the warp's term list (level-major, lane order within a level).  Phase 2 (the lanes
-// share the term list): per hit S = C~ + R C R^T, Omega = adj(S)/det(S), d = mu~ - q,
-// y = Omega d, e = d^T y, and the point's G-form contribution w [G^T Omega G, G^T y, e] with
-// G = [-(u)x, I] is accumulated.  Misses and discarded points cost no phase-2 lanes.
+// One round for the warp.  Phase 1 (every lane, its own point): transform, keys and one read
+// of every level in flight together (collision fallback for hash levels), R C R^T, then each
+// hit's record is written to the warp's term list at its compacted position (level-major,
+// lane order within a level).  Phase 2 (the lanes share the term list): per hit
+// w Omega = adj(S')/det(S'), y = w Omega d, e = d^T y, and the G-form contribution
+// [G^T (w Omega) G, G^T y, e] with G = [-(u)x, I].  Misses and discarded points cost no
+// phase-2 lanes.  Points must have positive weights (a zero weight contributes nothing).
 template <int LMAX, class A>
 __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in, bool live, int64_t k, int validate,
                                            WarpStage<LMAX>& ws, A& acc, int& inl) {
@@ -148,7 +147,9 @@ __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in,
     }
     nh += hit[l] ? 1 : 0;
   }
-  if (nh > 0) {  // stage this lane's point: q, u, R C R^T, w
+  // R C R^T / w and u, for the records of this lane's hits
+  float r00 = 0.f, r01 = 0.f, r02 = 0.f, r11 = 0.f, r12 = 0.f, r22 = 0.f, iw = 0.f;
+  if (nh > 0) {
     const float c00 = in.ca.x, c01 = in.ca.y, c02 = in.cb.x, c11 = in.cb.y, c12 = in.cc.x, c22 = in.cc.y;
     const float w00 = R[0] * c00 + R[1] * c01 + R[2] * c02;
     const float w01 = R[0] * c01 + R[1] * c11 + R[2] * c12;
@@ -159,14 +160,16 @@ __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in,
     const float w20 = R[6] * c00 + R[7] * c01 + R[8] * c02;
     const float w21 = R[6] * c01 + R[7] * c11 + R[8] * c12;
     const float w22 = R[6] * c02 + R[7] * c12 + R[8] * c22;
-    float4* pp = ws.pt + lane * 3;
-    pp[0] = make_float4(q.x, q.y, q.z, q.x - P.t[0]);
-    pp[1] = make_float4(q.y - P.t[1], q.z - P.t[2], w00 * R[0] + w01 * R[1] + w02 * R[2],
-                        w00 * R[3] + w01 * R[4] + w02 * R[5]);
-    pp[2] = make_float4(w00 * R[6] + w01 * R[7] + w02 * R[8], w10 * R[3] + w11 * R[4] + w12 * R[5],
-                        w10 * R[6] + w11 * R[7] + w12 * R[8], w20 * R[6] + w21 * R[7] + w22 * R[8]);
+    r00 = w00 * R[0] + w01 * R[1] + w02 * R[2];
+    r01 = w00 * R[3] + w01 * R[4] + w02 * R[5];
+    r02 = w00 * R[6] + w01 * R[7] + w02 * R[8];
+    r11 = w10 * R[3] + w11 * R[4] + w12 * R[5];
+    r12 = w10 * R[6] + w11 * R[7] + w12 * R[8];
+    r22 = w20 * R[6] + w21 * R[7] + w22 * R[8];
+    iw = __fdividef(1.0f, m.w);
     inl += nh;
   }
+  const float ux = q.x - P.t[0], uy = q.y - P.t[1], uz = q.z - P.t[2];
   // compaction of the hits: level-major, lane order within a level
   int base = 0;
 #pragma unroll
@@ -174,43 +177,40 @@ __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in,
     const unsigned mask = __ballot_sync(0xffffffffu, hit[l]);
     if (hit[l]) {
       float4* t = ws.term + (base + __popc(mask & lt)) * 3;
-      t[0] = s1[l];                                                     // voxel mean, C~00
-      t[1] = s2[l];                                                     // C~ 01 02 11 12
-      t[2] = make_float4(s0[l].w, m.w, __int_as_float(lane), 0.f);     // C~22, w, lane
+      // voxel record: s0 = {., ., ., C~22}, s1 = {mean, C~00}, s2 = {C~01, C~02, C~11, C~12}
+      t[0] = make_float4((s1[l].w + r00) * iw, (s2[l].x + r01) * iw, (s2[l].y + r02) * iw, (s2[l].z + r11) * iw);
+      t[1] = make_float4((s2[l].w + r12) * iw, (s0[l].w + r22) * iw, s1[l].x - q.x, s1[l].y - q.y);
+      t[2] = make_float4(s1[l].z - q.z, ux, uy, uz);
     }
     base += __popc(mask);
   }
   __syncwarp();
   for (int i = lane; i < base; i += 32) {
     const float4 t0 = ws.term[3 * i], t1 = ws.term[3 * i + 1], t2 = ws.term[3 * i + 2];
-    const float4* pp = ws.pt + 3 * __float_as_int(t2.z);
-    const float4 p0 = pp[0], p1 = pp[1], p2 = pp[2];
-    // S = C~ + R C R^T
-    const float a = t0.w + p1.z, b = t1.x + p1.w, c = t1.y + p2.x;
-    const float d = t1.z + p2.y, e = t1.w + p2.z, f = t2.x + p2.w;
+    const float a = t0.x, b = t0.y, c = t0.z, d = t0.w, e = t1.x, f = t1.y;  // S'
     const float A00 = d * f - e * e, A01 = c * e - b * f, A02 = b * e - c * d;
     const float A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
     const float det = a * A00 + b * A01 + c * A02;
     if (!(det > 0.f) || !(det < INFINITY)) continue;  // S not positive definite: skip the term
-    const float id = __fdividef(t2.y, det);          // w / det
+    const float id = __fdividef(1.0f, det);
     const float o00 = A00 * id, o01 = A01 * id, o02 = A02 * id, o11 = A11 * id, o12 = A12 * id, o22 = A22 * id;
-    const float dx = t0.x - p0.x, dy = t0.y - p0.y, dz = t0.z - p0.z;
+    const float dx = t1.z, dy = t1.w, dz = t2.x;
     const float g0 = o00 * dx + o01 * dy + o02 * dz;  // w Omega d
     const float g1 = o01 * dx + o11 * dy + o12 * dz;
     const float g2 = o02 * dx + o12 * dy + o22 * dz;
     const float es = dx * g0 + dy * g1 + dz * g2;     // w d^T Omega d
-    const float ux = p0.w, uy = p1.x, uz = p1.y;
+    const float ux2 = t2.y, uy2 = t2.z, uz2 = t2.w;
     // W = (u)x (w Omega)
-    const float W00 = -uz * o01 + uy * o02, W01 = -uz * o11 + uy * o12, W02 = -uz * o12 + uy * o22;
-    const float W10 = uz * o00 - ux * o02, W11 = uz * o01 - ux * o12, W12 = uz * o02 - ux * o22;
-    const float W20 = -uy * o00 + ux * o01, W21 = -uy * o01 + ux * o11, W22 = -uy * o02 + ux * o12;
+    const float W00 = -uz2 * o01 + uy2 * o02, W01 = -uz2 * o11 + uy2 * o12, W02 = -uz2 * o12 + uy2 * o22;
+    const float W10 = uz2 * o00 - ux2 * o02, W11 = uz2 * o01 - ux2 * o12, W12 = uz2 * o02 - ux2 * o22;
+    const float W20 = -uy2 * o00 + ux2 * o01, W21 = -uy2 * o01 + ux2 * o11, W22 = -uy2 * o02 + ux2 * o12;
     // M_rr = -(u)x Omega (u)x = W (u)x^T  (symmetric)
-    acc.add(0, -uz * W01 + uy * W02);
-    acc.add(1, uz * W00 - ux * W02);
-    acc.add(2, -uy * W00 + ux * W01);
-    acc.add(3, uz * W10 - ux * W12);
-    acc.add(4, -uy * W10 + ux * W11);
-    acc.add(5, -uy * W20 + ux * W21);
+    acc.add(0, -uz2 * W01 + uy2 * W02);
+    acc.add(1, uz2 * W00 - ux2 * W02);
+    acc.add(2, -uy2 * W00 + ux2 * W01);
+    acc.add(3, uz2 * W10 - ux2 * W12);
+    acc.add(4, -uy2 * W10 + ux2 * W11);
+    acc.add(5, -uy2 * W20 + ux2 * W21);
     // M_rt = (u)x Omega
     acc.add(6, W00); acc.add(7, W01); acc.add(8, W02);
     acc.add(9, W10); acc.add(10, W11); acc.add(11, W12);
@@ -218,9 +218,9 @@ __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in,
     // M_tt = Omega
     acc.add(15, o00); acc.add(16, o01); acc.add(17, o02); acc.add(18, o11); acc.add(19, o12); acc.add(20, o22);
     // g = [u x (w Omega d); w Omega d]
-    acc.add(21, uy * g2 - uz * g1);
-    acc.add(22, uz * g0 - ux * g2);
-    acc.add(23, ux * g1 - uy * g0);
+    acc.add(21, uy2 * g2 - uz2 * g1);
+    acc.add(22, uz2 * g0 - ux2 * g2);
+    acc.add(23, ux2 * g1 - uy2 * g0);
     acc.add(24, g0); acc.add(25, g1); acc.add(26, g2);
     acc.add(27, es);
   }

@@ -342,3 +342,67 @@ def test_linearize_independent_of_point_order(G, ctx, corridor):
     fr = [G.FrameData(src.pts4[perm].contiguous(), src.cov6[perm].contiguous(),
                       src.normal3[perm].contiguous())] + corridor.gframes[1:]
     _check(G.linearize(ctx, fr, corridor.gmaps, corridor.w.pairs, corridor.w.poses), ref)
+
+
+# ---------------------------------------------------------------------------- autograd
+@pytest.mark.parametrize("full", [True, False])
+def test_autograd_function_against_fd(G, ctx, full):
+    """GlimFactorFn on an odometry-window batch with per-point weights: the backward pass
+    matches central finite differences (h = 1e-6, FP64 oracle energy with the correspondences
+    and, for the frozen mode, Omega held at the linearization point) on a 500-point subset,
+    and the oracle's analytic gradient on all points."""
+    from gpu_helpers import Prepared
+    from paper_2407_10344_b300.autograd import FactorProblem, retract
+    P = Prepared(ctx, synth.corridor(n_cur=4000, kf_range=(3000, 5000), n_kf=3, weights=True))
+    w = P.w
+    prob = FactorProblem(ctx, P.gframes, P.gmaps, w.pairs, w.poses, omega_grad_full=full)
+    pts, wts = prob.points()
+    pts = pts.clone().requires_grad_(True)
+    wts = wts.clone().requires_grad_(True)
+    xi = torch.zeros((len(w.points), 6), dtype=torch.float64, device="cuda", requires_grad=True)
+    E = prob.energy(xi, pts, wts)
+    E.backward()
+    ref = P.oracle(want_ids=True)
+    assert abs(E.item() - ref["e"].sum()) <= 1e-4 * ref["e"].sum()
+    # analytic oracle gradient
+    odxi, odmu, odw = O.gradient(P.oframes, P.omaps, w.pairs, w.poses, omega_grad_full=full)
+    gxi = xi.grad.cpu().numpy()
+    assert np.linalg.norm(gxi - odxi) <= 1e-4 * np.linalg.norm(odxi)
+    n0 = len(w.points[0])
+    gmu = pts.grad.cpu().numpy()
+    assert np.linalg.norm(gmu[:n0] - odmu[0]) <= 1e-4 * np.linalg.norm(odmu[0])
+    assert np.linalg.norm(wts.grad.cpu().numpy()[:n0] - odw[0]) <= 1e-4 * np.linalg.norm(odw[0])
+    # central FD of the FP64 energy (frozen correspondences) on pose increments of two frames
+    ids = ref["ids"]
+
+    def E_fd(x):
+        poses = np.stack([retract(w.poses[f], x[6 * f:6 * f + 6]) for f in range(len(w.points))])
+        return O.energy(P.oframes, P.omaps, w.pairs, poses, ids, omega_poses=None if full else w.poses).sum()
+
+    h = 1e-6
+    for f in (0, 2):
+        for a in range(6):
+            x = np.zeros(6 * len(w.points))
+            x[6 * f + a] = h
+            fd = (E_fd(x) - E_fd(-x)) / (2 * h)
+            assert abs(fd - gxi[f, a]) <= 1e-4 * np.abs(gxi).max(), (f, a, fd, gxi[f, a])
+    # FD of points and weights on a 500-point subset of the source frame: the terms of point k
+    # depend only on point k, so each derivative is taken on a one-point frame with that
+    # point's frozen correspondences
+    sel = synth.Stream(7, "subset").integers(500, 0, n0)
+    L = len(w.resolutions)
+    ids_pp = ids.reshape(len(w.pairs), n0, L)
+    grads = np.concatenate([gmu[:n0], wts.grad.cpu().numpy()[:n0, None]], 1)
+    worst = 0.0
+    for k in sel:
+        one_ids = ids_pp[:, k, :].reshape(-1)
+        for a in range(4):
+            def Ep(hv):
+                p = P.oframes[0].pts4[k:k + 1].copy()
+                p[0, a] = np.float32(np.float64(p[0, a]) + hv)
+                fr = [O.Frame(p, P.oframes[0].cov6[k:k + 1], P.oframes[0].normal3[k:k + 1])] + P.oframes[1:]
+                return O.energy(fr, P.omaps, w.pairs, w.poses, one_ids).sum()
+            hv = 1e-3 if a < 3 else 1e-2
+            fd = (Ep(hv) - Ep(-hv)) / (2 * hv)
+            worst = max(worst, abs(fd - grads[k, a]) / max(1.0, abs(grads[k, a])))
+    assert worst <= 2e-3
