@@ -148,6 +148,103 @@ def oracle_sample(w, budget_s=15.0, nthreads=None, target_points=30_000_000):
                        f"{dt:.1f} s wall on {nthreads} threads"), dt
 
 
+# ---------------------------------------------------------------------------- small workloads
+def small_workloads(G, ctx, dev):
+    """Timings of the other factor batches of the paper's pipeline on the same GPU:
+    the odometry window (10 binary factors, one launch), the unary box-room factor with 10
+    Gauss-Newton iterations (linearize + device Cholesky step), and the differentiable cost
+    (forward + backward) on the odometry window.  Milliseconds, median of repeats."""
+    import torch
+    import synth
+    from paper_2407_10344_b300.autograd import FactorProblem, retract
+
+    def prep(w, order=True):
+        frames, maps = [], [None] * len(w.points)
+        targets = set(int(t) for t in w.pairs[:, 1])
+        for i, p in enumerate(w.points):
+            p4 = G.to_pts4(p, w.weights[i] if w.weights else None, device=dev)
+            cov, nrm = G.estimate_covariances(ctx, p4, k=10)
+            if order:
+                perm = G.spatial_order(ctx, p4, 0.5)
+                p4, cov, nrm = p4[perm].contiguous(), cov[perm].contiguous(), nrm[perm].contiguous()
+            frames.append(G.FrameData(p4, cov, nrm))
+            if i in targets:
+                maps[i] = G.VoxelMap(ctx, p4, cov, w.resolutions)
+        torch.cuda.synchronize()
+        return frames, maps
+
+    def med(f, reps=20, warm=3):
+        for _ in range(warm):
+            f()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            f()
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return float(np.median(ts))
+
+    out = {}
+    # odometry window
+    w = synth.corridor()
+    frames, maps = prep(w)
+    plan = G.Plan(ctx, frames, maps, w.pairs)
+    plan.set_poses(w.poses)
+    out["odometry_window"] = {
+        "workload": "corridor: 30k-pt frame vs 10 keyframes of 15k-40k pts, 0.5 m, 10 binary factors",
+        "pair_points": w.n_pair_points,
+        "graph_launch_ms": med(plan.launch),
+        "e2e_plan_linearize_ms": med(lambda: plan.linearize(w.poses)),
+        "plain_per_factor_ms": med(lambda: G.linearize(ctx, frames, maps, w.pairs, w.poses, plain=True), reps=10),
+    }
+    out["odometry_window"]["speedup_vs_plain"] = (out["odometry_window"]["plain_per_factor_ms"] /
+                                                  out["odometry_window"]["e2e_plan_linearize_ms"])
+    # differentiable cost on the odometry window (with per-point weights)
+    ww = synth.corridor(weights=True)
+    fr2, mp2 = prep(ww)
+    prob = FactorProblem(ctx, fr2, mp2, ww.pairs, ww.poses)
+    pts, wts = prob.points()
+    pts.requires_grad_(True)
+    wts.requires_grad_(True)
+    xi = torch.zeros((len(ww.points), 6), dtype=torch.float64, device=dev, requires_grad=True)
+
+    def fwd_bwd():
+        E = prob.energy(xi, pts, wts)
+        E.backward()
+
+    out["autograd"] = {"workload": "corridor with per-point weights, E and dE/d(xi, xyz, w)",
+                       "forward_backward_ms": med(fwd_bwd, reps=10),
+                       "forward_ms": med(lambda: prob.energy(xi, pts, wts), reps=10)}
+    # unary factor + 10 Gauss-Newton iterations
+    wb = synth.box_room()
+    fb, mb = prep(wb)
+    planb = G.Plan(ctx, fb, mb, wb.pairs)
+
+    def gn10():
+        import ctypes
+        poses = wb.poses.copy()
+        xi_t = torch.empty((1, 6), dtype=torch.float64, device=dev)
+        st_t = torch.empty(1, dtype=torch.int32, device=dev)
+        for _ in range(10):
+            planb.set_poses(poses)          # serialized pose upload
+            planb.launch()                  # graph: linearize + reduce, results stay on the device
+            _, Hp, bp, _ = planb.device_outputs()
+            # S9 on the device: Cholesky step on the top-left 6 x 6 block (unary factor)
+            ctx.call("gn_solve", ctx.lib.glim_gn_solve, ctx.h, ctypes.c_void_p(Hp), 12, 144, ctypes.c_void_p(bp),
+                     12, 6, 1, ctypes.c_void_p(xi_t.data_ptr()), ctypes.c_void_p(st_t.data_ptr()), ok=(0, -6))
+            poses[0] = retract(poses[0], xi_t.cpu().numpy()[0])  # pose update on the host (FP64)
+        return poses
+
+    poses = gn10()
+    D = np.linalg.inv(np.vstack([wb.poses_true[0], [0, 0, 0, 1]])) @ np.vstack([poses[0], [0, 0, 0, 1]])
+    ang = float(np.degrees(np.arccos(min(1.0, (np.trace(D[:3, :3]) - 1) / 2))))
+    out["gauss_newton_unary"] = {"workload": "box room 5k vs 20k, 1 m, unary factor, 10 iterations from 5 deg / 0.3 m",
+                                 "ms_10_iterations": med(gn10, reps=5, warm=1),
+                                 "final_rot_err_deg": ang, "final_trans_err_m": float(np.linalg.norm(D[:3, 3]))}
+    return out
+
+
 # ---------------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -283,6 +380,8 @@ def run_ours(args):
         "gpu_launches": gpu_launches,
         "clocks": clk,
     }
+    if rank == 0 and not args.no_small:
+        line["other_batches"] = small_workloads(G, ctx, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, _ = oracle_sample(w, budget_s=args.cpu_budget)
         line["cpu_baseline"] = cb
@@ -330,6 +429,7 @@ def main():
     ap.add_argument("--block", type=int, default=0, help="threads per block (0: default; autotune overrides)")
     ap.add_argument("--ppt", type=int, default=0, help="points per thread (0: default; autotune overrides)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-small", action="store_true", help="skip the odometry / GN / autograd timings")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-points", type=int, default=3_000_000)
     args = ap.parse_args()

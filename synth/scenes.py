@@ -117,9 +117,10 @@ class Cylinder:
         return 2.0 * math.pi * self.radius * (self.z1 - self.z0)
 
     def sample(self, s: Stream, n: int) -> np.ndarray:
-        th = s.uniform(n, 0.0, 2.0 * math.pi)
+        th = s.uniform(n, 0.0, 2.0 * math.pi).astype(np.float32)  # FP32 trig: ~1e-8 m at these radii
         z = s.uniform(n, self.z0, self.z1)
-        return np.stack([self.cx + self.radius * np.cos(th), self.cy + self.radius * np.sin(th), z], 1)
+        return np.stack([self.cx + self.radius * np.cos(th).astype(np.float64),
+                         self.cy + self.radius * np.sin(th).astype(np.float64), z], 1)
 
 
 def box_faces(x0, x1, y0, y1, z0, z1, roof=True, floor=False):
@@ -370,21 +371,36 @@ def urban(seed: int = 3, n_submaps: int = 400, n_range=(50000, 200000), neighbou
     )
 
 
+_K1, _K2, _K3, _K4 = 2 * np.pi / 140.0, 2 * np.pi / 110.0, 2 * np.pi / 60.0, 2 * np.pi / 25.0
+
+
+def _phase(a):
+    """Phase reduced to [0, 2 pi) in FP64, then rounded to FP32 for a fast FP32 sine/cosine."""
+    return np.mod(a, 2 * np.pi).astype(np.float32)
+
+
+def terrain_height_and_slope(x, y):
+    """Height of the sum-of-sinusoids terrain (amplitudes 0.4-3 m, wavelengths 25-140 m) and
+    the area factor sqrt(1 + |grad z|^2), from one set of sines and cosines.  The trigonometry
+    runs in FP32 on phases reduced in FP64 (the points are stored in FP32; the surface error
+    is ~1e-7 m)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    a1 = _phase(_K1 * x + 0.3)
+    b1 = _phase(_K2 * y)
+    a2 = _phase(_K3 * (0.6 * x + 0.8 * y) + 1.1)
+    a3 = _phase(_K4 * (0.9 * x - 0.4 * y))
+    s1, c1, sb, cb = np.sin(a1), np.cos(a1), np.sin(b1), np.cos(b1)
+    s2, c2 = np.sin(a2), np.cos(a2)
+    s3, c3 = np.sin(a3), np.cos(a3)
+    z = 3.0 * s1 * cb + 1.2 * s2 + 0.4 * c3
+    gx = np.float32(3.0 * _K1) * c1 * cb + np.float32(1.2 * _K3 * 0.6) * c2 - np.float32(0.4 * _K4 * 0.9) * s3
+    gy = np.float32(-3.0 * _K2) * s1 * sb + np.float32(1.2 * _K3 * 0.8) * c2 + np.float32(0.4 * _K4 * 0.4) * s3
+    return z, np.sqrt(1.0 + gx * gx + gy * gy)
+
+
 def terrain_height(x, y):
-    """Sum of sinusoids (amplitudes 0.4-3 m, wavelengths 25-140 m)."""
-    return (3.0 * np.sin(2 * np.pi * x / 140.0 + 0.3) * np.cos(2 * np.pi * y / 110.0)
-            + 1.2 * np.sin(2 * np.pi * (0.6 * x + 0.8 * y) / 60.0 + 1.1)
-            + 0.4 * np.cos(2 * np.pi * (0.9 * x - 0.4 * y) / 25.0))
-
-
-def terrain_grad(x, y):
-    gx = (3.0 * (2 * np.pi / 140.0) * np.cos(2 * np.pi * x / 140.0 + 0.3) * np.cos(2 * np.pi * y / 110.0)
-          + 1.2 * (2 * np.pi * 0.6 / 60.0) * np.cos(2 * np.pi * (0.6 * x + 0.8 * y) / 60.0 + 1.1)
-          - 0.4 * (2 * np.pi * 0.9 / 25.0) * np.sin(2 * np.pi * (0.9 * x - 0.4 * y) / 25.0))
-    gy = (-3.0 * (2 * np.pi / 110.0) * np.sin(2 * np.pi * x / 140.0 + 0.3) * np.sin(2 * np.pi * y / 110.0)
-          + 1.2 * (2 * np.pi * 0.8 / 60.0) * np.cos(2 * np.pi * (0.6 * x + 0.8 * y) / 60.0 + 1.1)
-          + 0.4 * (2 * np.pi * 0.4 / 25.0) * np.sin(2 * np.pi * (0.9 * x - 0.4 * y) / 25.0))
-    return gx, gy
+    return terrain_height_and_slope(x, y)[0]
 
 
 def _terrain_points(s: Stream, n: int, cx: float, cy: float, radius: float, half: float,
@@ -414,12 +430,11 @@ def _terrain_points(s: Stream, n: int, cx: float, cy: float, radius: float, half
         m = int((n_ground - have) * 1.7) + 64
         x = s.uniform(m, lo_x, hi_x)
         y = s.uniform(m, lo_y, hi_y)
-        gx, gy = terrain_grad(x, y)
-        keep = s.uniform(m) * gmax <= np.sqrt(1.0 + gx * gx + gy * gy)
+        z, area = terrain_height_and_slope(x, y)
+        keep = s.uniform(m) * gmax <= area
         keep &= (x - cx) ** 2 + (y - cy) ** 2 <= radius * radius
-        x, y = x[keep], y[keep]
-        out.append(np.stack([x, y, terrain_height(x, y)], 1))
-        have += len(x)
+        out.append(np.stack([x[keep], y[keep], z[keep].astype(np.float64)], 1))
+        have += int(keep.sum())
     g = np.concatenate(out)[:n_ground]
     if n_wall > 0:
         w = sample_scene(walls, n_wall, s)

@@ -1,0 +1,69 @@
+"""Precision at scale: one 1M-point scan against a 20M-point terrain map at 0.25 m (the
+precision / scale stress batch).  FP32 per-point arithmetic with three accumulations of the
+partial sums (FP32 naive, FP32 compensated, FP64 across warps and blocks) against the FP64
+oracle; the oracle's own rounding is bounded by its long-double sums.  Every output must be
+within 1e-4 of the oracle (norm-wise, as in the other parity tests); the error table is
+written to the test's output directory for the design notes."""
+import json
+import os
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import oracle as O
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+TOL = 1e-4
+
+
+def test_terrain_precision_all_accumulation_modes():
+    import paper_2407_10344_b300 as G
+    from gpu_helpers import rel_errors
+    t0 = time.time()
+    w = synth.terrain()
+    t_gen = time.time() - t0
+    ctx = G.Context(0)
+    dev = torch.device("cuda", 0)
+    p_src = G.to_pts4(w.points[0], device=dev)
+    p_map = G.to_pts4(w.points[1], device=dev)
+    t0 = time.time()
+    c_src, n_src = G.estimate_covariances(ctx, p_src)
+    c_map, _ = G.estimate_covariances(ctx, p_map)
+    perm = G.spatial_order(ctx, p_src, 0.5)
+    p_src, c_src, n_src = p_src[perm].contiguous(), c_src[perm].contiguous(), n_src[perm].contiguous()
+    vm = G.VoxelMap(ctx, p_map, c_map, w.resolutions)
+    torch.cuda.synchronize()
+    t_prep = time.time() - t0
+    frames = [G.FrameData(p_src, c_src, n_src), G.FrameData(p_map, c_map)]
+    res = {}
+    for name, acc in (("fp32", G.ACC_FP32), ("kahan", G.ACC_KAHAN), ("fp64", G.ACC_FP64)):
+        res[name] = G.linearize(ctx, frames, [None, vm], w.pairs, w.poses, accum_mode=acc)
+    # oracle on the same float32 inputs
+    of = [O.Frame(p_src.cpu().numpy(), c_src.cpu().numpy(), n_src.cpu().numpy()),
+          O.Frame(p_map.cpu().numpy(), c_map.cpu().numpy())]
+    t0 = time.time()
+    om = O.VMap(of[1].pts4, of[1].cov6, w.resolutions)
+    ref = O.linearize(of, [None, om], w.pairs, w.poses, want_comp=True)
+    t_oracle = time.time() - t0
+    assert res["fp64"][3][0] == ref["inliers"][0]
+    table = {"workload": w.name, "voxels": om.size(0), "inliers": int(ref["inliers"][0]),
+             "dense_grid": bool(vm.is_dense(0)), "seconds": {"generate": t_gen, "gpu_prep": t_prep,
+                                                             "oracle_build_and_linearize": t_oracle}}
+    for name, (e, H, b, inl) in res.items():
+        ee, eH, eb = rel_errors(e, H, b, ref)
+        table[name] = {"e": float(ee[0]), "H": float(eH[0]), "b": float(eb[0]),
+                       "H_max_elementwise_rel": float(np.abs(H[0] - ref["H"][0]).max() / np.abs(ref["H"][0]).max())}
+        assert np.array_equal(inl, ref["inliers"])
+        assert ee.max() <= TOL and eH.max() <= TOL and eb.max() <= TOL, (name, table[name])
+    oe = abs(ref["e"][0] - ref["comp_e"][0]) / ref["e"][0]
+    oH = np.linalg.norm(ref["H"][0] - ref["comp_H"][0]) / np.linalg.norm(ref["comp_H"][0])
+    table["oracle_fp64_vs_long_double"] = {"e": float(oe), "H": float(oH)}
+    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    os.makedirs(out, exist_ok=True)
+    with open(os.path.join(out, "precision_terrain.json"), "w") as f:
+        json.dump(table, f, indent=1)
+    print(json.dumps(table))
