@@ -148,6 +148,20 @@ def oracle_sample(w, budget_s=15.0, nthreads=None, target_points=30_000_000):
                        f"{dt:.1f} s wall on {nthreads} threads"), dt
 
 
+# ---------------------------------------------------------------------------- ranks
+def aggregate_over_ranks(step_ms_total, n_pair_points, device):
+    """Whole-job figures over the ranks: the slowest rank's time and the total work."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(step_ms_total), float(n_pair_points)
+    t = torch.tensor([float(step_ms_total)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(n_pair_points)], device=device, dtype=torch.float64)
+    dist.all_reduce(n)
+    return float(t.item()), float(n.item())
+
+
 # ---------------------------------------------------------------------------- small workloads
 def small_workloads(G, ctx, dev):
     """Timings of the other factor batches of the paper's pipeline on the same GPU:
@@ -308,16 +322,7 @@ def run_ours(args):
     gpu_launches = ctx.kernel_launches - launches0
     clk = clocks.stop()
     kern_ms = plan.kernel_ms(K)
-    tmax = step_ms_total
-    if ws > 1:
-        t = torch.tensor([step_ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
-        tot = torch.tensor([float(n_pp)], device=dev, dtype=torch.float64)
-        dist.all_reduce(tot)
-        total_pp = float(tot.item())
-    else:
-        total_pp = float(n_pp)
+    tmax, total_pp = aggregate_over_ranks(step_ms_total, n_pp, dev)
     value = total_pp * K / (tmax / 1e3)
     # e2e: public call with host poses in / host results out, copies in the timed region
     e2e_steps = max(3, min(K, 10))

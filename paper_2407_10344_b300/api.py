@@ -385,3 +385,30 @@ def gn_solve(ctx: Context, H: torch.Tensor, b: torch.Tensor, dim: int = None):
     ctx.call("gn_solve", ctx.lib.glim_gn_solve, ctx.h, _ptr(H), ld, H.shape[-2] * ld, _ptr(b), b.shape[-1], dim,
              count, _ptr(xi), _ptr(status), ok=(0, -6))
     return xi, status
+
+
+def shard_pairs(pairs, rank: int, world: int):
+    """Partition a factor batch across `world` GPUs by source frame: the source frames, in
+    order, are cut into `world` contiguous groups holding about the same number of pairs, and
+    rank `rank` gets the indices of the pairs whose source is in its group.  Pairs are
+    independent, so the ranks need no exchange until their (e, H, b) records are gathered;
+    a rank must hold its source frames and the voxelmaps of their targets (see frames_needed).
+    """
+    pairs = np.asarray(pairs).reshape(-1, 2)
+    if world < 1 or not (0 <= rank < world):
+        raise ValueError("bad rank / world size")
+    srcs = np.unique(pairs[:, 0])
+    counts = np.array([(pairs[:, 0] == f).sum() for f in srcs])
+    cum = np.cumsum(counts)
+    total = cum[-1] if len(cum) else 0
+    # group g holds the sources whose cumulative pair count falls in (g * total / world, ...]
+    group = np.minimum((cum - 1) * world // max(total, 1), world - 1) if total else np.zeros(0, int)
+    mine = set(srcs[group == rank].tolist())
+    return np.array([i for i, (s_, _) in enumerate(pairs) if int(s_) in mine], dtype=np.int64)
+
+
+def frames_needed(pairs, idx):
+    """Frames a rank must hold for the pairs `idx`: their sources and their targets."""
+    pairs = np.asarray(pairs).reshape(-1, 2)
+    sub = pairs[np.asarray(idx, dtype=np.int64)]
+    return sorted(set(sub[:, 0].tolist()) | set(sub[:, 1].tolist()))

@@ -14,3 +14,8 @@ if TESTS not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (B300, sm_103a)")
     config.addinivalue_line("markers", "slow: full-size parity case")
+
+
+def pytest_sessionstart(session):
+    # child processes started with "spawn" import from the repository root
+    os.environ["PYTHONPATH"] = os.pathsep.join([ROOT, TESTS] + [p for p in os.environ.get("PYTHONPATH", "").split(os.pathsep) if p])
