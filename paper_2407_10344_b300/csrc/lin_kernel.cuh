@@ -102,12 +102,22 @@ __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in,
   bool hit[LMAX];
   uint32_t hh[LMAX];  // hash level: first slot
   float4 s0[LMAX], s1[LMAX], s2[LMAX];
+  // keys: shifts of the level-0 key when the resolutions double per level, else per level
+  int k0x, k0y, k0z;
+  const bool shifted = P.M.pow2 && level0_key3(q, P.M.lv[0].inv_r, k0x, k0y, k0z);
   // one read of every level, all in flight together: a dense level reads its grid cell (the
   // record itself), a hash level its first slot (key and statistics)
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
     const LevelDev& L = P.M.lv[l];
-    hit[l] = live && (l < P.M.levels) && level_key3(q, L.inv_r, kx[l], ky[l], kz[l]);
+    if (shifted) {
+      kx[l] = k0x >> l;
+      ky[l] = k0y >> l;
+      kz[l] = k0z >> l;
+      hit[l] = live && (l < P.M.levels);
+    } else {
+      hit[l] = live && (l < P.M.levels) && level_key3(q, L.inv_r, kx[l], ky[l], kz[l]);
+    }
     if (hit[l]) {
       int64_t c;
       if (L.dense) {

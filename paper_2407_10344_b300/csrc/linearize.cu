@@ -375,7 +375,11 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
   for (size_t i = 0; i < maps.size(); ++i) {
     std::memset(&md[i], 0, sizeof(MapDev));
     md[i].levels = maps[i]->levels;
-    for (int l = 0; l < maps[i]->levels; ++l) md[i].lv[l] = maps[i]->dev(l);
+    md[i].pow2 = 1;
+    for (int l = 0; l < maps[i]->levels; ++l) {
+      md[i].lv[l] = maps[i]->dev(l);
+      if (maps[i]->inv_r[l] != std::ldexp(maps[i]->inv_r[0], -l)) md[i].pow2 = 0;
+    }
   }
   p->nmaps = int(maps.size());
   p->lmax = 1;

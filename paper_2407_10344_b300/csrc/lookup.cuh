@@ -59,11 +59,30 @@ __device__ __forceinline__ int probe_slot3(const LevelDev& L, int kx, int ky, in
   return probe_from(L, kx, ky, kz, hash3(kx, ky, kz, L.log2cap), 0);
 }
 
-// Dense grid cell of key (kx, ky, kz), or -1 outside the grid.
+// Dense grid cell of key (kx, ky, kz), or -1 outside the grid (grids have < 2^31 cells).
 __device__ __forceinline__ int64_t dense_cell(const LevelDev& L, int kx, int ky, int kz) {
   const uint32_t x = uint32_t(kx - L.ox), y = uint32_t(ky - L.oy), z = uint32_t(kz - L.oz);
   if (x >= L.nx || y >= L.ny || z >= L.nz) return -1;
-  return (int64_t(x) * L.ny + y) * L.nz + z;
+  return int64_t((x * L.ny + y) * L.nz + z);
+}
+
+// Keys of every level of a map whose resolutions are r_0 2^l (Sec. III-C): the level-0 product
+// p = q * inv_r_0 (one FP32 multiply per axis, as on every level) gives floor(p 2^-l) =
+// floor(p) >> l exactly, because inv_r_l = inv_r_0 2^-l scales the product by a power of two.
+// Valid while |p| < 2^20 on every axis and no product is so small (below 2^-100 but not
+// zero) that its scaled copy could become subnormal; otherwise false and the caller computes
+// each level.
+__device__ __forceinline__ bool level0_ok(float p) {
+  const float m = fabsf(p);
+  return m < 1048576.0f && (m >= 7.8886091e-31f || m == 0.0f);  // 2^-100
+}
+
+__device__ __forceinline__ bool level0_key3(const float3& q, float inv_r0, int& kx, int& ky, int& kz) {
+  const float px = __fmul_rn(q.x, inv_r0), py = __fmul_rn(q.y, inv_r0), pz = __fmul_rn(q.z, inv_r0);
+  kx = __float2int_rd(px);
+  ky = __float2int_rd(py);
+  kz = __float2int_rd(pz);
+  return level0_ok(px) && level0_ok(py) && level0_ok(pz);
 }
 
 // Voxel of key (kx, ky, kz) at a level: the index of its record in L.slots (dense: grid cell;

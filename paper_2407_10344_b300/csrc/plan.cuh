@@ -20,7 +20,8 @@ struct FrameDev {
 struct MapDev {
   LevelDev lv[GLIM_MAX_LEVELS];
   int32_t levels;
-  int32_t pad[3];
+  int32_t pow2;  // 1: inv_r of level l is exactly inv_r of level 0 times 2^-l
+  int32_t pad[2];
 };
 
 struct PairDev {
