@@ -30,6 +30,10 @@ sys.path.insert(0, ROOT)
 METRIC = "source points linearized/s (e+H+b) and % HBM peak; ms per global batch vs plain"
 UNIT = "points/s"
 BYTES_PER_POINT = 40  # float4 point + 6 floats covariance, read once per (pair, point)
+# DRAM bytes (read + write) per (pair, point) of the linearization kernel, from one ncu capture
+# of this kernel version on the 40-submap urban case (profiles/k_linearize_urban40_ncu_full.md),
+# scaled by the units of a launch.  Set to None when the kernel changes until it is re-measured.
+DRAM_BYTES_PER_PAIR_POINT = 11.05
 
 
 def peaks():
@@ -370,8 +374,10 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws} (independent batches per GPU, no collective)",
                    "generation_s": round(gen_s, 1)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
-                     "kernel": "k_linearize_queue (persistent)", "kernel_ms": kavg_ms,
+                     "frac": achieved / hbm_peak,
+                     "traffic": None if DRAM_BYTES_PER_PAIR_POINT is None else DRAM_BYTES_PER_PAIR_POINT * n_pp,
+                     "traffic_note": "ncu dram bytes of a 40-submap capture scaled by (pair, point) units",
+                     "kernel": "k_linearize (persistent work queue)", "kernel_ms": kavg_ms,
                      "algorithmic_bytes_per_launch": BYTES_PER_POINT * n_pp,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk else "fallback"},
         "e2e": {"value": total_pp / e2e_s if ws == 1 else n_pp / e2e_s * ws, "unit": UNIT,
