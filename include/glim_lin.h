@@ -308,6 +308,23 @@ glim_status glim_gn_solve(glim_ctx* ctx, const double* H, int32_t ldh, int64_t s
                           const double* b, int64_t stride_b, int32_t dim, int64_t count,
                           double* xi_out, int32_t* status_out);
 
+/* ---------------------------------------------------------------- small factor graphs */
+
+/* One Gauss-Newton (lambda = 0) or Levenberg-Marquardt (lambda > 0) step of a graph of
+ * matching-cost factors between nframes poses, on the device: the per-pair factors
+ * (H: device, npairs x 144, over [xi_src; xi_tgt]; b: device, npairs x 12, as produced by the
+ * linearization) are summed into the global system over all poses (pair_frames: host,
+ * npairs x 2 (source, target) frame indices), frame `fixed_frame` (-1: none) is held fixed,
+ * and (H_ff + lambda diag(H_ff)) xi_f = -b_f is solved by a dense FP64 Cholesky.  This is the
+ * step of the all-to-all submap optimisation of local mapping (Sec. V-A).  xi_out: device,
+ * nframes x 6 (zeros for the fixed frame); H_out (device, (6 nframes)^2) and b_out (device,
+ * 6 nframes) receive the assembled, undamped global system (may be NULL).  1 <= nframes <= 128.
+ * Returns GLIM_ENOTPD if the reduced system is not positive definite.  Synchronizes. */
+glim_status glim_graph_step(glim_ctx* ctx, const int32_t* pair_frames, int32_t npairs,
+                            int32_t nframes, const double* H, const double* b,
+                            int32_t fixed_frame, double lambda, double* xi_out, double* H_out,
+                            double* b_out);
+
 #ifdef __cplusplus
 }
 #endif

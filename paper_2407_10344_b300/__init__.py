@@ -5,9 +5,11 @@ this package only marshals arguments to it.  See ``api`` for the calls and ``aut
 the differentiable cost.
 """
 from .api import (ACC_FP32, ACC_FP64, ACC_KAHAN, Context, FrameData, GlimError, Plan, VoxelMap, backward,
-                  correspondences, estimate_covariances, frames_needed, gn_solve, linearize, overlap, shard_pairs,
+                  correspondences, estimate_covariances, frames_needed, gn_solve, graph_step, linearize, overlap,
+                  shard_pairs,
                   spatial_order, to_pts4)
 
 __all__ = ["ACC_FP32", "ACC_FP64", "ACC_KAHAN", "Context", "FrameData", "GlimError", "Plan", "VoxelMap",
-           "backward", "correspondences", "estimate_covariances", "frames_needed", "gn_solve", "linearize", "overlap",
+           "backward", "correspondences", "estimate_covariances", "frames_needed", "gn_solve", "graph_step", "linearize",
+           "overlap",
            "shard_pairs", "spatial_order", "to_pts4"]

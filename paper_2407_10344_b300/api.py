@@ -412,3 +412,18 @@ def frames_needed(pairs, idx):
     pairs = np.asarray(pairs).reshape(-1, 2)
     sub = pairs[np.asarray(idx, dtype=np.int64)]
     return sorted(set(sub[:, 0].tolist()) | set(sub[:, 1].tolist()))
+
+
+def graph_step(ctx: Context, pairs, nframes: int, H: torch.Tensor, b: torch.Tensor, fixed_frame: int = 0,
+               lam: float = 0.0, want_system: bool = False):
+    """Gauss-Newton / Levenberg-Marquardt step of a small factor graph (device): returns
+    xi (nframes, 6) float64 CUDA tensor, and the assembled global (H, b) if want_system."""
+    _dev(H, torch.float64, name="H")
+    _dev(b, torch.float64, name="b")
+    pf = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    xi = torch.empty((nframes, 6), dtype=torch.float64, device=H.device)
+    Hg = torch.empty((6 * nframes, 6 * nframes), dtype=torch.float64, device=H.device) if want_system else None
+    bg = torch.empty(6 * nframes, dtype=torch.float64, device=H.device) if want_system else None
+    ctx.call("graph_step", ctx.lib.glim_graph_step, ctx.h, _ptr(pf), len(pf), nframes, _ptr(H), _ptr(b),
+             int(fixed_frame), float(lam), _ptr(xi), _ptr(Hg), _ptr(bg))
+    return (xi, Hg, bg) if want_system else xi

@@ -406,3 +406,76 @@ def test_autograd_function_against_fd(G, ctx, full):
             fd = (Ep(hv) - Ep(-hv)) / (2 * hv)
             worst = max(worst, abs(fd - grads[k, a]) / max(1.0, abs(grads[k, a])))
     assert worst <= 2e-3
+
+
+# ---------------------------------------------------------------------------- small factor graph
+def test_graph_step_assembly_and_solve_against_numpy(G, ctx):
+    s = synth.Stream(77, "graph")
+    n, P = 7, 18
+    pairs = []
+    while len(pairs) < P:
+        a, b_ = s.integers(2, 0, n)
+        if a != b_:
+            pairs.append((int(a), int(b_)))
+    Hs, bs = [], []
+    for _ in range(P):
+        J = s.normal(12 * 40).reshape(40, 12)
+        Hs.append(J.T @ J)
+        bs.append(s.normal(12))
+    H = torch.as_tensor(np.stack(Hs), device="cuda")
+    b = torch.as_tensor(np.stack(bs), device="cuda")
+    for fixed, lam in ((0, 0.0), (3, 1e-3), (-1, 0.5)):
+        xi, Hg, bg = G.graph_step(ctx, pairs, n, H, b, fixed_frame=fixed, lam=lam, want_system=True)
+        Hn = np.zeros((6 * n, 6 * n))
+        bn = np.zeros(6 * n)
+        for p, (a, c) in enumerate(pairs):  # the global system, block by block, pairs in order
+            for (ra, fa) in ((0, a), (6, c)):
+                bn[6 * fa:6 * fa + 6] += bs[p][ra:ra + 6]
+                for (cb, fb) in ((0, a), (6, c)):
+                    Hn[6 * fa:6 * fa + 6, 6 * fb:6 * fb + 6] += Hs[p][ra:ra + 6, cb:cb + 6]
+        np.testing.assert_allclose(Hg.cpu().numpy(), Hn, rtol=1e-14, atol=1e-12)
+        np.testing.assert_allclose(bg.cpu().numpy(), bn, rtol=1e-14, atol=1e-12)
+        free = [i for i in range(6 * n) if fixed < 0 or not (6 * fixed <= i < 6 * fixed + 6)]
+        A = Hn[np.ix_(free, free)]
+        A = A + lam * np.diag(np.diag(A))
+        x = np.zeros(6 * n)
+        x[free] = np.linalg.solve(A, -bn[free])
+        np.testing.assert_allclose(xi.cpu().numpy().reshape(-1), x, rtol=1e-9, atol=1e-9 * np.abs(x).max())
+    # relative-pose factors alone leave the gauge free: not positive definite without a fixed frame
+    with pytest.raises(G.GlimError, match="ENOTPD"):
+        gh = torch.zeros((1, 144), dtype=torch.float64, device="cuda")
+        G.graph_step(ctx, [(0, 1)], 2, gh.view(1, 12, 12), torch.zeros((1, 12), dtype=torch.float64, device="cuda"),
+                     fixed_frame=-1)
+
+
+def test_local_mapping_all_to_all_converges(G, ctx):
+    """All-to-all factors between 5 corridor keyframes with perturbed poses (frame 0 fixed):
+    device Gauss-Newton steps of the whole graph recover the true relative poses."""
+    from gpu_helpers import Prepared
+    from paper_2407_10344_b300.autograd import retract
+    w = synth.corridor(n_kf=5, n_cur=20000, kf_range=(20000, 25000))
+    kf = list(range(1, 6))
+    pairs = np.array([[i, j] for i in kf for j in kf if i != j], np.int32)
+    w.pairs = pairs
+    P = Prepared(ctx, w)
+    s = synth.Stream(5, "lm")
+    poses = w.poses_true.copy()
+    for f in kf[1:]:
+        poses[f] = synth.perturb_pose(poses[f], 0.5, 0.05, s)
+    plan = G.Plan(ctx, P.gframes, P.gmaps, pairs)
+    idx = {f: i for i, f in enumerate(kf)}
+    local_pairs = [(idx[a], idx[b_]) for a, b_ in pairs]
+    costs = []
+    for _ in range(8):
+        e, H, b, _ = plan.linearize(poses)
+        costs.append(e.sum())
+        xi = G.graph_step(ctx, local_pairs, len(kf), torch.as_tensor(H, device="cuda"),
+                          torch.as_tensor(b, device="cuda"), fixed_frame=0).cpu().numpy()
+        for f in kf:
+            poses[f] = retract(poses[f], xi[idx[f]])
+    assert costs[-1] < costs[0]
+    for f in kf[1:]:
+        D = O.compose(O.inverse(O.compose(O.inverse(w.poses_true[kf[0]]), w.poses_true[f])),
+                      O.compose(O.inverse(poses[kf[0]]), poses[f]))
+        ang = math.degrees(math.acos(min(1.0, (np.trace(D[:, :3]) - 1) / 2)))
+        assert ang < 0.05 and np.linalg.norm(D[:, 3]) < 0.01, (f, ang, np.linalg.norm(D[:, 3]))
