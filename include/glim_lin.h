@@ -170,6 +170,21 @@ glim_status glim_build_voxelmap_ex(glim_ctx* ctx, const float* pts4, const float
                                    const double* resolutions, int32_t levels, int32_t layout,
                                    glim_vmap** out);
 void glim_vmap_free(glim_vmap* vmap);
+/* Incremental insertion (NEXT: submaps grow as frames are merged into them, Sec. V-A; the
+ * voxel statistics are the running means of Sec. III-C).  Adds n map-frame points (pts4 /
+ * cov6 laid out and aligned as for glim_build_voxelmap, device memory, borrowed) to every
+ * level of vmap.  Per voxel the FP64 sums of the existing members and of the new points
+ * are added and the means recomputed; the canonical ids are again the ranks of the keys,
+ * so the result equals glim_build_voxelmap of all points ever inserted (keys, ids and
+ * counts exactly; statistics up to the order of the FP64 additions).  layout as for
+ * glim_build_voxelmap_ex (0 re-decides from the grown key box).  The device is
+ * synchronised before the old tables are freed.  Plans created on vmap before the call
+ * fail with GLIM_EINVAL afterwards (their table pointers are stale): create new ones.
+ * On error vmap is unchanged: GLIM_EINVAL for bad arguments or non-finite input,
+ * GLIM_ERANGE for a key outside [-2^20, 2^20), GLIM_EINVAL for layout 1 when the grown
+ * box exceeds the dense limit, GLIM_ENOMEM. */
+glim_status glim_vmap_insert(glim_ctx* ctx, glim_vmap* vmap, const float* pts4, const float* cov6,
+                             int64_t n, int32_t layout);
 /* Number of occupied voxels, table capacity (hash slots, or grid cells for a dense level)
  * and longest probe sequence (1 for a dense level) of a level. */
 glim_status glim_vmap_info(const glim_vmap* vmap, int32_t level, int64_t* n_voxels,

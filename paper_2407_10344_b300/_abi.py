@@ -45,6 +45,7 @@ SIGNATURES = {
     "glim_build_voxelmap": (_i32, [_vp, _vp, _vp, _i64, _vp, _i32, C.POINTER(_vp)]),
     "glim_build_voxelmap_ex": (_i32, [_vp, _vp, _vp, _i64, _vp, _i32, _i32, C.POINTER(_vp)]),
     "glim_vmap_free": (None, [_vp]),
+    "glim_vmap_insert": (_i32, [_vp, _vp, _vp, _vp, _i64, _i32]),
     "glim_vmap_is_dense": (_i32, [_vp, _i32]),
     "glim_vmap_info": (_i32, [_vp, _i32, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i32)]),
     "glim_vmap_export": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),

@@ -165,6 +165,19 @@ class VoxelMap:
     def is_dense(self, level):
         return bool(self.ctx.lib.glim_vmap_is_dense(self.h, level))
 
+    def insert(self, pts4: torch.Tensor, cov6: torch.Tensor, layout: str = "auto"):
+        """Add map-frame points to every level (running FP64 sums per voxel, ids re-ranked);
+        the result equals a build from all points inserted so far.  Plans created on this
+        map before the call must be recreated."""
+        _dev(pts4, torch.float32, 4, "pts4")
+        _dev(cov6, torch.float32, 6, "cov6")
+        if pts4.shape[0] != cov6.shape[0]:
+            raise ValueError("pts4 and cov6 differ in length")
+        lay = {"auto": 0, "dense": 1, "hash": 2}[layout]
+        self.ctx.call("vmap_insert", self.ctx.lib.glim_vmap_insert, self.ctx.h, self.h, _ptr(pts4), _ptr(cov6),
+                      pts4.shape[0], lay)
+        return self
+
     def export(self, level):
         m = self.info(level)["n_voxels"]
         dev = torch.device("cuda", self.ctx.device)

@@ -158,6 +158,8 @@ struct glim_vmap {
   float* vmean[GLIM_MAX_LEVELS] = {nullptr};              // n_vox x 3
   float* vcov[GLIM_MAX_LEVELS] = {nullptr};               // n_vox x 6
   int32_t* vcount[GLIM_MAX_LEVELS] = {nullptr};
+  double* vsum[GLIM_MAX_LEVELS] = {nullptr};              // n_vox x 9 FP64 sums (mean 3, cov 6)
+  uint64_t version = 0;  // incremented whenever the tables are replaced (insertion)
   LevelDev dev(int l) const {
     LevelDev d;
     d.slots = slots[l];
@@ -215,5 +217,8 @@ struct SortedCells {
 };
 glim_status sort_into_cells(glim_ctx* ctx, const float* pts4, int64_t n, float inv_r, SortedCells& out,
                             bool range_is_error);
+// Segments (unique keys and their first positions) of an already sorted key array; fills
+// out.cell_start (m + 1), out.cell_key (m) and out.m.  EMPTY keys (sorted last) are excluded.
+glim_status segment_sorted(glim_ctx* ctx, const unsigned long long* key_sorted, int64_t n, SortedCells& out);
 
 inline int ceil_div_i(int64_t a, int64_t b) { return int((a + b - 1) / b); }

@@ -270,6 +270,15 @@ void plan_pack_poses(glim_plan* p, const double* poses12) {
 
 namespace {
 
+// The plan holds device pointers to its maps' tables; a map changed since (an insertion
+// frees and replaces them) makes the plan unusable.
+glim_status maps_current(glim_plan* p) {
+  for (const auto& mv : p->map_versions)
+    if (mv.first->version != mv.second)
+      return set_error(p->ctx, GLIM_EINVAL, "plan: a target voxelmap changed after the plan was created");
+  return GLIM_OK;
+}
+
 glim_status capture(glim_plan* p, bool full, cudaGraphExec_t* out) {
   glim_ctx* ctx = p->ctx;
   cudaGraph_t g = nullptr;
@@ -382,6 +391,7 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
     }
   }
   p->nmaps = int(maps.size());
+  for (const glim_vmap* m : maps) p->map_versions.emplace_back(m, m->version);
   p->lmax = 1;
   for (const glim_vmap* m : maps) p->lmax = std::max(p->lmax, m->levels);
   auto fail = [&](glim_status s) {
@@ -440,6 +450,7 @@ extern "C" glim_status glim_plan_set_poses(glim_plan* p, const double* poses12) 
 
 extern "C" glim_status glim_plan_launch(glim_plan* p) {
   if (!p) return GLIM_EINVAL;
+  if (maps_current(p) != GLIM_OK) return GLIM_EINVAL;
   glim_ctx* ctx = p->ctx;
   if (!p->use_graph) return plan_enqueue_kernels(p);
   if (!p->g_dev) {
@@ -453,6 +464,7 @@ extern "C" glim_status glim_plan_launch(glim_plan* p) {
 
 extern "C" glim_status glim_plan_launch_timed(glim_plan* p, int32_t slot) {
   if (!p || slot < 0 || slot >= 4096) return GLIM_EINVAL;
+  if (maps_current(p) != GLIM_OK) return GLIM_EINVAL;
   glim_ctx* ctx = p->ctx;
   while (int(p->ev.size()) < 2 * (slot + 1)) {
     cudaEvent_t e;
@@ -489,6 +501,7 @@ extern "C" glim_status glim_plan_device_outputs(glim_plan* p, double** e, double
 extern "C" glim_status glim_plan_linearize(glim_plan* p, const double* poses12, double* e_out, double* H_out,
                                            double* b_out, int64_t* inliers_out) {
   if (!p || !poses12) return GLIM_EINVAL;
+  if (maps_current(p) != GLIM_OK) return GLIM_EINVAL;
   glim_ctx* ctx = p->ctx;
   if (p->npairs > 0 && (!e_out || !H_out || !b_out))
     return set_error(ctx, GLIM_EINVAL, "plan_linearize: null output");
@@ -522,6 +535,7 @@ extern "C" glim_status glim_plan_get_opts(const glim_plan* p, glim_lin_opts* out
 extern "C" glim_status glim_plan_autotune(glim_plan* p, const double* poses12, int32_t iters, glim_lin_opts* best_out,
                                           float* best_ms_out) {
   if (!p || !poses12 || iters < 1) return GLIM_EINVAL;
+  if (maps_current(p) != GLIM_OK) return GLIM_EINVAL;
   glim_ctx* ctx = p->ctx;
   glim_status st = glim_plan_set_poses(p, poses12);
   if (st != GLIM_OK) return st;

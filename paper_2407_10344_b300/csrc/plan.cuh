@@ -1,6 +1,7 @@
 // plan.cuh -- device descriptions of a factor batch (frames, voxelmaps, pairs, work items)
 // and the plan object that owns them; shared by the forward and backward kernels.
 #pragma once
+#include <utility>
 #include <vector>
 
 #include "lookup.cuh"
@@ -76,6 +77,7 @@ struct glim_plan {
   MapDev* d_maps = nullptr;
   PairDev* d_pairs = nullptr;
   int nmaps = 0;
+  std::vector<std::pair<const glim_vmap*, uint64_t>> map_versions;  // target maps as the plan saw them
   int lmax = 1;  // most levels of any target map (kernel template parameter)
   // work list (depends on the tile size)
   Item* d_items = nullptr;

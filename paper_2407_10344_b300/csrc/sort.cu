@@ -342,9 +342,16 @@ glim_status sort_into_cells(glim_ctx* ctx, const float* pts4, int64_t n, float i
   if (st != GLIM_OK) return st;
   st = radix_sort_pairs(ctx, keys.p, idx.p, out.key_sorted.p, out.idx_sorted.p, n, varying);
   if (st != GLIM_OK) return st;
+  return segment_sorted(ctx, out.key_sorted.p, n, out);
+}
+
+glim_status segment_sorted(glim_ctx* ctx, const unsigned long long* key_sorted, int64_t n, SortedCells& out) {
+  out.m = 0;
+  if (n <= 0) return GLIM_OK;
+  glim_status st = GLIM_OK;
   DevBuf<uint32_t> head;
   GLIM_CUDA(ctx, head.alloc(n + 1, ctx->stream));
-  k_heads<<<ceil_div_i(n, 256), 256, 0, ctx->stream>>>(out.key_sorted.p, n, head.p);
+  k_heads<<<ceil_div_i(n, 256), 256, 0, ctx->stream>>>(key_sorted, n, head.p);
   GLIM_LAUNCHED(ctx);
   GLIM_CUDA(ctx, cudaMemsetAsync(head.p + n, 0, sizeof(uint32_t), ctx->stream));
   st = scan_exclusive_u32(ctx, head.p, head.p, n + 1);
@@ -359,10 +366,10 @@ glim_status sort_into_cells(glim_ctx* ctx, const float* pts4, int64_t n, float i
     GLIM_CUDA(ctx, cudaMemsetAsync(out.cell_start.p, 0, sizeof(uint32_t), ctx->stream));
     return GLIM_OK;
   }
-  k_cell_starts<<<ceil_div_i(n, 256), 256, 0, ctx->stream>>>(out.key_sorted.p, head.p, n, out.cell_start.p,
+  k_cell_starts<<<ceil_div_i(n, 256), 256, 0, ctx->stream>>>(key_sorted, head.p, n, out.cell_start.p,
                                                              out.cell_key.p);
   GLIM_LAUNCHED(ctx);
-  k_cell_end<<<ceil_div_i(n, 256), 256, 0, ctx->stream>>>(out.key_sorted.p, n, out.cell_start.p, m);
+  k_cell_end<<<ceil_div_i(n, 256), 256, 0, ctx->stream>>>(key_sorted, n, out.cell_start.p, m);
   GLIM_LAUNCHED(ctx);
   return GLIM_OK;
 }

@@ -18,7 +18,7 @@ __global__ void k_voxel_stats(const float4* __restrict__ pts, const float* __res
                               const uint32_t* __restrict__ idx_sorted, const uint32_t* __restrict__ cell_start,
                               const unsigned long long* __restrict__ cell_key, int64_t m,
                               unsigned long long* __restrict__ vkey, float* __restrict__ vmean,
-                              float* __restrict__ vcov, int32_t* __restrict__ vcount,
+                              float* __restrict__ vcov, int32_t* __restrict__ vcount, double* __restrict__ vsum,
                               unsigned int* __restrict__ status) {
   const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (v >= m) return;
@@ -42,6 +42,7 @@ __global__ void k_voxel_stats(const float4* __restrict__ pts, const float* __res
     s[8] += c2.y;
   }
   const double inv = 1.0 / double(e - b);
+  for (int c = 0; c < 9; ++c) vsum[9 * v + c] = s[c];
   vkey[v] = cell_key[v];
   for (int c = 0; c < 3; ++c) vmean[3 * v + c] = float(s[c] * inv);
   for (int c = 0; c < 6; ++c) vcov[6 * v + c] = float(s[3 + c] * inv);
@@ -82,6 +83,38 @@ __global__ void k_hash_insert(const unsigned long long* __restrict__ vkey, const
     h = (h + 1u) & mask;
   }
   atomicOr(status, GLIM_DS_HASHFULL);
+}
+
+// Merge of two canonical voxel sets: entries [0, m_old) are the existing voxels, [m_old, ...)
+// the voxels of the inserted points; `src` lists them in key order (equal keys: existing
+// first), `start` delimits the merged voxels.  Sums are added in that order.
+__global__ void k_merge_voxels(const uint32_t* __restrict__ src, const uint32_t* __restrict__ start,
+                               const unsigned long long* __restrict__ mkey, int64_t m, int64_t m_old,
+                               const double* __restrict__ sum_old, const int32_t* __restrict__ cnt_old,
+                               const double* __restrict__ sum_new, const int32_t* __restrict__ cnt_new,
+                               unsigned long long* __restrict__ vkey, float* __restrict__ vmean,
+                               float* __restrict__ vcov, int32_t* __restrict__ vcount, double* __restrict__ vsum) {
+  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v >= m) return;
+  double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t cnt = 0;
+  for (uint32_t j = start[v]; j < start[v + 1]; ++j) {
+    const int64_t i = src[j];
+    const double* a = i < m_old ? sum_old + 9 * i : sum_new + 9 * (i - m_old);
+    cnt += i < m_old ? cnt_old[i] : cnt_new[i - m_old];
+    for (int c = 0; c < 9; ++c) s[c] += a[c];
+  }
+  const double inv = 1.0 / double(cnt);
+  vkey[v] = mkey[v];
+  for (int c = 0; c < 9; ++c) vsum[9 * v + c] = s[c];
+  for (int c = 0; c < 3; ++c) vmean[3 * v + c] = float(s[c] * inv);
+  for (int c = 0; c < 6; ++c) vcov[6 * v + c] = float(s[3 + c] * inv);
+  vcount[v] = int32_t(cnt);
+}
+
+__global__ void k_iota_offset(uint32_t* __restrict__ a, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = uint32_t(i);
 }
 
 __global__ void k_key_bbox(const unsigned long long* __restrict__ vkey, int64_t m, int* __restrict__ bb) {
@@ -192,16 +225,57 @@ int log2_ceil(int64_t x) {
   return l;
 }
 
+void free_level(glim_vmap* vm, int l) {
+  cudaFree(vm->grid[l]);
+  cudaFree(vm->slots[l]);
+  cudaFree(vm->slot_id[l]);
+  cudaFree(vm->vkey[l]);
+  cudaFree(vm->vmean[l]);
+  cudaFree(vm->vcov[l]);
+  cudaFree(vm->vcount[l]);
+  cudaFree(vm->vsum[l]);
+  vm->grid[l] = nullptr;
+  vm->slots[l] = nullptr;
+  vm->slot_id[l] = nullptr;
+  vm->vkey[l] = nullptr;
+  vm->vmean[l] = nullptr;
+  vm->vcov[l] = nullptr;
+  vm->vcount[l] = nullptr;
+  vm->vsum[l] = nullptr;
+}
+
 void free_levels(glim_vmap* vm) {
-  for (int l = 0; l < GLIM_MAX_LEVELS; ++l) {
-    cudaFree(vm->grid[l]);
-    cudaFree(vm->slots[l]);
-    cudaFree(vm->slot_id[l]);
-    cudaFree(vm->vkey[l]);
-    cudaFree(vm->vmean[l]);
-    cudaFree(vm->vcov[l]);
-    cudaFree(vm->vcount[l]);
+  for (int l = 0; l < GLIM_MAX_LEVELS; ++l) free_level(vm, l);
+}
+
+// Level l of src replaces level l of dst (whose arrays are freed); src gives up its arrays.
+void move_level(glim_vmap* dst, glim_vmap* src, int l) {
+  free_level(dst, l);
+  dst->n_vox[l] = src->n_vox[l];
+  dst->cap[l] = src->cap[l];
+  dst->log2cap[l] = src->log2cap[l];
+  dst->max_probe[l] = src->max_probe[l];
+  dst->dense[l] = src->dense[l];
+  for (int c = 0; c < 3; ++c) {
+    dst->org[l][c] = src->org[l][c];
+    dst->dim[l][c] = src->dim[l][c];
   }
+  dst->slots[l] = src->slots[l];
+  dst->slot_id[l] = src->slot_id[l];
+  dst->grid[l] = src->grid[l];
+  dst->vkey[l] = src->vkey[l];
+  dst->vmean[l] = src->vmean[l];
+  dst->vcov[l] = src->vcov[l];
+  dst->vcount[l] = src->vcount[l];
+  dst->vsum[l] = src->vsum[l];
+  src->slots[l] = nullptr;
+  src->slot_id[l] = nullptr;
+  src->grid[l] = nullptr;
+  src->vkey[l] = nullptr;
+  src->vmean[l] = nullptr;
+  src->vcov[l] = nullptr;
+  src->vcount[l] = nullptr;
+  src->vsum[l] = nullptr;
 }
 
 // Dense grids (48 bytes per cell) are used when the key bounding box has at most this many
@@ -210,25 +284,82 @@ constexpr int64_t DENSE_CELLS_PER_VOXEL = 256;
 constexpr int64_t DENSE_CELLS_ALLOWANCE = int64_t(1) << 22;
 constexpr int64_t DENSE_MAX_BYTES = int64_t(32) << 30;
 
-glim_status build_level(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n, glim_vmap* vm, int l,
-                        int layout) {
+// Canonical voxel arrays (sorted keys, FP64 sums, counts, means, covariances) of a point set
+// at one resolution; the arrays are allocated here and owned by the caller.
+struct Canon {
+  int64_t m = 0;
+  unsigned long long* key = nullptr;
+  double* sum = nullptr;
+  int32_t* count = nullptr;
+  float* mean = nullptr;
+  float* cov = nullptr;
+  void release() {
+    cudaFree(key);
+    cudaFree(sum);
+    cudaFree(count);
+    cudaFree(mean);
+    cudaFree(cov);
+    key = nullptr;
+    sum = nullptr;
+    count = nullptr;
+    mean = nullptr;
+    cov = nullptr;
+  }
+};
+
+glim_status canon_alloc(glim_ctx* ctx, Canon& c, int64_t m) {
+  c.m = m;
+  const size_t mm = size_t(std::max<int64_t>(m, 1));
+  GLIM_CUDA(ctx, cudaMalloc(&c.key, mm * sizeof(unsigned long long)));
+  GLIM_CUDA(ctx, cudaMalloc(&c.sum, mm * 9 * sizeof(double)));
+  GLIM_CUDA(ctx, cudaMalloc(&c.count, mm * sizeof(int32_t)));
+  GLIM_CUDA(ctx, cudaMalloc(&c.mean, mm * 3 * sizeof(float)));
+  GLIM_CUDA(ctx, cudaMalloc(&c.cov, mm * 6 * sizeof(float)));
+  return GLIM_OK;
+}
+
+glim_status canon_from_points(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n, float inv_r, Canon& c) {
   SortedCells cells;
-  glim_status st = sort_into_cells(ctx, pts4, n, vm->inv_r[l], cells, true);
+  glim_status st = sort_into_cells(ctx, pts4, n, inv_r, cells, true);
   if (st != GLIM_OK) return st;
   st = take_device_status(ctx, "voxel keys");
   if (st != GLIM_OK) return st;
-  const int64_t m = cells.m;
-  vm->n_vox[l] = m;
-  GLIM_CUDA(ctx, cudaMalloc(&vm->vkey[l], std::max<int64_t>(m, 1) * sizeof(unsigned long long)));
-  GLIM_CUDA(ctx, cudaMalloc(&vm->vmean[l], std::max<int64_t>(m, 1) * 3 * sizeof(float)));
-  GLIM_CUDA(ctx, cudaMalloc(&vm->vcov[l], std::max<int64_t>(m, 1) * 6 * sizeof(float)));
-  GLIM_CUDA(ctx, cudaMalloc(&vm->vcount[l], std::max<int64_t>(m, 1) * sizeof(int32_t)));
-  if (m > 0) {
-    k_voxel_stats<<<ceil_div_i(m, 128), 128, 0, ctx->stream>>>(
-        reinterpret_cast<const float4*>(pts4), cov6, cells.idx_sorted.p, cells.cell_start.p, cells.cell_key.p, m,
-        vm->vkey[l], vm->vmean[l], vm->vcov[l], vm->vcount[l], ctx->d_status);
+  st = canon_alloc(ctx, c, cells.m);
+  if (st != GLIM_OK) return st;
+  if (c.m > 0) {
+    k_voxel_stats<<<ceil_div_i(c.m, 128), 128, 0, ctx->stream>>>(
+        reinterpret_cast<const float4*>(pts4), cov6, cells.idx_sorted.p, cells.cell_start.p, cells.cell_key.p, c.m,
+        c.key, c.mean, c.cov, c.count, c.sum, ctx->d_status);
     GLIM_LAUNCHED(ctx);
   }
+  return take_device_status(ctx, "voxel statistics");
+}
+
+void adopt_canon(glim_vmap* vm, int l, Canon& c) {
+  vm->n_vox[l] = c.m;
+  vm->vkey[l] = c.key;
+  vm->vsum[l] = c.sum;
+  vm->vcount[l] = c.count;
+  vm->vmean[l] = c.mean;
+  vm->vcov[l] = c.cov;
+  c.key = nullptr;
+  c.sum = nullptr;
+  c.count = nullptr;
+  c.mean = nullptr;
+  c.cov = nullptr;
+}
+
+// Lookup tables of a level (dense grid or hash) from its canonical arrays; replaces any
+// existing tables of the level.
+glim_status build_tables(glim_ctx* ctx, glim_vmap* vm, int l, int layout) {
+  cudaFree(vm->slots[l]);
+  cudaFree(vm->slot_id[l]);
+  cudaFree(vm->grid[l]);
+  vm->slots[l] = nullptr;
+  vm->slot_id[l] = nullptr;
+  vm->grid[l] = nullptr;
+  vm->dense[l] = 0;
+  const int64_t m = vm->n_vox[l];
   // dense grid over the key bounding box when it is small enough (or requested)
   int bb[6] = {0, 0, 0, -1, -1, -1};
   if (m > 0) {
@@ -292,6 +423,78 @@ glim_status build_level(glim_ctx* ctx, const float* pts4, const float* cov6, int
   return take_device_status(ctx, "voxel statistics / hash insert");
 }
 
+glim_status build_level(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n, glim_vmap* vm, int l,
+                        int layout) {
+  Canon c;
+  glim_status st = canon_from_points(ctx, pts4, cov6, n, vm->inv_r[l], c);
+  if (st != GLIM_OK) {
+    cudaStreamSynchronize(ctx->stream);
+    c.release();
+    return st;
+  }
+  adopt_canon(vm, l, c);
+  return build_tables(ctx, vm, l, layout);
+}
+
+// Level l of `out` = level l of `vm` with the points added: the canonical voxels of the new
+// points are merged with the existing ones by a stable sort of the concatenated keys
+// (existing entries first), their FP64 sums added, and the tables rebuilt.  The ids are
+// again the ranks of the keys, so the result equals a build from all points up to the
+// order of the FP64 additions.
+glim_status insert_level(glim_ctx* ctx, const glim_vmap* vm, glim_vmap* out, int l, const float* pts4,
+                         const float* cov6, int64_t n, int layout) {
+  Canon add, merged;
+  auto fail = [&](glim_status st) {
+    cudaStreamSynchronize(ctx->stream);
+    add.release();
+    merged.release();
+    return st;
+  };
+  glim_status st = canon_from_points(ctx, pts4, cov6, n, vm->inv_r[l], add);
+  if (st != GLIM_OK) return fail(st);
+  const int64_t m0 = vm->n_vox[l], m1 = add.m, mt = m0 + m1;
+  if (mt > 0x7FFFFFFFll) return fail(set_error(ctx, GLIM_EINVAL, "vmap_insert: too many voxels"));
+  SortedCells seg;
+  {
+    DevBuf<unsigned long long> ck, ks;
+    DevBuf<uint32_t> cv, vs;
+    const size_t mm = size_t(std::max<int64_t>(mt, 1));
+    if (ck.alloc(mm, ctx->stream) != cudaSuccess || ks.alloc(mm, ctx->stream) != cudaSuccess ||
+        cv.alloc(mm, ctx->stream) != cudaSuccess || vs.alloc(mm, ctx->stream) != cudaSuccess)
+      return fail(set_error(ctx, GLIM_ENOMEM, "vmap_insert: device allocation failed"));
+    if (m0 > 0 && cudaMemcpyAsync(ck.p, vm->vkey[l], m0 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                                  ctx->stream) != cudaSuccess)
+      return fail(set_error(ctx, GLIM_ECUDA, "vmap_insert: copy failed"));
+    if (m1 > 0 && cudaMemcpyAsync(ck.p + m0, add.key, m1 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                                  ctx->stream) != cudaSuccess)
+      return fail(set_error(ctx, GLIM_ECUDA, "vmap_insert: copy failed"));
+    if (mt > 0) {
+      k_iota_offset<<<ceil_div_i(mt, 256), 256, 0, ctx->stream>>>(cv.p, mt);
+      if (cudaGetLastError() != cudaSuccess) return fail(set_error(ctx, GLIM_ECUDA, "vmap_insert: launch failed"));
+      ctx->launches += 1;
+      unsigned long long varying = 0;
+      st = key_varying_bits(ctx, ck.p, mt, &varying);
+      if (st == GLIM_OK) st = radix_sort_pairs(ctx, ck.p, cv.p, ks.p, vs.p, mt, varying);
+      if (st == GLIM_OK) st = segment_sorted(ctx, ks.p, mt, seg);
+      if (st != GLIM_OK) return fail(st);
+    }
+    st = canon_alloc(ctx, merged, seg.m);
+    if (st != GLIM_OK) return fail(st);
+    if (seg.m > 0) {
+      k_merge_voxels<<<ceil_div_i(seg.m, 128), 128, 0, ctx->stream>>>(
+          vs.p, seg.cell_start.p, seg.cell_key.p, seg.m, m0, vm->vsum[l], vm->vcount[l], add.sum, add.count,
+          merged.key, merged.mean, merged.cov, merged.count, merged.sum);
+      if (cudaGetLastError() != cudaSuccess) return fail(set_error(ctx, GLIM_ECUDA, "vmap_insert: launch failed"));
+      ctx->launches += 1;
+    }
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+      return fail(set_error(ctx, GLIM_ECUDA, "vmap_insert: merge failed"));
+  }
+  add.release();
+  adopt_canon(out, l, merged);
+  return build_tables(ctx, out, l, layout);
+}
+
 }  // namespace
 
 extern "C" glim_status glim_build_voxelmap(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n,
@@ -329,6 +532,43 @@ extern "C" glim_status glim_build_voxelmap_ex(glim_ctx* ctx, const float* pts4, 
     }
   }
   *out = vm;
+  ctx->err.clear();
+  return GLIM_OK;
+}
+
+extern "C" glim_status glim_vmap_insert(glim_ctx* ctx, glim_vmap* vm, const float* pts4, const float* cov6, int64_t n,
+                                        int32_t layout) {
+  if (!ctx || !vm) return GLIM_EINVAL;
+  if (layout < 0 || layout > 2) return set_error(ctx, GLIM_EINVAL, "vmap_insert: layout must be 0, 1 or 2");
+  if (n < 0 || (n > 0 && (!pts4 || !cov6)))
+    return set_error(ctx, GLIM_EINVAL, "vmap_insert: bad arguments (n=%lld)", (long long)n);
+  if (n > 0x7FFFFFFFll) return set_error(ctx, GLIM_EINVAL, "vmap_insert: n too large");
+  if ((reinterpret_cast<uintptr_t>(pts4) & 15) || (reinterpret_cast<uintptr_t>(cov6) & 7))
+    return set_error(ctx, GLIM_EINVAL, "vmap_insert: pts4 must be 16-byte and cov6 8-byte aligned");
+  if (vm->device != ctx->device) return set_error(ctx, GLIM_EINVAL, "vmap_insert: map and context devices differ");
+  GLIM_CUDA(ctx, cudaSetDevice(ctx->device));
+  // every level is rebuilt into a scratch map first, so that a failure leaves vm unchanged
+  glim_vmap tmp;
+  tmp.device = vm->device;
+  tmp.levels = vm->levels;
+  for (int l = 0; l < vm->levels; ++l) {
+    tmp.res[l] = vm->res[l];
+    tmp.inv_r[l] = vm->inv_r[l];
+    glim_status st = insert_level(ctx, vm, &tmp, l, pts4, cov6, n, layout);
+    if (st != GLIM_OK) {
+      cudaStreamSynchronize(ctx->stream);
+      free_levels(&tmp);
+      return st;
+    }
+  }
+  // no launch on any stream may still read the old tables when they are freed
+  const cudaError_t ce = cudaDeviceSynchronize();
+  if (ce != cudaSuccess) {
+    free_levels(&tmp);
+    return cuda_check(ctx, ce, "vmap_insert: cudaDeviceSynchronize");
+  }
+  for (int l = 0; l < vm->levels; ++l) move_level(vm, &tmp, l);
+  ++vm->version;
   ctx->err.clear();
   return GLIM_OK;
 }
