@@ -97,7 +97,12 @@ typedef struct {
  *                     a work item (tile) covers block * pts_per_thread points of one pair.
  *   blocks_per_sm     resident blocks per SM of the persistent kernel (default: occupancy).
  *   persistent        1 (default) = one persistent kernel over an atomic work queue;
- *                     2 = one block per work item (hardware scheduling). */
+ *                     2 = one block per work item (hardware scheduling).
+ *   kernel            0 (default) = the dense-grid kernel when every level of every target
+ *                     map is a dense grid, else the general kernel; 1 = the general kernel
+ *                     (dense grids and hash tables); 2 = the dense-grid kernel (GLIM_EINVAL
+ *                     if a target level is a hash table).  Both give the same results.
+ *   reserved          must be 0. */
 typedef struct {
   int32_t validate_surface;
   int32_t accum_mode;
@@ -105,7 +110,8 @@ typedef struct {
   int32_t pts_per_thread;
   int32_t blocks_per_sm;
   int32_t persistent;
-  int32_t reserved[2];
+  int32_t kernel;
+  int32_t reserved;
 } glim_lin_opts;
 
 /* ---------------------------------------------------------------- context */

@@ -31,7 +31,7 @@ class Pair(C.Structure):
 
 class LinOpts(C.Structure):
     _fields_ = [("validate_surface", _i32), ("accum_mode", _i32), ("block", _i32), ("pts_per_thread", _i32),
-                ("blocks_per_sm", _i32), ("persistent", _i32), ("reserved", _i32 * 2)]
+                ("blocks_per_sm", _i32), ("persistent", _i32), ("kernel", _i32), ("reserved", _i32)]
 
 
 SIGNATURES = {

@@ -238,9 +238,15 @@ def _pairs(pairs, vmaps):
     return arr, len(pairs)
 
 
+KERNELS = {"auto": 0, "general": 1, "dense": 2}
+
+
 def _opts(validate_surface=False, accum_mode=ACC_FP64, block=0, pts_per_thread=0, blocks_per_sm=0,
-          persistent=0):
+          persistent=0, kernel="auto"):
+    """kernel: "auto" (the dense-grid kernel when every target level is a dense grid),
+    "general" or "dense"."""
     o = _abi.LinOpts()
+    o.kernel = KERNELS[kernel]
     o.validate_surface = int(validate_surface)
     o.accum_mode = int(accum_mode)
     o.block = int(block)
@@ -335,8 +341,10 @@ class Plan:
     def opts(self):
         o = _abi.LinOpts()
         self.ctx.call("plan_get_opts", self.ctx.lib.glim_plan_get_opts, self.h, C.byref(o))
+        kernels = {v: k for k, v in KERNELS.items()}
         return dict(validate_surface=o.validate_surface, accum_mode=o.accum_mode, block=o.block,
-                    pts_per_thread=o.pts_per_thread, blocks_per_sm=o.blocks_per_sm, persistent=o.persistent)
+                    pts_per_thread=o.pts_per_thread, blocks_per_sm=o.blocks_per_sm, persistent=o.persistent,
+                    kernel=kernels[o.kernel])
 
     def close(self):
         if getattr(self, "h", None):

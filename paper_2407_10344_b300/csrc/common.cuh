@@ -148,7 +148,8 @@ struct glim_vmap {
   int64_t cap[GLIM_MAX_LEVELS] = {0};
   int32_t log2cap[GLIM_MAX_LEVELS] = {0};
   int32_t max_probe[GLIM_MAX_LEVELS] = {0};
-  VoxSlot* slots[GLIM_MAX_LEVELS] = {nullptr};
+  VoxSlot* slots[GLIM_MAX_LEVELS] = {nullptr};       // hash slots, or dense cell (0, 0, 0)
+  VoxSlot* slots_alloc[GLIM_MAX_LEVELS] = {nullptr}; // allocation; a dense grid has an empty record at slots - 1
   int32_t* slot_id[GLIM_MAX_LEVELS] = {nullptr};
   int32_t dense[GLIM_MAX_LEVELS] = {0};
   int32_t* grid[GLIM_MAX_LEVELS] = {nullptr};

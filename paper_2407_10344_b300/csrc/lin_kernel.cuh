@@ -26,6 +26,10 @@ struct AccPlain {  // plain FP32 running sums
     for (int i = 0; i < NACC; ++i) s[i] = 0.f;
   }
   __device__ __forceinline__ void add(int i, float x) { s[i] += x; }
+  // s += a b + c d, fused into the running sum
+  __device__ __forceinline__ void add2(int i, float a, float b, float c, float d) {
+    s[i] = __fmaf_rn(a, b, __fmaf_rn(c, d, s[i]));
+  }
 };
 
 // Neumaier-compensated FP32 running sums (Neumaier 1974): c collects the rounding error of
@@ -40,6 +44,9 @@ struct AccComp {
     const float t = s[i] + x;
     c[i] += (fabsf(s[i]) >= fabsf(x)) ? ((s[i] - t) + x) : ((x - t) + s[i]);
     s[i] = t;
+  }
+  __device__ __forceinline__ void add2(int i, float a, float b, float c, float d) {
+    add(i, __fmaf_rn(a, b, c * d));
   }
 };
 
@@ -65,6 +72,49 @@ __device__ __forceinline__ PointIn load_point(const FrameDev& F, int64_t k) {
   p.cb = __ldg(&F.cov[3 * k + 1]);
   p.cc = __ldg(&F.cov[3 * k + 2]);
   return p;
+}
+
+// Phase 2 of one term record {S'00, S'01, S'02, S'11} {S'12, S'22, d.x, d.y} {d.z, u.x, u.y, u.z}:
+// w Omega = adj(S')/det(S'), y = w Omega d, e = d^T y, and the G-form contribution
+// [G^T (w Omega) G, G^T y, e] with G = [-(u)x, I].  A term whose S' is not positive definite
+// contributes nothing.
+template <class A>
+__device__ __forceinline__ void accumulate_term(const float4 t0, const float4 t1, const float4 t2, A& acc) {
+  const float a = t0.x, b = t0.y, c = t0.z, d = t0.w, e = t1.x, f = t1.y;  // S'
+  const float A00 = d * f - e * e, A01 = c * e - b * f, A02 = b * e - c * d;
+  const float A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
+  const float det = a * A00 + b * A01 + c * A02;
+  if (!(det > 0.f) || !(det < INFINITY)) return;
+  const float id = __fdividef(1.0f, det);
+  const float o00 = A00 * id, o01 = A01 * id, o02 = A02 * id, o11 = A11 * id, o12 = A12 * id, o22 = A22 * id;
+  const float dx = t1.z, dy = t1.w, dz = t2.x;
+  const float g0 = o00 * dx + o01 * dy + o02 * dz;  // w Omega d
+  const float g1 = o01 * dx + o11 * dy + o12 * dz;
+  const float g2 = o02 * dx + o12 * dy + o22 * dz;
+  const float ux = t2.y, uy = t2.z, uz = t2.w;
+  // W = (u)x (w Omega)
+  const float W00 = -uz * o01 + uy * o02, W01 = -uz * o11 + uy * o12, W02 = -uz * o12 + uy * o22;
+  const float W10 = uz * o00 - ux * o02, W11 = uz * o01 - ux * o12, W12 = uz * o02 - ux * o22;
+  const float W20 = -uy * o00 + ux * o01, W21 = -uy * o01 + ux * o11, W22 = -uy * o02 + ux * o12;
+  // M_rr = -(u)x Omega (u)x = W (u)x^T  (symmetric)
+  acc.add2(0, -uz, W01, uy, W02);
+  acc.add2(1, uz, W00, -ux, W02);
+  acc.add2(2, -uy, W00, ux, W01);
+  acc.add2(3, uz, W10, -ux, W12);
+  acc.add2(4, -uy, W10, ux, W11);
+  acc.add2(5, -uy, W20, ux, W21);
+  // M_rt = (u)x Omega
+  acc.add(6, W00); acc.add(7, W01); acc.add(8, W02);
+  acc.add(9, W10); acc.add(10, W11); acc.add(11, W12);
+  acc.add(12, W20); acc.add(13, W21); acc.add(14, W22);
+  // M_tt = Omega
+  acc.add(15, o00); acc.add(16, o01); acc.add(17, o02); acc.add(18, o11); acc.add(19, o12); acc.add(20, o22);
+  // g = [u x (w Omega d); w Omega d]
+  acc.add2(21, uy, g2, -uz, g1);
+  acc.add2(22, uz, g0, -ux, g2);
+  acc.add2(23, ux, g1, -uy, g0);
+  acc.add(24, g0); acc.add(25, g1); acc.add(26, g2);
+  acc.add(27, dx * g0 + dy * g1 + dz * g2);  // w d^T Omega d
 }
 
 // Per-warp staging of one round: the compacted list of (point, level) hits.  A term record is
@@ -195,45 +245,7 @@ __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in,
     base += __popc(mask);
   }
   __syncwarp();
-  for (int i = lane; i < base; i += 32) {
-    const float4 t0 = ws.term[3 * i], t1 = ws.term[3 * i + 1], t2 = ws.term[3 * i + 2];
-    const float a = t0.x, b = t0.y, c = t0.z, d = t0.w, e = t1.x, f = t1.y;  // S'
-    const float A00 = d * f - e * e, A01 = c * e - b * f, A02 = b * e - c * d;
-    const float A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
-    const float det = a * A00 + b * A01 + c * A02;
-    if (!(det > 0.f) || !(det < INFINITY)) continue;  // S not positive definite: skip the term
-    const float id = __fdividef(1.0f, det);
-    const float o00 = A00 * id, o01 = A01 * id, o02 = A02 * id, o11 = A11 * id, o12 = A12 * id, o22 = A22 * id;
-    const float dx = t1.z, dy = t1.w, dz = t2.x;
-    const float g0 = o00 * dx + o01 * dy + o02 * dz;  // w Omega d
-    const float g1 = o01 * dx + o11 * dy + o12 * dz;
-    const float g2 = o02 * dx + o12 * dy + o22 * dz;
-    const float es = dx * g0 + dy * g1 + dz * g2;     // w d^T Omega d
-    const float ux2 = t2.y, uy2 = t2.z, uz2 = t2.w;
-    // W = (u)x (w Omega)
-    const float W00 = -uz2 * o01 + uy2 * o02, W01 = -uz2 * o11 + uy2 * o12, W02 = -uz2 * o12 + uy2 * o22;
-    const float W10 = uz2 * o00 - ux2 * o02, W11 = uz2 * o01 - ux2 * o12, W12 = uz2 * o02 - ux2 * o22;
-    const float W20 = -uy2 * o00 + ux2 * o01, W21 = -uy2 * o01 + ux2 * o11, W22 = -uy2 * o02 + ux2 * o12;
-    // M_rr = -(u)x Omega (u)x = W (u)x^T  (symmetric)
-    acc.add(0, -uz2 * W01 + uy2 * W02);
-    acc.add(1, uz2 * W00 - ux2 * W02);
-    acc.add(2, -uy2 * W00 + ux2 * W01);
-    acc.add(3, uz2 * W10 - ux2 * W12);
-    acc.add(4, -uy2 * W10 + ux2 * W11);
-    acc.add(5, -uy2 * W20 + ux2 * W21);
-    // M_rt = (u)x Omega
-    acc.add(6, W00); acc.add(7, W01); acc.add(8, W02);
-    acc.add(9, W10); acc.add(10, W11); acc.add(11, W12);
-    acc.add(12, W20); acc.add(13, W21); acc.add(14, W22);
-    // M_tt = Omega
-    acc.add(15, o00); acc.add(16, o01); acc.add(17, o02); acc.add(18, o11); acc.add(19, o12); acc.add(20, o22);
-    // g = [u x (w Omega d); w Omega d]
-    acc.add(21, uy2 * g2 - uz2 * g1);
-    acc.add(22, uz2 * g0 - ux2 * g2);
-    acc.add(23, ux2 * g1 - uy2 * g0);
-    acc.add(24, g0); acc.add(25, g1); acc.add(26, g2);
-    acc.add(27, es);
-  }
+  for (int i = lane; i < base; i += 32) accumulate_term(ws.term[3 * i], ws.term[3 * i + 1], ws.term[3 * i + 2], acc);
   __syncwarp();  // the stage is rewritten by the next round
 }
 
@@ -395,6 +407,198 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize(const LinArgs 
   }
 }
 
+// ---------------------------------------------------------------- dense-grid kernel
+// Every target level is a dense grid: a lookup is an index computation and one read, so
+// phase 1 runs without divergent branches.  A key outside the grid's box reads the empty
+// record before cell 0; a lane past the end of its tile reads its tile's last point and is
+// masked.  Hit records are appended to a per-warp ring of 32 (LMAX + 1) records, the lanes
+// without a hit writing scratch copies just past the appended ones (overwritten later,
+// never read).  Phase 2 takes full batches of 32 records only; the rest waits for the next
+// round, and the item's last partial batch is taken at its end.  Results equal those of the
+// general kernel up to FP32 summation order.
+
+struct DenseView {  // per-item constants, written by thread 0
+  float R[9], t[3], v[3];
+  const float4* pts;
+  const float2* cov;
+  const float* nrm;
+  int end;  // one past the item's last point
+  DenseMapDev M;
+};
+
+template <int LMAX>
+struct DenseRing {
+  static constexpr int S = 32 * (LMAX + 1);
+  float4 term[S * 3];
+};
+
+__device__ __forceinline__ PointIn load_point32(const float4* pts, const float2* cov, int k) {
+  PointIn p;
+  p.m = ldg4(pts + k);
+  const float2* c = cov + 3 * int64_t(k);
+  p.ca = __ldg(c);
+  p.cb = __ldg(c + 1);
+  p.cc = __ldg(c + 2);
+  return p;
+}
+
+template <int LMAX, class A>
+__device__ __forceinline__ void dense_round(const DenseView& V, const PointIn& in, bool live, int validate,
+                                            DenseRing<LMAX>& ring, int& head, int& tail, A& acc, int& inl,
+                                            int lane, unsigned lt, int kk) {
+  constexpr int S = DenseRing<LMAX>::S;
+  const float4 m = in.m;
+  if (validate && V.nrm) {
+    const float* nk = V.nrm + 3 * int64_t(kk);
+    live = live && !behind_surface(m.x, m.y, m.z, V.v, __ldg(nk), __ldg(nk + 1), __ldg(nk + 2));
+  }
+  const float3 q = transform_pinned(V.R, V.t, m.x, m.y, m.z);
+  // keys of infinite or huge coordinates saturate outside every box; a NaN would convert to 0
+  live = live && q.x == q.x && q.y == q.y && q.z == q.z;
+  float4 s0[LMAX], s1[LMAX], s2[LMAX];
+#pragma unroll
+  for (int l = 0; l < LMAX; ++l) {
+    const DenseLevelDev& L = V.M.lv[l];
+    const float ir = V.M.inv_r[l];
+    // keys floor(q * inv_r) (FP32 product); a key outside [-2^20, 2^20) is outside every box
+    const uint32_t x = uint32_t(__float2int_rd(__fmul_rn(q.x, ir))) - uint32_t(L.ox);
+    const uint32_t y = uint32_t(__float2int_rd(__fmul_rn(q.y, ir))) - uint32_t(L.oy);
+    const uint32_t z = uint32_t(__float2int_rd(__fmul_rn(q.z, ir))) - uint32_t(L.oz);
+    const bool in_box = live && x < L.nx && y < L.ny && z < L.nz;
+    const VoxSlot* sl = L.cells + (in_box ? int((x * L.ny + y) * L.nz + z) : -1);
+    s0[l] = ldg4(&sl->w0);
+    s1[l] = ldg4(&sl->w1);
+    s2[l] = ldg4(&sl->w2);
+  }
+  // R C R^T / w (once for all levels) and u = R mu
+  const float* R = V.R;
+  const float iw = __fdividef(1.0f, m.w);
+  const float c00 = in.ca.x, c01 = in.ca.y, c02 = in.cb.x, c11 = in.cb.y, c12 = in.cc.x, c22 = in.cc.y;
+  const float w00 = R[0] * c00 + R[1] * c01 + R[2] * c02;
+  const float w01 = R[0] * c01 + R[1] * c11 + R[2] * c12;
+  const float w02 = R[0] * c02 + R[1] * c12 + R[2] * c22;
+  const float w10 = R[3] * c00 + R[4] * c01 + R[5] * c02;
+  const float w11 = R[3] * c01 + R[4] * c11 + R[5] * c12;
+  const float w12 = R[3] * c02 + R[4] * c12 + R[5] * c22;
+  const float w20 = R[6] * c00 + R[7] * c01 + R[8] * c02;
+  const float w21 = R[6] * c01 + R[7] * c11 + R[8] * c12;
+  const float w22 = R[6] * c02 + R[7] * c12 + R[8] * c22;
+  const float r00 = (w00 * R[0] + w01 * R[1] + w02 * R[2]) * iw;
+  const float r01 = (w00 * R[3] + w01 * R[4] + w02 * R[5]) * iw;
+  const float r02 = (w00 * R[6] + w01 * R[7] + w02 * R[8]) * iw;
+  const float r11 = (w10 * R[3] + w11 * R[4] + w12 * R[5]) * iw;
+  const float r12 = (w10 * R[6] + w11 * R[7] + w12 * R[8]) * iw;
+  const float r22 = (w20 * R[6] + w21 * R[7] + w22 * R[8]) * iw;
+  const float ux = q.x - V.t[0], uy = q.y - V.t[1], uz = q.z - V.t[2];
+  // append the hits to the ring: level-major, lane order within a level
+#pragma unroll
+  for (int l = 0; l < LMAX; ++l) {
+    const bool hit = __float_as_int(s0[l].x) >= 0;  // occupied cell (empty records hold 0x80808080)
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    const int below = __popc(mask & lt), nhit = __popc(mask);
+    int slot = tail + (hit ? below : nhit + lane - below);
+    slot = slot >= S ? slot - S : slot;
+    float4* t = ring.term + 3 * slot;
+    // voxel record: s0 = {id, ., ., C~22}, s1 = {mean, C~00}, s2 = {C~01, C~02, C~11, C~12}
+    t[0] = make_float4(__fmaf_rn(s1[l].w, iw, r00), __fmaf_rn(s2[l].x, iw, r01), __fmaf_rn(s2[l].y, iw, r02),
+                       __fmaf_rn(s2[l].z, iw, r11));
+    t[1] = make_float4(__fmaf_rn(s2[l].w, iw, r12), __fmaf_rn(s0[l].w, iw, r22), s1[l].x - q.x, s1[l].y - q.y);
+    t[2] = make_float4(s1[l].z - q.z, ux, uy, uz);
+    inl += hit ? 1 : 0;
+    tail += nhit;
+    tail = tail >= S ? tail - S : tail;
+  }
+  __syncwarp();
+  int avail = tail - head;
+  avail = avail < 0 ? avail + S : avail;
+  while (avail >= 32) {
+    int i = head + lane;
+    i = i >= S ? i - S : i;
+    accumulate_term(ring.term[3 * i], ring.term[3 * i + 1], ring.term[3 * i + 2], acc);
+    head += 32;
+    head = head >= S ? head - S : head;
+    avail -= 32;
+  }
+  __syncwarp();  // taken records may be overwritten by the next round
+}
+
+template <int BLOCK, int ACC, int LMAX>
+__device__ __forceinline__ void process_item_dense(const LinArgs& a, int item, DenseView& V, DenseRing<LMAX>& ring) {
+  const Item it = a.items[item];
+  if (threadIdx.x == 0) {
+    const PairDev pd = a.pairs[it.pair];
+    const PoseF pf = a.pose[it.pair];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) V.R[i] = pf.R[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      V.t[i] = pf.t[i];
+      V.v[i] = pf.v[i];
+    }
+    const FrameDev F = a.frames[pd.src];
+    V.pts = F.pts;
+    V.cov = F.cov;
+    V.nrm = F.nrm;
+    V.M = a.dmaps[pd.map];
+    V.end = int(min(int64_t(it.start) + a.tile, F.n));
+  }
+  __syncthreads();
+  typename AccOf<ACC>::type acc;
+  acc.zero();
+  int inl = 0;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int last = V.end - 1;  // items are never empty
+  const int first = it.start + int(threadIdx.x);
+  const int rounds = min(a.ppt, (last - it.start) / BLOCK + 1);
+  int head = 0, tail = 0;
+  // software pipeline: the next round's point is read while the current round is processed
+  PointIn cur = load_point32(V.pts, V.cov, min(first, last));
+#pragma unroll 1
+  for (int j = 0; j < rounds; ++j) {
+    const int k = first + j * BLOCK;
+    const PointIn nxt = load_point32(V.pts, V.cov, min(k + BLOCK, last));
+    dense_round<LMAX>(V, cur, k <= last, a.validate, ring, head, tail, acc, inl, lane, lt, min(k, last));
+    cur = nxt;
+  }
+  int avail = tail - head;  // the last partial batch
+  avail = avail < 0 ? avail + DenseRing<LMAX>::S : avail;
+  if (lane < avail) {
+    int i = head + lane;
+    i = i >= DenseRing<LMAX>::S ? i - DenseRing<LMAX>::S : i;
+    accumulate_term(ring.term[3 * i], ring.term[3 * i + 1], ring.term[3 * i + 2], acc);
+  }
+  __syncwarp();
+  block_reduce_store<BLOCK, ACC>(acc, inl, a.part + int64_t(item) * PSTRIDE);
+}
+
+template <int BLOCK, int LMAX>
+constexpr size_t lin_dense_dyn_smem() {
+  return size_t(BLOCK / 32) * sizeof(DenseRing<LMAX>);
+}
+
+template <int BLOCK, int ACC, int LMAX>
+__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize_dense(const LinArgs a) {
+  __shared__ DenseView V;
+  __shared__ int s_item[2];
+  extern __shared__ float4 dyn_smem[];
+  DenseRing<LMAX>& ring = reinterpret_cast<DenseRing<LMAX>*>(dyn_smem)[threadIdx.x >> 5];
+  if (a.head == nullptr) {
+    const int item = a.item_base + blockIdx.x;
+    if (item < a.nitems) process_item_dense<BLOCK, ACC, LMAX>(a, item, V, ring);
+    return;
+  }
+  if (threadIdx.x == 0) s_item[0] = atomicAdd(a.head, 1);
+  __syncthreads();
+  int cur = s_item[0];
+  for (int b = 1;; b ^= 1) {
+    if (cur >= a.nitems) break;
+    if (threadIdx.x == 0) s_item[b] = atomicAdd(a.head, 1);
+    process_item_dense<BLOCK, ACC, LMAX>(a, cur, V, ring);  // ends with a barrier
+    cur = s_item[b];
+  }
+}
+
 // Kernel and its dynamic shared memory (bytes) for a configuration; the attribute allowing
 // that much dynamic shared memory is set on first use.
 template <int B, int ACC, int L>
@@ -423,8 +627,37 @@ LinKernelInfo pick_lin(int block, int lmax) {
 #undef GLIM_PICK_L
 }
 
+template <int B, int ACC, int L>
+LinKernelInfo lin_dense_info() {
+  LinKernelInfo k;
+  k.fn = k_linearize_dense<B, ACC, L>;
+  k.smem = lin_dense_dyn_smem<B, L>();
+  return k;
+}
+
+template <int ACC>
+LinKernelInfo pick_lin_dense(int block, int lmax) {
+#define GLIM_PICK_DENSE_L(B)                      \
+  switch (lmax) {                                 \
+    case 1: return lin_dense_info<B, ACC, 1>();   \
+    case 2: return lin_dense_info<B, ACC, 2>();   \
+    case 3: return lin_dense_info<B, ACC, 3>();   \
+    case 4: return lin_dense_info<B, ACC, 4>();   \
+  }                                               \
+  return LinKernelInfo{};
+  switch (block) {
+    case 128: { GLIM_PICK_DENSE_L(128) }
+    case 256: { GLIM_PICK_DENSE_L(256) }
+  }
+#undef GLIM_PICK_DENSE_L
+  return LinKernelInfo{};
+}
+
 LinKernelInfo pick_lin_fp32(int block, int lmax);
 LinKernelInfo pick_lin_kahan(int block, int lmax);
 LinKernelInfo pick_lin_fp64(int block, int lmax);
+LinKernelInfo pick_lin_dense_fp32(int block, int lmax);
+LinKernelInfo pick_lin_dense_kahan(int block, int lmax);
+LinKernelInfo pick_lin_dense_fp64(int block, int lmax);
 
 }  // namespace glim_detail

@@ -122,7 +122,15 @@ __global__ void __launch_bounds__(128) k_reduce_expand(const ReduceArgs a) {
 }
 
 // ---------------------------------------------------------------- kernel table
-LinKernelInfo pick_kernel(int block, int acc, int lmax) {
+LinKernelInfo pick_kernel(int block, int acc, int lmax, bool dense) {
+  if (dense) {
+    switch (acc) {
+      case GLIM_ACC_FP32: return pick_lin_dense_fp32(block, lmax);
+      case GLIM_ACC_KAHAN: return pick_lin_dense_kahan(block, lmax);
+      case GLIM_ACC_FP64: return pick_lin_dense_fp64(block, lmax);
+    }
+    return LinKernelInfo{};
+  }
   switch (acc) {
     case GLIM_ACC_FP32: return pick_lin_fp32(block, lmax);
     case GLIM_ACC_KAHAN: return pick_lin_kahan(block, lmax);
@@ -141,7 +149,7 @@ bool opts_valid(const glim_lin_opts& o) {
   return (o.block == 128 || o.block == 256) &&
          (o.pts_per_thread >= 1 && o.pts_per_thread <= 256) &&
          (o.accum_mode >= 0 && o.accum_mode <= 2) && (o.persistent == 1 || o.persistent == 2) &&
-         o.blocks_per_sm >= 0 && o.blocks_per_sm <= 32;
+         o.blocks_per_sm >= 0 && o.blocks_per_sm <= 32 && o.kernel >= 0 && o.kernel <= 2;
 }
 
 bool is_device_ptr(const void* p) {
@@ -192,7 +200,11 @@ glim_status plan_configure(glim_plan* p, const glim_lin_opts& o) {
   if (!items.empty())
     GLIM_CUDA(ctx, cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice));
   GLIM_CUDA(ctx, cudaMemcpy(p->d_item_begin, begin.data(), begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  const LinKernelInfo ki = pick_kernel(o.block, o.accum_mode, p->lmax);
+  if (o.kernel == 2 && !p->d_dmaps)
+    return set_error(ctx, GLIM_EINVAL, "the dense-grid kernel needs every target level to be a dense grid");
+  p->dense_kernel = p->d_dmaps != nullptr && o.kernel != 1;
+  p->opts.kernel = p->dense_kernel ? 2 : 1;  // the kernel actually used
+  const LinKernelInfo ki = pick_kernel(o.block, o.accum_mode, p->lmax, p->dense_kernel);
   p->kernel = ki.fn;
   p->kernel_smem = ki.smem;
   if (!p->kernel) return set_error(ctx, GLIM_EINVAL, "no kernel for block=%d ppt=%d acc=%d", o.block, o.pts_per_thread, o.accum_mode);
@@ -225,6 +237,7 @@ glim_status plan_enqueue_kernels(glim_plan* p, int slot = -1) {
     a.pairs = p->d_pairs;
     a.frames = p->d_frames;
     a.maps = p->d_maps;
+    a.dmaps = p->dense_kernel ? p->d_dmaps : nullptr;
     a.pose = p->in_pose32();
     a.head = p->opts.persistent == 1 ? p->d_head : nullptr;
     a.part = p->d_part;
@@ -390,6 +403,35 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
       if (maps[i]->inv_r[l] != std::ldexp(maps[i]->inv_r[0], -l)) md[i].pow2 = 0;
     }
   }
+  // dense-grid descriptors when every level of every target map is a dense grid
+  bool all_dense = !maps.empty();
+  for (const glim_vmap* m : maps)
+    for (int l = 0; l < m->levels; ++l) all_dense = all_dense && m->dense[l] && m->slots[l];
+  // the dense-grid kernel indexes points in 32 bits, up to two blocks past an item's end
+  for (int f = 0; f < nframes; ++f) all_dense = all_dense && frames[f].n <= 0x7FFFFFFFll - (1 << 17);
+  std::vector<DenseMapDev> dmd(std::max<size_t>(maps.size(), 1));
+  if (all_dense) {
+    for (size_t i = 0; i < maps.size(); ++i) {
+      const glim_vmap* m = maps[i];
+      std::memset(&dmd[i], 0, sizeof(DenseMapDev));
+      for (int l = 0; l < GLIM_MAX_LEVELS; ++l) {
+        DenseLevelDev& d = dmd[i].lv[l];
+        if (l < m->levels) {
+          d.cells = m->slots[l];
+          d.ox = m->org[l][0];
+          d.oy = m->org[l][1];
+          d.oz = m->org[l][2];
+          d.nx = m->dim[l][0];
+          d.ny = m->dim[l][1];
+          d.nz = m->dim[l][2];
+          dmd[i].inv_r[l] = m->inv_r[l];
+        } else {  // an absent level: empty box, reads level 0's empty record
+          d.cells = m->slots[0];
+          dmd[i].inv_r[l] = m->inv_r[0];
+        }
+      }
+    }
+  }
   p->nmaps = int(maps.size());
   for (const glim_vmap* m : maps) p->map_versions.emplace_back(m, m->version);
   p->lmax = 1;
@@ -406,6 +448,11 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
   cudaMemcpy(p->d_frames, fd.data(), fd.size() * sizeof(FrameDev), cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_pairs, pd.data(), pd.size() * sizeof(PairDev), cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_maps, md.data(), md.size() * sizeof(MapDev), cudaMemcpyHostToDevice);
+  if (all_dense) {
+    if (cudaMalloc(&p->d_dmaps, dmd.size() * sizeof(DenseMapDev)) != cudaSuccess)
+      return fail(set_error(ctx, GLIM_ENOMEM, "plan: device allocation failed"));
+    cudaMemcpy(p->d_dmaps, dmd.data(), dmd.size() * sizeof(DenseMapDev), cudaMemcpyHostToDevice);
+  }
   p->in_bytes = std::max<size_t>(size_t(npairs) * (sizeof(PoseF) + 12 * sizeof(double)), 16);
   p->out_bytes = std::max<size_t>(size_t(npairs) * (157 * sizeof(double) + sizeof(int64_t)), 16);
   if (cudaMalloc(&p->d_in, p->in_bytes) != cudaSuccess || cudaMalloc(&p->d_out, p->out_bytes) != cudaSuccess ||
@@ -427,6 +474,7 @@ extern "C" void glim_plan_destroy(glim_plan* p) {
   cudaFree(p->d_frames);
   cudaFree(p->d_pairs);
   cudaFree(p->d_maps);
+  cudaFree(p->d_dmaps);
   cudaFree(p->d_items);
   cudaFree(p->d_item_begin);
   cudaFree(p->d_part);
@@ -625,6 +673,7 @@ extern "C" glim_status glim_linearize_factors_plain(glim_ctx* ctx, const glim_fr
     a.pairs = p->d_pairs;
     a.frames = p->d_frames;
     a.maps = p->d_maps;
+    a.dmaps = p->dense_kernel ? p->d_dmaps : nullptr;
     a.pose = p->in_pose32();
     a.head = nullptr;  // one block per item of this factor
     a.part = p->d_part;

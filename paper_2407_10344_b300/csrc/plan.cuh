@@ -25,6 +25,21 @@ struct MapDev {
   int32_t pad[2];
 };
 
+// One dense level as the dense-grid kernel sees it: the record of key (kx, ky, kz) is
+// cells[((kx - ox) * ny + (ky - oy)) * nz + (kz - oz)] inside the box, and cells[-1] (an empty
+// record) is read for every key outside it.  A level that a map does not have is a box of
+// size 0 whose cells[-1] is some map's empty record.
+struct DenseLevelDev {
+  const VoxSlot* cells;
+  int32_t ox, oy, oz;
+  uint32_t nx, ny, nz;
+};
+
+struct DenseMapDev {
+  DenseLevelDev lv[GLIM_MAX_LEVELS];
+  float inv_r[GLIM_MAX_LEVELS];
+};
+
 struct PairDev {
   int32_t src;
   int32_t map;
@@ -42,6 +57,7 @@ struct LinArgs {
   const PairDev* pairs;
   const FrameDev* frames;
   const MapDev* maps;
+  const DenseMapDev* dmaps = nullptr;  // per map, when every target level is a dense grid
   const PoseF* pose;   // per pair
   int* head;           // work-queue head (persistent)
   double* part;        // nitems x PSTRIDE
@@ -77,6 +93,7 @@ struct glim_plan {
   MapDev* d_maps = nullptr;
   PairDev* d_pairs = nullptr;
   int nmaps = 0;
+  DenseMapDev* d_dmaps = nullptr;  // set when every level of every target map is a dense grid
   std::vector<std::pair<const glim_vmap*, uint64_t>> map_versions;  // target maps as the plan saw them
   int lmax = 1;  // most levels of any target map (kernel template parameter)
   // work list (depends on the tile size)
@@ -88,6 +105,7 @@ struct glim_plan {
   int* d_head = nullptr;
   int grid = 0;
   LinKernel kernel = nullptr;
+  bool dense_kernel = false;  // kernel is the dense-grid kernel (a.dmaps = d_dmaps)
   size_t kernel_smem = 0;
   // serialized input block: PoseF[npairs] then double[npairs * 12]
   size_t in_bytes = 0;

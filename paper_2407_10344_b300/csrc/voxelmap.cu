@@ -227,7 +227,7 @@ int log2_ceil(int64_t x) {
 
 void free_level(glim_vmap* vm, int l) {
   cudaFree(vm->grid[l]);
-  cudaFree(vm->slots[l]);
+  cudaFree(vm->slots_alloc[l]);
   cudaFree(vm->slot_id[l]);
   cudaFree(vm->vkey[l]);
   cudaFree(vm->vmean[l]);
@@ -236,6 +236,7 @@ void free_level(glim_vmap* vm, int l) {
   cudaFree(vm->vsum[l]);
   vm->grid[l] = nullptr;
   vm->slots[l] = nullptr;
+  vm->slots_alloc[l] = nullptr;
   vm->slot_id[l] = nullptr;
   vm->vkey[l] = nullptr;
   vm->vmean[l] = nullptr;
@@ -261,6 +262,7 @@ void move_level(glim_vmap* dst, glim_vmap* src, int l) {
     dst->dim[l][c] = src->dim[l][c];
   }
   dst->slots[l] = src->slots[l];
+  dst->slots_alloc[l] = src->slots_alloc[l];
   dst->slot_id[l] = src->slot_id[l];
   dst->grid[l] = src->grid[l];
   dst->vkey[l] = src->vkey[l];
@@ -269,6 +271,7 @@ void move_level(glim_vmap* dst, glim_vmap* src, int l) {
   dst->vcount[l] = src->vcount[l];
   dst->vsum[l] = src->vsum[l];
   src->slots[l] = nullptr;
+  src->slots_alloc[l] = nullptr;
   src->slot_id[l] = nullptr;
   src->grid[l] = nullptr;
   src->vkey[l] = nullptr;
@@ -352,10 +355,11 @@ void adopt_canon(glim_vmap* vm, int l, Canon& c) {
 // Lookup tables of a level (dense grid or hash) from its canonical arrays; replaces any
 // existing tables of the level.
 glim_status build_tables(glim_ctx* ctx, glim_vmap* vm, int l, int layout) {
-  cudaFree(vm->slots[l]);
+  cudaFree(vm->slots_alloc[l]);
   cudaFree(vm->slot_id[l]);
   cudaFree(vm->grid[l]);
   vm->slots[l] = nullptr;
+  vm->slots_alloc[l] = nullptr;
   vm->slot_id[l] = nullptr;
   vm->grid[l] = nullptr;
   vm->dense[l] = 0;
@@ -390,8 +394,10 @@ glim_status build_tables(glim_ctx* ctx, glim_vmap* vm, int l, int layout) {
     vm->cap[l] = ncell;
     vm->log2cap[l] = 0;
     vm->max_probe[l] = 1;
-    GLIM_CUDA(ctx, cudaMalloc(&vm->slots[l], ncell * sizeof(VoxSlot)));
-    GLIM_CUDA(ctx, cudaMemsetAsync(vm->slots[l], 0x80, ncell * sizeof(VoxSlot), ctx->stream));
+    // one empty record before cell 0: lookups outside the box may read it instead of branching
+    GLIM_CUDA(ctx, cudaMalloc(&vm->slots_alloc[l], (ncell + 1) * sizeof(VoxSlot)));
+    GLIM_CUDA(ctx, cudaMemsetAsync(vm->slots_alloc[l], 0x80, (ncell + 1) * sizeof(VoxSlot), ctx->stream));
+    vm->slots[l] = vm->slots_alloc[l] + 1;
     k_dense_build<<<ceil_div_i(m, 256), 256, 0, ctx->stream>>>(vm->vkey[l], vm->vmean[l], vm->vcov[l], m,
                                                                vm->slots[l], bb[0], bb[1], bb[2], uint32_t(ny),
                                                                uint32_t(nz));
@@ -401,7 +407,8 @@ glim_status build_tables(glim_ctx* ctx, glim_vmap* vm, int l, int layout) {
   const int64_t cap = std::max<int64_t>(16, int64_t(1) << log2_ceil(2 * m));
   vm->cap[l] = cap;
   vm->log2cap[l] = log2_ceil(cap);
-  GLIM_CUDA(ctx, cudaMalloc(&vm->slots[l], cap * sizeof(VoxSlot)));
+  GLIM_CUDA(ctx, cudaMalloc(&vm->slots_alloc[l], cap * sizeof(VoxSlot)));
+  vm->slots[l] = vm->slots_alloc[l];
   GLIM_CUDA(ctx, cudaMalloc(&vm->slot_id[l], cap * sizeof(int32_t)));
   GLIM_CUDA(ctx, cudaMemsetAsync(vm->slots[l], 0x80, cap * sizeof(VoxSlot), ctx->stream));
   GLIM_CUDA(ctx, cudaMemsetAsync(vm->slot_id[l], 0xFF, cap * sizeof(int32_t), ctx->stream));

@@ -227,6 +227,79 @@ def test_edge_cases_empty_ragged_and_misses(G, ctx, room):
         assert np.array_equal(res[3], ref["inliers"])
 
 
+@pytest.mark.parametrize("kernel", ["general", "dense"])
+@pytest.mark.parametrize("validate", [False, True])
+def test_dense_grid_kernel_and_general_kernel(G, ctx, room, kernel, validate):
+    """The dense-grid kernel (chosen automatically when every target level is a dense grid)
+    and the general kernel both match the oracle on the same dense maps, across every
+    accumulation mode, one block per item and the persistent queue."""
+    assert all(room.gmaps[1].is_dense(l) for l in range(len(room.w.resolutions)))
+    ref = room.oracle(validate=validate)
+    for acc in (G.ACC_FP32, G.ACC_KAHAN, G.ACC_FP64):
+        for persistent, block, ppt in ((1, 128, 64), (2, 256, 3)):
+            res = G.linearize(ctx, room.gframes, room.gmaps, room.w.pairs, room.w.poses, kernel=kernel,
+                              validate_surface=validate, accum_mode=acc, persistent=persistent, block=block,
+                              pts_per_thread=ppt)
+            _check(res, ref)
+    plan = G.Plan(ctx, room.gframes, room.gmaps, room.w.pairs, kernel="auto")
+    assert plan.opts()["kernel"] == "dense"
+
+
+def test_dense_kernel_mixed_levels_ragged_and_nonfinite(G, ctx):
+    """One batch whose target maps have 3, 1 and 2 levels (absent levels read the empty
+    record), sources of 1, 37, and 130 * 64 + 5 points (ragged tiles, lanes past the end), a
+    source point at NaN and one at 1e30 (misses), against the oracle."""
+    w = synth.corridor(n_kf=3, n_cur=9000, kf_range=(6000, 9000))
+    dev = torch.device("cuda")
+    res_of = {1: [0.5, 1.0, 2.0], 2: [1.0], 3: [0.5, 1.0]}
+    gframes, oframes, gmaps, omaps = [], [], [], []
+    for i, p in enumerate(w.points):
+        p = np.asarray(p, np.float32).copy()
+        if i == 0:
+            p = p[:130 * 64 + 5]
+            p[7] = np.nan
+            p[8] = 1e30
+        p4 = G.to_pts4(p, device=dev)
+        good = torch.isfinite(p4).all(1) & (p4.abs() < 1e20).all(1)
+        cov = torch.zeros((len(p4), 6), dtype=torch.float32, device=dev)
+        cg, _ = G.estimate_covariances(ctx, p4[good].contiguous())
+        cov[good] = cg
+        cov[~good] = torch.tensor([1, 0, 0, 1, 0, 1], dtype=torch.float32, device=dev)
+        gframes.append(G.FrameData(p4, cov))
+        oframes.append(O.Frame(p4.cpu().numpy(), cov.cpu().numpy()))
+        gmaps.append(G.VoxelMap(ctx, p4, cov, res_of[i]) if i in res_of else None)
+        omaps.append(O.VMap(oframes[i].pts4, oframes[i].cov6, res_of[i]) if i in res_of else None)
+    # small sources: single points and a 37-point prefix of frame 0
+    for n in (1, 37):
+        gframes.append(G.FrameData(gframes[0].pts4[:n].clone(), gframes[0].cov6[:n].clone()))
+        oframes.append(O.Frame(oframes[0].pts4[:n].copy(), oframes[0].cov6[:n].copy()))
+        gmaps.append(None)
+        omaps.append(None)
+    poses = np.concatenate([w.poses, w.poses[:1], w.poses[:1]])
+    pairs = np.array([[0, 1], [0, 2], [0, 3], [4, 1], [5, 3], [5, 2], [1, 2], [3, 1]], np.int32)
+    assert all(gmaps[t].is_dense(l) for t in (1, 2, 3) for l in range(len(res_of[t])))
+    ref = O.linearize(oframes, omaps, pairs, poses, want_comp=True)
+    for kernel in ("dense", "general"):
+        for block, ppt in ((128, 64), (256, 1), (128, 5)):
+            res = G.linearize(ctx, gframes, gmaps, pairs, poses, kernel=kernel, block=block, pts_per_thread=ppt)
+            from gpu_helpers import numpy_of, rel_errors
+            e, H, b, inl = [numpy_of(x) for x in res]
+            assert np.array_equal(inl, ref["inliers"])
+            ok = ref["e"] > 0
+            ee, eH, eb = rel_errors(e[ok], H[ok], b[ok], {k: v[ok] for k, v in ref.items()})
+            assert ee.max() <= TOL and eH.max() <= TOL and eb.max() <= TOL, (kernel, block, ppt)
+
+
+def test_dense_kernel_refused_on_hash_maps(G, ctx, room):
+    g = room.gframes[1]
+    hm = G.VoxelMap(ctx, g.pts4, g.cov6, room.w.resolutions, layout="hash")
+    with pytest.raises(G.GlimError, match="EINVAL"):
+        G.linearize(ctx, room.gframes, [None, hm], room.w.pairs, room.w.poses, kernel="dense")
+    plan = G.Plan(ctx, room.gframes, [None, hm], room.w.pairs)
+    assert plan.opts()["kernel"] == "general"
+    _check(plan.linearize(room.w.poses), room.oracle())
+
+
 def test_invalid_arguments(G, ctx, room):
     with pytest.raises(G.GlimError, match="EINVAL"):
         G.linearize(ctx, room.gframes, room.gmaps, [[0, 1]], room.w.poses, block=96)
