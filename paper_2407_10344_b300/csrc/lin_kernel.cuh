@@ -411,25 +411,28 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize(const LinArgs 
 // Every target level is a dense grid: a lookup is an index computation and one read, so
 // phase 1 runs without divergent branches.  A key outside the grid's box reads the empty
 // record before cell 0; a lane past the end of its tile reads its tile's last point and is
-// masked.  Hit records are appended to a per-warp ring of 32 (LMAX + 1) records, the lanes
-// without a hit writing scratch copies just past the appended ones (overwritten later,
-// never read).  Phase 2 takes full batches of 32 records only; the rest waits for the next
-// round, and the item's last partial batch is taken at its end.  Results equal those of the
-// general kernel up to FP32 summation order.
+// masked.  Hit records are appended (predicated stores) to a per-warp ring of S records,
+// kept as three arrays of float4 so that a record's parts share one index.  Phase 2 takes
+// full batches of 32 records only; the rest waits for the next round, and the item's last
+// partial batch is taken at its end.  Results equal those of the general kernel up to FP32
+// summation order.
 
-struct DenseView {  // per-item constants, written by thread 0
-  float R[9], t[3], v[3];
+struct __align__(16) DenseView {  // per-item constants, written by thread 0
+  float4 Rt[3];  // rows of [R | t]
+  float4 v;      // target viewpoint (surface validation)
   const float4* pts;
   const float2* cov;
   const float* nrm;
   int end;  // one past the item's last point
+  int pad;
   DenseMapDev M;
 };
 
 template <int LMAX>
 struct DenseRing {
-  static constexpr int S = 32 * (LMAX + 1);
-  float4 term[S * 3];
+  // 31 waiting records + 32 LMAX appended ones fit; a power of two for the index wrap
+  static constexpr int S = LMAX == 1 ? 64 : (LMAX <= 3 ? 128 : 256);
+  float4 r0[S], r1[S], r2[S];
 };
 
 __device__ __forceinline__ PointIn load_point32(const float4* pts, const float2* cov, int k) {
@@ -442,6 +445,16 @@ __device__ __forceinline__ PointIn load_point32(const float4* pts, const float2*
   return p;
 }
 
+// Shared-memory store of a float4 by the lanes whose predicate is set.
+__device__ __forceinline__ void st_shared_if(bool p, float4* addr, float4 v) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(addr));
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.shared.v4.f32 [%1], {%2, %3, %4, %5};\n\t}"
+      :
+      : "r"(int(p)), "r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+      : "memory");
+}
+
 template <int LMAX, class A>
 __device__ __forceinline__ void dense_round(const DenseView& V, const PointIn& in, bool live, int validate,
                                             DenseRing<LMAX>& ring, int& head, int& tail, A& acc, int& inl,
@@ -450,12 +463,18 @@ __device__ __forceinline__ void dense_round(const DenseView& V, const PointIn& i
   const float4 m = in.m;
   if (validate && V.nrm) {
     const float* nk = V.nrm + 3 * int64_t(kk);
-    live = live && !behind_surface(m.x, m.y, m.z, V.v, __ldg(nk), __ldg(nk + 1), __ldg(nk + 2));
+    const float vv[3] = {V.v.x, V.v.y, V.v.z};
+    live = live && !behind_surface(m.x, m.y, m.z, vv, __ldg(nk), __ldg(nk + 1), __ldg(nk + 2));
   }
-  const float3 q = transform_pinned(V.R, V.t, m.x, m.y, m.z);
+  const float4 R0 = V.Rt[0], R1 = V.Rt[1], R2 = V.Rt[2];
+  float3 q;  // R mu + t, one fused multiply-add per term from t in x, y, z order
+  q.x = __fmaf_rn(R0.z, m.z, __fmaf_rn(R0.y, m.y, __fmaf_rn(R0.x, m.x, R0.w)));
+  q.y = __fmaf_rn(R1.z, m.z, __fmaf_rn(R1.y, m.y, __fmaf_rn(R1.x, m.x, R1.w)));
+  q.z = __fmaf_rn(R2.z, m.z, __fmaf_rn(R2.y, m.y, __fmaf_rn(R2.x, m.x, R2.w)));
   // keys of infinite or huge coordinates saturate outside every box; a NaN would convert to 0
   live = live && q.x == q.x && q.y == q.y && q.z == q.z;
-  float4 s0[LMAX], s1[LMAX], s2[LMAX];
+  float2 s0[LMAX];
+  float4 s1[LMAX], s2[LMAX];
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
     const DenseLevelDev& L = V.M.lv[l];
@@ -466,57 +485,51 @@ __device__ __forceinline__ void dense_round(const DenseView& V, const PointIn& i
     const uint32_t z = uint32_t(__float2int_rd(__fmul_rn(q.z, ir))) - uint32_t(L.oz);
     const bool in_box = live && x < L.nx && y < L.ny && z < L.nz;
     const VoxSlot* sl = L.cells + (in_box ? int((x * L.ny + y) * L.nz + z) : -1);
-    s0[l] = ldg4(&sl->w0);
-    s1[l] = ldg4(&sl->w1);
-    s2[l] = ldg4(&sl->w2);
+    s0[l] = __ldg(reinterpret_cast<const float2*>(&sl->w0));  // {id, C~22}
+    s1[l] = ldg4(&sl->w1);                                    // {mean, C~00}
+    s2[l] = ldg4(&sl->w2);                                    // {C~01, C~02, C~11, C~12}
   }
   // R C R^T / w (once for all levels) and u = R mu
-  const float* R = V.R;
   const float iw = __fdividef(1.0f, m.w);
   const float c00 = in.ca.x, c01 = in.ca.y, c02 = in.cb.x, c11 = in.cb.y, c12 = in.cc.x, c22 = in.cc.y;
-  const float w00 = R[0] * c00 + R[1] * c01 + R[2] * c02;
-  const float w01 = R[0] * c01 + R[1] * c11 + R[2] * c12;
-  const float w02 = R[0] * c02 + R[1] * c12 + R[2] * c22;
-  const float w10 = R[3] * c00 + R[4] * c01 + R[5] * c02;
-  const float w11 = R[3] * c01 + R[4] * c11 + R[5] * c12;
-  const float w12 = R[3] * c02 + R[4] * c12 + R[5] * c22;
-  const float w20 = R[6] * c00 + R[7] * c01 + R[8] * c02;
-  const float w21 = R[6] * c01 + R[7] * c11 + R[8] * c12;
-  const float w22 = R[6] * c02 + R[7] * c12 + R[8] * c22;
-  const float r00 = (w00 * R[0] + w01 * R[1] + w02 * R[2]) * iw;
-  const float r01 = (w00 * R[3] + w01 * R[4] + w02 * R[5]) * iw;
-  const float r02 = (w00 * R[6] + w01 * R[7] + w02 * R[8]) * iw;
-  const float r11 = (w10 * R[3] + w11 * R[4] + w12 * R[5]) * iw;
-  const float r12 = (w10 * R[6] + w11 * R[7] + w12 * R[8]) * iw;
-  const float r22 = (w20 * R[6] + w21 * R[7] + w22 * R[8]) * iw;
-  const float ux = q.x - V.t[0], uy = q.y - V.t[1], uz = q.z - V.t[2];
+  const float w00 = R0.x * c00 + R0.y * c01 + R0.z * c02;
+  const float w01 = R0.x * c01 + R0.y * c11 + R0.z * c12;
+  const float w02 = R0.x * c02 + R0.y * c12 + R0.z * c22;
+  const float w10 = R1.x * c00 + R1.y * c01 + R1.z * c02;
+  const float w11 = R1.x * c01 + R1.y * c11 + R1.z * c12;
+  const float w12 = R1.x * c02 + R1.y * c12 + R1.z * c22;
+  const float w20 = R2.x * c00 + R2.y * c01 + R2.z * c02;
+  const float w21 = R2.x * c01 + R2.y * c11 + R2.z * c12;
+  const float w22 = R2.x * c02 + R2.y * c12 + R2.z * c22;
+  const float r00 = (w00 * R0.x + w01 * R0.y + w02 * R0.z) * iw;
+  const float r01 = (w00 * R1.x + w01 * R1.y + w02 * R1.z) * iw;
+  const float r02 = (w00 * R2.x + w01 * R2.y + w02 * R2.z) * iw;
+  const float r11 = (w10 * R1.x + w11 * R1.y + w12 * R1.z) * iw;
+  const float r12 = (w10 * R2.x + w11 * R2.y + w12 * R2.z) * iw;
+  const float r22 = (w20 * R2.x + w21 * R2.y + w22 * R2.z) * iw;
+  const float ux = q.x - R0.w, uy = q.y - R1.w, uz = q.z - R2.w;
   // append the hits to the ring: level-major, lane order within a level
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
     const bool hit = __float_as_int(s0[l].x) >= 0;  // occupied cell (empty records hold 0x80808080)
     const unsigned mask = __ballot_sync(0xffffffffu, hit);
-    const int below = __popc(mask & lt), nhit = __popc(mask);
-    int slot = tail + (hit ? below : nhit + lane - below);
-    slot = slot >= S ? slot - S : slot;
-    float4* t = ring.term + 3 * slot;
-    // voxel record: s0 = {id, ., ., C~22}, s1 = {mean, C~00}, s2 = {C~01, C~02, C~11, C~12}
-    t[0] = make_float4(__fmaf_rn(s1[l].w, iw, r00), __fmaf_rn(s2[l].x, iw, r01), __fmaf_rn(s2[l].y, iw, r02),
-                       __fmaf_rn(s2[l].z, iw, r11));
-    t[1] = make_float4(__fmaf_rn(s2[l].w, iw, r12), __fmaf_rn(s0[l].w, iw, r22), s1[l].x - q.x, s1[l].y - q.y);
-    t[2] = make_float4(s1[l].z - q.z, ux, uy, uz);
+    const int slot = (tail + __popc(mask & lt)) & (S - 1);
+    st_shared_if(hit, &ring.r0[slot],
+                 make_float4(__fmaf_rn(s1[l].w, iw, r00), __fmaf_rn(s2[l].x, iw, r01), __fmaf_rn(s2[l].y, iw, r02),
+                             __fmaf_rn(s2[l].z, iw, r11)));
+    st_shared_if(hit, &ring.r1[slot],
+                 make_float4(__fmaf_rn(s2[l].w, iw, r12), __fmaf_rn(s0[l].y, iw, r22), s1[l].x - q.x,
+                             s1[l].y - q.y));
+    st_shared_if(hit, &ring.r2[slot], make_float4(s1[l].z - q.z, ux, uy, uz));
     inl += hit ? 1 : 0;
-    tail += nhit;
-    tail = tail >= S ? tail - S : tail;
+    tail = (tail + __popc(mask)) & (S - 1);
   }
   __syncwarp();
-  int avail = tail - head;
-  avail = avail < 0 ? avail + S : avail;
+  int avail = (tail - head) & (S - 1);
   while (avail >= 32) {
-    int i = head + lane;
-    i = i >= S ? i - S : i;
-    accumulate_term(ring.term[3 * i], ring.term[3 * i + 1], ring.term[3 * i + 2], acc);
-    head += 32;
-    head = head >= S ? head - S : head;
+    const int i = (head + lane) & (S - 1);
+    accumulate_term(ring.r0[i], ring.r1[i], ring.r2[i], acc);
+    head = (head + 32) & (S - 1);
     avail -= 32;
   }
   __syncwarp();  // taken records may be overwritten by the next round
@@ -529,12 +542,8 @@ __device__ __forceinline__ void process_item_dense(const LinArgs& a, int item, D
     const PairDev pd = a.pairs[it.pair];
     const PoseF pf = a.pose[it.pair];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) V.R[i] = pf.R[i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      V.t[i] = pf.t[i];
-      V.v[i] = pf.v[i];
-    }
+    for (int r = 0; r < 3; ++r) V.Rt[r] = make_float4(pf.R[3 * r], pf.R[3 * r + 1], pf.R[3 * r + 2], pf.t[r]);
+    V.v = make_float4(pf.v[0], pf.v[1], pf.v[2], 0.f);
     const FrameDev F = a.frames[pd.src];
     V.pts = F.pts;
     V.cov = F.cov;
@@ -552,21 +561,26 @@ __device__ __forceinline__ void process_item_dense(const LinArgs& a, int item, D
   const int first = it.start + int(threadIdx.x);
   const int rounds = min(a.ppt, (last - it.start) / BLOCK + 1);
   int head = 0, tail = 0;
-  // software pipeline: the next round's point is read while the current round is processed
-  PointIn cur = load_point32(V.pts, V.cov, min(first, last));
+  // software pipeline, unrolled twice so that the two point buffers alternate without copies
+  PointIn p0 = load_point32(V.pts, V.cov, min(first, last));
+  int j = 0;
 #pragma unroll 1
-  for (int j = 0; j < rounds; ++j) {
+  for (; j + 1 < rounds; j += 2) {
     const int k = first + j * BLOCK;
-    const PointIn nxt = load_point32(V.pts, V.cov, min(k + BLOCK, last));
-    dense_round<LMAX>(V, cur, k <= last, a.validate, ring, head, tail, acc, inl, lane, lt, min(k, last));
-    cur = nxt;
+    const PointIn p1 = load_point32(V.pts, V.cov, min(k + BLOCK, last));
+    dense_round<LMAX>(V, p0, k <= last, a.validate, ring, head, tail, acc, inl, lane, lt, min(k, last));
+    p0 = load_point32(V.pts, V.cov, min(k + 2 * BLOCK, last));
+    dense_round<LMAX>(V, p1, k + BLOCK <= last, a.validate, ring, head, tail, acc, inl, lane, lt,
+                      min(k + BLOCK, last));
   }
-  int avail = tail - head;  // the last partial batch
-  avail = avail < 0 ? avail + DenseRing<LMAX>::S : avail;
+  if (j < rounds) {
+    const int k = first + j * BLOCK;
+    dense_round<LMAX>(V, p0, k <= last, a.validate, ring, head, tail, acc, inl, lane, lt, min(k, last));
+  }
+  const int avail = (tail - head) & (DenseRing<LMAX>::S - 1);  // the last partial batch
   if (lane < avail) {
-    int i = head + lane;
-    i = i >= DenseRing<LMAX>::S ? i - DenseRing<LMAX>::S : i;
-    accumulate_term(ring.term[3 * i], ring.term[3 * i + 1], ring.term[3 * i + 2], acc);
+    const int i = (head + lane) & (DenseRing<LMAX>::S - 1);
+    accumulate_term(ring.r0[i], ring.r1[i], ring.r2[i], acc);
   }
   __syncwarp();
   block_reduce_store<BLOCK, ACC>(acc, inl, a.part + int64_t(item) * PSTRIDE);

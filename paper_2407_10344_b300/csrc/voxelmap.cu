@@ -142,7 +142,8 @@ __global__ void k_dense_build(const unsigned long long* __restrict__ vkey, const
   const unsigned long long key = vkey[v];
   const int kx = unpack_x(key), ky = unpack_y(key), kz = unpack_z(key);
   VoxSlot r;
-  r.w0 = make_float4(__int_as_float(int(v)), __int_as_float(kx), __int_as_float(ky), vcov[6 * v + 5]);
+  // {id, C~22, kx, C~22}: C~22 at .w as in a hash slot, and next to the id for one 8-byte read
+  r.w0 = make_float4(__int_as_float(int(v)), vcov[6 * v + 5], __int_as_float(kx), vcov[6 * v + 5]);
   r.w1 = make_float4(vmean[3 * v], vmean[3 * v + 1], vmean[3 * v + 2], vcov[6 * v + 0]);
   r.w2 = make_float4(vcov[6 * v + 1], vcov[6 * v + 2], vcov[6 * v + 3], vcov[6 * v + 4]);
   cells[(int64_t(kx - ox) * ny + (ky - oy)) * nz + (kz - oz)] = r;
