@@ -14,6 +14,8 @@
 // ([u x g_sum; g_sum]) and e += e_sum: 28 accumulators, expanded once per pair into
 // H = Lift^T M Lift and b = Lift^T g with Lift = [-diag(R, R), S_t].
 #pragma once
+#include <cstddef>
+
 #include "plan.cuh"
 
 namespace glim_detail {
@@ -428,22 +430,17 @@ struct __align__(16) DenseView {  // per-item constants, written by thread 0
   DenseMapDev M;
 };
 
+// The level descriptors and inverse resolutions are read as 16-byte words.
+static_assert(sizeof(DenseLevelDev) == 32 && offsetof(DenseView, M) % 16 == 0 &&
+                  offsetof(DenseMapDev, inv_r) % 16 == 0,
+              "dense descriptors must sit on 16-byte boundaries");
+
 template <int LMAX>
 struct DenseRing {
   // 31 waiting records + 32 LMAX appended ones fit; a power of two for the index wrap
   static constexpr int S = LMAX == 1 ? 64 : (LMAX <= 3 ? 128 : 256);
   float4 r0[S], r1[S], r2[S];
 };
-
-__device__ __forceinline__ PointIn load_point32(const float4* pts, const float2* cov, int k) {
-  PointIn p;
-  p.m = ldg4(pts + k);
-  const float2* c = cov + 3 * int64_t(k);
-  p.ca = __ldg(c);
-  p.cb = __ldg(c + 1);
-  p.cc = __ldg(c + 2);
-  return p;
-}
 
 // Shared-memory store of a float4 by the lanes whose predicate is set.
 __device__ __forceinline__ void st_shared_if(bool p, float4* addr, float4 v) {
@@ -456,11 +453,14 @@ __device__ __forceinline__ void st_shared_if(bool p, float4* addr, float4 v) {
 }
 
 template <int LMAX, class A>
-__device__ __forceinline__ void dense_round(const DenseView& V, const PointIn& in, bool live, int validate,
+__device__ __forceinline__ void dense_round(const DenseView& V, const float4 m, bool live, int validate,
                                             DenseRing<LMAX>& ring, int& head, int& tail, A& acc, int& inl,
                                             int lane, unsigned lt, int kk) {
   constexpr int S = DenseRing<LMAX>::S;
-  const float4 m = in.m;
+  // the covariance is read here rather than a round ahead: it is needed only after the voxel
+  // reads are in flight, and the registers it would hold are worth more as occupancy
+  const float2* cp = V.cov + 3 * int64_t(kk);
+  const float2 ca = __ldg(cp), cb = __ldg(cp + 1), cc = __ldg(cp + 2);
   if (validate && V.nrm) {
     const float* nk = V.nrm + 3 * int64_t(kk);
     const float vv[3] = {V.v.x, V.v.y, V.v.z};
@@ -475,23 +475,29 @@ __device__ __forceinline__ void dense_round(const DenseView& V, const PointIn& i
   live = live && q.x == q.x && q.y == q.y && q.z == q.z;
   float2 s0[LMAX];
   float4 s1[LMAX], s2[LMAX];
+  const float4 irq = *reinterpret_cast<const float4*>(V.M.inv_r);  // one 16-byte shared load
+  const float irv[4] = {irq.x, irq.y, irq.z, irq.w};
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
-    const DenseLevelDev& L = V.M.lv[l];
-    const float ir = V.M.inv_r[l];
+    // the level's descriptor as two 16-byte shared loads: {cells, ox, oy} {oz, nx, ny, nz}
+    const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
+    const uint4 lb = reinterpret_cast<const uint4*>(&V.M.lv[l])[1];
+    const float ir = irv[l];
+    const VoxSlot* cells =
+        reinterpret_cast<const VoxSlot*>(uint64_t(uint32_t(la.x)) | (uint64_t(uint32_t(la.y)) << 32));
     // keys floor(q * inv_r) (FP32 product); a key outside [-2^20, 2^20) is outside every box
-    const uint32_t x = uint32_t(__float2int_rd(__fmul_rn(q.x, ir))) - uint32_t(L.ox);
-    const uint32_t y = uint32_t(__float2int_rd(__fmul_rn(q.y, ir))) - uint32_t(L.oy);
-    const uint32_t z = uint32_t(__float2int_rd(__fmul_rn(q.z, ir))) - uint32_t(L.oz);
-    const bool in_box = live && x < L.nx && y < L.ny && z < L.nz;
-    const VoxSlot* sl = L.cells + (in_box ? int((x * L.ny + y) * L.nz + z) : -1);
+    const uint32_t x = uint32_t(__float2int_rd(__fmul_rn(q.x, ir))) - uint32_t(la.z);
+    const uint32_t y = uint32_t(__float2int_rd(__fmul_rn(q.y, ir))) - uint32_t(la.w);
+    const uint32_t z = uint32_t(__float2int_rd(__fmul_rn(q.z, ir))) - lb.x;
+    const bool in_box = live && x < lb.y && y < lb.z && z < lb.w;
+    const VoxSlot* sl = cells + (in_box ? int((x * lb.z + y) * lb.w + z) : -1);
     s0[l] = __ldg(reinterpret_cast<const float2*>(&sl->w0));  // {id, C~22}
     s1[l] = ldg4(&sl->w1);                                    // {mean, C~00}
     s2[l] = ldg4(&sl->w2);                                    // {C~01, C~02, C~11, C~12}
   }
   // R C R^T / w (once for all levels) and u = R mu
   const float iw = __fdividef(1.0f, m.w);
-  const float c00 = in.ca.x, c01 = in.ca.y, c02 = in.cb.x, c11 = in.cb.y, c12 = in.cc.x, c22 = in.cc.y;
+  const float c00 = ca.x, c01 = ca.y, c02 = cb.x, c11 = cb.y, c12 = cc.x, c22 = cc.y;
   const float w00 = R0.x * c00 + R0.y * c01 + R0.z * c02;
   const float w01 = R0.x * c01 + R0.y * c11 + R0.z * c12;
   const float w02 = R0.x * c02 + R0.y * c12 + R0.z * c22;
@@ -561,15 +567,16 @@ __device__ __forceinline__ void process_item_dense(const LinArgs& a, int item, D
   const int first = it.start + int(threadIdx.x);
   const int rounds = min(a.ppt, (last - it.start) / BLOCK + 1);
   int head = 0, tail = 0;
-  // software pipeline, unrolled twice so that the two point buffers alternate without copies
-  PointIn p0 = load_point32(V.pts, V.cov, min(first, last));
+  // software pipeline of the point coordinates, unrolled twice so that the two buffers
+  // alternate without copies
+  float4 p0 = ldg4(V.pts + min(first, last));
   int j = 0;
 #pragma unroll 1
   for (; j + 1 < rounds; j += 2) {
     const int k = first + j * BLOCK;
-    const PointIn p1 = load_point32(V.pts, V.cov, min(k + BLOCK, last));
+    const float4 p1 = ldg4(V.pts + min(k + BLOCK, last));
     dense_round<LMAX>(V, p0, k <= last, a.validate, ring, head, tail, acc, inl, lane, lt, min(k, last));
-    p0 = load_point32(V.pts, V.cov, min(k + 2 * BLOCK, last));
+    p0 = ldg4(V.pts + min(k + 2 * BLOCK, last));
     dense_round<LMAX>(V, p1, k + BLOCK <= last, a.validate, ring, head, tail, acc, inl, lane, lt,
                       min(k + BLOCK, last));
   }
@@ -591,8 +598,10 @@ constexpr size_t lin_dense_dyn_smem() {
   return size_t(BLOCK / 32) * sizeof(DenseRing<LMAX>);
 }
 
+// 128-thread blocks: five per SM (at most 102 registers a thread), which hides the voxel
+// reads' latency better than four blocks with more registers.
 template <int BLOCK, int ACC, int LMAX>
-__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize_dense(const LinArgs a) {
+__global__ void __launch_bounds__(BLOCK, 640 / BLOCK) k_linearize_dense(const LinArgs a) {
   __shared__ DenseView V;
   __shared__ int s_item[2];
   extern __shared__ float4 dyn_smem[];

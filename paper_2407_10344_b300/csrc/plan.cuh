@@ -29,6 +29,7 @@ struct MapDev {
 // cells[((kx - ox) * ny + (ky - oy)) * nz + (kz - oz)] inside the box, and cells[-1] (an empty
 // record) is read for every key outside it.  A level that a map does not have is a box of
 // size 0 whose cells[-1] is some map's empty record.
+// 32 bytes, read by the kernel as two 16-byte words (offsets checked where it is read).
 struct DenseLevelDev {
   const VoxSlot* cells;
   int32_t ox, oy, oz;
