@@ -31,9 +31,16 @@ METRIC = "source points linearized/s (e+H+b) and % HBM peak; ms per global batch
 UNIT = "points/s"
 BYTES_PER_POINT = 40  # float4 point + 6 floats covariance, read once per (pair, point)
 # DRAM bytes (read + write) per (pair, point) of the linearization kernel, from one ncu capture
-# of this kernel version on the 40-submap urban case (profiles/k_linearize_urban40_ncu_full.md),
-# scaled by the units of a launch.  Set to None when the kernel changes until it is re-measured.
-DRAM_BYTES_PER_PAIR_POINT = 11.05
+# of this kernel version on the 40-submap urban case, scaled by the units of a launch.  None
+# when the kernel has changed since the capture.
+DRAM_BYTES_PER_PAIR_POINT = None
+# Algorithmic FP32 flops of the linearization (the formulation the kernels implement; a fused
+# multiply-add counts two): per (pair, point) the transform (18), 3 keys per level (9 at 3
+# levels), R C R^T (75), 1/w and the scaling (7), u (3); per hit term S' (12), d (3), the
+# adjugate (18), det (5), 1/det (1), Omega (6), Omega d (15), (u)x Omega (27), M_rr (24),
+# M_rt (9), M_tt (6), g (15), e (6).
+FLOPS_PER_PAIR_POINT_BASE = 103  # + 3 per level
+FLOPS_PER_HIT = 147
 
 
 def peaks():
@@ -367,7 +374,8 @@ def run_ours(args):
     value = total_pp * K / (tmax / 1e3)
     # e2e: public call with host poses in / host results out, copies in the timed region
     e2e_steps = max(3, min(K, 10))
-    plan.linearize(w.poses)  # capture the full graph outside the timing
+    _, _, _, inl_out = plan.linearize(w.poses)  # capture the full graph outside the timing
+    hits = int(np.asarray(inl_out).sum())
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -398,6 +406,11 @@ def run_ours(args):
     hbm_peak = pk.get("hbm_gbs", 6400.0)
     kavg_ms = float(np.mean(kern_ms))
     achieved = BYTES_PER_POINT * n_pp / (kavg_ms / 1e3) / 1e9
+    flops = (FLOPS_PER_PAIR_POINT_BASE + 3 * len(w.resolutions)) * n_pp + FLOPS_PER_HIT * hits
+    fma_peak = ctx.fp32_fma_peak()
+    sm_max = pk.get("sm_max_mhz", 2032.0)
+    fp32_nominal = ctx.num_sms * 128 * 2 * sm_max * 1e6 / 1e12
+    kernel_name = "k_linearize_dense" if opts.get("kernel") == "dense" else "k_linearize"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": tmax / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -414,9 +427,16 @@ def run_ours(args):
                      "frac": achieved / hbm_peak,
                      "traffic": None if DRAM_BYTES_PER_PAIR_POINT is None else DRAM_BYTES_PER_PAIR_POINT * n_pp,
                      "traffic_note": "ncu dram bytes of a 40-submap capture scaled by (pair, point) units",
-                     "kernel": "k_linearize (persistent work queue)", "kernel_ms": kavg_ms,
+                     "kernel": kernel_name + " (persistent work queue)", "kernel_ms": kavg_ms,
                      "algorithmic_bytes_per_launch": BYTES_PER_POINT * n_pp,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk else "fallback"},
+        "roofline_fp32": {"bound": "alu", "achieved": flops / (kavg_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                          "peak": fp32_nominal, "frac": flops / (kavg_ms / 1e3) / 1e12 / fp32_nominal,
+                          "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % (ctx.num_sms, sm_max),
+                          "fma_chain_measured_tflops": fma_peak,
+                          "frac_of_measured": flops / (kavg_ms / 1e3) / 1e12 / fma_peak,
+                          "algorithmic_flops_per_launch": flops, "hit_terms_per_launch": hits,
+                          "note": "the kernel is bound by instruction issue and the L1 data pipe, not DRAM"},
         "e2e": {"value": total_pp / e2e_s if ws == 1 else n_pp / e2e_s * ws, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "note": "glim_plan_linearize: host poses -> serialized upload -> graph -> download -> sync; "

@@ -126,6 +126,11 @@ const char* glim_last_error(const glim_ctx* ctx);
 int32_t glim_num_sms(const glim_ctx* ctx);
 /* Number of kernels this context has launched since creation (for accounting). */
 int64_t glim_kernel_launches(const glim_ctx* ctx);
+/* Measured FP32 multiply-add throughput of the context's device in TFLOP/s (two flops per
+ * FMA): eight independent register-resident FMA chains per thread, eight 256-thread blocks
+ * per SM, `iters` x 128 FMAs per thread, best of three timed launches after a warm-up.  The
+ * denominator of the FP32 roofline of the linearization kernel.  Synchronizes the stream. */
+glim_status glim_fp32_fma_peak(glim_ctx* ctx, int32_t iters, double* tflops_out);
 
 /* ---------------------------------------------------------------- covariances */
 

@@ -92,6 +92,12 @@ class Context:
     def kernel_launches(self):
         return int(self.lib.glim_kernel_launches(self.h))
 
+    def fp32_fma_peak(self, iters=4096):
+        """Measured FP32 FMA throughput of the device in TFLOP/s (FMA-chain kernel)."""
+        out = C.c_double()
+        self.call("fp32_fma_peak", self.lib.glim_fp32_fma_peak, self.h, int(iters), C.byref(out))
+        return out.value
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.glim_destroy(self.h)

@@ -410,16 +410,16 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize(const LinArgs 
 }
 
 // ---------------------------------------------------------------- dense-grid kernel
-// Every target level is a dense grid: a lookup is an index computation and one read, so
-// phase 1 runs without divergent branches.  A key outside the grid's box reads the empty
-// record before cell 0; a lane past the end of its tile reads its tile's last point and is
-// masked.  Hit records are appended (predicated stores) to a per-warp ring of S records,
-// kept as three arrays of float4 so that a record's parts share one index.  Phase 2 takes
-// full batches of 32 records only; the rest waits for the next round, and the item's last
-// partial batch is taken at its end.  Results equal those of the general kernel up to FP32
-// summation order.
+// Every target level is a dense grid: a lookup is an index computation and one read, so a
+// lane handles its own point from start to end without divergent branches.  A key outside
+// the grid's box reads the empty record before cell 0; a lane past the end of its tile reads
+// its tile's last point and is masked.  Because G = [-(u)x, I] is the same for all levels of
+// a point, the lane sums w Omega, w Omega d and e over the levels (a miss, or a term whose S'
+// is not positive definite, adds exact zeros) and adds the G-form of the sums once: 28
+// accumulator updates per point instead of per hit.  Results equal those of the general
+// kernel up to FP32 rounding order.
 
-struct __align__(16) DenseView {  // per-item constants, written by thread 0
+struct DenseView {  // per-item constants, written by thread 0
   float4 Rt[3];  // rows of [R | t]
   float4 v;      // target viewpoint (surface validation)
   const float4* pts;
@@ -435,28 +435,9 @@ static_assert(sizeof(DenseLevelDev) == 32 && offsetof(DenseView, M) % 16 == 0 &&
                   offsetof(DenseMapDev, inv_r) % 16 == 0,
               "dense descriptors must sit on 16-byte boundaries");
 
-template <int LMAX>
-struct DenseRing {
-  // 31 waiting records + 32 LMAX appended ones fit; a power of two for the index wrap
-  static constexpr int S = LMAX == 1 ? 64 : (LMAX <= 3 ? 128 : 256);
-  float4 r0[S], r1[S], r2[S];
-};
-
-// Shared-memory store of a float4 by the lanes whose predicate is set.
-__device__ __forceinline__ void st_shared_if(bool p, float4* addr, float4 v) {
-  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(addr));
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.shared.v4.f32 [%1], {%2, %3, %4, %5};\n\t}"
-      :
-      : "r"(int(p)), "r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-      : "memory");
-}
-
 template <int LMAX, class A>
-__device__ __forceinline__ void dense_round(const DenseView& V, const float4 m, bool live, int validate,
-                                            DenseRing<LMAX>& ring, int& head, int& tail, A& acc, int& inl,
-                                            int lane, unsigned lt, int kk) {
-  constexpr int S = DenseRing<LMAX>::S;
+__device__ __forceinline__ void dense_point(const DenseView& V, const float4 m, bool live, int validate, A& acc,
+                                            int& inl, int kk) {
   // the covariance is read here rather than a round ahead: it is needed only after the voxel
   // reads are in flight, and the registers it would hold are worth more as occupancy
   const float2* cp = V.cov + 3 * int64_t(kk);
@@ -471,8 +452,13 @@ __device__ __forceinline__ void dense_round(const DenseView& V, const float4 m, 
   q.x = __fmaf_rn(R0.z, m.z, __fmaf_rn(R0.y, m.y, __fmaf_rn(R0.x, m.x, R0.w)));
   q.y = __fmaf_rn(R1.z, m.z, __fmaf_rn(R1.y, m.y, __fmaf_rn(R1.x, m.x, R1.w)));
   q.z = __fmaf_rn(R2.z, m.z, __fmaf_rn(R2.y, m.y, __fmaf_rn(R2.x, m.x, R2.w)));
-  // keys of infinite or huge coordinates saturate outside every box; a NaN would convert to 0
-  live = live && q.x == q.x && q.y == q.y && q.z == q.z;
+  // keys of infinite or huge coordinates saturate outside every box; a NaN would convert to
+  // 0, so a NaN point is masked (and zeroed, so that its masked arithmetic stays finite)
+  const bool finite_q = q.x == q.x && q.y == q.y && q.z == q.z;
+  live = live && finite_q;
+  q.x = finite_q ? q.x : 0.f;
+  q.y = finite_q ? q.y : 0.f;
+  q.z = finite_q ? q.z : 0.f;
   float2 s0[LMAX];
   float4 s1[LMAX], s2[LMAX];
   const float4 irq = *reinterpret_cast<const float4*>(V.M.inv_r);  // one 16-byte shared load
@@ -495,7 +481,7 @@ __device__ __forceinline__ void dense_round(const DenseView& V, const float4 m, 
     s1[l] = ldg4(&sl->w1);                                    // {mean, C~00}
     s2[l] = ldg4(&sl->w2);                                    // {C~01, C~02, C~11, C~12}
   }
-  // R C R^T / w (once for all levels) and u = R mu
+  // R C R^T / w (once for all levels)
   const float iw = __fdividef(1.0f, m.w);
   const float c00 = ca.x, c01 = ca.y, c02 = cb.x, c11 = cb.y, c12 = cc.x, c22 = cc.y;
   const float w00 = R0.x * c00 + R0.y * c01 + R0.z * c02;
@@ -513,36 +499,56 @@ __device__ __forceinline__ void dense_round(const DenseView& V, const float4 m, 
   const float r11 = (w10 * R1.x + w11 * R1.y + w12 * R1.z) * iw;
   const float r12 = (w10 * R2.x + w11 * R2.y + w12 * R2.z) * iw;
   const float r22 = (w20 * R2.x + w21 * R2.y + w22 * R2.z) * iw;
-  const float ux = q.x - R0.w, uy = q.y - R1.w, uz = q.z - R2.w;
-  // append the hits to the ring: level-major, lane order within a level
+  // per level: S' = C~ / w + R C R^T / w, w Omega = adj(S') / det(S'), y = w Omega d; the
+  // sums over levels (a term that is a miss or not positive definite adds zeros)
+  float O00 = 0.f, O01 = 0.f, O02 = 0.f, O11 = 0.f, O12 = 0.f, O22 = 0.f;
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, es = 0.f;
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
     const bool hit = __float_as_int(s0[l].x) >= 0;  // occupied cell (empty records hold 0x80808080)
-    const unsigned mask = __ballot_sync(0xffffffffu, hit);
-    const int slot = (tail + __popc(mask & lt)) & (S - 1);
-    st_shared_if(hit, &ring.r0[slot],
-                 make_float4(__fmaf_rn(s1[l].w, iw, r00), __fmaf_rn(s2[l].x, iw, r01), __fmaf_rn(s2[l].y, iw, r02),
-                             __fmaf_rn(s2[l].z, iw, r11)));
-    st_shared_if(hit, &ring.r1[slot],
-                 make_float4(__fmaf_rn(s2[l].w, iw, r12), __fmaf_rn(s0[l].y, iw, r22), s1[l].x - q.x,
-                             s1[l].y - q.y));
-    st_shared_if(hit, &ring.r2[slot], make_float4(s1[l].z - q.z, ux, uy, uz));
     inl += hit ? 1 : 0;
-    tail = (tail + __popc(mask)) & (S - 1);
+    const float a = __fmaf_rn(s1[l].w, iw, r00), b = __fmaf_rn(s2[l].x, iw, r01), c = __fmaf_rn(s2[l].y, iw, r02);
+    const float d = __fmaf_rn(s2[l].z, iw, r11), e = __fmaf_rn(s2[l].w, iw, r12), f = __fmaf_rn(s0[l].y, iw, r22);
+    const float dx = s1[l].x - q.x, dy = s1[l].y - q.y, dz = s1[l].z - q.z;
+    const float A00 = d * f - e * e, A01 = c * e - b * f, A02 = b * e - c * d;
+    const float A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
+    const float det = a * A00 + b * A01 + c * A02;
+    const bool ok = hit && det > 0.f && det < INFINITY;
+    const float id = __fdividef(1.0f, det);
+    // selected, not multiplied by 0: adj(S') of a masked term need not be finite
+    const float o00 = ok ? A00 * id : 0.f, o01 = ok ? A01 * id : 0.f, o02 = ok ? A02 * id : 0.f;
+    const float o11 = ok ? A11 * id : 0.f, o12 = ok ? A12 * id : 0.f, o22 = ok ? A22 * id : 0.f;
+    const float y0 = o00 * dx + o01 * dy + o02 * dz;
+    const float y1 = o01 * dx + o11 * dy + o12 * dz;
+    const float y2 = o02 * dx + o12 * dy + o22 * dz;
+    es = __fmaf_rn(dx, y0, __fmaf_rn(dy, y1, __fmaf_rn(dz, y2, es)));
+    O00 += o00; O01 += o01; O02 += o02; O11 += o11; O12 += o12; O22 += o22;
+    g0 += y0; g1 += y1; g2 += y2;
   }
-  __syncwarp();
-  int avail = (tail - head) & (S - 1);
-  while (avail >= 32) {
-    const int i = (head + lane) & (S - 1);
-    accumulate_term(ring.r0[i], ring.r1[i], ring.r2[i], acc);
-    head = (head + 32) & (S - 1);
-    avail -= 32;
-  }
-  __syncwarp();  // taken records may be overwritten by the next round
+  // the G-form of the sums, G = [-(u)x, I] with u = R mu
+  const float ux = q.x - R0.w, uy = q.y - R1.w, uz = q.z - R2.w;
+  const float W00 = -uz * O01 + uy * O02, W01 = -uz * O11 + uy * O12, W02 = -uz * O12 + uy * O22;
+  const float W10 = uz * O00 - ux * O02, W11 = uz * O01 - ux * O12, W12 = uz * O02 - ux * O22;
+  const float W20 = -uy * O00 + ux * O01, W21 = -uy * O01 + ux * O11, W22 = -uy * O02 + ux * O12;
+  acc.add2(0, -uz, W01, uy, W02);
+  acc.add2(1, uz, W00, -ux, W02);
+  acc.add2(2, -uy, W00, ux, W01);
+  acc.add2(3, uz, W10, -ux, W12);
+  acc.add2(4, -uy, W10, ux, W11);
+  acc.add2(5, -uy, W20, ux, W21);
+  acc.add(6, W00); acc.add(7, W01); acc.add(8, W02);
+  acc.add(9, W10); acc.add(10, W11); acc.add(11, W12);
+  acc.add(12, W20); acc.add(13, W21); acc.add(14, W22);
+  acc.add(15, O00); acc.add(16, O01); acc.add(17, O02); acc.add(18, O11); acc.add(19, O12); acc.add(20, O22);
+  acc.add2(21, uy, g2, -uz, g1);
+  acc.add2(22, uz, g0, -ux, g2);
+  acc.add2(23, ux, g1, -uy, g0);
+  acc.add(24, g0); acc.add(25, g1); acc.add(26, g2);
+  acc.add(27, es);
 }
 
 template <int BLOCK, int ACC, int LMAX>
-__device__ __forceinline__ void process_item_dense(const LinArgs& a, int item, DenseView& V, DenseRing<LMAX>& ring) {
+__device__ __forceinline__ void process_item_dense(const LinArgs& a, int item, DenseView& V) {
   const Item it = a.items[item];
   if (threadIdx.x == 0) {
     const PairDev pd = a.pairs[it.pair];
@@ -561,12 +567,9 @@ __device__ __forceinline__ void process_item_dense(const LinArgs& a, int item, D
   typename AccOf<ACC>::type acc;
   acc.zero();
   int inl = 0;
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
   const int last = V.end - 1;  // items are never empty
   const int first = it.start + int(threadIdx.x);
   const int rounds = min(a.ppt, (last - it.start) / BLOCK + 1);
-  int head = 0, tail = 0;
   // software pipeline of the point coordinates, unrolled twice so that the two buffers
   // alternate without copies
   float4 p0 = ldg4(V.pts + min(first, last));
@@ -575,40 +578,29 @@ __device__ __forceinline__ void process_item_dense(const LinArgs& a, int item, D
   for (; j + 1 < rounds; j += 2) {
     const int k = first + j * BLOCK;
     const float4 p1 = ldg4(V.pts + min(k + BLOCK, last));
-    dense_round<LMAX>(V, p0, k <= last, a.validate, ring, head, tail, acc, inl, lane, lt, min(k, last));
+    dense_point<LMAX>(V, p0, k <= last, a.validate, acc, inl, min(k, last));
     p0 = ldg4(V.pts + min(k + 2 * BLOCK, last));
-    dense_round<LMAX>(V, p1, k + BLOCK <= last, a.validate, ring, head, tail, acc, inl, lane, lt,
-                      min(k + BLOCK, last));
+    dense_point<LMAX>(V, p1, k + BLOCK <= last, a.validate, acc, inl, min(k + BLOCK, last));
   }
   if (j < rounds) {
     const int k = first + j * BLOCK;
-    dense_round<LMAX>(V, p0, k <= last, a.validate, ring, head, tail, acc, inl, lane, lt, min(k, last));
+    dense_point<LMAX>(V, p0, k <= last, a.validate, acc, inl, min(k, last));
   }
-  const int avail = (tail - head) & (DenseRing<LMAX>::S - 1);  // the last partial batch
-  if (lane < avail) {
-    const int i = (head + lane) & (DenseRing<LMAX>::S - 1);
-    accumulate_term(ring.r0[i], ring.r1[i], ring.r2[i], acc);
-  }
-  __syncwarp();
   block_reduce_store<BLOCK, ACC>(acc, inl, a.part + int64_t(item) * PSTRIDE);
 }
 
 template <int BLOCK, int LMAX>
 constexpr size_t lin_dense_dyn_smem() {
-  return size_t(BLOCK / 32) * sizeof(DenseRing<LMAX>);
+  return 0;
 }
 
-// 128-thread blocks: five per SM (at most 102 registers a thread), which hides the voxel
-// reads' latency better than four blocks with more registers.
 template <int BLOCK, int ACC, int LMAX>
-__global__ void __launch_bounds__(BLOCK, 640 / BLOCK) k_linearize_dense(const LinArgs a) {
+__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize_dense(const LinArgs a) {
   __shared__ DenseView V;
   __shared__ int s_item[2];
-  extern __shared__ float4 dyn_smem[];
-  DenseRing<LMAX>& ring = reinterpret_cast<DenseRing<LMAX>*>(dyn_smem)[threadIdx.x >> 5];
   if (a.head == nullptr) {
     const int item = a.item_base + blockIdx.x;
-    if (item < a.nitems) process_item_dense<BLOCK, ACC, LMAX>(a, item, V, ring);
+    if (item < a.nitems) process_item_dense<BLOCK, ACC, LMAX>(a, item, V);
     return;
   }
   if (threadIdx.x == 0) s_item[0] = atomicAdd(a.head, 1);
@@ -617,7 +609,7 @@ __global__ void __launch_bounds__(BLOCK, 640 / BLOCK) k_linearize_dense(const Li
   for (int b = 1;; b ^= 1) {
     if (cur >= a.nitems) break;
     if (threadIdx.x == 0) s_item[b] = atomicAdd(a.head, 1);
-    process_item_dense<BLOCK, ACC, LMAX>(a, cur, V, ring);  // ends with a barrier
+    process_item_dense<BLOCK, ACC, LMAX>(a, cur, V);  // ends with a barrier
     cur = s_item[b];
   }
 }
