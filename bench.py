@@ -31,16 +31,18 @@ METRIC = "source points linearized/s (e+H+b) and % HBM peak; ms per global batch
 UNIT = "points/s"
 BYTES_PER_POINT = 40  # float4 point + 6 floats covariance, read once per (pair, point)
 # DRAM bytes (read + write) per (pair, point) of the linearization kernel, from one ncu capture
-# of this kernel version on the 40-submap urban case, scaled by the units of a launch.  None
+# of this kernel version on the 40-submap urban case (k_linearize_dense_urban40_ncu_full.md
+# under profiles), scaled by the units of a launch.  None
 # when the kernel has changed since the capture.
-DRAM_BYTES_PER_PAIR_POINT = None
-# Algorithmic FP32 flops of the linearization (the formulation the kernels implement; a fused
-# multiply-add counts two): per (pair, point) the transform (18), 3 keys per level (9 at 3
-# levels), R C R^T (75), 1/w and the scaling (7), u (3); per hit term S' (12), d (3), the
-# adjugate (18), det (5), 1/det (1), Omega (6), Omega d (15), (u)x Omega (27), M_rr (24),
-# M_rt (9), M_tt (6), g (15), e (6).
-FLOPS_PER_PAIR_POINT_BASE = 103  # + 3 per level
-FLOPS_PER_HIT = 147
+DRAM_BYTES_PER_PAIR_POINT = 11.30
+# Algorithmic FP32 flops of the linearization, counted on the per-term evaluation (a fused
+# multiply-add counts two): per (pair, point) the transform (18), 3 key products per level,
+# R C R^T (75) and u (3); per hit term S = C~ + R C R^T (6), d (3), the adjugate (18), det (5),
+# w / det (2), w Omega (6), y = w Omega d (15), and that term's G-form: (u)x w Omega (27),
+# M_rr (24), M_rt (9), M_tt (6), g (15), e (6).  The dense-grid kernel forms one G-form per
+# point from the level sums, so it executes fewer flops than this count.
+FLOPS_PER_PAIR_POINT_BASE = 96  # + 3 per level
+FLOPS_PER_HIT = 142
 
 
 def peaks():
@@ -436,7 +438,7 @@ def run_ours(args):
                           "fma_chain_measured_tflops": fma_peak,
                           "frac_of_measured": flops / (kavg_ms / 1e3) / 1e12 / fma_peak,
                           "algorithmic_flops_per_launch": flops, "hit_terms_per_launch": hits,
-                          "note": "the kernel is bound by instruction issue and the L1 data pipe, not DRAM"},
+                          "note": "the kernel is bound by instruction issue (64 % of its instructions are FP32 arithmetic), not DRAM"},
         "e2e": {"value": total_pp / e2e_s if ws == 1 else n_pp / e2e_s * ws, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "note": "glim_plan_linearize: host poses -> serialized upload -> graph -> download -> sync; "

@@ -414,10 +414,10 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize(const LinArgs 
 // lane handles its own point from start to end without divergent branches.  A key outside
 // the grid's box reads the empty record before cell 0; a lane past the end of its tile reads
 // its tile's last point and is masked.  Because G = [-(u)x, I] is the same for all levels of
-// a point, the lane sums w Omega, w Omega d and e over the levels (a miss, or a term whose S'
+// a point, the lane sums w Omega, w Omega d and e over the levels (a miss, or a term whose S
 // is not positive definite, adds exact zeros) and adds the G-form of the sums once: 28
-// accumulator updates per point instead of per hit.  Results equal those of the general
-// kernel up to FP32 rounding order.
+// accumulator updates per point instead of per hit.  The weight enters as w adj(S)/det(S)
+// (the general kernel divides S by w instead); results agree up to FP32 rounding.
 
 struct DenseView {  // per-item constants, written by thread 0
   float4 Rt[3];  // rows of [R | t]
@@ -481,8 +481,16 @@ __device__ __forceinline__ void dense_point(const DenseView& V, const float4 m, 
     s1[l] = ldg4(&sl->w1);                                    // {mean, C~00}
     s2[l] = ldg4(&sl->w2);                                    // {C~01, C~02, C~11, C~12}
   }
-  // R C R^T / w (once for all levels)
-  const float iw = __fdividef(1.0f, m.w);
+  bool hit[LMAX];
+  int nh = 0;
+#pragma unroll
+  for (int l = 0; l < LMAX; ++l) {
+    hit[l] = __float_as_int(s0[l].x) >= 0;  // occupied cell (empty records hold 0x80808080)
+    nh += hit[l] ? 1 : 0;
+  }
+  inl += nh;
+  // R C R^T (once for all levels)
+  const float w = m.w;
   const float c00 = ca.x, c01 = ca.y, c02 = cb.x, c11 = cb.y, c12 = cc.x, c22 = cc.y;
   const float w00 = R0.x * c00 + R0.y * c01 + R0.z * c02;
   const float w01 = R0.x * c01 + R0.y * c11 + R0.z * c12;
@@ -493,29 +501,29 @@ __device__ __forceinline__ void dense_point(const DenseView& V, const float4 m, 
   const float w20 = R2.x * c00 + R2.y * c01 + R2.z * c02;
   const float w21 = R2.x * c01 + R2.y * c11 + R2.z * c12;
   const float w22 = R2.x * c02 + R2.y * c12 + R2.z * c22;
-  const float r00 = (w00 * R0.x + w01 * R0.y + w02 * R0.z) * iw;
-  const float r01 = (w00 * R1.x + w01 * R1.y + w02 * R1.z) * iw;
-  const float r02 = (w00 * R2.x + w01 * R2.y + w02 * R2.z) * iw;
-  const float r11 = (w10 * R1.x + w11 * R1.y + w12 * R1.z) * iw;
-  const float r12 = (w10 * R2.x + w11 * R2.y + w12 * R2.z) * iw;
-  const float r22 = (w20 * R2.x + w21 * R2.y + w22 * R2.z) * iw;
-  // per level: S' = C~ / w + R C R^T / w, w Omega = adj(S') / det(S'), y = w Omega d; the
-  // sums over levels (a term that is a miss or not positive definite adds zeros)
+  const float r00 = w00 * R0.x + w01 * R0.y + w02 * R0.z;
+  const float r01 = w00 * R1.x + w01 * R1.y + w02 * R1.z;
+  const float r02 = w00 * R2.x + w01 * R2.y + w02 * R2.z;
+  const float r11 = w10 * R1.x + w11 * R1.y + w12 * R1.z;
+  const float r12 = w10 * R2.x + w11 * R2.y + w12 * R2.z;
+  const float r22 = w20 * R2.x + w21 * R2.y + w22 * R2.z;
+  // per level: S = C~ + R C R^T, w Omega = w adj(S) / det(S), y = w Omega d, and the sums over
+  // levels (a term that is a miss or not positive definite adds zeros).  Skipping a level
+  // (or the whole point) when no lane of the warp hits it was measured slower: the vote has
+  // to wait for the voxel reads, which stops R C R^T from overlapping their latency.
   float O00 = 0.f, O01 = 0.f, O02 = 0.f, O11 = 0.f, O12 = 0.f, O22 = 0.f;
   float g0 = 0.f, g1 = 0.f, g2 = 0.f, es = 0.f;
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
-    const bool hit = __float_as_int(s0[l].x) >= 0;  // occupied cell (empty records hold 0x80808080)
-    inl += hit ? 1 : 0;
-    const float a = __fmaf_rn(s1[l].w, iw, r00), b = __fmaf_rn(s2[l].x, iw, r01), c = __fmaf_rn(s2[l].y, iw, r02);
-    const float d = __fmaf_rn(s2[l].z, iw, r11), e = __fmaf_rn(s2[l].w, iw, r12), f = __fmaf_rn(s0[l].y, iw, r22);
+    const float a = s1[l].w + r00, b = s2[l].x + r01, c = s2[l].y + r02;
+    const float d = s2[l].z + r11, e = s2[l].w + r12, f = s0[l].y + r22;
     const float dx = s1[l].x - q.x, dy = s1[l].y - q.y, dz = s1[l].z - q.z;
     const float A00 = d * f - e * e, A01 = c * e - b * f, A02 = b * e - c * d;
     const float A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
     const float det = a * A00 + b * A01 + c * A02;
-    const bool ok = hit && det > 0.f && det < INFINITY;
-    const float id = __fdividef(1.0f, det);
-    // selected, not multiplied by 0: adj(S') of a masked term need not be finite
+    const bool ok = hit[l] && det > 0.f && det < INFINITY;
+    const float id = __fdividef(w, det);
+    // selected, not multiplied by 0: adj(S) of a masked term need not be finite
     const float o00 = ok ? A00 * id : 0.f, o01 = ok ? A01 * id : 0.f, o02 = ok ? A02 * id : 0.f;
     const float o11 = ok ? A11 * id : 0.f, o12 = ok ? A12 * id : 0.f, o22 = ok ? A22 * id : 0.f;
     const float y0 = o00 * dx + o01 * dy + o02 * dz;
