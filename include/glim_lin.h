@@ -321,6 +321,14 @@ glim_status glim_backward(glim_ctx* ctx, const glim_frame* frames, int32_t nfram
                           const glim_pair* pairs, int32_t npairs, const double* poses12,
                           int32_t omega_grad_full, int32_t validate_surface, double* dxi_out,
                           float* dmu_out, float* dw_out);
+/* The same gradient for the batch of a plan, so that repeated evaluations (an optimiser's
+ * iterations, autograd) reuse the plan's descriptors: the plan must have been created with
+ * block 256 and pts_per_thread 1 (GLIM_EINVAL otherwise); its validate_surface option
+ * applies.  The gradient scratch (host tables, per-(pair, point) slots) is allocated at the
+ * first call and kept until glim_plan_destroy.  The frames' point arrays may be rewritten in
+ * place between calls.  Outputs as for glim_backward; synchronizes the stream. */
+glim_status glim_plan_backward(glim_plan* plan, const double* poses12, int32_t omega_grad_full,
+                               double* dxi_out, float* dmu_out, float* dw_out);
 
 /* ---------------------------------------------------------------- Gauss-Newton step */
 

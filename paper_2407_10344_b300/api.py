@@ -314,6 +314,23 @@ class Plan:
         Pz = _poses(poses, self.nframes)
         self.ctx.call("plan_set_poses", self.ctx.lib.glim_plan_set_poses, self.h, _ptr(Pz))
 
+    def device_outputs_alloc(self):
+        """Device tensors (e, H, b, inliers) to pass as `out` to linearize."""
+        return _outputs(self.npairs, self.frames[0].pts4.device)
+
+    def backward(self, poses, omega_grad_full=True):
+        """dE/dxi (nframes, 6) f64, dE/dmu (sum n, 3) f32, dE/dw (sum n,) f32 of the plan's
+        batch (the plan must use block 256, pts_per_thread 1)."""
+        Pz = _poses(poses, self.nframes)
+        dev = self.frames[0].pts4.device
+        ntot = sum(f.n for f in self.frames)
+        dxi = torch.empty((self.nframes, 6), dtype=torch.float64, device=dev)
+        dmu = torch.empty((ntot, 3), dtype=torch.float32, device=dev)
+        dw = torch.empty((ntot,), dtype=torch.float32, device=dev)
+        self.ctx.call("plan_backward", self.ctx.lib.glim_plan_backward, self.h, _ptr(Pz), int(omega_grad_full),
+                      _ptr(dxi), _ptr(dmu), _ptr(dw))
+        return dxi, dmu, dw
+
     def launch(self):
         self.ctx.call("plan_launch", self.ctx.lib.glim_plan_launch, self.h)
 

@@ -50,9 +50,38 @@ def retract(T, xi):
     return out
 
 
+def retract_many(T, xi):
+    """T_f Exp(xi_f) for a stack of 3x4 poses (n, 3, 4) and increments (n, 6), vectorised
+    over f with the same Rodrigues / left-Jacobian formulas as se3_exp."""
+    T = np.asarray(T, dtype=np.float64).reshape(-1, 3, 4)
+    xi = np.asarray(xi, dtype=np.float64).reshape(-1, 6)
+    w, v = xi[:, :3], xi[:, 3:]
+    th = np.linalg.norm(w, axis=1)
+    K = np.zeros((len(xi), 3, 3))
+    K[:, 0, 1], K[:, 0, 2], K[:, 1, 2] = -w[:, 2], w[:, 1], -w[:, 0]
+    K[:, 1, 0], K[:, 2, 0], K[:, 2, 1] = w[:, 2], -w[:, 1], w[:, 0]
+    K2 = K @ K
+    small = th < 1e-10
+    ts = np.where(small, 1.0, th)
+    a = np.where(small, 1.0, np.sin(ts) / ts)
+    b = np.where(small, 0.5, (1 - np.cos(ts)) / ts ** 2)
+    c = np.where(small, 1.0 / 6.0, (ts - np.sin(ts)) / ts ** 3)
+    I = np.eye(3)[None]
+    R = I + a[:, None, None] * K + b[:, None, None] * K2
+    V = I + b[:, None, None] * K + c[:, None, None] * K2
+    out = np.empty_like(T)
+    out[:, :, :3] = T[:, :, :3] @ R
+    out[:, :, 3] = np.einsum("nij,nj->ni", T[:, :, :3], np.einsum("nij,nj->ni", V, v)) + T[:, :, 3]
+    return out
+
+
 class FactorProblem:
     """A fixed batch of factors: frame covariances and normals, target voxelmaps, pairs, the
-    base poses, and the split of the concatenated point array into frames."""
+    base poses, and the split of the concatenated point array into frames.
+
+    The problem owns one packed (n, 4) point buffer (the frames are row ranges of it) and one
+    plan over it (block 256, one point per thread, as the gradient pass needs), so that an
+    evaluation only writes the current points and weights into the buffer and launches."""
 
     def __init__(self, ctx: api.Context, frames, vmaps, pairs, poses, validate_surface=False,
                  omega_grad_full=True):
@@ -65,6 +94,12 @@ class FactorProblem:
         self.full = bool(omega_grad_full)
         self.sizes = [f.n for f in self.frames]
         self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self._p4 = torch.cat([f.pts4 for f in self.frames]).contiguous()
+        self._bufs = [api.FrameData(self._p4[int(self.offsets[i]):int(self.offsets[i + 1])], f.cov6, f.normal3)
+                      for i, f in enumerate(self.frames)]
+        self._plan = api.Plan(ctx, self._bufs, self.vmaps, self.pairs, validate_surface=self.validate,
+                              block=256, pts_per_thread=1)
+        self._out = self._plan.device_outputs_alloc()
 
     def points(self):
         """Concatenated source coordinates (n, 3) and weights (n,) of the frames."""
@@ -72,19 +107,14 @@ class FactorProblem:
         w = torch.cat([f.pts4[:, 3] for f in self.frames])
         return pts, w
 
-    def _frames_with(self, points, weights):
-        out = []
-        for i, f in enumerate(self.frames):
-            a, b = int(self.offsets[i]), int(self.offsets[i + 1])
-            p4 = torch.empty((b - a, 4), dtype=torch.float32, device=f.pts4.device)
-            p4[:, :3] = points[a:b]
-            p4[:, 3] = weights[a:b]
-            out.append(api.FrameData(p4, f.cov6, f.normal3))
-        return out
+    def _load(self, points, weights):
+        """Write the points and weights of an evaluation into the plan's buffer."""
+        self._p4[:, :3].copy_(points)
+        self._p4[:, 3].copy_(weights)
 
     def poses_at(self, xi):
         x = xi.detach().cpu().numpy().astype(np.float64).reshape(-1, 6)
-        return np.stack([retract(self.poses[f], x[f]) for f in range(len(self.poses))])
+        return retract_many(self.poses, x)
 
     def energy(self, xi, points, weights):
         """Differentiable E(xi, points, weights) (0-dim float64 CUDA tensor)."""
@@ -94,13 +124,13 @@ class FactorProblem:
 class GlimFactorFn(torch.autograd.Function):
     @staticmethod
     def forward(fctx, xi, points, weights, problem: FactorProblem):
-        frames = problem._frames_with(points.detach().float().contiguous(), weights.detach().float().contiguous())
+        pts = points.detach().float()
+        wts = weights.detach().float()
+        problem._load(pts, wts)
         poses = problem.poses_at(xi)
-        dev = points.device
-        e, _, _, _ = api.linearize(problem.ctx, frames, problem.vmaps, problem.pairs, poses, out=dev,
-                                   validate_surface=problem.validate)
+        e, _, _, _ = problem._plan.linearize(poses, out=problem._out)
         fctx.problem = problem
-        fctx.frames = frames
+        fctx.save_for_backward(pts, wts)
         fctx.poses = poses
         fctx.xi_device = xi.device
         fctx.xi_dtype = xi.dtype
@@ -109,8 +139,9 @@ class GlimFactorFn(torch.autograd.Function):
     @staticmethod
     def backward(fctx, grad_out):
         p: FactorProblem = fctx.problem
-        dxi, dmu, dw = api.backward(p.ctx, fctx.frames, p.vmaps, p.pairs, fctx.poses, omega_grad_full=p.full,
-                                    validate_surface=p.validate)
+        pts, wts = fctx.saved_tensors
+        p._load(pts, wts)  # other evaluations may have used the buffer since this forward
+        dxi, dmu, dw = p._plan.backward(fctx.poses, omega_grad_full=p.full)
         g = grad_out.to(torch.float64)
         gxi = (g * dxi).to(device=fctx.xi_device, dtype=fctx.xi_dtype)
         return gxi, (g * dmu.double()).float(), (g * dw.double()).float(), None

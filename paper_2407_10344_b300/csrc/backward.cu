@@ -219,6 +219,91 @@ __global__ void k_backward_points(const float4* __restrict__ pp, const int64_t* 
   if (dw) dw[g] = sw;
 }
 
+// Host tables of a batch, uploaded into freshly allocated scratch (synchronous copies).
+glim_status bwd_prepare(glim_plan* p, BwdScratch& sc) {
+  glim_ctx* ctx = p->ctx;
+  const int npairs = p->npairs, nframes = p->nframes;
+  std::vector<int64_t> pair_off(std::max(npairs, 1), 0), frame_off(nframes + 1, 0);
+  int64_t npp = 0;
+  for (int q = 0; q < npairs; ++q) {
+    pair_off[q] = npp;
+    npp += p->frames[p->pairs[q].src_frame].n;
+  }
+  for (int f = 0; f < nframes; ++f) frame_off[f + 1] = frame_off[f] + p->frames[f].n;
+  std::vector<int32_t> src_begin(nframes + 1, 0), src_list, tgt(std::max(npairs, 1), 0);
+  for (int f = 0; f < nframes; ++f) {
+    src_begin[f] = int32_t(src_list.size());
+    for (int q = 0; q < npairs; ++q)
+      if (p->pairs[q].src_frame == f) src_list.push_back(q);
+  }
+  src_begin[nframes] = int32_t(src_list.size());
+  for (int q = 0; q < npairs; ++q) tgt[q] = p->pairs[q].tgt_frame;
+  if (src_list.empty()) src_list.push_back(0);
+  sc.npp = npp;
+  sc.ntot = frame_off[nframes];
+  if (cudaMalloc(&sc.pair_off, pair_off.size() * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&sc.frame_off, frame_off.size() * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&sc.src_begin, src_begin.size() * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&sc.src_list, src_list.size() * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&sc.tgt, tgt.size() * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&sc.pp, size_t(std::max<int64_t>(npp, 1)) * sizeof(float4)) != cudaSuccess ||
+      cudaMalloc(&sc.part, size_t(std::max(p->nitems, 1)) * BSTRIDE * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&sc.pair_grad, size_t(std::max(npairs, 1)) * 12 * sizeof(double)) != cudaSuccess) {
+    sc.release();
+    return set_error(ctx, GLIM_ENOMEM, "backward: scratch allocation failed");
+  }
+  GLIM_CUDA(ctx, cudaMemcpy(sc.pair_off, pair_off.data(), pair_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  GLIM_CUDA(ctx, cudaMemcpy(sc.frame_off, frame_off.data(), frame_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  GLIM_CUDA(ctx, cudaMemcpy(sc.src_begin, src_begin.data(), src_begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  GLIM_CUDA(ctx, cudaMemcpy(sc.src_list, src_list.data(), src_list.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  GLIM_CUDA(ctx, cudaMemcpy(sc.tgt, tgt.data(), tgt.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  return GLIM_OK;
+}
+
+// The gradient kernels of a batch whose poses are already uploaded into p->d_in; synchronizes.
+glim_status bwd_run(glim_plan* p, const BwdScratch& sc, int32_t omega_grad_full, int32_t validate_surface,
+                    double* dxi_out, float* dmu_out, float* dw_out) {
+  glim_ctx* ctx = p->ctx;
+  const int npairs = p->npairs, nframes = p->nframes;
+  if (p->nitems > 0) {
+    BwdArgs a;
+    a.items = p->d_items;
+    a.nitems = p->nitems;
+    a.pairs = p->d_pairs;
+    a.frames = p->d_frames;
+    a.maps = p->d_maps;
+    a.pose = p->in_pose32();
+    a.tile = p->tile;
+    a.validate = validate_surface;
+    a.full = omega_grad_full;
+    a.pair_pt_off = sc.pair_off;
+    a.pp = sc.pp;
+    a.part = sc.part;
+    k_backward_items<<<p->nitems, 256, 0, ctx->stream>>>(a);
+    ctx->launches++;
+  }
+  if (npairs > 0) {
+    k_backward_pairs<<<ceil_div_i(npairs, 64), 64, 0, ctx->stream>>>(sc.part, p->d_item_begin, p->in_pose64(),
+                                                                     npairs, sc.pair_grad);
+    ctx->launches++;
+  }
+  if (nframes > 0) {
+    k_backward_frames<<<ceil_div_i(nframes, 64), 64, 0, ctx->stream>>>(sc.pair_grad, p->d_pairs, sc.tgt, npairs,
+                                                                       nframes, dxi_out);
+    ctx->launches++;
+  }
+  if (sc.ntot > 0 && (dmu_out || dw_out)) {
+    k_backward_points<<<ceil_div_i(sc.ntot, 256), 256, 0, ctx->stream>>>(
+        sc.pp, sc.pair_off, sc.src_list, sc.src_begin, sc.frame_off, nullptr, nframes, sc.ntot, dmu_out, dw_out);
+    ctx->launches++;
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(ctx, e, "backward launch");
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return set_error(ctx, GLIM_ECUDA, "backward: sync failed");
+  ctx->err.clear();
+  return GLIM_OK;
+}
+
 }  // namespace
 
 extern "C" glim_status glim_backward(glim_ctx* ctx, const glim_frame* frames, int32_t nframes, const glim_pair* pairs,
@@ -235,84 +320,40 @@ extern "C" glim_status glim_backward(glim_ctx* ctx, const glim_frame* frames, in
   glim_plan* p = nullptr;
   glim_status st = glim_plan_create(ctx, frames, nframes, pairs, npairs, &o, &p);
   if (st != GLIM_OK) return st;
-  auto done = [&](glim_status s) {
-    glim_plan_destroy(p);
-    return s;
-  };
+  BwdScratch sc;
+  st = bwd_prepare(p, sc);
+  if (st == GLIM_OK) {
+    plan_pack_poses(p, poses12);
+    if (cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+      st = set_error(ctx, GLIM_ECUDA, "backward: upload failed");
+  }
+  if (st == GLIM_OK) st = bwd_run(p, sc, omega_grad_full, validate_surface, dxi_out, dmu_out, dw_out);
+  cudaStreamSynchronize(ctx->stream);
+  sc.release();
+  glim_plan_destroy(p);
+  return st;
+}
+
+extern "C" glim_status glim_plan_backward(glim_plan* p, const double* poses12, int32_t omega_grad_full,
+                                          double* dxi_out, float* dmu_out, float* dw_out) {
+  if (!p || !poses12) return GLIM_EINVAL;
+  glim_ctx* ctx = p->ctx;
+  if (p->nframes > 0 && !dxi_out) return set_error(ctx, GLIM_EINVAL, "plan_backward: null argument");
+  if (p->opts.block != 256 || p->tile != 256)
+    return set_error(ctx, GLIM_EINVAL, "plan_backward: the plan needs block 256 and pts_per_thread 1");
+  if (!plan_maps_current(p)) return set_error(ctx, GLIM_EINVAL, "plan_backward: a target voxelmap changed");
+  GLIM_CUDA(ctx, cudaSetDevice(ctx->device));
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the pose block may still be in use
+  if (!p->bwd) {
+    BwdScratch* sc = new BwdScratch;
+    const glim_status st = bwd_prepare(p, *sc);
+    if (st != GLIM_OK) {
+      delete sc;
+      return st;
+    }
+    p->bwd = sc;
+  }
   plan_pack_poses(p, poses12);
-  if (cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
-    return done(set_error(ctx, GLIM_ECUDA, "backward: upload failed"));
-  // host-side tables
-  std::vector<int64_t> pair_off(std::max(npairs, 1), 0), frame_off(nframes + 1, 0);
-  int64_t npp = 0;
-  for (int q = 0; q < npairs; ++q) {
-    pair_off[q] = npp;
-    npp += frames[pairs[q].src_frame].n;
-  }
-  for (int f = 0; f < nframes; ++f) frame_off[f + 1] = frame_off[f] + frames[f].n;
-  const int64_t ntot = frame_off[nframes];
-  std::vector<int32_t> src_begin(nframes + 1, 0), src_list, tgt(std::max(npairs, 1), 0);
-  for (int f = 0; f < nframes; ++f) {
-    src_begin[f] = int32_t(src_list.size());
-    for (int q = 0; q < npairs; ++q)
-      if (pairs[q].src_frame == f) src_list.push_back(q);
-  }
-  src_begin[nframes] = int32_t(src_list.size());
-  for (int q = 0; q < npairs; ++q) tgt[q] = pairs[q].tgt_frame;
-  if (src_list.empty()) src_list.push_back(0);
-  DevBuf<int64_t> d_pair_off, d_frame_off;
-  DevBuf<int32_t> d_src_begin, d_src_list, d_tgt;
-  DevBuf<float4> d_pp;
-  DevBuf<double> d_part, d_pair_grad;
-  if (d_pair_off.alloc(pair_off.size(), ctx->stream) != cudaSuccess ||
-      d_frame_off.alloc(frame_off.size(), ctx->stream) != cudaSuccess ||
-      d_src_begin.alloc(src_begin.size(), ctx->stream) != cudaSuccess ||
-      d_src_list.alloc(src_list.size(), ctx->stream) != cudaSuccess ||
-      d_tgt.alloc(tgt.size(), ctx->stream) != cudaSuccess ||
-      d_pp.alloc(std::max<int64_t>(npp, 1), ctx->stream) != cudaSuccess ||
-      d_part.alloc(size_t(std::max(p->nitems, 1)) * BSTRIDE, ctx->stream) != cudaSuccess ||
-      d_pair_grad.alloc(size_t(std::max(npairs, 1)) * 12, ctx->stream) != cudaSuccess)
-    return done(set_error(ctx, GLIM_ENOMEM, "backward: scratch allocation failed"));
-  cudaMemcpyAsync(d_pair_off.p, pair_off.data(), pair_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream);
-  cudaMemcpyAsync(d_frame_off.p, frame_off.data(), frame_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream);
-  cudaMemcpyAsync(d_src_begin.p, src_begin.data(), src_begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream);
-  cudaMemcpyAsync(d_src_list.p, src_list.data(), src_list.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream);
-  cudaMemcpyAsync(d_tgt.p, tgt.data(), tgt.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream);
-  if (p->nitems > 0) {
-    BwdArgs a;
-    a.items = p->d_items;
-    a.nitems = p->nitems;
-    a.pairs = p->d_pairs;
-    a.frames = p->d_frames;
-    a.maps = p->d_maps;
-    a.pose = p->in_pose32();
-    a.tile = p->tile;
-    a.validate = validate_surface;
-    a.full = omega_grad_full;
-    a.pair_pt_off = d_pair_off.p;
-    a.pp = d_pp.p;
-    a.part = d_part.p;
-    k_backward_items<<<p->nitems, 256, 0, ctx->stream>>>(a);
-    ctx->launches++;
-  }
-  if (npairs > 0) {
-    k_backward_pairs<<<ceil_div_i(npairs, 64), 64, 0, ctx->stream>>>(d_part.p, p->d_item_begin, p->in_pose64(),
-                                                                     npairs, d_pair_grad.p);
-    ctx->launches++;
-  }
-  if (nframes > 0) {
-    k_backward_frames<<<ceil_div_i(nframes, 64), 64, 0, ctx->stream>>>(d_pair_grad.p, p->d_pairs, d_tgt.p, npairs,
-                                                                       nframes, dxi_out);
-    ctx->launches++;
-  }
-  if (ntot > 0 && (dmu_out || dw_out)) {
-    k_backward_points<<<ceil_div_i(ntot, 256), 256, 0, ctx->stream>>>(
-        d_pp.p, d_pair_off.p, d_src_list.p, d_src_begin.p, d_frame_off.p, nullptr, nframes, ntot, dmu_out, dw_out);
-    ctx->launches++;
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return done(cuda_check(ctx, e, "backward launch"));
-  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return done(set_error(ctx, GLIM_ECUDA, "backward: sync failed"));
-  ctx->err.clear();
-  return done(GLIM_OK);
+  GLIM_CUDA(ctx, cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream));
+  return bwd_run(p, *p->bwd, omega_grad_full, p->opts.validate_surface, dxi_out, dmu_out, dw_out);
 }

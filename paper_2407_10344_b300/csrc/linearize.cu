@@ -270,6 +270,14 @@ glim_status plan_enqueue_kernels(glim_plan* p, int slot = -1) {
 
 }  // namespace
 
+// The plan holds device pointers to its maps' tables; a map changed since (an insertion
+// frees and replaces them) makes the plan unusable.
+bool plan_maps_current(const glim_plan* p) {
+  for (const auto& mv : p->map_versions)
+    if (mv.first->version != mv.second) return false;
+  return true;
+}
+
 void plan_pack_poses(glim_plan* p, const double* poses12) {
   PoseF* pf = reinterpret_cast<PoseF*>(p->h_in);
   double* pd = reinterpret_cast<double*>(reinterpret_cast<char*>(p->h_in) + sizeof(PoseF) * p->npairs);
@@ -283,12 +291,9 @@ void plan_pack_poses(glim_plan* p, const double* poses12) {
 
 namespace {
 
-// The plan holds device pointers to its maps' tables; a map changed since (an insertion
-// frees and replaces them) makes the plan unusable.
 glim_status maps_current(glim_plan* p) {
-  for (const auto& mv : p->map_versions)
-    if (mv.first->version != mv.second)
-      return set_error(p->ctx, GLIM_EINVAL, "plan: a target voxelmap changed after the plan was created");
+  if (!plan_maps_current(p))
+    return set_error(p->ctx, GLIM_EINVAL, "plan: a target voxelmap changed after the plan was created");
   return GLIM_OK;
 }
 
@@ -475,6 +480,10 @@ extern "C" void glim_plan_destroy(glim_plan* p) {
   cudaFree(p->d_pairs);
   cudaFree(p->d_maps);
   cudaFree(p->d_dmaps);
+  if (p->bwd) {
+    p->bwd->release();
+    delete p->bwd;
+  }
   cudaFree(p->d_items);
   cudaFree(p->d_item_begin);
   cudaFree(p->d_part);

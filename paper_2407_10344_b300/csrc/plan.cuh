@@ -73,6 +73,31 @@ struct PairView {
   MapDev M;
 };
 
+// Scratch of the gradient pass of a plan (host tables uploaded once, per-(pair, point)
+// gradient slots), created at the first glim_plan_backward and kept by the plan.
+struct BwdScratch {
+  int64_t* pair_off = nullptr;   // npairs: offset of the pair's points in pp
+  int64_t* frame_off = nullptr;  // nframes + 1
+  int32_t* src_begin = nullptr;  // nframes + 1
+  int32_t* src_list = nullptr;   // pairs grouped by source frame
+  int32_t* tgt = nullptr;        // npairs
+  float4* pp = nullptr;          // per (pair, point)
+  double* part = nullptr;        // nitems x 12
+  double* pair_grad = nullptr;   // npairs x 12
+  int64_t npp = 0, ntot = 0;
+  void release() {
+    cudaFree(pair_off);
+    cudaFree(frame_off);
+    cudaFree(src_begin);
+    cudaFree(src_list);
+    cudaFree(tgt);
+    cudaFree(pp);
+    cudaFree(part);
+    cudaFree(pair_grad);
+    *this = BwdScratch{};
+  }
+};
+
 using LinKernel = void (*)(const LinArgs);
 struct LinKernelInfo {
   LinKernel fn = nullptr;
@@ -120,6 +145,7 @@ struct glim_plan {
   bool use_graph = true;
   cudaGraphExec_t g_full = nullptr;  // upload + kernels + download
   cudaGraphExec_t g_dev = nullptr;   // kernels only
+  BwdScratch* bwd = nullptr;         // gradient pass scratch (glim_plan_backward)
 
   PoseF* in_pose32() const { return reinterpret_cast<PoseF*>(d_in); }
   double* in_pose64() const { return reinterpret_cast<double*>(reinterpret_cast<char*>(d_in) + sizeof(PoseF) * npairs); }
@@ -132,6 +158,7 @@ struct glim_plan {
 
 // shared host helpers (linearize.cu)
 void plan_pack_poses(glim_plan* p, const double* poses12);
+bool plan_maps_current(const glim_plan* p);  // false once a target map changed since creation
 glim_status plan_configure(glim_plan* p, const glim_lin_opts& o);
 glim_status enqueue_reduce_expand(glim_ctx* ctx, const double* part, const int32_t* item_begin,
                                   const double* pose64, int32_t npairs, int32_t fp32_sum, double* e, double* H,

@@ -481,6 +481,52 @@ def test_autograd_function_against_fd(G, ctx, full):
     assert worst <= 2e-3
 
 
+@pytest.mark.parametrize("full", [False, True])
+def test_plan_backward_equals_one_shot_and_reuses_scratch(G, ctx, full):
+    """glim_plan_backward on a plan (block 256, one point per thread) gives the one-shot
+    glim_backward's gradient bit for bit, again on a second call with the kept scratch, and
+    refuses a plan with another tile."""
+    from gpu_helpers import Prepared
+    P = Prepared(ctx, synth.corridor(n_cur=4000, kf_range=(3000, 5000), n_kf=3, weights=True))
+    w = P.w
+    one = G.backward(ctx, P.gframes, P.gmaps, w.pairs, w.poses, omega_grad_full=full)
+    plan = G.Plan(ctx, P.gframes, P.gmaps, w.pairs, block=256, pts_per_thread=1)
+    for _ in range(2):
+        got = plan.backward(w.poses, omega_grad_full=full)
+        for a, b in zip(one, got):
+            assert torch.equal(a, b)
+    other = G.Plan(ctx, P.gframes, P.gmaps, w.pairs, block=128, pts_per_thread=16)
+    with pytest.raises(G.GlimError, match="EINVAL"):
+        other.backward(w.poses)
+
+
+def test_autograd_interleaved_evaluations(G, ctx):
+    """Two evaluations at different points before the first one's backward: the gradient is
+    the first evaluation's (the problem's shared point buffer is reloaded for the backward)."""
+    from gpu_helpers import Prepared
+    from paper_2407_10344_b300.autograd import FactorProblem
+    P = Prepared(ctx, synth.corridor(n_cur=4000, kf_range=(3000, 5000), n_kf=3, weights=True))
+    w = P.w
+
+    def grads(prob, pts, wts, second=None):
+        p1 = pts.clone().requires_grad_(True)
+        w1 = wts.clone().requires_grad_(True)
+        xi = torch.zeros((len(w.points), 6), dtype=torch.float64, device="cuda", requires_grad=True)
+        E = prob.energy(xi, p1, w1)
+        if second is not None:
+            prob.energy(xi.detach(), second, wts)
+        E.backward()
+        return E.item(), xi.grad.clone(), p1.grad.clone(), w1.grad.clone()
+
+    prob = FactorProblem(ctx, P.gframes, P.gmaps, w.pairs, w.poses)
+    pts, wts = prob.points()
+    ref = grads(FactorProblem(ctx, P.gframes, P.gmaps, w.pairs, w.poses), pts, wts)
+    got = grads(prob, pts, wts, second=pts + 0.05)
+    assert got[0] == ref[0]
+    for a, b in zip(got[1:], ref[1:]):
+        assert torch.equal(a, b)
+
+
 # ---------------------------------------------------------------------------- small factor graph
 def test_graph_step_assembly_and_solve_against_numpy(G, ctx):
     s = synth.Stream(77, "graph")
