@@ -283,6 +283,21 @@ def small_workloads(G, ctx, dev):
                             "ms_per_iteration": med(lm_iter, reps=10),
                             "note": "serialized upload, graph launch, download, device assembly + 66x66 Cholesky"}
 
+    # precision / scale batch: one 1M-point scan against a 20M-point terrain map at 0.25 m
+    wt = synth.terrain()
+    ft, mt = prep(wt)
+    plant = G.Plan(ctx, ft, mt, wt.pairs)
+    plant.set_poses(wt.poses)
+    for i in range(8):
+        plant.launch_timed(i)
+    t_ms = float(np.median(plant.kernel_ms(8)[3:]))
+    out["terrain"] = {"workload": "terrain: 1M-pt scan vs 20M-pt map (0.25 m, one level), unary factor",
+                      "pair_points": wt.n_pair_points, "kernel": plant.opts()["kernel"],
+                      "kernel_ms": t_ms, "points_per_s": wt.n_pair_points / (t_ms / 1e3),
+                      "e2e_plan_linearize_ms": med(lambda: plant.linearize(wt.poses), reps=10),
+                      "voxels": mt[int(wt.pairs[0, 1])].info(0)["n_voxels"],
+                      "dense_grid": bool(mt[int(wt.pairs[0, 1])].is_dense(0))}
+    del ft, mt, plant
     poses = gn10()
     D = np.linalg.inv(np.vstack([wb.poses_true[0], [0, 0, 0, 1]])) @ np.vstack([poses[0], [0, 0, 0, 1]])
     ang = float(np.degrees(np.arccos(min(1.0, (np.trace(D[:3, :3]) - 1) / 2))))
