@@ -1,0 +1,80 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the benchmark times.
+
+* Urban global step (400 submaps of log-U[50k, 200k] points, 4000 pairs, 0.5 / 1 / 2 m): the
+  whole batch runs as one plan (dense-grid kernel, block 128, 64 points per thread, FP64
+  cross-block sums, Z-ordered points, persistent work queue); a seeded sample of pairs is
+  recomputed by the oracle one pair at a time on the same float32 inputs, and each sampled
+  pair must match (inliers exactly, e / H / b within 1e-4).
+* Odometry window at its full size (30k-point frame, 10 keyframes, per-point weights): the
+  gradient of the batch against the oracle's analytic gradient.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import oracle as O
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def G():
+    import paper_2407_10344_b300 as G
+    return G
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    return G.Context(0)
+
+
+def test_urban_global_step_full_size_sampled_pairs(G, ctx):
+    from gpu_helpers import rel_errors
+    w = synth.urban(n_submaps=400)
+    dev = torch.device("cuda", ctx.device)
+    frames, maps = [], [None] * len(w.points)
+    targets = set(int(t) for t in w.pairs[:, 1])
+    for i, p in enumerate(w.points):
+        p4 = G.to_pts4(p, device=dev)
+        cov, nrm = G.estimate_covariances(ctx, p4, k=10)
+        perm = G.spatial_order(ctx, p4, 0.5)
+        p4, cov, nrm = p4[perm].contiguous(), cov[perm].contiguous(), nrm[perm].contiguous()
+        frames.append(G.FrameData(p4, cov, nrm))
+        if i in targets:
+            maps[i] = G.VoxelMap(ctx, p4, cov, w.resolutions)
+    plan = G.Plan(ctx, frames, maps, w.pairs, accum_mode=G.ACC_FP64, block=128, pts_per_thread=64)
+    assert plan.opts()["kernel"] == "dense"
+    e, H, b, inl = plan.linearize(w.poses)
+    assert np.isfinite(e).all() and np.isfinite(H).all() and np.isfinite(b).all()
+    sample = np.sort(synth.Stream(11, "urban-sample").integers(8, 0, len(w.pairs)))
+    worst = [0.0, 0.0, 0.0]
+    for q in sample:
+        s, t = int(w.pairs[q, 0]), int(w.pairs[q, 1])
+        fs = O.Frame(frames[s].pts4.cpu().numpy(), frames[s].cov6.cpu().numpy(), frames[s].normal3.cpu().numpy())
+        ft = O.Frame(frames[t].pts4.cpu().numpy(), frames[t].cov6.cpu().numpy())
+        vm = O.VMap(ft.pts4, ft.cov6, w.resolutions)
+        ref = O.linearize([fs, ft], [None, vm], np.array([[0, 1]], np.int32), np.stack([w.poses[s], w.poses[t]]),
+                          want_comp=True)
+        assert inl[q] == ref["inliers"][0], (q, inl[q], ref["inliers"][0])
+        ee, eH, eb = rel_errors(e[q:q + 1], H[q:q + 1], b[q:q + 1], ref)
+        worst = [max(worst[0], ee[0]), max(worst[1], eH[0]), max(worst[2], eb[0])]
+    assert max(worst) <= TOL, worst
+
+
+def test_odometry_window_gradient_full_size(G, ctx):
+    from gpu_helpers import Prepared
+    P = Prepared(ctx, synth.corridor(weights=True))
+    w = P.w
+    assert w.n_pair_points == 300000
+    for full in (True, False):
+        dxi, dmu, dw = G.backward(ctx, P.gframes, P.gmaps, w.pairs, w.poses, omega_grad_full=full)
+        odxi, odmu, odw = O.gradient(P.oframes, P.omaps, w.pairs, w.poses, omega_grad_full=full)
+        gxi = dxi.cpu().numpy()
+        assert np.linalg.norm(gxi - odxi) <= TOL * np.linalg.norm(odxi)
+        n0 = len(w.points[0])
+        gmu, gw = dmu.cpu().numpy()[:n0], dw.cpu().numpy()[:n0]
+        assert np.linalg.norm(gmu - odmu[0]) <= TOL * np.linalg.norm(odmu[0])
+        assert np.linalg.norm(gw - odw[0]) <= TOL * np.linalg.norm(odw[0])
