@@ -98,10 +98,12 @@ typedef struct {
  *   blocks_per_sm     resident blocks per SM of the persistent kernel (default: occupancy).
  *   persistent        1 (default) = one persistent kernel over an atomic work queue;
  *                     2 = one block per work item (hardware scheduling).
- *   kernel            0 (default) = the dense-grid kernel when every level of every target
- *                     map is a dense grid, else the general kernel; 1 = the general kernel
- *                     (dense grids and hash tables); 2 = the dense-grid kernel (GLIM_EINVAL
- *                     if a target level is a hash table).  Both give the same results.
+ *   kernel            0 (default) = the per-lane dense-grid kernel when every level of
+ *                     every target map is a dense grid, the per-lane hash kernel when every
+ *                     one is a hash table, else the general kernel; 1 = the general kernel
+ *                     (any mix of dense grids and hash tables); 2 = the dense-grid kernel,
+ *                     3 = the hash kernel (GLIM_EINVAL if a target level has the other
+ *                     layout).  All give the same results up to FP32 rounding order.
  *   reserved          must be 0. */
 typedef struct {
   int32_t validate_surface;

@@ -244,13 +244,13 @@ def _pairs(pairs, vmaps):
     return arr, len(pairs)
 
 
-KERNELS = {"auto": 0, "general": 1, "dense": 2}
+KERNELS = {"auto": 0, "general": 1, "dense": 2, "hash": 3}
 
 
 def _opts(validate_surface=False, accum_mode=ACC_FP64, block=0, pts_per_thread=0, blocks_per_sm=0,
           persistent=0, kernel="auto"):
-    """kernel: "auto" (the dense-grid kernel when every target level is a dense grid),
-    "general" or "dense"."""
+    """kernel: "auto" (the per-lane dense-grid or hash kernel when every target level has
+    that layout, else the general kernel), "general", "dense" or "hash"."""
     o = _abi.LinOpts()
     o.kernel = KERNELS[kernel]
     o.validate_surface = int(validate_surface)

@@ -15,6 +15,7 @@
 // H = Lift^T M Lift and b = Lift^T g with Lift = [-diag(R, R), S_t].
 #pragma once
 #include <cstddef>
+#include <type_traits>
 
 #include "plan.cuh"
 
@@ -409,17 +410,22 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize(const LinArgs 
   }
 }
 
-// ---------------------------------------------------------------- dense-grid kernel
-// Every target level is a dense grid: a lookup is an index computation and one read, so a
-// lane handles its own point from start to end without divergent branches.  A key outside
-// the grid's box reads the empty record before cell 0; a lane past the end of its tile reads
+// ---------------------------------------------------------------- per-lane kernels
+// Every target level is a dense grid (k_linearize_dense) or every one a hash table
+// (k_linearize_hash): a lane handles its own point from start to end.  Dense grid: a lookup
+// is an index computation and one read, without divergent branches; a key outside the
+// grid's box reads the empty record before cell 0.  Hash table: the first probe (one
+// 48-byte slot with key and statistics) is read the same way, unconditionally; the lanes
+// whose first slot holds another key continue the linear probe in a loop bounded by the
+// table's longest probe sequence (rare at load 1/4).  A lane past the end of its tile reads
 // its tile's last point and is masked.  Because G = [-(u)x, I] is the same for all levels of
 // a point, the lane sums w Omega, w Omega d and e over the levels (a miss, or a term whose S
 // is not positive definite, adds exact zeros) and adds the G-form of the sums once: 28
 // accumulator updates per point instead of per hit.  The weight enters as w adj(S)/det(S)
 // (the general kernel divides S by w instead); results agree up to FP32 rounding.
 
-struct DenseView {  // per-item constants, written by thread 0
+template <class MapT>
+struct LaneView {  // per-item constants, written by thread 0
   float4 Rt[3];  // rows of [R | t]
   float4 v;      // target viewpoint (surface validation)
   const float4* pts;
@@ -427,17 +433,20 @@ struct DenseView {  // per-item constants, written by thread 0
   const float* nrm;
   int end;  // one past the item's last point
   int pad;
-  DenseMapDev M;
+  MapT M;
 };
+using DenseView = LaneView<DenseMapDev>;
+using HashView = LaneView<HashMapDev>;
 
 // The level descriptors and inverse resolutions are read as 16-byte words.
-static_assert(sizeof(DenseLevelDev) == 32 && offsetof(DenseView, M) % 16 == 0 &&
-                  offsetof(DenseMapDev, inv_r) % 16 == 0,
-              "dense descriptors must sit on 16-byte boundaries");
+static_assert(sizeof(DenseLevelDev) == 32 && sizeof(HashLevelDev) == 32 && offsetof(DenseView, M) % 16 == 0 &&
+                  offsetof(HashView, M) % 16 == 0 && offsetof(DenseMapDev, inv_r) % 16 == 0 &&
+                  offsetof(HashMapDev, inv_r) % 16 == 0,
+              "lane-kernel descriptors must sit on 16-byte boundaries");
 
-template <int LMAX, class A>
-__device__ __forceinline__ void dense_point(const DenseView& V, const float4 m, bool live, int validate, A& acc,
-                                            int& inl, int kk) {
+template <int LMAX, bool HASH, class A>
+__device__ __forceinline__ void lane_point(const LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V,
+                                           const float4 m, bool live, int validate, A& acc, int& inl, int kk) {
   // the covariance is read here rather than a round ahead: it is needed only after the voxel
   // reads are in flight, and the registers it would hold are worth more as occupancy
   const float2* cp = V.cov + 3 * int64_t(kk);
@@ -459,36 +468,38 @@ __device__ __forceinline__ void dense_point(const DenseView& V, const float4 m, 
   q.x = finite_q ? q.x : 0.f;
   q.y = finite_q ? q.y : 0.f;
   q.z = finite_q ? q.z : 0.f;
-  float2 s0[LMAX];
+  float4 s0[LMAX];  // dense: {id, C~22, ., .} (8 bytes read); hash: {kx, ky, kz, C~22}
   float4 s1[LMAX], s2[LMAX];
+  uint32_t slot[LMAX];  // hash: the first probe's slot
   const float4 irq = *reinterpret_cast<const float4*>(V.M.inv_r);  // one 16-byte shared load
   const float irv[4] = {irq.x, irq.y, irq.z, irq.w};
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
-    // the level's descriptor as two 16-byte shared loads: {cells, ox, oy} {oz, nx, ny, nz}
+    // the level's descriptor as two 16-byte shared loads
     const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
     const uint4 lb = reinterpret_cast<const uint4*>(&V.M.lv[l])[1];
     const float ir = irv[l];
-    const VoxSlot* cells =
+    const VoxSlot* base =
         reinterpret_cast<const VoxSlot*>(uint64_t(uint32_t(la.x)) | (uint64_t(uint32_t(la.y)) << 32));
-    // keys floor(q * inv_r) (FP32 product); a key outside [-2^20, 2^20) is outside every box
-    const uint32_t x = uint32_t(__float2int_rd(__fmul_rn(q.x, ir))) - uint32_t(la.z);
-    const uint32_t y = uint32_t(__float2int_rd(__fmul_rn(q.y, ir))) - uint32_t(la.w);
-    const uint32_t z = uint32_t(__float2int_rd(__fmul_rn(q.z, ir))) - lb.x;
-    const bool in_box = live && x < lb.y && y < lb.z && z < lb.w;
-    const VoxSlot* sl = cells + (in_box ? int((x * lb.z + y) * lb.w + z) : -1);
-    s0[l] = __ldg(reinterpret_cast<const float2*>(&sl->w0));  // {id, C~22}
-    s1[l] = ldg4(&sl->w1);                                    // {mean, C~00}
-    s2[l] = ldg4(&sl->w2);                                    // {C~01, C~02, C~11, C~12}
+    // keys floor(q * inv_r) (FP32 product); a key outside [-2^20, 2^20) is in no table
+    const int kx = __float2int_rd(__fmul_rn(q.x, ir));
+    const int ky = __float2int_rd(__fmul_rn(q.y, ir));
+    const int kz = __float2int_rd(__fmul_rn(q.z, ir));
+    const VoxSlot* sl;
+    if constexpr (HASH) {  // {slots, mask, log2cap} {max_probe, ...}
+      slot[l] = hash3(kx, ky, kz, la.w);
+      sl = base + slot[l];
+      s0[l] = ldg4(&sl->w0);
+    } else {  // {cells, ox, oy} {oz, nx, ny, nz}
+      const uint32_t x = uint32_t(kx) - uint32_t(la.z), y = uint32_t(ky) - uint32_t(la.w), z = uint32_t(kz) - lb.x;
+      const bool in_box = live && x < lb.y && y < lb.z && z < lb.w;
+      sl = base + (in_box ? int((x * lb.z + y) * lb.w + z) : -1);
+      const float2 h = __ldg(reinterpret_cast<const float2*>(&sl->w0));
+      s0[l] = make_float4(h.x, h.y, 0.f, 0.f);
+    }
+    s1[l] = ldg4(&sl->w1);  // {mean, C~00}
+    s2[l] = ldg4(&sl->w2);  // {C~01, C~02, C~11, C~12}
   }
-  bool hit[LMAX];
-  int nh = 0;
-#pragma unroll
-  for (int l = 0; l < LMAX; ++l) {
-    hit[l] = __float_as_int(s0[l].x) >= 0;  // occupied cell (empty records hold 0x80808080)
-    nh += hit[l] ? 1 : 0;
-  }
-  inl += nh;
   // R C R^T (once for all levels)
   const float w = m.w;
   const float c00 = ca.x, c01 = ca.y, c02 = cb.x, c11 = cb.y, c12 = cc.x, c22 = cc.y;
@@ -507,6 +518,49 @@ __device__ __forceinline__ void dense_point(const DenseView& V, const float4 m, 
   const float r11 = w10 * R1.x + w11 * R1.y + w12 * R1.z;
   const float r12 = w10 * R2.x + w11 * R2.y + w12 * R2.z;
   const float r22 = w20 * R2.x + w21 * R2.y + w22 * R2.z;
+  // hits (after R C R^T, which overlaps the reads' latency)
+  bool hit[LMAX];
+  float vc22[LMAX];  // C~22 of the level's voxel
+  int nh = 0;
+#pragma unroll
+  for (int l = 0; l < LMAX; ++l) {
+    if constexpr (HASH) {
+      const int kx = __float2int_rd(__fmul_rn(q.x, irv[l]));
+      const int ky = __float2int_rd(__fmul_rn(q.y, irv[l]));
+      const int kz = __float2int_rd(__fmul_rn(q.z, irv[l]));
+      bool match = live && __float_as_int(s0[l].x) == kx && __float_as_int(s0[l].y) == ky &&
+                   __float_as_int(s0[l].z) == kz;
+      const bool more = live && !match && __float_as_int(s0[l].x) != GLIM_EMPTY_COORD;
+      if (__any_sync(0xffffffffu, more)) {  // some first slot held another key
+        if (more) {
+          const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
+          const int max_probe = reinterpret_cast<const int4*>(&V.M.lv[l])[1].x;
+          const VoxSlot* slots =
+              reinterpret_cast<const VoxSlot*>(uint64_t(uint32_t(la.x)) | (uint64_t(uint32_t(la.y)) << 32));
+          uint32_t h = slot[l];
+          for (int p = 1; p < max_probe; ++p) {  // bounded by the longest probe sequence of the table
+            h = (h + 1u) & uint32_t(la.z);
+            const float4 w0 = ldg4(&slots[h].w0);
+            if (__float_as_int(w0.x) == kx && __float_as_int(w0.y) == ky && __float_as_int(w0.z) == kz) {
+              s0[l] = w0;
+              s1[l] = ldg4(&slots[h].w1);
+              s2[l] = ldg4(&slots[h].w2);
+              match = true;
+              break;
+            }
+            if (__float_as_int(w0.x) == GLIM_EMPTY_COORD) break;
+          }
+        }
+      }
+      hit[l] = match;
+      vc22[l] = s0[l].w;
+    } else {
+      hit[l] = __float_as_int(s0[l].x) >= 0;  // occupied cell (empty records hold 0x80808080)
+      vc22[l] = s0[l].y;
+    }
+    nh += hit[l] ? 1 : 0;
+  }
+  inl += nh;
   // per level: S = C~ + R C R^T, w Omega = w adj(S) / det(S), y = w Omega d, and the sums over
   // levels (a term that is a miss or not positive definite adds zeros).  Skipping a level
   // (or the whole point) when no lane of the warp hits it was measured slower: the vote has
@@ -516,7 +570,7 @@ __device__ __forceinline__ void dense_point(const DenseView& V, const float4 m, 
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
     const float a = s1[l].w + r00, b = s2[l].x + r01, c = s2[l].y + r02;
-    const float d = s2[l].z + r11, e = s2[l].w + r12, f = s0[l].y + r22;
+    const float d = s2[l].z + r11, e = s2[l].w + r12, f = vc22[l] + r22;
     const float dx = s1[l].x - q.x, dy = s1[l].y - q.y, dz = s1[l].z - q.z;
     const float A00 = d * f - e * e, A01 = c * e - b * f, A02 = b * e - c * d;
     const float A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
@@ -555,8 +609,9 @@ __device__ __forceinline__ void dense_point(const DenseView& V, const float4 m, 
   acc.add(27, es);
 }
 
-template <int BLOCK, int ACC, int LMAX>
-__device__ __forceinline__ void process_item_dense(const LinArgs& a, int item, DenseView& V) {
+template <int BLOCK, int ACC, int LMAX, bool HASH>
+__device__ __forceinline__ void process_item_lane(const LinArgs& a, int item,
+                                                  LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V) {
   const Item it = a.items[item];
   if (threadIdx.x == 0) {
     const PairDev pd = a.pairs[it.pair];
@@ -568,7 +623,8 @@ __device__ __forceinline__ void process_item_dense(const LinArgs& a, int item, D
     V.pts = F.pts;
     V.cov = F.cov;
     V.nrm = F.nrm;
-    V.M = a.dmaps[pd.map];
+    if constexpr (HASH) V.M = a.hmaps[pd.map];
+    else V.M = a.dmaps[pd.map];
     V.end = int(min(int64_t(it.start) + a.tile, F.n));
   }
   __syncthreads();
@@ -586,29 +642,24 @@ __device__ __forceinline__ void process_item_dense(const LinArgs& a, int item, D
   for (; j + 1 < rounds; j += 2) {
     const int k = first + j * BLOCK;
     const float4 p1 = ldg4(V.pts + min(k + BLOCK, last));
-    dense_point<LMAX>(V, p0, k <= last, a.validate, acc, inl, min(k, last));
+    lane_point<LMAX, HASH>(V, p0, k <= last, a.validate, acc, inl, min(k, last));
     p0 = ldg4(V.pts + min(k + 2 * BLOCK, last));
-    dense_point<LMAX>(V, p1, k + BLOCK <= last, a.validate, acc, inl, min(k + BLOCK, last));
+    lane_point<LMAX, HASH>(V, p1, k + BLOCK <= last, a.validate, acc, inl, min(k + BLOCK, last));
   }
   if (j < rounds) {
     const int k = first + j * BLOCK;
-    dense_point<LMAX>(V, p0, k <= last, a.validate, acc, inl, min(k, last));
+    lane_point<LMAX, HASH>(V, p0, k <= last, a.validate, acc, inl, min(k, last));
   }
   block_reduce_store<BLOCK, ACC>(acc, inl, a.part + int64_t(item) * PSTRIDE);
 }
 
-template <int BLOCK, int LMAX>
-constexpr size_t lin_dense_dyn_smem() {
-  return 0;
-}
-
-template <int BLOCK, int ACC, int LMAX>
-__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize_dense(const LinArgs a) {
-  __shared__ DenseView V;
+template <int BLOCK, int ACC, int LMAX, bool HASH>
+__device__ __forceinline__ void lane_kernel_body(const LinArgs& a) {
+  __shared__ LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type> V;
   __shared__ int s_item[2];
   if (a.head == nullptr) {
     const int item = a.item_base + blockIdx.x;
-    if (item < a.nitems) process_item_dense<BLOCK, ACC, LMAX>(a, item, V);
+    if (item < a.nitems) process_item_lane<BLOCK, ACC, LMAX, HASH>(a, item, V);
     return;
   }
   if (threadIdx.x == 0) s_item[0] = atomicAdd(a.head, 1);
@@ -617,9 +668,19 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize_dense(const Li
   for (int b = 1;; b ^= 1) {
     if (cur >= a.nitems) break;
     if (threadIdx.x == 0) s_item[b] = atomicAdd(a.head, 1);
-    process_item_dense<BLOCK, ACC, LMAX>(a, cur, V);  // ends with a barrier
+    process_item_lane<BLOCK, ACC, LMAX, HASH>(a, cur, V);  // ends with a barrier
     cur = s_item[b];
   }
+}
+
+template <int BLOCK, int ACC, int LMAX>
+__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize_dense(const LinArgs a) {
+  lane_kernel_body<BLOCK, ACC, LMAX, false>(a);
+}
+
+template <int BLOCK, int ACC, int LMAX>
+__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize_hash(const LinArgs a) {
+  lane_kernel_body<BLOCK, ACC, LMAX, true>(a);
 }
 
 // Kernel and its dynamic shared memory (bytes) for a configuration; the attribute allowing
@@ -650,29 +711,30 @@ LinKernelInfo pick_lin(int block, int lmax) {
 #undef GLIM_PICK_L
 }
 
-template <int B, int ACC, int L>
-LinKernelInfo lin_dense_info() {
+template <int B, int ACC, int L, bool HASH>
+LinKernelInfo lin_lane_info() {
   LinKernelInfo k;
-  k.fn = k_linearize_dense<B, ACC, L>;
-  k.smem = lin_dense_dyn_smem<B, L>();
+  if constexpr (HASH) k.fn = k_linearize_hash<B, ACC, L>;
+  else k.fn = k_linearize_dense<B, ACC, L>;
+  k.smem = 0;
   return k;
 }
 
-template <int ACC>
-LinKernelInfo pick_lin_dense(int block, int lmax) {
-#define GLIM_PICK_DENSE_L(B)                      \
-  switch (lmax) {                                 \
-    case 1: return lin_dense_info<B, ACC, 1>();   \
-    case 2: return lin_dense_info<B, ACC, 2>();   \
-    case 3: return lin_dense_info<B, ACC, 3>();   \
-    case 4: return lin_dense_info<B, ACC, 4>();   \
-  }                                               \
+template <int ACC, bool HASH>
+LinKernelInfo pick_lin_lane(int block, int lmax) {
+#define GLIM_PICK_LANE_L(B)                             \
+  switch (lmax) {                                       \
+    case 1: return lin_lane_info<B, ACC, 1, HASH>();    \
+    case 2: return lin_lane_info<B, ACC, 2, HASH>();    \
+    case 3: return lin_lane_info<B, ACC, 3, HASH>();    \
+    case 4: return lin_lane_info<B, ACC, 4, HASH>();    \
+  }                                                     \
   return LinKernelInfo{};
   switch (block) {
-    case 128: { GLIM_PICK_DENSE_L(128) }
-    case 256: { GLIM_PICK_DENSE_L(256) }
+    case 128: { GLIM_PICK_LANE_L(128) }
+    case 256: { GLIM_PICK_LANE_L(256) }
   }
-#undef GLIM_PICK_DENSE_L
+#undef GLIM_PICK_LANE_L
   return LinKernelInfo{};
 }
 
@@ -682,5 +744,8 @@ LinKernelInfo pick_lin_fp64(int block, int lmax);
 LinKernelInfo pick_lin_dense_fp32(int block, int lmax);
 LinKernelInfo pick_lin_dense_kahan(int block, int lmax);
 LinKernelInfo pick_lin_dense_fp64(int block, int lmax);
+LinKernelInfo pick_lin_hash_fp32(int block, int lmax);
+LinKernelInfo pick_lin_hash_kahan(int block, int lmax);
+LinKernelInfo pick_lin_hash_fp64(int block, int lmax);
 
 }  // namespace glim_detail

@@ -122,12 +122,20 @@ __global__ void __launch_bounds__(128) k_reduce_expand(const ReduceArgs a) {
 }
 
 // ---------------------------------------------------------------- kernel table
-LinKernelInfo pick_kernel(int block, int acc, int lmax, bool dense) {
-  if (dense) {
+LinKernelInfo pick_kernel(int block, int acc, int lmax, int lane) {
+  if (lane == 1) {
     switch (acc) {
       case GLIM_ACC_FP32: return pick_lin_dense_fp32(block, lmax);
       case GLIM_ACC_KAHAN: return pick_lin_dense_kahan(block, lmax);
       case GLIM_ACC_FP64: return pick_lin_dense_fp64(block, lmax);
+    }
+    return LinKernelInfo{};
+  }
+  if (lane == 2) {
+    switch (acc) {
+      case GLIM_ACC_FP32: return pick_lin_hash_fp32(block, lmax);
+      case GLIM_ACC_KAHAN: return pick_lin_hash_kahan(block, lmax);
+      case GLIM_ACC_FP64: return pick_lin_hash_fp64(block, lmax);
     }
     return LinKernelInfo{};
   }
@@ -149,7 +157,7 @@ bool opts_valid(const glim_lin_opts& o) {
   return (o.block == 128 || o.block == 256) &&
          (o.pts_per_thread >= 1 && o.pts_per_thread <= 256) &&
          (o.accum_mode >= 0 && o.accum_mode <= 2) && (o.persistent == 1 || o.persistent == 2) &&
-         o.blocks_per_sm >= 0 && o.blocks_per_sm <= 32 && o.kernel >= 0 && o.kernel <= 2;
+         o.blocks_per_sm >= 0 && o.blocks_per_sm <= 32 && o.kernel >= 0 && o.kernel <= 3;
 }
 
 bool is_device_ptr(const void* p) {
@@ -202,9 +210,11 @@ glim_status plan_configure(glim_plan* p, const glim_lin_opts& o) {
   GLIM_CUDA(ctx, cudaMemcpy(p->d_item_begin, begin.data(), begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   if (o.kernel == 2 && !p->d_dmaps)
     return set_error(ctx, GLIM_EINVAL, "the dense-grid kernel needs every target level to be a dense grid");
-  p->dense_kernel = p->d_dmaps != nullptr && o.kernel != 1;
-  p->opts.kernel = p->dense_kernel ? 2 : 1;  // the kernel actually used
-  const LinKernelInfo ki = pick_kernel(o.block, o.accum_mode, p->lmax, p->dense_kernel);
+  if (o.kernel == 3 && !p->d_hmaps)
+    return set_error(ctx, GLIM_EINVAL, "the hash kernel needs every target level to be a hash table");
+  p->lane_kernel = o.kernel == 1 ? 0 : (p->d_dmaps ? 1 : (p->d_hmaps ? 2 : 0));
+  p->opts.kernel = p->lane_kernel == 1 ? 2 : (p->lane_kernel == 2 ? 3 : 1);  // the kernel actually used
+  const LinKernelInfo ki = pick_kernel(o.block, o.accum_mode, p->lmax, p->lane_kernel);
   p->kernel = ki.fn;
   p->kernel_smem = ki.smem;
   if (!p->kernel) return set_error(ctx, GLIM_EINVAL, "no kernel for block=%d ppt=%d acc=%d", o.block, o.pts_per_thread, o.accum_mode);
@@ -237,7 +247,8 @@ glim_status plan_enqueue_kernels(glim_plan* p, int slot = -1) {
     a.pairs = p->d_pairs;
     a.frames = p->d_frames;
     a.maps = p->d_maps;
-    a.dmaps = p->dense_kernel ? p->d_dmaps : nullptr;
+    a.dmaps = p->lane_kernel == 1 ? p->d_dmaps : nullptr;
+    a.hmaps = p->lane_kernel == 2 ? p->d_hmaps : nullptr;
     a.pose = p->in_pose32();
     a.head = p->opts.persistent == 1 ? p->d_head : nullptr;
     a.part = p->d_part;
@@ -408,12 +419,47 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
       if (maps[i]->inv_r[l] != std::ldexp(maps[i]->inv_r[0], -l)) md[i].pow2 = 0;
     }
   }
-  // dense-grid descriptors when every level of every target map is a dense grid
-  bool all_dense = !maps.empty();
+  // per-lane kernel descriptors when every level of every target map is a dense grid, or
+  // every one a hash table
+  bool all_dense = !maps.empty(), all_hash = !maps.empty();
   for (const glim_vmap* m : maps)
-    for (int l = 0; l < m->levels; ++l) all_dense = all_dense && m->dense[l] && m->slots[l];
-  // the dense-grid kernel indexes points in 32 bits, up to two blocks past an item's end
-  for (int f = 0; f < nframes; ++f) all_dense = all_dense && frames[f].n <= 0x7FFFFFFFll - (1 << 17);
+    for (int l = 0; l < m->levels; ++l) {
+      all_dense = all_dense && m->dense[l] && m->slots[l];
+      all_hash = all_hash && !m->dense[l] && m->slots[l] && m->max_probe[l] >= 1;
+    }
+  // the per-lane kernels index points in 32 bits, up to two blocks past an item's end
+  for (int f = 0; f < nframes; ++f)
+    if (frames[f].n > 0x7FFFFFFFll - (1 << 17)) all_dense = all_hash = false;
+  std::vector<HashMapDev> hmd(std::max<size_t>(maps.size(), 1));
+  if (all_hash) {
+    // a level that a map does not have probes an all-empty table of 16 slots owned by the plan
+    constexpr int EMPTY_LOG2 = 4;
+    if (cudaMalloc(&p->d_empty_slots, (1 << EMPTY_LOG2) * sizeof(VoxSlot)) != cudaSuccess ||
+        cudaMemset(p->d_empty_slots, 0x80, (1 << EMPTY_LOG2) * sizeof(VoxSlot)) != cudaSuccess) {
+      glim_plan_destroy(p);
+      return set_error(ctx, GLIM_ENOMEM, "plan: device allocation failed");
+    }
+    for (size_t i = 0; i < maps.size(); ++i) {
+      const glim_vmap* m = maps[i];
+      std::memset(&hmd[i], 0, sizeof(HashMapDev));
+      for (int l = 0; l < GLIM_MAX_LEVELS; ++l) {
+        HashLevelDev& d = hmd[i].lv[l];
+        if (l < m->levels) {
+          d.slots = m->slots[l];
+          d.mask = uint32_t(m->cap[l] - 1);
+          d.log2cap = m->log2cap[l];
+          d.max_probe = m->max_probe[l];
+          hmd[i].inv_r[l] = m->inv_r[l];
+        } else {
+          d.slots = p->d_empty_slots;
+          d.mask = (1u << EMPTY_LOG2) - 1u;
+          d.log2cap = EMPTY_LOG2;
+          d.max_probe = 1;
+          hmd[i].inv_r[l] = m->inv_r[0];
+        }
+      }
+    }
+  }
   std::vector<DenseMapDev> dmd(std::max<size_t>(maps.size(), 1));
   if (all_dense) {
     for (size_t i = 0; i < maps.size(); ++i) {
@@ -458,6 +504,11 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
       return fail(set_error(ctx, GLIM_ENOMEM, "plan: device allocation failed"));
     cudaMemcpy(p->d_dmaps, dmd.data(), dmd.size() * sizeof(DenseMapDev), cudaMemcpyHostToDevice);
   }
+  if (all_hash) {
+    if (cudaMalloc(&p->d_hmaps, hmd.size() * sizeof(HashMapDev)) != cudaSuccess)
+      return fail(set_error(ctx, GLIM_ENOMEM, "plan: device allocation failed"));
+    cudaMemcpy(p->d_hmaps, hmd.data(), hmd.size() * sizeof(HashMapDev), cudaMemcpyHostToDevice);
+  }
   p->in_bytes = std::max<size_t>(size_t(npairs) * (sizeof(PoseF) + 12 * sizeof(double)), 16);
   p->out_bytes = std::max<size_t>(size_t(npairs) * (157 * sizeof(double) + sizeof(int64_t)), 16);
   if (cudaMalloc(&p->d_in, p->in_bytes) != cudaSuccess || cudaMalloc(&p->d_out, p->out_bytes) != cudaSuccess ||
@@ -480,6 +531,8 @@ extern "C" void glim_plan_destroy(glim_plan* p) {
   cudaFree(p->d_pairs);
   cudaFree(p->d_maps);
   cudaFree(p->d_dmaps);
+  cudaFree(p->d_hmaps);
+  cudaFree(p->d_empty_slots);
   if (p->bwd) {
     p->bwd->release();
     delete p->bwd;
@@ -682,7 +735,8 @@ extern "C" glim_status glim_linearize_factors_plain(glim_ctx* ctx, const glim_fr
     a.pairs = p->d_pairs;
     a.frames = p->d_frames;
     a.maps = p->d_maps;
-    a.dmaps = p->dense_kernel ? p->d_dmaps : nullptr;
+    a.dmaps = p->lane_kernel == 1 ? p->d_dmaps : nullptr;
+    a.hmaps = p->lane_kernel == 2 ? p->d_hmaps : nullptr;
     a.pose = p->in_pose32();
     a.head = nullptr;  // one block per item of this factor
     a.part = p->d_part;

@@ -41,6 +41,21 @@ struct DenseMapDev {
   float inv_r[GLIM_MAX_LEVELS];
 };
 
+// One hash level as the per-lane hash kernel sees it (32 bytes, two 16-byte words):
+// {slots, mask, log2cap} {max_probe, ...}.
+struct HashLevelDev {
+  const VoxSlot* slots;
+  uint32_t mask;
+  int32_t log2cap;
+  int32_t max_probe;
+  int32_t pad[3];
+};
+
+struct HashMapDev {
+  HashLevelDev lv[GLIM_MAX_LEVELS];
+  float inv_r[GLIM_MAX_LEVELS];
+};
+
 struct PairDev {
   int32_t src;
   int32_t map;
@@ -59,6 +74,7 @@ struct LinArgs {
   const FrameDev* frames;
   const MapDev* maps;
   const DenseMapDev* dmaps = nullptr;  // per map, when every target level is a dense grid
+  const HashMapDev* hmaps = nullptr;   // per map, when every target level is a hash table
   const PoseF* pose;   // per pair
   int* head;           // work-queue head (persistent)
   double* part;        // nitems x PSTRIDE
@@ -120,6 +136,8 @@ struct glim_plan {
   PairDev* d_pairs = nullptr;
   int nmaps = 0;
   DenseMapDev* d_dmaps = nullptr;  // set when every level of every target map is a dense grid
+  HashMapDev* d_hmaps = nullptr;   // set when every level of every target map is a hash table
+  VoxSlot* d_empty_slots = nullptr;  // an all-empty table for the levels a hash map lacks
   std::vector<std::pair<const glim_vmap*, uint64_t>> map_versions;  // target maps as the plan saw them
   int lmax = 1;  // most levels of any target map (kernel template parameter)
   // work list (depends on the tile size)
@@ -131,7 +149,7 @@ struct glim_plan {
   int* d_head = nullptr;
   int grid = 0;
   LinKernel kernel = nullptr;
-  bool dense_kernel = false;  // kernel is the dense-grid kernel (a.dmaps = d_dmaps)
+  int lane_kernel = 0;  // 0: general kernel; 1: per-lane dense-grid kernel; 2: per-lane hash kernel
   size_t kernel_smem = 0;
   // serialized input block: PoseF[npairs] then double[npairs * 12]
   size_t in_bytes = 0;

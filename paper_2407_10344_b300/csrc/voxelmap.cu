@@ -405,7 +405,7 @@ glim_status build_tables(glim_ctx* ctx, glim_vmap* vm, int l, int layout) {
     GLIM_LAUNCHED(ctx);
     return take_device_status(ctx, "voxel statistics / dense grid");
   }
-  const int64_t cap = std::max<int64_t>(16, int64_t(1) << log2_ceil(2 * m));
+  const int64_t cap = std::max<int64_t>(16, int64_t(1) << log2_ceil(4 * m));  // load <= 1/4
   vm->cap[l] = cap;
   vm->log2cap[l] = log2_ceil(cap);
   GLIM_CUDA(ctx, cudaMalloc(&vm->slots_alloc[l], cap * sizeof(VoxSlot)));

@@ -245,10 +245,12 @@ def test_dense_grid_kernel_and_general_kernel(G, ctx, room, kernel, validate):
     assert plan.opts()["kernel"] == "dense"
 
 
-def test_dense_kernel_mixed_levels_ragged_and_nonfinite(G, ctx):
-    """One batch whose target maps have 3, 1 and 2 levels (absent levels read the empty
-    record), sources of 1, 37, and 130 * 64 + 5 points (ragged tiles, lanes past the end), a
-    source point at NaN and one at 1e30 (misses), against the oracle."""
+@pytest.mark.parametrize("layout", ["dense", "hash"])
+def test_lane_kernels_mixed_levels_ragged_and_nonfinite(G, ctx, layout):
+    """One batch whose target maps have 3, 1 and 2 levels (absent levels read an empty record
+    or probe an empty table), sources of 1, 37, and 130 * 64 + 5 points (ragged tiles, lanes
+    past the end), a source point at NaN and one at 1e30 (misses), against the oracle, with
+    the per-lane kernel of the layout and with the general kernel."""
     w = synth.corridor(n_kf=3, n_cur=9000, kf_range=(6000, 9000))
     dev = torch.device("cuda")
     res_of = {1: [0.5, 1.0, 2.0], 2: [1.0], 3: [0.5, 1.0]}
@@ -267,7 +269,7 @@ def test_dense_kernel_mixed_levels_ragged_and_nonfinite(G, ctx):
         cov[~good] = torch.tensor([1, 0, 0, 1, 0, 1], dtype=torch.float32, device=dev)
         gframes.append(G.FrameData(p4, cov))
         oframes.append(O.Frame(p4.cpu().numpy(), cov.cpu().numpy()))
-        gmaps.append(G.VoxelMap(ctx, p4, cov, res_of[i]) if i in res_of else None)
+        gmaps.append(G.VoxelMap(ctx, p4, cov, res_of[i], layout=layout) if i in res_of else None)
         omaps.append(O.VMap(oframes[i].pts4, oframes[i].cov6, res_of[i]) if i in res_of else None)
     # small sources: single points and a 37-point prefix of frame 0
     for n in (1, 37):
@@ -277,9 +279,9 @@ def test_dense_kernel_mixed_levels_ragged_and_nonfinite(G, ctx):
         omaps.append(None)
     poses = np.concatenate([w.poses, w.poses[:1], w.poses[:1]])
     pairs = np.array([[0, 1], [0, 2], [0, 3], [4, 1], [5, 3], [5, 2], [1, 2], [3, 1]], np.int32)
-    assert all(gmaps[t].is_dense(l) for t in (1, 2, 3) for l in range(len(res_of[t])))
+    assert all(gmaps[t].is_dense(l) == (layout == "dense") for t in (1, 2, 3) for l in range(len(res_of[t])))
     ref = O.linearize(oframes, omaps, pairs, poses, want_comp=True)
-    for kernel in ("dense", "general"):
+    for kernel in (layout, "general"):
         for block, ppt in ((128, 64), (256, 1), (128, 5)):
             res = G.linearize(ctx, gframes, gmaps, pairs, poses, kernel=kernel, block=block, pts_per_thread=ppt)
             from gpu_helpers import numpy_of, rel_errors
@@ -290,14 +292,34 @@ def test_dense_kernel_mixed_levels_ragged_and_nonfinite(G, ctx):
             assert ee.max() <= TOL and eH.max() <= TOL and eb.max() <= TOL, (kernel, block, ppt)
 
 
-def test_dense_kernel_refused_on_hash_maps(G, ctx, room):
+@pytest.mark.parametrize("validate", [False, True])
+def test_hash_kernel_and_general_kernel_on_hash_maps(G, ctx, room, validate):
+    """Hash-table maps: the per-lane hash kernel (chosen automatically) and the general kernel
+    match the oracle across accumulation modes and launch shapes; each per-lane kernel is
+    refused on the other layout, and a batch mixing layouts runs on the general kernel."""
     g = room.gframes[1]
     hm = G.VoxelMap(ctx, g.pts4, g.cov6, room.w.resolutions, layout="hash")
+    ref = room.oracle(validate=validate)
+    for kernel in ("hash", "general"):
+        for acc in (G.ACC_FP32, G.ACC_KAHAN, G.ACC_FP64):
+            for persistent, block, ppt in ((1, 128, 64), (2, 256, 3)):
+                _check(G.linearize(ctx, room.gframes, [None, hm], room.w.pairs, room.w.poses, kernel=kernel,
+                                   validate_surface=validate, accum_mode=acc, persistent=persistent, block=block,
+                                   pts_per_thread=ppt), ref)
+    assert G.Plan(ctx, room.gframes, [None, hm], room.w.pairs).opts()["kernel"] == "hash"
     with pytest.raises(G.GlimError, match="EINVAL"):
         G.linearize(ctx, room.gframes, [None, hm], room.w.pairs, room.w.poses, kernel="dense")
-    plan = G.Plan(ctx, room.gframes, [None, hm], room.w.pairs)
+    with pytest.raises(G.GlimError, match="EINVAL"):
+        G.linearize(ctx, room.gframes, room.gmaps, room.w.pairs, room.w.poses, kernel="hash")
+    # one dense and one hash target in the same batch
+    pairs = np.array([[0, 1], [0, 2]], np.int32)
+    frames = room.gframes + [room.gframes[1]]
+    poses = np.concatenate([room.w.poses, room.w.poses[1:2]])
+    plan = G.Plan(ctx, frames, [None, room.gmaps[1], hm], pairs)
     assert plan.opts()["kernel"] == "general"
-    _check(plan.linearize(room.w.poses), room.oracle())
+    e, H, b, inl = plan.linearize(poses)
+    for q in range(2):
+        _check((e[q:q + 1], H[q:q + 1], b[q:q + 1], inl[q:q + 1]), room.oracle())
 
 
 def test_invalid_arguments(G, ctx, room):
