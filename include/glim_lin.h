@@ -174,7 +174,7 @@ glim_status glim_build_voxelmap(glim_ctx* ctx, const float* pts4, const float* c
  *   layout 0 (default): a dense grid over the bounding box of the occupied keys whose cells
  *            hold the voxel records (48 bytes per cell) when the box has at most 256 cells
  *            per voxel plus 2^22 cells and needs at most 32 GiB, else an open-addressing hash
- *            table (linear probing, load <= 1/2);
+ *            table (linear probing, load <= 1/4);
  *   layout 1: dense grid (GLIM_EINVAL if the bounding box exceeds the limit);
  *   layout 2: hash table.
  * Both layouts give identical correspondences and results; the dense grid resolves every

@@ -6,8 +6,9 @@
 //      stable radix sort, so the members of a voxel are contiguous and in point order;
 //   2. one thread per voxel sums its members' means and covariances in FP64 in that order
 //      and stores the averages (canonical id = rank of the key = position in sorted order);
-//   3. the voxels are inserted into an open-addressing table (linear probing, load <= 1/2)
-//      whose 48-byte slots carry the key and the statistics together.
+//   3. the voxels are written into a dense grid over their key box (48-byte records) when it
+//      is small enough, else inserted into an open-addressing table (linear probing, load
+//      <= 1/4) whose 48-byte slots carry the key and the statistics together.
 #include <climits>
 
 #include "lookup.cuh"
