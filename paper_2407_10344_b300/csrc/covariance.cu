@@ -6,9 +6,14 @@
 // Chebyshev radius r around its own cell.  After shell r every point within r*h - delta of
 // the query has been seen (delta covers the FP32 rounding of the cell assignment), so the
 // search stops once the k-th best squared distance is below (r*h - delta)^2.  Queries that
-// still lack an answer after MAX_SHELL shells scan the whole frame.  Squared distances are
-// FP64 sums (dx*dx + dy*dy) + dz*dz of exact FP64 differences, and ties are broken by point
-// index, so the neighbour sets are exactly those of a brute-force search.
+// still lack an answer after MAX_SHELL shells (isolated points) are listed and scanned
+// against the whole frame by one warp each (the lanes split the points and merge their k
+// best); frames of at most 4096 points are scanned that way throughout.  Squared distances
+// that decide the order are FP64 sums (dx*dx + dy*dy) + dz*dz of exact FP64 differences,
+// and ties are broken by point index, so the neighbour sets are exactly those of a
+// brute-force search; an FP32 distance, within a relative 4e-7 of the exact one, first
+// rejects the candidates that cannot beat the current k-th best (B300's FP64 rate is a
+// small fraction of its FP32 rate).
 //
 // Covariance: 1/k sample covariance of the neighbours in FP64; the normal is the eigenvector
 // of the smallest eigenvalue, from the closed-form eigenvalues of a symmetric 3x3 matrix
@@ -66,58 +71,81 @@ __device__ __forceinline__ bool cand_less(double da, int32_t ia, double db, int3
   return da < db || (da == db && ia < ib);
 }
 
+// The same order on the bit patterns of non-negative doubles (or +inf), which sort as
+// unsigned integers: the top-k list compares with the integer units instead of FP64.
+__device__ __forceinline__ bool key_less(unsigned long long da, int32_t ia, unsigned long long db, int32_t ib) {
+  return da < db || (da == db && ia < ib);
+}
+
 template <int KMAX>
 struct TopK {
-  double d[KMAX];
+  unsigned long long d[KMAX];  // FP64 squared distances as bit patterns (non-negative)
   int32_t i[KMAX];
   int k;
   int have;
+  double wst;   // the k-th best distance once k candidates were seen, else +inf
+  float wthr;   // FP32 bound: a candidate whose FP32 distance exceeds it cannot enter
+  static constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;
   __device__ __forceinline__ void init(int kk) {
     k = kk;
     have = 0;
+    wst = INFINITY;
+    wthr = INFINITY;
 #pragma unroll
     for (int j = 0; j < KMAX; ++j) {
-      d[j] = INFINITY;
+      d[j] = INF_BITS;
       i[j] = 0x7FFFFFFF;
     }
   }
-  __device__ __forceinline__ double worst() const {
-    double w = d[0];
-#pragma unroll
-    for (int j = 0; j < KMAX; ++j)
-      if (j == k - 1) w = d[j];
-    return w;
-  }
+  __device__ __forceinline__ double dist(int j) const { return __longlong_as_double((long long)d[j]); }
   // insert (dc, ic) keeping d[0..k) sorted ascending by (distance, index)
-  __device__ __forceinline__ void push(double dc, int32_t ic) {
+  __device__ __forceinline__ void push(double dcd, int32_t ic) {
+    const unsigned long long dc = (unsigned long long)__double_as_longlong(dcd);
     ++have;
 #pragma unroll
     for (int j = KMAX - 1; j > 0; --j) {
       if (j < k) {
-        if (cand_less(dc, ic, d[j - 1], i[j - 1])) {
+        if (key_less(dc, ic, d[j - 1], i[j - 1])) {
           d[j] = d[j - 1];
           i[j] = i[j - 1];
-        } else if (cand_less(dc, ic, d[j], i[j])) {
+        } else if (key_less(dc, ic, d[j], i[j])) {
           d[j] = dc;
           i[j] = ic;
         }
       }
     }
-    if (cand_less(dc, ic, d[0], i[0])) {
+    if (key_less(dc, ic, d[0], i[0])) {
       d[0] = dc;
       i[0] = ic;
     }
+    if (have >= k) {
+      unsigned long long w = d[0];
+#pragma unroll
+      for (int j = 0; j < KMAX; ++j)
+        if (j == k - 1) w = d[j];
+      wst = __longlong_as_double((long long)w);
+      // FP32 distances have a relative error below 4e-7 (three rounded differences, squares
+      // and sums of non-negative terms), so any candidate with d64 <= wst has
+      // d32 <= wst (1 + 1e-6); the bound is rounded up and +inf beyond the FP32 range
+      const double t = wst * (1.0 + 1e-6);
+      wthr = t < 3.0e38 ? __double2float_ru(t) : INFINITY;
+    }
+  }
+  // offer a candidate at FP32 distance d32: the FP64 distance is formed only if it may enter
+  __device__ __forceinline__ void offer(double qx, double qy, double qz, float qxf, float qyf, float qzf,
+                                        const float4& p, int32_t pi) {
+    const float fx = p.x - qxf, fy = p.y - qyf, fz = p.z - qzf;
+    const float d32 = fx * fx + fy * fy + fz * fz;
+    if (have >= k && d32 > wthr) return;
+    const double dx = __dsub_rn(double(p.x), qx), dy = __dsub_rn(double(p.y), qy), dz = __dsub_rn(double(p.z), qz);
+    const double dc = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    if (have < k || cand_less(dc, pi, wst, 0x7FFFFFFF)) push(dc, pi);
   }
 };
 
-__device__ __forceinline__ double sqdist(double qx, double qy, double qz, const float4& p) {
-  const double dx = __dsub_rn(double(p.x), qx), dy = __dsub_rn(double(p.y), qy), dz = __dsub_rn(double(p.z), qz);
-  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-}
-
 struct GridArgs {
   const float4* sorted;      // points in cell order, w = original index bits
-  const float4* pts;         // original order (brute-force fallback)
+  const float4* pts;         // original order (warp scan, covariance)
   int64_t n;
   const CellSlot* slots;
   uint32_t mask;
@@ -128,7 +156,6 @@ struct GridArgs {
   int k;
   int reg_mode;
   float eps;
-  int brute;                 // 1: skip the grid, scan all points
   float* cov6;
   float* normal3;
 };
@@ -149,7 +176,7 @@ __device__ __forceinline__ bool find_cell(const GridArgs& a, unsigned long long 
 }
 
 // Eigenvector of the smallest eigenvalue of a symmetric 3x3 matrix (FP64).
-__device__ void smallest_eigvec(const double A[6], double n[3]) {
+__device__ __forceinline__ void smallest_eigvec(const double A[6], double n[3]) {
   const double a00 = A[0], a01 = A[1], a02 = A[2], a11 = A[3], a12 = A[4], a22 = A[5];
   const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
   double lam;
@@ -172,13 +199,17 @@ __device__ void smallest_eigvec(const double A[6], double n[3]) {
   c[0][0] = r0[1] * r1[2] - r0[2] * r1[1]; c[0][1] = r0[2] * r1[0] - r0[0] * r1[2]; c[0][2] = r0[0] * r1[1] - r0[1] * r1[0];
   c[1][0] = r0[1] * r2[2] - r0[2] * r2[1]; c[1][1] = r0[2] * r2[0] - r0[0] * r2[2]; c[1][2] = r0[0] * r2[1] - r0[1] * r2[0];
   c[2][0] = r1[1] * r2[2] - r1[2] * r2[1]; c[2][1] = r1[2] * r2[0] - r1[0] * r2[2]; c[2][2] = r1[0] * r2[1] - r1[1] * r2[0];
-  int best = 0;
-  double bn = -1.0;
-  for (int j = 0; j < 3; ++j) {
+  // the longest of the three cross products (the first on ties), selected without indexing
+  double b0 = c[0][0], b1 = c[0][1], b2 = c[0][2];
+  double bn = b0 * b0 + b1 * b1 + b2 * b2;
+#pragma unroll
+  for (int j = 1; j < 3; ++j) {
     const double nn = c[j][0] * c[j][0] + c[j][1] * c[j][1] + c[j][2] * c[j][2];
     if (nn > bn) {
       bn = nn;
-      best = j;
+      b0 = c[j][0];
+      b1 = c[j][1];
+      b2 = c[j][2];
     }
   }
   if (bn <= 0.0) {  // A - lam I has rank <= 1 (repeated smallest eigenvalue): any vector works
@@ -186,64 +217,15 @@ __device__ void smallest_eigvec(const double A[6], double n[3]) {
     return;
   }
   const double inv = 1.0 / sqrt(bn);
-  n[0] = c[best][0] * inv;
-  n[1] = c[best][1] * inv;
-  n[2] = c[best][2] * inv;
+  n[0] = b0 * inv;
+  n[1] = b1 * inv;
+  n[2] = b2 * inv;
 }
 
+// Sample covariance (FP64, 1/k) of a query's k neighbours, its normal, and the outputs.
 template <int KMAX>
-__global__ void __launch_bounds__(128) k_knn_cov(const GridArgs a) {
-  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (s >= a.n) return;
-  const float4 qp = a.brute ? a.pts[s] : a.sorted[s];
-  const int32_t self = a.brute ? int32_t(s) : int32_t(__float_as_uint(qp.w));
-  const double qx = qp.x, qy = qp.y, qz = qp.z;
-  TopK<KMAX> top;
-  top.init(a.k);
-  bool done = false;
-  if (!a.brute) {
-    int cx, cy, cz;
-    voxel_coord(qp.x, a.inv_h, cx);
-    voxel_coord(qp.y, a.inv_h, cy);
-    voxel_coord(qp.z, a.inv_h, cz);
-    const double amax = fmax(fabs(qx), fmax(fabs(qy), fabs(qz)));
-#pragma unroll 1
-    for (int r = 0; r <= MAX_SHELL && !done; ++r) {
-#pragma unroll 1
-      for (int dx = -r; dx <= r; ++dx)
-#pragma unroll 1
-        for (int dy = -r; dy <= r; ++dy)
-#pragma unroll 1
-          for (int dz = -r; dz <= r; ++dz) {
-            if (max(abs(dx), max(abs(dy), abs(dz))) != r) continue;
-            const int x = cx + dx, y = cy + dy, z = cz + dz;
-            if (x < -GLIM_KEY_BIAS || x >= GLIM_KEY_BIAS || y < -GLIM_KEY_BIAS || y >= GLIM_KEY_BIAS ||
-                z < -GLIM_KEY_BIAS || z >= GLIM_KEY_BIAS)
-              continue;
-            uint32_t st, cnt;
-            if (!find_cell(a, pack_key(x, y, z), st, cnt)) continue;
-#pragma unroll 1
-            for (uint32_t j = st; j < st + cnt; ++j) {
-              const float4 p = a.sorted[j];
-              const double d = sqdist(qx, qy, qz, p);
-              const int32_t pi = int32_t(__float_as_uint(p.w));
-              if (top.have < a.k || cand_less(d, pi, top.worst(), 0x7FFFFFFF)) top.push(d, pi);
-            }
-          }
-      const double rad = double(r) * a.h - 1e-6 * (amax + double(r + 1) * a.h);
-      if (top.have >= a.k && rad > 0.0 && top.worst() <= rad * rad) done = true;
-    }
-  }
-  if (!done) {  // brute force over the whole frame
-    top.init(a.k);
-#pragma unroll 1
-    for (int64_t j = 0; j < a.n; ++j) {
-      const float4 p = a.pts[j];
-      const double d = sqdist(qx, qy, qz, p);
-      if (top.have < a.k || cand_less(d, int32_t(j), top.worst(), 0x7FFFFFFF)) top.push(d, int32_t(j));
-    }
-  }
-  // sample covariance of the k neighbours (FP64, 1/k)
+__device__ __forceinline__ void finish_point(const GridArgs& a, int32_t self, double qx, double qy, double qz,
+                                             const TopK<KMAX>& top) {
   double m[3] = {0, 0, 0};
 #pragma unroll
   for (int j = 0; j < KMAX; ++j)
@@ -264,6 +246,7 @@ __global__ void __launch_bounds__(128) k_knn_cov(const GridArgs a) {
       C[0] += vx * vx; C[1] += vx * vy; C[2] += vx * vz;
       C[3] += vy * vy; C[4] += vy * vz; C[5] += vz * vz;
     }
+#pragma unroll
   for (int c = 0; c < 6; ++c) C[c] *= ik;
   double nv[3];
   smallest_eigvec(C, nv);
@@ -284,6 +267,101 @@ __global__ void __launch_bounds__(128) k_knn_cov(const GridArgs a) {
     float* nn = a.normal3 + 3 * int64_t(self);
     nn[0] = float(nv[0]); nn[1] = float(nv[1]); nn[2] = float(nv[2]);
   }
+}
+
+// Grid search, one thread per point (in cell order).  A query not settled after MAX_SHELL
+// shells is appended to `unres` for the warp-per-query scan.
+template <int KMAX>
+__global__ void __launch_bounds__(128) k_knn_cov(const GridArgs a, int32_t* __restrict__ unres,
+                                                 int* __restrict__ nunres) {
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= a.n) return;
+  const float4 qp = a.sorted[s];
+  const int32_t self = int32_t(__float_as_uint(qp.w));
+  const double qx = qp.x, qy = qp.y, qz = qp.z;
+  TopK<KMAX> top;
+  top.init(a.k);
+  bool done = false;
+  int cx, cy, cz;
+  voxel_coord(qp.x, a.inv_h, cx);
+  voxel_coord(qp.y, a.inv_h, cy);
+  voxel_coord(qp.z, a.inv_h, cz);
+  const double amax = fmax(fabs(qx), fmax(fabs(qy), fabs(qz)));
+#pragma unroll 1
+  for (int r = 0; r <= MAX_SHELL && !done; ++r) {
+#pragma unroll 1
+    for (int dx = -r; dx <= r; ++dx)
+#pragma unroll 1
+      for (int dy = -r; dy <= r; ++dy)
+#pragma unroll 1
+        for (int dz = -r; dz <= r; ++dz) {
+          if (max(abs(dx), max(abs(dy), abs(dz))) != r) continue;
+          const int x = cx + dx, y = cy + dy, z = cz + dz;
+          if (x < -GLIM_KEY_BIAS || x >= GLIM_KEY_BIAS || y < -GLIM_KEY_BIAS || y >= GLIM_KEY_BIAS ||
+              z < -GLIM_KEY_BIAS || z >= GLIM_KEY_BIAS)
+            continue;
+          uint32_t st, cnt;
+          if (!find_cell(a, pack_key(x, y, z), st, cnt)) continue;
+#pragma unroll 1
+          for (uint32_t j = st; j < st + cnt; ++j) {
+            const float4 p = a.sorted[j];
+            top.offer(qx, qy, qz, qp.x, qp.y, qp.z, p, int32_t(__float_as_uint(p.w)));
+          }
+        }
+    const double rad = double(r) * a.h - 1e-6 * (amax + double(r + 1) * a.h);
+    if (top.have >= a.k && rad > 0.0 && top.wst <= rad * rad) done = true;
+  }
+  if (!done) {
+    unres[atomicAdd(nunres, 1)] = self;
+    return;
+  }
+  finish_point(a, self, qx, qy, qz, top);
+}
+
+// Exact scan of the whole frame for the listed queries, one warp per query: every lane keeps
+// the k best of its stride of the points, then k rounds of a warp arg-min over the lanes'
+// heads (distance, then index) give the k best of the frame in order.
+template <int KMAX>
+__global__ void __launch_bounds__(128) k_knn_warp_scan(const GridArgs a, const int32_t* __restrict__ list,
+                                                       int count) {
+  const int warp = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= count) return;  // whole warps leave together
+  const int32_t self = list[warp];
+  const float4 qp = a.pts[self];
+  const double qx = qp.x, qy = qp.y, qz = qp.z;
+  TopK<KMAX> mine;
+  mine.init(a.k);
+#pragma unroll 1
+  for (int64_t j = lane; j < a.n; j += 32) mine.offer(qx, qy, qz, qp.x, qp.y, qp.z, a.pts[j], int32_t(j));
+  TopK<KMAX> top;
+  top.init(a.k);
+  int head = 0;  // next unused entry of this lane's list
+#pragma unroll 1
+  for (int r = 0; r < a.k; ++r) {
+    unsigned long long hd = TopK<KMAX>::INF_BITS;
+    int32_t hi = 0x7FFFFFFF;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j == head && j < mine.have && j < a.k) {
+        hd = mine.d[j];
+        hi = mine.i[j];
+      }
+    unsigned long long bd = hd;
+    int32_t bi = hi;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long od = __shfl_xor_sync(0xffffffffu, bd, o);
+      const int32_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (key_less(od, oi, bd, bi)) {
+        bd = od;
+        bi = oi;
+      }
+    }
+    if (bd == hd && bi == hi) ++head;  // this lane supplied the winner (indices are unique)
+    top.push(__longlong_as_double((long long)bd), bi);
+  }
+  if (lane == 0) finish_point(a, self, qx, qy, qz, top);
 }
 
 __global__ void k_bbox(const float4* __restrict__ pts, int64_t n, float* __restrict__ out /*6: min xyz, max xyz*/) {
@@ -320,6 +398,11 @@ __global__ void k_bbox(const float4* __restrict__ pts, int64_t n, float* __restr
   }
 }
 
+__global__ void k_iota_i32(int32_t* __restrict__ a, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = int32_t(i);
+}
+
 __global__ void k_check_finite(const float4* __restrict__ pts, int64_t n, unsigned int* __restrict__ status) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const float4 p = pts[i];
@@ -333,12 +416,25 @@ int log2_ceil64(int64_t x) {
   return l;
 }
 
-glim_status launch_knn(glim_ctx* ctx, const GridArgs& a) {
-  const int grid = ceil_div_i(a.n, 128);
-  if (a.k <= 16) k_knn_cov<16><<<grid, 128, 0, ctx->stream>>>(a);
-  else k_knn_cov<32><<<grid, 128, 0, ctx->stream>>>(a);
+// The warp scan of `count` listed queries.
+glim_status launch_warp_scan(glim_ctx* ctx, const GridArgs& a, const int32_t* list, int count) {
+  if (count <= 0) return GLIM_OK;
+  const int grid = ceil_div_i(int64_t(count) * 32, 128);
+  if (a.k <= 16) k_knn_warp_scan<16><<<grid, 128, 0, ctx->stream>>>(a, list, count);
+  else k_knn_warp_scan<32><<<grid, 128, 0, ctx->stream>>>(a, list, count);
   GLIM_LAUNCHED(ctx);
   return GLIM_OK;
+}
+
+// Every point by the warp scan (small frames, or keys out of the packable range).
+glim_status knn_all_by_scan(glim_ctx* ctx, const GridArgs& a) {
+  DevBuf<int32_t> list;
+  GLIM_CUDA(ctx, list.alloc(std::max<int64_t>(a.n, 1), ctx->stream));
+  k_iota_i32<<<ceil_div_i(std::max<int64_t>(a.n, 1), 256), 256, 0, ctx->stream>>>(list.p, a.n);
+  GLIM_LAUNCHED(ctx);
+  glim_status st = launch_warp_scan(ctx, a, list.p, int(a.n));
+  if (st != GLIM_OK) return st;
+  return take_device_status(ctx, "estimate_covariances");
 }
 
 }  // namespace
@@ -368,12 +464,7 @@ extern "C" glim_status glim_estimate_covariances(glim_ctx* ctx, const float* pts
     glim_status st = take_device_status(ctx, "estimate_covariances");
     if (st != GLIM_OK) return st;
   }
-  if (n <= 4096) {
-    a.brute = 1;
-    glim_status st = launch_knn(ctx, a);
-    if (st != GLIM_OK) return st;
-    return take_device_status(ctx, "estimate_covariances");
-  }
+  if (n <= 4096) return knn_all_by_scan(ctx, a);
   // cell size: start from the bounding box assuming points on surfaces, then adjust so that
   // an occupied cell holds about k/2 points
   DevBuf<float> bb;
@@ -405,12 +496,7 @@ extern "C" glim_status glim_estimate_covariances(glim_ctx* ctx, const float* pts
   uint32_t covered = 0;  // points with a cell key (keys outside the packable range have none)
   GLIM_CUDA(ctx, cudaMemcpyAsync(&covered, cells.cell_start.p + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
   GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (int64_t(covered) != n) {
-    a.brute = 1;
-    glim_status st = launch_knn(ctx, a);
-    if (st != GLIM_OK) return st;
-    return take_device_status(ctx, "estimate_covariances");
-  }
+  if (int64_t(covered) != n) return knn_all_by_scan(ctx, a);
   const int64_t cap = std::max<int64_t>(16, int64_t(1) << log2_ceil64(2 * m));
   DevBuf<CellSlot> slots;
   DevBuf<float4> sorted;
@@ -436,8 +522,18 @@ extern "C" glim_status glim_estimate_covariances(glim_ctx* ctx, const float* pts
   a.max_probe = mp;
   a.inv_h = float(1.0 / h);
   a.h = h;
-  a.brute = 0;
-  glim_status st = launch_knn(ctx, a);
+  DevBuf<int32_t> unres;
+  DevBuf<int> nunres;
+  GLIM_CUDA(ctx, unres.alloc(n, ctx->stream));
+  GLIM_CUDA(ctx, nunres.alloc(1, ctx->stream));
+  GLIM_CUDA(ctx, cudaMemsetAsync(nunres.p, 0, sizeof(int), ctx->stream));
+  if (a.k <= 16) k_knn_cov<16><<<ceil_div_i(n, 128), 128, 0, ctx->stream>>>(a, unres.p, nunres.p);
+  else k_knn_cov<32><<<ceil_div_i(n, 128), 128, 0, ctx->stream>>>(a, unres.p, nunres.p);
+  GLIM_LAUNCHED(ctx);
+  int nu = 0;
+  GLIM_CUDA(ctx, cudaMemcpyAsync(&nu, nunres.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  glim_status st = launch_warp_scan(ctx, a, unres.p, nu);
   if (st != GLIM_OK) return st;
   st = take_device_status(ctx, "estimate_covariances");
   if (st == GLIM_OK) ctx->err.clear();
