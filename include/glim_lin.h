@@ -281,6 +281,11 @@ void glim_plan_destroy(glim_plan* plan);
  * download.  Outputs as in glim_linearize_factors (host or device). */
 glim_status glim_plan_linearize(glim_plan* plan, const double* poses12, double* e_out,
                                 double* H_out, double* b_out, int64_t* inliers_out);
+/* The same without the final host copy: runs the graph, synchronizes and returns pointers
+ * into the plan's pinned host output block (e: npairs, H: npairs x 144, b: npairs x 12
+ * doubles, inliers: npairs int64), valid until the plan's next launch or destruction. */
+glim_status glim_plan_linearize_pinned(glim_plan* plan, const double* poses12, const double** e,
+                                       const double** H, const double** b, const int64_t** inliers);
 /* Device-resident use: glim_plan_set_poses uploads the serialized pose block (async);
  * glim_plan_launch enqueues queue reset, linearize and reduce (no copies, no sync) and
  * leaves the results in the plan's device output block, whose arrays

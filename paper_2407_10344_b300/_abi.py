@@ -69,6 +69,7 @@ SIGNATURES = {
     "glim_plan_launch_timed": (_i32, [_vp, _i32]),
     "glim_plan_kernel_ms": (_i32, [_vp, _i32, C.POINTER(_f32)]),
     "glim_plan_autotune": (_i32, [_vp, _vp, _i32, C.POINTER(LinOpts), C.POINTER(_f32)]),
+    "glim_plan_linearize_pinned": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "glim_plan_get_opts": (_i32, [_vp, C.POINTER(LinOpts)]),
     "glim_backward": (_i32, [_vp, C.POINTER(Frame), _i32, C.POINTER(Pair), _i32, _vp, _i32, _i32, _vp, _vp,
                              _vp]),

@@ -303,9 +303,23 @@ class Plan:
         self.h = h
         self._host = _outputs(P, "host")
 
-    def linearize(self, poses, out=None):
-        """One upload, one graph launch, one download; returns host arrays (e, H, b, inliers)."""
+    def linearize(self, poses, out=None, copy=True):
+        """One upload, one graph launch, one download; returns host arrays (e, H, b, inliers).
+        copy=False returns read-only views of the plan's pinned output block instead (no host
+        copy), valid until the plan's next launch."""
         Pz = _poses(poses, self.nframes)
+        if not copy and out is None:
+            ptrs = [C.c_void_p() for _ in range(4)]
+            self.ctx.call("plan_linearize_pinned", self.ctx.lib.glim_plan_linearize_pinned, self.h, _ptr(Pz),
+                          *[C.byref(q) for q in ptrs])
+            P = self.npairs
+            views = []
+            for q, shape, ct in zip(ptrs, [(P,), (P, 12, 12), (P, 12), (P,)],
+                                    [C.c_double, C.c_double, C.c_double, C.c_int64]):
+                a = np.ctypeslib.as_array(C.cast(q, C.POINTER(ct)), shape=shape) if P > 0 else np.zeros(shape)
+                a.flags.writeable = False
+                views.append(a)
+            return tuple(views)
         e, H, b, inl = out if out is not None else self._host
         self.ctx.call("plan_linearize", self.ctx.lib.glim_plan_linearize, self.h, _ptr(Pz), _ptr(e), _ptr(H), _ptr(b), _ptr(inl))
         return e, H, b, inl

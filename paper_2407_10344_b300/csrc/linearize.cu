@@ -636,6 +636,37 @@ extern "C" glim_status glim_plan_linearize(glim_plan* p, const double* poses12, 
   return copy_outputs(p, e_out, H_out, b_out, inliers_out, true);
 }
 
+extern "C" glim_status glim_plan_linearize_pinned(glim_plan* p, const double* poses12, const double** e,
+                                                  const double** H, const double** b, const int64_t** inl) {
+  if (!p || !poses12) return GLIM_EINVAL;
+  if (maps_current(p) != GLIM_OK) return GLIM_EINVAL;
+  glim_ctx* ctx = p->ctx;
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  plan_pack_poses(p, poses12);
+  if (p->use_graph) {
+    if (!p->g_full) {
+      glim_status st = capture(p, true, &p->g_full);
+      if (st != GLIM_OK) return st;
+    }
+    GLIM_CUDA(ctx, cudaGraphLaunch(p->g_full, ctx->stream));
+    ctx->launches += glim_plan_kernels_per_launch(p);
+  } else {
+    GLIM_CUDA(ctx, cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream));
+    glim_status st = plan_enqueue_kernels(p);
+    if (st != GLIM_OK) return st;
+    GLIM_CUDA(ctx, cudaMemcpyAsync(p->h_out, p->d_out, p->out_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const double* base = reinterpret_cast<const double*>(p->h_out);
+  const int P = p->npairs;
+  if (e) *e = base;
+  if (H) *H = base + P;
+  if (b) *b = base + size_t(P) * 145;
+  if (inl) *inl = reinterpret_cast<const int64_t*>(base + size_t(P) * 157);
+  ctx->err.clear();
+  return GLIM_OK;
+}
+
 extern "C" glim_status glim_plan_get_opts(const glim_plan* p, glim_lin_opts* out) {
   if (!p || !out) return GLIM_EINVAL;
   *out = p->opts;

@@ -245,6 +245,22 @@ def test_dense_grid_kernel_and_general_kernel(G, ctx, room, kernel, validate):
     assert plan.opts()["kernel"] == "dense"
 
 
+def test_plan_linearize_pinned_views(G, ctx, corridor):
+    """The zero-copy form returns the same numbers as the copying form, as read-only views
+    of the plan's pinned block that the next launch overwrites."""
+    w = corridor.w
+    plan = G.Plan(ctx, corridor.gframes, corridor.gmaps, w.pairs)
+    ref = [np.array(x) for x in plan.linearize(w.poses)]
+    views = plan.linearize(w.poses, copy=False)
+    for a, b in zip(views, ref):
+        assert np.array_equal(a, b)
+    assert not views[1].flags.writeable
+    moved = w.poses.copy()
+    moved[0, :, 3] += 0.05
+    e2 = np.array(plan.linearize(moved, copy=False)[0])
+    assert np.array_equal(views[0], e2) and not np.array_equal(e2, ref[0])
+
+
 @pytest.mark.parametrize("layout", ["dense", "hash"])
 def test_lane_kernels_mixed_levels_ragged_and_nonfinite(G, ctx, layout):
     """One batch whose target maps have 3, 1 and 2 levels (absent levels read an empty record
