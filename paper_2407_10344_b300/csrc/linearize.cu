@@ -281,6 +281,60 @@ glim_status plan_enqueue_kernels(glim_plan* p, int slot = -1) {
 
 }  // namespace
 
+LinKernelInfo pick_lin_kernel(int block, int acc, int lmax, int lane) { return pick_kernel(block, acc, lmax, lane); }
+
+bool map_all_dense(const glim_vmap* m) {
+  for (int l = 0; l < m->levels; ++l)
+    if (!m->dense[l] || !m->slots[l]) return false;
+  return true;
+}
+
+bool map_all_hash(const glim_vmap* m) {
+  for (int l = 0; l < m->levels; ++l)
+    if (m->dense[l] || !m->slots[l] || m->max_probe[l] < 1) return false;
+  return true;
+}
+
+void fill_dense_map(const glim_vmap* m, DenseMapDev& d) {
+  std::memset(&d, 0, sizeof(DenseMapDev));
+  for (int l = 0; l < GLIM_MAX_LEVELS; ++l) {
+    DenseLevelDev& v = d.lv[l];
+    if (l < m->levels) {
+      v.cells = m->slots[l];
+      v.ox = m->org[l][0];
+      v.oy = m->org[l][1];
+      v.oz = m->org[l][2];
+      v.nx = m->dim[l][0];
+      v.ny = m->dim[l][1];
+      v.nz = m->dim[l][2];
+      d.inv_r[l] = m->inv_r[l];
+    } else {  // an absent level: empty box, reads level 0's empty record
+      v.cells = m->slots[0];
+      d.inv_r[l] = m->inv_r[0];
+    }
+  }
+}
+
+void fill_hash_map(const glim_vmap* m, const VoxSlot* empty16, HashMapDev& d) {
+  std::memset(&d, 0, sizeof(HashMapDev));
+  for (int l = 0; l < GLIM_MAX_LEVELS; ++l) {
+    HashLevelDev& v = d.lv[l];
+    if (l < m->levels) {
+      v.slots = m->slots[l];
+      v.mask = uint32_t(m->cap[l] - 1);
+      v.log2cap = m->log2cap[l];
+      v.max_probe = m->max_probe[l];
+      d.inv_r[l] = m->inv_r[l];
+    } else {  // an absent level probes an all-empty table of 16 slots
+      v.slots = empty16;
+      v.mask = 15u;
+      v.log2cap = 4;
+      v.max_probe = 1;
+      d.inv_r[l] = m->inv_r[0];
+    }
+  }
+}
+
 // The plan holds device pointers to its maps' tables; a map changed since (an insertion
 // frees and replaces them) makes the plan unusable.
 bool plan_maps_current(const glim_plan* p) {
@@ -422,66 +476,24 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
   // per-lane kernel descriptors when every level of every target map is a dense grid, or
   // every one a hash table
   bool all_dense = !maps.empty(), all_hash = !maps.empty();
-  for (const glim_vmap* m : maps)
-    for (int l = 0; l < m->levels; ++l) {
-      all_dense = all_dense && m->dense[l] && m->slots[l];
-      all_hash = all_hash && !m->dense[l] && m->slots[l] && m->max_probe[l] >= 1;
-    }
+  for (const glim_vmap* m : maps) {
+    all_dense = all_dense && map_all_dense(m);
+    all_hash = all_hash && map_all_hash(m);
+  }
   // the per-lane kernels index points in 32 bits, up to two blocks past an item's end
   for (int f = 0; f < nframes; ++f)
     if (frames[f].n > 0x7FFFFFFFll - (1 << 17)) all_dense = all_hash = false;
+  std::vector<DenseMapDev> dmd(std::max<size_t>(maps.size(), 1));
+  if (all_dense)
+    for (size_t i = 0; i < maps.size(); ++i) fill_dense_map(maps[i], dmd[i]);
   std::vector<HashMapDev> hmd(std::max<size_t>(maps.size(), 1));
   if (all_hash) {
-    // a level that a map does not have probes an all-empty table of 16 slots owned by the plan
-    constexpr int EMPTY_LOG2 = 4;
-    if (cudaMalloc(&p->d_empty_slots, (1 << EMPTY_LOG2) * sizeof(VoxSlot)) != cudaSuccess ||
-        cudaMemset(p->d_empty_slots, 0x80, (1 << EMPTY_LOG2) * sizeof(VoxSlot)) != cudaSuccess) {
+    if (cudaMalloc(&p->d_empty_slots, 16 * sizeof(VoxSlot)) != cudaSuccess ||
+        cudaMemset(p->d_empty_slots, 0x80, 16 * sizeof(VoxSlot)) != cudaSuccess) {
       glim_plan_destroy(p);
       return set_error(ctx, GLIM_ENOMEM, "plan: device allocation failed");
     }
-    for (size_t i = 0; i < maps.size(); ++i) {
-      const glim_vmap* m = maps[i];
-      std::memset(&hmd[i], 0, sizeof(HashMapDev));
-      for (int l = 0; l < GLIM_MAX_LEVELS; ++l) {
-        HashLevelDev& d = hmd[i].lv[l];
-        if (l < m->levels) {
-          d.slots = m->slots[l];
-          d.mask = uint32_t(m->cap[l] - 1);
-          d.log2cap = m->log2cap[l];
-          d.max_probe = m->max_probe[l];
-          hmd[i].inv_r[l] = m->inv_r[l];
-        } else {
-          d.slots = p->d_empty_slots;
-          d.mask = (1u << EMPTY_LOG2) - 1u;
-          d.log2cap = EMPTY_LOG2;
-          d.max_probe = 1;
-          hmd[i].inv_r[l] = m->inv_r[0];
-        }
-      }
-    }
-  }
-  std::vector<DenseMapDev> dmd(std::max<size_t>(maps.size(), 1));
-  if (all_dense) {
-    for (size_t i = 0; i < maps.size(); ++i) {
-      const glim_vmap* m = maps[i];
-      std::memset(&dmd[i], 0, sizeof(DenseMapDev));
-      for (int l = 0; l < GLIM_MAX_LEVELS; ++l) {
-        DenseLevelDev& d = dmd[i].lv[l];
-        if (l < m->levels) {
-          d.cells = m->slots[l];
-          d.ox = m->org[l][0];
-          d.oy = m->org[l][1];
-          d.oz = m->org[l][2];
-          d.nx = m->dim[l][0];
-          d.ny = m->dim[l][1];
-          d.nz = m->dim[l][2];
-          dmd[i].inv_r[l] = m->inv_r[l];
-        } else {  // an absent level: empty box, reads level 0's empty record
-          d.cells = m->slots[0];
-          dmd[i].inv_r[l] = m->inv_r[0];
-        }
-      }
-    }
+    for (size_t i = 0; i < maps.size(); ++i) fill_hash_map(maps[i], p->d_empty_slots, hmd[i]);
   }
   p->nmaps = int(maps.size());
   for (const glim_vmap* m : maps) p->map_versions.emplace_back(m, m->version);

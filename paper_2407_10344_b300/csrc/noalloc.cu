@@ -21,6 +21,8 @@ constexpr int NA_MAX_DEVICES = 64;
 struct NoAllocHostPart {
   FrameDev frames[NA_MAX_FRAMES];
   MapDev maps[NA_MAX_PAIRS];
+  DenseMapDev dmaps[NA_MAX_PAIRS];  // per pair, when every target level is a dense grid
+  HashMapDev hmaps[NA_MAX_PAIRS];   // per pair, when every target level is a hash table
   PairDev pairs[NA_MAX_PAIRS];
   PoseF pose32[NA_MAX_PAIRS];
   double pose64[NA_MAX_PAIRS * 12];
@@ -30,6 +32,7 @@ struct NoAllocHostPart {
 
 struct NoAllocScratch {
   NoAllocHostPart host;
+  alignas(256) VoxSlot empty16[16];  // all-empty table for the levels a hash map lacks
   alignas(256) int32_t head[64];
   alignas(256) double part[size_t(NA_MAX_ITEMS) * PSTRIDE];
 };
@@ -79,6 +82,8 @@ extern "C" glim_status glim_linearize_factors_noalloc(glim_ctx* ctx, const glim_
     const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_check(ctx, e, "linearize_noalloc: cudaGetSymbolAddress");
     g_scratch_addr[ctx->device] = ptr;
+    NoAllocScratch* d0 = static_cast<NoAllocScratch*>(ptr);
+    GLIM_CUDA(ctx, cudaMemsetAsync(d0->empty16, 0x80, sizeof(d0->empty16), ctx->stream));
   }
   NoAllocScratch* dev = static_cast<NoAllocScratch*>(g_scratch_addr[ctx->device]);
 
@@ -93,6 +98,17 @@ extern "C" glim_status glim_linearize_factors_noalloc(glim_ctx* ctx, const glim_
   }
   const int tile = o.block * o.pts_per_thread;
   int nitems = 0;
+  bool all_dense = npairs > 0, all_hash = npairs > 0;
+  for (int q = 0; q < npairs; ++q)
+    if (pairs[q].tgt) {
+      all_dense = all_dense && map_all_dense(pairs[q].tgt);
+      all_hash = all_hash && map_all_hash(pairs[q].tgt);
+    }
+  for (int f = 0; f < nframes; ++f)
+    if (frames[f].n > 0x7FFFFFFFll - (1 << 17)) all_dense = all_hash = false;
+  if ((o.kernel == 2 && !all_dense) || (o.kernel == 3 && !all_hash) || o.kernel < 0 || o.kernel > 3)
+    return set_error(ctx, GLIM_EINVAL, "linearize_noalloc: the requested kernel does not fit the maps' layout");
+  const int lane = o.kernel == 1 ? 0 : (all_dense ? 1 : (all_hash ? 2 : 0));
   for (int q = 0; q < npairs; ++q) {
     const glim_pair& P = pairs[q];
     if (P.src_frame < 0 || P.src_frame >= nframes || P.tgt_frame < 0 || P.tgt_frame >= nframes || !P.tgt ||
@@ -102,6 +118,8 @@ extern "C" glim_status glim_linearize_factors_noalloc(glim_ctx* ctx, const glim_
     h.maps[q].levels = P.tgt->levels;
     for (int l = 0; l < P.tgt->levels; ++l) h.maps[q].lv[l] = P.tgt->dev(l);
     lmax = P.tgt->levels > lmax ? P.tgt->levels : lmax;
+    if (lane == 1) fill_dense_map(P.tgt, h.dmaps[q]);
+    if (lane == 2) fill_hash_map(P.tgt, dev->empty16, h.hmaps[q]);
     h.pairs[q].src = P.src_frame;
     h.pairs[q].map = q;
     const RelPose T = relative_pose(poses12 + 12 * P.src_frame, poses12 + 12 * P.tgt_frame);
@@ -122,12 +140,7 @@ extern "C" glim_status glim_linearize_factors_noalloc(glim_ctx* ctx, const glim_
   GLIM_CUDA(ctx, cudaMemcpyAsync(&dev->host, &h, sizeof(NoAllocHostPart), cudaMemcpyHostToDevice, ctx->stream));
 
   if (nitems > 0) {
-    LinKernelInfo ki;
-    switch (o.accum_mode) {
-      case GLIM_ACC_FP32: ki = pick_lin_fp32(o.block, lmax); break;
-      case GLIM_ACC_KAHAN: ki = pick_lin_kahan(o.block, lmax); break;
-      default: ki = pick_lin_fp64(o.block, lmax); break;
-    }
+    const LinKernelInfo ki = pick_lin_kernel(o.block, o.accum_mode, lmax, lane);
     if (!ki.fn) return set_error(ctx, GLIM_EINVAL, "linearize_noalloc: no kernel for these options");
     GLIM_CUDA(ctx, cudaFuncSetAttribute(reinterpret_cast<const void*>(ki.fn),
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(ki.smem)));
@@ -143,6 +156,8 @@ extern "C" glim_status glim_linearize_factors_noalloc(glim_ctx* ctx, const glim_
     a.pairs = dev->host.pairs;
     a.frames = dev->host.frames;
     a.maps = dev->host.maps;
+    a.dmaps = lane == 1 ? dev->host.dmaps : nullptr;
+    a.hmaps = lane == 2 ? dev->host.hmaps : nullptr;
     a.pose = dev->host.pose32;
     a.head = dev->head;
     a.part = dev->part;

@@ -177,6 +177,13 @@ struct glim_plan {
 // shared host helpers (linearize.cu)
 void plan_pack_poses(glim_plan* p, const double* poses12);
 bool plan_maps_current(const glim_plan* p);  // false once a target map changed since creation
+bool map_all_dense(const glim_vmap* m);     // every level a dense grid
+bool map_all_hash(const glim_vmap* m);      // every level a hash table
+void fill_dense_map(const glim_vmap* m, DenseMapDev& d);
+void fill_hash_map(const glim_vmap* m, const VoxSlot* empty16, HashMapDev& d);  // empty16: 16 empty slots
+// the kernel for an options' accumulation mode and block size, the deepest map's levels and
+// lane (0: general, 1: per-lane dense grid, 2: per-lane hash)
+LinKernelInfo pick_lin_kernel(int block, int acc, int lmax, int lane);
 glim_status plan_configure(glim_plan* p, const glim_lin_opts& o);
 glim_status enqueue_reduce_expand(glim_ctx* ctx, const double* part, const int32_t* item_begin,
                                   const double* pose64, int32_t npairs, int32_t fp32_sum, double* e, double* H,

@@ -24,7 +24,7 @@ def _rel(a, b):
     return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300)
 
 
-def _setup():
+def _setup(layout="auto"):
     import paper_2407_10344_b300 as G
     from paper_2407_10344_b300 import _abi
     ctx = G.Context(0)
@@ -36,12 +36,12 @@ def _setup():
         cov, nrm = G.estimate_covariances(ctx, p4)
         frames.append(G.FrameData(p4, cov, nrm))
         if i > 0:
-            maps[i] = G.VoxelMap(ctx, p4, cov, w.resolutions)
+            maps[i] = G.VoxelMap(ctx, p4, cov, w.resolutions, layout=layout)
     torch.cuda.synchronize()
     return G, _abi, ctx, w, frames, maps
 
 
-def _call_noalloc(G, _abi, ctx, w, frames, maps, pairs):
+def _call_noalloc(G, _abi, ctx, w, frames, maps, pairs, kernel=0):
     fr = (_abi.Frame * len(frames))(*[f.c() for f in frames])
     pr = (_abi.Pair * len(pairs))(*[_abi.Pair(int(s), int(t), maps[int(t)].h.value) for s, t in pairs])
     poses = np.ascontiguousarray(w.poses.reshape(-1, 12))
@@ -51,6 +51,7 @@ def _call_noalloc(G, _abi, ctx, w, frames, maps, pairs):
     b = torch.full((P, 12), float("nan"), dtype=torch.float64, device="cuda")
     inl = torch.full((P,), -1, dtype=torch.int64, device="cuda")
     opts = _abi.LinOpts()
+    opts.kernel = kernel
     st = ctx.call("linearize_factors_noalloc", ctx.lib.glim_linearize_factors_noalloc, ctx.h, fr, len(frames), pr,
                   P, poses.ctypes.data_as(C.c_void_p), C.byref(opts), C.c_void_p(e.data_ptr()),
                   C.c_void_p(H.data_ptr()), C.c_void_p(b.data_ptr()), C.c_void_p(inl.data_ptr()))
@@ -59,14 +60,19 @@ def _call_noalloc(G, _abi, ctx, w, frames, maps, pairs):
     return e.cpu().numpy(), H.cpu().numpy(), b.cpu().numpy(), inl.cpu().numpy()
 
 
-def test_noalloc_matches_regular_entry_point_twice():
-    G, _abi, ctx, w, frames, maps = _setup()
+@pytest.mark.parametrize("layout", ["auto", "hash"])
+def test_noalloc_matches_regular_entry_point_twice(layout):
+    G, _abi, ctx, w, frames, maps = _setup(layout)
     ref = G.linearize(ctx, frames, maps, w.pairs, w.poses, out="cuda")
     ref = [x.cpu().numpy() for x in ref]
-    for _ in range(2):  # two calls in a row share (and overwrite) the static scratch
-        e, H, b, inl = _call_noalloc(G, _abi, ctx, w, frames, maps, w.pairs)
+    lane_kernel = 2 if layout == "auto" else 3
+    for kernel in (0, 0, 1, lane_kernel):  # two calls in a row share (and overwrite) the static scratch
+        e, H, b, inl = _call_noalloc(G, _abi, ctx, w, frames, maps, w.pairs, kernel=kernel)
         assert np.array_equal(inl, ref[3])
         assert _rel(e, ref[0]) <= TOL and _rel(H, ref[1]) <= TOL and _rel(b, ref[2]) <= TOL
+    other = 3 if layout == "auto" else 2  # the per-lane kernel of the other layout is refused
+    with pytest.raises(G.GlimError, match="EINVAL"):
+        _call_noalloc(G, _abi, ctx, w, frames, maps, w.pairs, kernel=other)
     # a different batch (fewer pairs) through the same scratch
     e, H, b, inl = _call_noalloc(G, _abi, ctx, w, frames, maps, w.pairs[3:5])
     assert np.array_equal(inl, ref[3][3:5])
