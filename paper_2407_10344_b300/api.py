@@ -225,23 +225,45 @@ class FrameData:
                           None if self.normal3 is None else self.normal3.data_ptr(), self.n)
 
 
+_FRAME_DTYPE = np.dtype([("pts4", "<u8"), ("cov6", "<u8"), ("normal3", "<u8"), ("n", "<i8")])  # glim_frame
+
+
 def _frames(frames):
-    arr = (_abi.Frame * max(len(frames), 1))()
-    for i, f in enumerate(frames):
-        arr[i] = f.c()
-    return arr
+    """A packed glim_frame array (one numpy record per frame) and a pointer to it."""
+    arr = np.zeros(max(len(frames), 1), dtype=_FRAME_DTYPE)
+    if frames:
+        arr[:len(frames)] = [(f.pts4.data_ptr(), f.cov6.data_ptr(), 0 if f.normal3 is None else f.normal3.data_ptr(),
+                              f.n) for f in frames]
+    ptr = arr.ctypes.data_as(C.POINTER(_abi.Frame))
+    ptr._keep = arr
+    return ptr
+
+
+_PAIR_DTYPE = np.dtype([("src_frame", "<i4"), ("tgt_frame", "<i4"), ("tgt", "<u8")])  # glim_pair
 
 
 def _pairs(pairs, vmaps):
-    """pairs: (P, 2) (source, target); vmaps: per frame VoxelMap or None (target frames)."""
+    """pairs: (P, 2) (source, target); vmaps: per frame VoxelMap or None (target frames).
+    Returns a pointer to a packed glim_pair array (built with numpy, not per pair) and P."""
     pairs = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
-    arr = (_abi.Pair * max(len(pairs), 1))()
-    for i, (s, t) in enumerate(pairs):
-        vm = vmaps[int(t)]
-        if vm is None:
-            raise ValueError(f"pair {i}: target frame {t} has no voxelmap")
-        arr[i] = _abi.Pair(int(s), int(t), vm.h.value)
-    return arr, len(pairs)
+    P = len(pairs)
+    handles = np.array([0 if vm is None else (vm.h.value or 0) for vm in vmaps], dtype=np.uint64)
+    arr = np.zeros(max(P, 1), dtype=_PAIR_DTYPE)
+    if P:
+        t = pairs[:, 1]
+        if ((t < 0) | (t >= len(vmaps))).any():
+            raise ValueError("pair target outside the frame list")
+        h = handles[t]
+        missing = np.flatnonzero(h == 0)
+        if len(missing):
+            i = int(missing[0])
+            raise ValueError(f"pair {i}: target frame {t[i]} has no voxelmap")
+        arr["src_frame"][:P] = pairs[:, 0]
+        arr["tgt_frame"][:P] = t
+        arr["tgt"][:P] = h
+    ptr = arr.ctypes.data_as(C.POINTER(_abi.Pair))
+    ptr._keep = arr  # the array lives as long as the pointer
+    return ptr, P
 
 
 KERNELS = {"auto": 0, "general": 1, "dense": 2, "hash": 3}

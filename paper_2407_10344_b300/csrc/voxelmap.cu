@@ -201,14 +201,48 @@ struct OverlapPair {
   PoseF pose;
 };
 
-__global__ void k_overlap(const OverlapPair* __restrict__ pairs, double* __restrict__ out) {
-  const OverlapPair P = pairs[blockIdx.x];
+// One block per pair; each thread takes OV_UNROLL points per step so that their point reads,
+// and then their voxel reads, are in flight together (a dense level reads only the 4-byte id).
+constexpr int OV_UNROLL = 4;
+
+__global__ void __launch_bounds__(256) k_overlap(const OverlapPair* __restrict__ pairs, double* __restrict__ out) {
+  const OverlapPair& P = pairs[blockIdx.x];
+  const int64_t n = P.n;
+  const float4* pts = P.pts;
+  const LevelDev L = P.lv;
+  float R[9], t[3];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) R[i] = P.pose.R[i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) t[i] = P.pose.t[i];
   int64_t hits = 0;
-  for (int64_t k = threadIdx.x; k < P.n; k += blockDim.x) {
-    const float4 m = ldg4(&P.pts[k]);
-    const float3 q = transform_pinned(P.pose.R, P.pose.t, m.x, m.y, m.z);
-    int kx, ky, kz, id;
-    if (level_key3(q, P.lv.inv_r, kx, ky, kz) && find_voxel(P.lv, kx, ky, kz, &id) >= 0) ++hits;
+  const int64_t step = int64_t(OV_UNROLL) * blockDim.x;
+  for (int64_t k0 = threadIdx.x; k0 < n; k0 += step) {
+    float4 m[OV_UNROLL];
+#pragma unroll
+    for (int u = 0; u < OV_UNROLL; ++u) {
+      const int64_t k = k0 + int64_t(u) * blockDim.x;
+      m[u] = k < n ? ldg4(&pts[k]) : make_float4(NAN, NAN, NAN, 1.f);
+    }
+    if (L.dense) {
+      int id[OV_UNROLL];
+#pragma unroll
+      for (int u = 0; u < OV_UNROLL; ++u) {
+        const float3 q = transform_pinned(R, t, m[u].x, m[u].y, m[u].z);
+        int kx, ky, kz;
+        const int64_t c = level_key3(q, L.inv_r, kx, ky, kz) ? dense_cell(L, kx, ky, kz) : -1;
+        id[u] = c >= 0 ? __ldg(reinterpret_cast<const int*>(&L.slots[c].w0)) : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < OV_UNROLL; ++u) hits += id[u] >= 0 ? 1 : 0;
+    } else {
+#pragma unroll
+      for (int u = 0; u < OV_UNROLL; ++u) {
+        const float3 q = transform_pinned(R, t, m[u].x, m[u].y, m[u].z);
+        int kx, ky, kz, id;
+        if (level_key3(q, L.inv_r, kx, ky, kz) && find_voxel(L, kx, ky, kz, &id) >= 0) ++hits;
+      }
+    }
   }
   __shared__ unsigned long long s[8];
   unsigned long long h = __reduce_add_sync(0xffffffffu, unsigned(hits));
