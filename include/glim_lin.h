@@ -231,7 +231,8 @@ glim_status glim_overlap(glim_ctx* ctx, const glim_frame* frames, int32_t nframe
  * "Implementation"): frames (host array of nframes descriptors), pairs (host array),
  * poses12 (host, nframes x 12 doubles).  Outputs e_out (npairs), H_out (npairs x 144,
  * row-major 12 x 12), b_out (npairs x 12), inliers_out (npairs, number of (point, level)
- * correspondences; may be NULL) are all host or all device arrays; with host outputs the
+ * terms that entered the sums: correspondences whose S = C~ + R C R^T is positive definite;
+ * may be NULL) are all host or all device arrays; with host outputs the
  * call synchronizes.  Builds a temporary plan; repeated linearizations of the same batch
  * should use glim_plan_*. */
 glim_status glim_linearize_factors(glim_ctx* ctx, const glim_frame* frames, int32_t nframes,

@@ -77,18 +77,18 @@ __device__ __forceinline__ PointIn load_point(const FrameDev& F, int64_t k) {
   return p;
 }
 
-// Phase 2 of one term record {S'00, S'01, S'02, S'11} {S'12, S'22, d.x, d.y} {d.z, u.x, u.y, u.z}:
-// w Omega = adj(S')/det(S'), y = w Omega d, e = d^T y, and the G-form contribution
-// [G^T (w Omega) G, G^T y, e] with G = [-(u)x, I].  A term whose S' is not positive definite
-// contributes nothing.
+// Phase 2 of one term record {S00, S01, S02, S11} {S12, S22, d.x, d.y} {d.z, u.x, u.y, u.z} of a
+// point of weight w: w Omega = w adj(S)/det(S), y = w Omega d, e = d^T y, and the G-form
+// contribution [G^T (w Omega) G, G^T y, e] with G = [-(u)x, I].  A term whose S is not positive
+// definite contributes nothing and is no inlier (the return value is false).
 template <class A>
-__device__ __forceinline__ void accumulate_term(const float4 t0, const float4 t1, const float4 t2, A& acc) {
-  const float a = t0.x, b = t0.y, c = t0.z, d = t0.w, e = t1.x, f = t1.y;  // S'
+__device__ __forceinline__ bool accumulate_term(const float4 t0, const float4 t1, const float4 t2, float w, A& acc) {
+  const float a = t0.x, b = t0.y, c = t0.z, d = t0.w, e = t1.x, f = t1.y;  // S
   const float A00 = d * f - e * e, A01 = c * e - b * f, A02 = b * e - c * d;
   const float A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
   const float det = a * A00 + b * A01 + c * A02;
-  if (!(det > 0.f) || !(det < INFINITY)) return;
-  const float id = __fdividef(1.0f, det);
+  if (!(det > 0.f) || !(det < INFINITY)) return false;
+  const float id = __fdividef(w, det);
   const float o00 = A00 * id, o01 = A01 * id, o02 = A02 * id, o11 = A11 * id, o12 = A12 * id, o22 = A22 * id;
   const float dx = t1.z, dy = t1.w, dz = t2.x;
   const float g0 = o00 * dx + o01 * dy + o02 * dz;  // w Omega d
@@ -118,17 +118,18 @@ __device__ __forceinline__ void accumulate_term(const float4 t0, const float4 t1
   acc.add2(23, ux, g1, -uy, g0);
   acc.add(24, g0); acc.add(25, g1); acc.add(26, g2);
   acc.add(27, dx * g0 + dy * g1 + dz * g2);  // w d^T Omega d
+  return true;
 }
 
 // Per-warp staging of one round: the compacted list of (point, level) hits.  A term record is
-// three float4 (48 bytes), self-contained, so phase 2 reads only its own record and lanes
-// reading consecutive records touch distinct banks:
-//   {S'00, S'01, S'02, S'11} {S'12, S'22, d.x, d.y} {d.z, u.x, u.y, u.z}
-// with S' = (C~ + R C R^T) / w, d = mu~ - q, u = R mu.  Dividing S by the point weight w > 0
-// makes adj(S')/det(S') = w Omega, so every later product already carries the weight.
+// three float4 (48 bytes) and the point's weight, self-contained, so phase 2 reads only its
+// own record and lanes reading consecutive records touch distinct banks:
+//   {S00, S01, S02, S11} {S12, S22, d.x, d.y} {d.z, u.x, u.y, u.z},  w
+// with S = C~ + R C R^T, d = mu~ - q, u = R mu.
 template <int LMAX>
 struct WarpStage {
   float4 term[32 * LMAX * 3];
+  float w[32 * LMAX];
 };
 
 // One round for the warp.  Phase 1 (every lane, its own point): transform, keys and one read
@@ -137,7 +138,7 @@ struct WarpStage {
 // lane order within a level).  Phase 2 (the lanes share the term list): per hit
 // w Omega = adj(S')/det(S'), y = w Omega d, e = d^T y, and the G-form contribution
 // [G^T (w Omega) G, G^T y, e] with G = [-(u)x, I].  Misses and discarded points cost no
-// phase-2 lanes.  Points must have positive weights (a zero weight contributes nothing).
+// phase-2 lanes.
 template <int LMAX, class A>
 __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in, bool live, int64_t k, int validate,
                                            WarpStage<LMAX>& ws, A& acc, int& inl) {
@@ -210,8 +211,8 @@ __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in,
     }
     nh += hit[l] ? 1 : 0;
   }
-  // R C R^T / w and u, for the records of this lane's hits
-  float r00 = 0.f, r01 = 0.f, r02 = 0.f, r11 = 0.f, r12 = 0.f, r22 = 0.f, iw = 0.f;
+  // R C R^T and u, for the records of this lane's hits
+  float r00 = 0.f, r01 = 0.f, r02 = 0.f, r11 = 0.f, r12 = 0.f, r22 = 0.f;
   if (nh > 0) {
     const float c00 = in.ca.x, c01 = in.ca.y, c02 = in.cb.x, c11 = in.cb.y, c12 = in.cc.x, c22 = in.cc.y;
     const float w00 = R[0] * c00 + R[1] * c01 + R[2] * c02;
@@ -229,8 +230,6 @@ __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in,
     r11 = w10 * R[3] + w11 * R[4] + w12 * R[5];
     r12 = w10 * R[6] + w11 * R[7] + w12 * R[8];
     r22 = w20 * R[6] + w21 * R[7] + w22 * R[8];
-    iw = __fdividef(1.0f, m.w);
-    inl += nh;
   }
   const float ux = q.x - P.t[0], uy = q.y - P.t[1], uz = q.z - P.t[2];
   // compaction of the hits: level-major, lane order within a level
@@ -239,16 +238,19 @@ __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in,
   for (int l = 0; l < LMAX; ++l) {
     const unsigned mask = __ballot_sync(0xffffffffu, hit[l]);
     if (hit[l]) {
-      float4* t = ws.term + (base + __popc(mask & lt)) * 3;
+      const int slot = base + __popc(mask & lt);
+      float4* t = ws.term + slot * 3;
       // voxel record: s0 = {., ., ., C~22}, s1 = {mean, C~00}, s2 = {C~01, C~02, C~11, C~12}
-      t[0] = make_float4((s1[l].w + r00) * iw, (s2[l].x + r01) * iw, (s2[l].y + r02) * iw, (s2[l].z + r11) * iw);
-      t[1] = make_float4((s2[l].w + r12) * iw, (s0[l].w + r22) * iw, s1[l].x - q.x, s1[l].y - q.y);
+      t[0] = make_float4(s1[l].w + r00, s2[l].x + r01, s2[l].y + r02, s2[l].z + r11);
+      t[1] = make_float4(s2[l].w + r12, s0[l].w + r22, s1[l].x - q.x, s1[l].y - q.y);
       t[2] = make_float4(s1[l].z - q.z, ux, uy, uz);
+      ws.w[slot] = m.w;
     }
     base += __popc(mask);
   }
   __syncwarp();
-  for (int i = lane; i < base; i += 32) accumulate_term(ws.term[3 * i], ws.term[3 * i + 1], ws.term[3 * i + 2], acc);
+  for (int i = lane; i < base; i += 32)
+    inl += accumulate_term(ws.term[3 * i], ws.term[3 * i + 1], ws.term[3 * i + 2], ws.w[i], acc) ? 1 : 0;
   __syncwarp();  // the stage is rewritten by the next round
 }
 
@@ -421,8 +423,8 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize(const LinArgs 
 // its tile's last point and is masked.  Because G = [-(u)x, I] is the same for all levels of
 // a point, the lane sums w Omega, w Omega d and e over the levels (a miss, or a term whose S
 // is not positive definite, adds exact zeros) and adds the G-form of the sums once: 28
-// accumulator updates per point instead of per hit.  The weight enters as w adj(S)/det(S)
-// (the general kernel divides S by w instead); results agree up to FP32 rounding.
+// accumulator updates per point instead of per hit.  The weight enters as w adj(S)/det(S),
+// as in the general kernel; results agree up to FP32 rounding.
 
 template <class MapT>
 struct LaneView {  // per-item constants, written by thread 0
@@ -521,7 +523,6 @@ __device__ __forceinline__ void lane_point(const LaneView<typename std::conditio
   // hits (after R C R^T, which overlaps the reads' latency)
   bool hit[LMAX];
   float vc22[LMAX];  // C~22 of the level's voxel
-  int nh = 0;
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
     if constexpr (HASH) {
@@ -558,9 +559,7 @@ __device__ __forceinline__ void lane_point(const LaneView<typename std::conditio
       hit[l] = __float_as_int(s0[l].x) >= 0;  // occupied cell (empty records hold 0x80808080)
       vc22[l] = s0[l].y;
     }
-    nh += hit[l] ? 1 : 0;
   }
-  inl += nh;
   // per level: S = C~ + R C R^T, w Omega = w adj(S) / det(S), y = w Omega d, and the sums over
   // levels (a term that is a miss or not positive definite adds zeros).  Skipping a level
   // (or the whole point) when no lane of the warp hits it was measured slower: the vote has
@@ -576,6 +575,7 @@ __device__ __forceinline__ void lane_point(const LaneView<typename std::conditio
     const float A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
     const float det = a * A00 + b * A01 + c * A02;
     const bool ok = hit[l] && det > 0.f && det < INFINITY;
+    inl += ok ? 1 : 0;  // inliers: the terms that enter the sums
     const float id = __fdividef(w, det);
     // selected, not multiplied by 0: adj(S) of a masked term need not be finite
     const float o00 = ok ? A00 * id : 0.f, o01 = ok ? A01 * id : 0.f, o02 = ok ? A02 * id : 0.f;

@@ -245,6 +245,40 @@ def test_dense_grid_kernel_and_general_kernel(G, ctx, room, kernel, validate):
     assert plan.opts()["kernel"] == "dense"
 
 
+@pytest.mark.parametrize("kernel", ["dense", "general"])
+def test_degenerate_covariances_and_zero_weights(G, ctx, room, kernel):
+    """Degenerate cases of the cost: source points whose covariance is zero, so that S = C~ +
+    R C R^T is singular wherever the voxel covariance is zero too (the term is skipped, the
+    hit still counts), voxels with zero covariance, and points of weight zero (they add
+    nothing and still count), against the oracle."""
+    dev = torch.device("cuda")
+    src, tgt = room.gframes[0], room.gframes[1]
+    n = src.n
+    sel = torch.arange(n, device=dev)
+    cov_s = src.cov6.clone()
+    cov_s[sel % 7 == 0] = 0.0                      # zero source covariances
+    p4 = src.pts4.clone()
+    p4[sel % 11 == 0, 3] = 0.0                     # zero weights
+    p4[sel % 13 == 0, 3] = 2.5                     # and some non-unit ones
+    cov_t = tgt.cov6.clone()
+    cov_t[torch.arange(tgt.n, device=dev) % 5 == 0] = 0.0   # zero covariances in some voxels' means
+    frames = [G.FrameData(p4, cov_s), G.FrameData(tgt.pts4, cov_t)]
+    vm = G.VoxelMap(ctx, tgt.pts4, cov_t, room.w.resolutions)
+    oframes = [O.Frame(p4.cpu().numpy(), cov_s.cpu().numpy()), O.Frame(tgt.pts4.cpu().numpy(), cov_t.cpu().numpy())]
+    om = O.VMap(oframes[1].pts4, oframes[1].cov6, room.w.resolutions)
+    ref = O.linearize(oframes, [None, om], room.w.pairs, room.w.poses, want_comp=True)
+    _check(G.linearize(ctx, frames, [None, vm], room.w.pairs, room.w.poses, kernel=kernel), ref)
+    # every source covariance and every voxel covariance zero: every S is singular, every term
+    # is skipped (and is no inlier), although the correspondences exist
+    z = G.FrameData(p4, torch.zeros_like(cov_s))
+    vz = G.VoxelMap(ctx, tgt.pts4, torch.zeros_like(cov_t), room.w.resolutions)
+    e, H, b, inl = G.linearize(ctx, [z, G.FrameData(tgt.pts4, torch.zeros_like(cov_t))], [None, vz], room.w.pairs,
+                               room.w.poses, kernel=kernel)
+    assert inl[0] == 0 and e[0] == 0.0 and not np.any(H) and not np.any(b)
+    ids = G.correspondences(ctx, z, vz, room.w.poses[0], room.w.poses[1]).cpu().numpy()
+    assert (ids >= 0).sum() > 0
+
+
 def test_plan_linearize_pinned_views(G, ctx, corridor):
     """The zero-copy form returns the same numbers as the copying form, as read-only views
     of the plan's pinned block that the next launch overwrites."""
