@@ -249,8 +249,8 @@ def test_dense_grid_kernel_and_general_kernel(G, ctx, room, kernel, validate):
 def test_degenerate_covariances_and_zero_weights(G, ctx, room, kernel):
     """Degenerate cases of the cost: source points whose covariance is zero, so that S = C~ +
     R C R^T is singular wherever the voxel covariance is zero too (the term is skipped, the
-    hit still counts), voxels with zero covariance, and points of weight zero (they add
-    nothing and still count), against the oracle."""
+    hit is no inlier), voxels with zero covariance, points of weight zero (they add nothing
+    and still count) and of negative weight, against the oracle."""
     dev = torch.device("cuda")
     src, tgt = room.gframes[0], room.gframes[1]
     n = src.n
@@ -259,7 +259,8 @@ def test_degenerate_covariances_and_zero_weights(G, ctx, room, kernel):
     cov_s[sel % 7 == 0] = 0.0                      # zero source covariances
     p4 = src.pts4.clone()
     p4[sel % 11 == 0, 3] = 0.0                     # zero weights
-    p4[sel % 13 == 0, 3] = 2.5                     # and some non-unit ones
+    p4[sel % 13 == 0, 3] = 2.5                     # some non-unit ones
+    p4[sel % 17 == 0, 3] = -0.5                    # and negative ones (the sums take w as given)
     cov_t = tgt.cov6.clone()
     cov_t[torch.arange(tgt.n, device=dev) % 5 == 0] = 0.0   # zero covariances in some voxels' means
     frames = [G.FrameData(p4, cov_s), G.FrameData(tgt.pts4, cov_t)]
