@@ -409,9 +409,11 @@ def test_covariances_small_cloud_bruteforce_path(G, ctx):
 
 # ---------------------------------------------------------------------------- gradient
 @pytest.mark.parametrize("full", [False, True])
-def test_backward_matches_oracle_gradient(G, ctx, full):
+@pytest.mark.parametrize("layout", ["auto", "hash"])
+def test_backward_matches_oracle_gradient(G, ctx, full, layout):
     from gpu_helpers import Prepared
-    P = Prepared(ctx, synth.corridor(n_cur=4000, kf_range=(3000, 5000), n_kf=3, weights=True))
+    P = Prepared(ctx, synth.corridor(n_cur=4000, kf_range=(3000, 5000), n_kf=3, weights=True), layout=layout)
+    assert all(P.gmaps[t].is_dense(0) == (layout == "auto") for t in set(int(t) for t in P.w.pairs[:, 1]))
     w = P.w
     dxi, dmu, dw = G.backward(ctx, P.gframes, P.gmaps, w.pairs, w.poses, omega_grad_full=full)
     odxi, odmu, odw = O.gradient(P.oframes, P.omaps, w.pairs, w.poses, omega_grad_full=full)
