@@ -65,6 +65,12 @@ def make_workload(args, rank):
         return synth.urban(seed=3 + 1000 * rank, n_submaps=args.submaps, keep=args.keep)
     if args.workload == "corridor":
         return synth.corridor(seed=2 + 1000 * rank)
+    if args.workload == "corridor_weights":
+        return synth.corridor(seed=2 + 1000 * rank, weights=True)
+    if args.workload == "box":
+        return synth.box_room(seed=1 + 1000 * rank)
+    if args.workload == "terrain":
+        return synth.terrain(seed=5 + 1000 * rank)
     raise ValueError(args.workload)
 
 
@@ -73,7 +79,12 @@ def workload_desc(w, args):
         sub = f" (first {len(w.points)} of a {args.submaps}-submap trajectory)" if args.keep else ""
         return (f"urban global step: {len(w.points)} submaps of log-U[50k,200k] pts{sub}, {len(w.pairs)} pairs "
                 f"(10 nearest), voxels 0.5/1/2 m")
-    return "corridor odometry window: 30k-pt frame vs 10 keyframes of 15k-40k pts, 0.5 m voxels"
+    if args.workload == "box":
+        return "box room 10 x 8 x 3 m: 5k-pt scan vs 20k-pt map, 1 m voxels, one unary factor"
+    if args.workload == "terrain":
+        return "terrain: 1M-pt scan vs 20M-pt map, 0.25 m voxels, one unary factor"
+    extra = ", per-point weights U[0.5, 1.5], forward + backward" if args.workload == "corridor_weights" else ""
+    return "corridor odometry window: 30k-pt frame vs 10 keyframes of 15k-40k pts, 0.5 m voxels" + extra
 
 
 # ---------------------------------------------------------------------------- clocks
@@ -330,7 +341,7 @@ def run_ours(args):
     targets = set(int(t) for t in w.pairs[:, 1])
     cov_s = build_s = 0.0
     for i, p in enumerate(w.points):
-        p4 = G.to_pts4(p, device=dev)
+        p4 = G.to_pts4(p, w.weights[i] if w.weights else None, device=dev)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cov, nrm = G.estimate_covariances(ctx, p4, k=10)
@@ -439,6 +450,20 @@ def run_ours(args):
     plan_h.close()
     del plan_h, hmaps
     torch.cuda.synchronize()
+    # per-point weights: the backward pass of the same batch (dE/dxi, dE/dmu, dE/dw)
+    backward_line = None
+    if w.weights:
+        plan_b = G.Plan(ctx, frames, maps, w.pairs, accum_mode=acc, block=256, pts_per_thread=1)
+        for _ in range(3):
+            plan_b.backward(w.poses)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(10):
+            plan_b.backward(w.poses)
+        torch.cuda.synchronize()
+        backward_line = {"ms_per_call": (time.perf_counter() - t0) / 10 * 1e3,
+                         "note": "glim_plan_backward with Omega differentiated through R, host poses in"}
+        plan_b.close()
     pk = peaks()
     hbm_peak = pk.get("hbm_gbs", 6400.0)
     kavg_ms = float(np.mean(kern_ms))
@@ -462,7 +487,7 @@ def run_ours(args):
                    "generation_s": round(gen_s, 1)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
-                     "traffic": None if DRAM_BYTES_PER_PAIR_POINT is None else DRAM_BYTES_PER_PAIR_POINT * n_pp,
+                     "traffic": DRAM_BYTES_PER_PAIR_POINT * n_pp if args.workload == "urban" else None,
                      "traffic_note": "ncu dram bytes of a 40-submap capture scaled by (pair, point) units",
                      "kernel": kernel_name + " (persistent work queue)", "kernel_ms": kavg_ms,
                      "algorithmic_bytes_per_launch": BYTES_PER_POINT * n_pp,
@@ -471,6 +496,7 @@ def run_ours(args):
                           "peak": fp32_nominal, "frac": flops / (kavg_ms / 1e3) / 1e12 / fp32_nominal,
                           "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % (ctx.num_sms, sm_max),
                           "fma_chain_measured_tflops": fma_peak,
+                          "fp64_fma_chain_measured_tflops": ctx.fp64_fma_peak(),
                           "frac_of_measured": flops / (kavg_ms / 1e3) / 1e12 / fma_peak,
                           "algorithmic_flops_per_launch": flops, "hit_terms_per_launch": hits,
                           "note": "the kernel is bound by instruction issue (64 % of its instructions are FP32 arithmetic), not DRAM"},
@@ -481,6 +507,7 @@ def run_ours(args):
         "plain": {"ms_per_batch": plain_ms, "batched_ms_per_batch": batched_ms,
                   "speedup": plain_ms / batched_ms if batched_ms > 0 else None},
         "hash_layout": hash_line,
+        "backward": backward_line,
         "random_point_order": None if random_ms is None else {
             "kernel_ms": random_ms, "value": n_pp / (random_ms / 1e3), "unit": UNIT},
         "preprocessing": {
@@ -531,7 +558,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="urban", choices=["urban", "corridor"])
+    ap.add_argument("--workload", default="urban", choices=["urban", "corridor", "corridor_weights", "box", "terrain"],
+                    help="urban: the global step (default); the others are the smaller batches, for profiling")
     ap.add_argument("--submaps", type=int, default=400)
     ap.add_argument("--keep", type=int, default=None, help="keep only the first N submaps (profiling cases)")
     ap.add_argument("--accum", default="fp64", choices=["fp32", "kahan", "fp64"])

@@ -133,6 +133,10 @@ int64_t glim_kernel_launches(const glim_ctx* ctx);
  * per SM, `iters` x 128 FMAs per thread, best of three timed launches after a warm-up.  The
  * denominator of the FP32 roofline of the linearization kernel.  Synchronizes the stream. */
 glim_status glim_fp32_fma_peak(glim_ctx* ctx, int32_t iters, double* tflops_out);
+/* The same measurement with FP64 chains (`__fma_rn` on doubles): the device's FP64 FMA rate
+ * in TFLOP/s.  B300's FP64 rate is a small fraction of its FP32 rate, so `iters` should be
+ * correspondingly smaller.  Synchronizes the stream.  GLIM_EINVAL if iters < 1. */
+glim_status glim_fp64_fma_peak(glim_ctx* ctx, int32_t iters, double* tflops_out);
 
 /* ---------------------------------------------------------------- covariances */
 

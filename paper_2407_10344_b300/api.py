@@ -98,6 +98,12 @@ class Context:
         self.call("fp32_fma_peak", self.lib.glim_fp32_fma_peak, self.h, int(iters), C.byref(out))
         return out.value
 
+    def fp64_fma_peak(self, iters=128):
+        """Measured FP64 FMA throughput of the device in TFLOP/s (the same FMA-chain kernel)."""
+        out = C.c_double()
+        self.call("fp64_fma_peak", self.lib.glim_fp64_fma_peak, self.h, int(iters), C.byref(out))
+        return out.value
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.glim_destroy(self.h)

@@ -449,6 +449,15 @@ def test_gauss_newton_recovers_pose(G, ctx):
     D = O.compose(O.inverse(P.w.poses_true[0]), poses[0])
     ang = math.degrees(math.acos(min(1.0, (np.trace(D[:, :3]) - 1) / 2)))
     assert ang < 0.05 and np.linalg.norm(D[:, 3]) < 0.005
+    # parity at the optimum, where b is the difference of large cancelling terms: the b error
+    # is taken against the cancellation-free scale sum |w J^T Omega d|
+    from gpu_helpers import rel_errors
+    e, H, b, inl = plan.linearize(poses)
+    ref = O.linearize(P.oframes, P.omaps, P.w.pairs, poses, want_comp=True)
+    assert np.linalg.norm(ref["b"][:, :6]) < 1e-2 * ref["b_scale"].max()
+    ee, eH, eb = rel_errors(e, H, b, ref)
+    assert (np.asarray(inl) == ref["inliers"]).all()
+    assert ee.max() <= TOL and eH.max() <= TOL and eb.max() <= TOL, (ee.max(), eH.max(), eb.max())
 
 
 # ---------------------------------------------------------------------------- overlap
@@ -673,3 +682,24 @@ def test_local_mapping_all_to_all_converges(G, ctx):
                       O.compose(O.inverse(poses[kf[0]]), poses[f]))
         ang = math.degrees(math.acos(min(1.0, (np.trace(D[:, :3]) - 1) / 2)))
         assert ang < 0.05 and np.linalg.norm(D[:, 3]) < 0.01, (f, ang, np.linalg.norm(D[:, 3]))
+    # every factor of the converged graph agrees with the oracle at the final poses
+    from gpu_helpers import rel_errors
+    e, H, b, inl = plan.linearize(poses)
+    ref = O.linearize(P.oframes, P.omaps, pairs, poses, want_comp=True)
+    ee, eH, eb = rel_errors(e, H, b, ref)
+    assert (np.asarray(inl) == ref["inliers"]).all()
+    assert ee.max() <= TOL and eH.max() <= TOL and eb.max() <= TOL, (ee.max(), eH.max(), eb.max())
+
+
+# ---------------------------------------------------------------------------- FMA rates
+def test_fma_peaks_are_plausible(G, ctx):
+    """The FMA-chain kernels give the FP32 roofline's denominator and the FP64 rate: both
+    positive and below the nominal rate of the device (128 FP32 lanes per SM at the maximum
+    clock), FP64 far below FP32."""
+    fp32 = ctx.fp32_fma_peak(iters=1024)
+    fp64 = ctx.fp64_fma_peak(iters=16)
+    nominal = ctx.num_sms * 128 * 2 * 2.1e9 / 1e12
+    assert 0.3 * nominal < fp32 <= 1.02 * nominal, (fp32, nominal)
+    assert 0.0 < fp64 < 0.5 * fp32, (fp64, fp32)
+    with pytest.raises(G.GlimError, match="EINVAL"):
+        ctx.fp64_fma_peak(iters=0)
