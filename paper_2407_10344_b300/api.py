@@ -6,7 +6,9 @@ dtypes, passes pointers and reports errors.  There is no CPU path.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
+import weakref
 
 import numpy as np
 import torch
@@ -49,6 +51,24 @@ def _poses(poses, nframes=None):
     return P
 
 
+# Library objects still open at interpreter exit are released by an exit hook, plans and
+# maps before the contexts they use: the interpreter's own teardown destroys objects in no
+# fixed order, and it may do so after CUDA has started to shut down.
+_LIVE = {"plans": weakref.WeakSet(), "maps": weakref.WeakSet(), "contexts": weakref.WeakSet()}
+
+
+def _release_all():
+    for kind, method in (("plans", "close"), ("maps", "free"), ("contexts", "close")):
+        for obj in list(_LIVE[kind]):
+            try:
+                getattr(obj, method)()
+            except Exception:
+                pass
+
+
+atexit.register(_release_all)
+
+
 class Context:
     """A library context on one CUDA device, enqueuing on a torch stream."""
 
@@ -65,6 +85,7 @@ class Context:
         if st != 0:
             raise GlimError(st, "glim_create failed")
         self.h = h
+        _LIVE["contexts"].add(self)
 
     def check(self, st, what):
         if st != 0:
@@ -164,6 +185,7 @@ class VoxelMap:
         ctx.call("build_voxelmap", ctx.lib.glim_build_voxelmap_ex, ctx.h, _ptr(pts4), _ptr(cov6), pts4.shape[0],
                  _ptr(res), len(res), lay, C.byref(h))
         self.h = h
+        _LIVE["maps"].add(self)
 
     @property
     def levels(self):
@@ -329,6 +351,7 @@ class Plan:
         h = C.c_void_p()
         ctx.call("plan_create", ctx.lib.glim_plan_create, ctx.h, fr, self.nframes, pr, P, C.byref(o), C.byref(h))
         self.h = h
+        _LIVE["plans"].add(self)
         self._host = _outputs(P, "host")
 
     def linearize(self, poses, out=None, copy=True):

@@ -703,3 +703,27 @@ def test_fma_peaks_are_plausible(G, ctx):
     assert 0.0 < fp64 < 0.5 * fp32, (fp64, fp32)
     with pytest.raises(G.GlimError, match="EINVAL"):
         ctx.fp64_fma_peak(iters=0)
+
+
+def test_process_exit_with_open_objects():
+    """A script that ends with a context, voxelmaps and a plan (with pinned output views)
+    still open exits cleanly: the binding releases them before the interpreter tears down."""
+    import subprocess
+    import sys
+    import os
+    code = (
+        "import numpy as np, torch, synth\n"
+        "import paper_2407_10344_b300 as G\n"
+        "from gpu_helpers import Prepared\n"
+        "ctx = G.Context(0)\n"
+        "P = Prepared(ctx, synth.box_room())\n"
+        "plan = G.Plan(ctx, P.gframes, P.gmaps, P.w.pairs)\n"
+        "e, H, b, inl = plan.linearize(P.w.poses, copy=False)\n"
+        "print(float(e[0]) > 0)\n"
+    )
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PYTHONPATH=os.pathsep.join([root, os.path.join(root, "tests")]))
+    r = subprocess.run([sys.executable, "-X", "faulthandler", "-c", code], cwd=root, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
+    assert r.stdout.strip().endswith("True")
