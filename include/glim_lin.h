@@ -275,9 +275,12 @@ glim_status glim_linearize_factors_noalloc(glim_ctx* ctx, const glim_frame* fram
                                            int64_t* inliers_out);
 
 /* A plan fixes a batch (frames, pairs, options) and owns its device work list, partial-sum
- * slots, a pinned serialized input block (relative poses) and output block (e, H, b,
- * inliers), and a CUDA graph of [upload, queue reset, linearize, reduce, download].  The
- * frames and voxelmaps must stay alive and unchanged while the plan exists. */
+ * slots, a pinned staging block for the frame poses (nframes x 12 doubles, the only pose data
+ * uploaded), the device pose block that a packing kernel forms from them (per pair T_rel =
+ * T_t^-1 T_s in FP64, its FP32 rounding and the target viewpoint; the same bits as the host
+ * arithmetic of the one-shot calls), a pinned output block (e, H, b, inliers), and a CUDA
+ * graph of [upload, pose packing, queue reset, linearize, reduce, download].  The frames and
+ * voxelmaps must stay alive and unchanged while the plan exists. */
 glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames, int32_t nframes,
                              const glim_pair* pairs, int32_t npairs, const glim_lin_opts* opts,
                              glim_plan** out);
@@ -291,12 +294,17 @@ glim_status glim_plan_linearize(glim_plan* plan, const double* poses12, double* 
  * doubles, inliers: npairs int64), valid until the plan's next launch or destruction. */
 glim_status glim_plan_linearize_pinned(glim_plan* plan, const double* poses12, const double** e,
                                        const double** H, const double** b, const int64_t** inliers);
-/* Device-resident use: glim_plan_set_poses uploads the serialized pose block (async);
+/* Device-resident use: glim_plan_set_poses uploads the frame poses and packs the pairs'
+ * relative poses on the device (async);
  * glim_plan_launch enqueues queue reset, linearize and reduce (no copies, no sync) and
  * leaves the results in the plan's device output block, whose arrays
  * glim_plan_device_outputs returns (e: npairs doubles, H: npairs x 144, b: npairs x 12,
  * inliers: npairs int64). */
 glim_status glim_plan_set_poses(glim_plan* plan, const double* poses12);
+/* Copy the plan's current device pose block to the host (synchronizes): rt64_out (npairs x 12
+ * doubles, [R row-major | t] of T_rel) and pose32_out (npairs x 16 floats: R, t, v, 0), either
+ * may be NULL.  For inspection and tests of the pose packing. */
+glim_status glim_plan_relative_poses(glim_plan* plan, double* rt64_out, float* pose32_out);
 glim_status glim_plan_launch(glim_plan* plan);
 glim_status glim_plan_device_outputs(glim_plan* plan, double** e, double** H, double** b,
                                      int64_t** inliers);

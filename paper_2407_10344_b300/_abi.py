@@ -64,6 +64,7 @@ SIGNATURES = {
     "glim_plan_destroy": (None, [_vp]),
     "glim_plan_linearize": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "glim_plan_set_poses": (_i32, [_vp, _vp]),
+    "glim_plan_relative_poses": (_i32, [_vp, _vp, _vp]),
     "glim_plan_launch": (_i32, [_vp]),
     "glim_plan_device_outputs": (_i32, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp)]),
     "glim_plan_kernels_per_launch": (_i32, [_vp]),

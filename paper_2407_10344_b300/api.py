@@ -375,6 +375,17 @@ class Plan:
         self.ctx.call("plan_linearize", self.ctx.lib.glim_plan_linearize, self.h, _ptr(Pz), _ptr(e), _ptr(H), _ptr(b), _ptr(inl))
         return e, H, b, inl
 
+    def relative_poses(self):
+        """The plan's current device pose block: (npairs, 3, 4) FP64 T_rel and (npairs, 16) FP32
+        (R, t, target viewpoint, 0), as the kernels read them."""
+        rt = np.empty((self.npairs, 12), np.float64)
+        p32 = np.empty((self.npairs, 16), np.float32)
+        self.ctx.call("plan_relative_poses", self.ctx.lib.glim_plan_relative_poses, self.h, _ptr(rt), _ptr(p32))
+        T = np.empty((self.npairs, 3, 4), np.float64)
+        T[:, :, :3] = rt[:, :9].reshape(-1, 3, 3)
+        T[:, :, 3] = rt[:, 9:]
+        return T, p32
+
     def set_poses(self, poses):
         Pz = _poses(poses, self.nframes)
         self.ctx.call("plan_set_poses", self.ctx.lib.glim_plan_set_poses, self.h, _ptr(Pz))

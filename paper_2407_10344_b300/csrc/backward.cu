@@ -323,9 +323,7 @@ extern "C" glim_status glim_backward(glim_ctx* ctx, const glim_frame* frames, in
   BwdScratch sc;
   st = bwd_prepare(p, sc);
   if (st == GLIM_OK) {
-    plan_pack_poses(p, poses12);
-    if (cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
-      st = set_error(ctx, GLIM_ECUDA, "backward: upload failed");
+    st = plan_upload_poses(p, poses12);
   }
   if (st == GLIM_OK) st = bwd_run(p, sc, omega_grad_full, validate_surface, dxi_out, dmu_out, dw_out);
   cudaStreamSynchronize(ctx->stream);
@@ -353,7 +351,7 @@ extern "C" glim_status glim_plan_backward(glim_plan* p, const double* poses12, i
     }
     p->bwd = sc;
   }
-  plan_pack_poses(p, poses12);
-  GLIM_CUDA(ctx, cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream));
+  const glim_status st = plan_upload_poses(p, poses12);
+  if (st != GLIM_OK) return st;
   return bwd_run(p, *p->bwd, omega_grad_full, p->opts.validate_surface, dxi_out, dmu_out, dw_out);
 }

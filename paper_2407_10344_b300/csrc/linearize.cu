@@ -343,15 +343,59 @@ bool plan_maps_current(const glim_plan* p) {
   return true;
 }
 
-void plan_pack_poses(glim_plan* p, const double* poses12) {
-  PoseF* pf = reinterpret_cast<PoseF*>(p->h_in);
-  double* pd = reinterpret_cast<double*>(reinterpret_cast<char*>(p->h_in) + sizeof(PoseF) * p->npairs);
-  for (int q = 0; q < p->npairs; ++q) {
-    const RelPose T = relative_pose(poses12 + 12 * p->pairs[q].src_frame, poses12 + 12 * p->pairs[q].tgt_frame);
-    pf[q] = pose_to_f32(T);
-    std::memcpy(pd + 12 * q, T.R, 9 * sizeof(double));
-    std::memcpy(pd + 12 * q + 9, T.t, 3 * sizeof(double));
+namespace {
+
+// S0 on the device: T_rel = T_t^-1 T_s in FP64 for every pair, its FP32 rounding and the
+// target viewpoint v = -R^T t.  Every product and sum is rounded on its own, in the order of
+// the host helpers relative_pose / pose_to_f32 (no fused multiply-add), so the results are
+// the same bits as the host's.
+__global__ void k_pack_poses(const double* __restrict__ fposes, const int2* __restrict__ pair_frames, int npairs,
+                             PoseF* __restrict__ pose32, double* __restrict__ pose64) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= npairs) return;
+  const int2 f = pair_frames[q];
+  const double* s = fposes + 12 * int64_t(f.x);
+  const double* t = fposes + 12 * int64_t(f.y);
+  double R[9], tr[3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < 3; ++k) v = __dadd_rn(v, __dmul_rn(t[4 * k + i], s[4 * k + j]));
+      R[3 * i + j] = v;
+    }
+  const double dt[3] = {__dsub_rn(s[3], t[3]), __dsub_rn(s[7], t[7]), __dsub_rn(s[11], t[11])};
+  for (int i = 0; i < 3; ++i)
+    tr[i] = __dadd_rn(__dadd_rn(__dmul_rn(t[i], dt[0]), __dmul_rn(t[4 + i], dt[1])), __dmul_rn(t[8 + i], dt[2]));
+  PoseF o;
+  for (int i = 0; i < 9; ++i) o.R[i] = __double2float_rn(R[i]);
+  for (int i = 0; i < 3; ++i) {
+    o.t[i] = __double2float_rn(tr[i]);
+    double v = 0.0;
+    for (int k = 0; k < 3; ++k) v = __dadd_rn(v, __dmul_rn(R[3 * k + i], tr[k]));
+    o.v[i] = __double2float_rn(-v);
   }
+  o.pad = 0.f;
+  pose32[q] = o;
+  double* d = pose64 + 12 * int64_t(q);
+  for (int i = 0; i < 9; ++i) d[i] = R[i];
+  for (int i = 0; i < 3; ++i) d[9 + i] = tr[i];
+}
+
+}  // namespace
+
+void plan_stage_poses(glim_plan* p, const double* poses12) {
+  std::memcpy(p->h_fposes, poses12, size_t(p->nframes) * 12 * sizeof(double));
+}
+
+glim_status plan_enqueue_poses(glim_plan* p) {
+  glim_ctx* ctx = p->ctx;
+  if (p->npairs == 0) return GLIM_OK;
+  GLIM_CUDA(ctx, cudaMemcpyAsync(p->d_fposes, p->h_fposes, size_t(p->nframes) * 12 * sizeof(double),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+  k_pack_poses<<<ceil_div_i(p->npairs, 128), 128, 0, ctx->stream>>>(p->d_fposes, p->d_pair_frames, p->npairs,
+                                                                     p->in_pose32(), p->in_pose64());
+  GLIM_LAUNCHED(ctx);
+  return GLIM_OK;
 }
 
 namespace {
@@ -367,8 +411,7 @@ glim_status capture(glim_plan* p, bool full, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   GLIM_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
   glim_status st = GLIM_OK;
-  if (full && cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
-    st = GLIM_ECUDA;
+  if (full) st = plan_enqueue_poses(p);
   if (st == GLIM_OK) st = plan_enqueue_kernels(p);
   if (st == GLIM_OK && full &&
       cudaMemcpyAsync(p->h_out, p->d_out, p->out_bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
@@ -523,9 +566,18 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
   }
   p->in_bytes = std::max<size_t>(size_t(npairs) * (sizeof(PoseF) + 12 * sizeof(double)), 16);
   p->out_bytes = std::max<size_t>(size_t(npairs) * (157 * sizeof(double) + sizeof(int64_t)), 16);
+  const size_t fpose_bytes = std::max<size_t>(size_t(nframes) * 12 * sizeof(double), 16);
   if (cudaMalloc(&p->d_in, p->in_bytes) != cudaSuccess || cudaMalloc(&p->d_out, p->out_bytes) != cudaSuccess ||
-      cudaMallocHost(&p->h_in, p->in_bytes) != cudaSuccess || cudaMallocHost(&p->h_out, p->out_bytes) != cudaSuccess)
+      cudaMalloc(&p->d_fposes, fpose_bytes) != cudaSuccess ||
+      cudaMalloc(&p->d_pair_frames, std::max(npairs, 1) * sizeof(int2)) != cudaSuccess ||
+      cudaMallocHost(&p->h_fposes, fpose_bytes) != cudaSuccess ||
+      cudaMallocHost(&p->h_out, p->out_bytes) != cudaSuccess)
     return fail(set_error(ctx, GLIM_ENOMEM, "plan: serialized block allocation failed"));
+  {
+    std::vector<int2> pf(std::max(npairs, 1), make_int2(0, 0));
+    for (int q = 0; q < npairs; ++q) pf[q] = make_int2(pairs[q].src_frame, pairs[q].tgt_frame);
+    cudaMemcpy(p->d_pair_frames, pf.data(), pf.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  }
   st = plan_configure(p, o);
   if (st != GLIM_OK) return fail(st);
   *out = p;
@@ -554,8 +606,10 @@ extern "C" void glim_plan_destroy(glim_plan* p) {
   cudaFree(p->d_part);
   cudaFree(p->d_head);
   cudaFree(p->d_in);
+  cudaFree(p->d_fposes);
+  cudaFree(p->d_pair_frames);
+  if (p->h_fposes) cudaFreeHost(p->h_fposes);
   cudaFree(p->d_out);
-  if (p->h_in) cudaFreeHost(p->h_in);
   if (p->h_out) cudaFreeHost(p->h_out);
   delete p;
 }
@@ -565,8 +619,20 @@ extern "C" glim_status glim_plan_set_poses(glim_plan* p, const double* poses12) 
   glim_ctx* ctx = p->ctx;
   // the pinned block may still be read by an earlier upload
   GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  plan_pack_poses(p, poses12);
-  GLIM_CUDA(ctx, cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream));
+  return plan_upload_poses(p, poses12);
+}
+
+extern "C" glim_status glim_plan_relative_poses(glim_plan* p, double* rt64_out, float* pose32_out) {
+  if (!p) return GLIM_EINVAL;
+  glim_ctx* ctx = p->ctx;
+  if (p->npairs == 0) return GLIM_OK;
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (rt64_out)
+    GLIM_CUDA(ctx, cudaMemcpy(rt64_out, p->in_pose64(), size_t(p->npairs) * 12 * sizeof(double), cudaMemcpyDeviceToHost));
+  if (pose32_out) {
+    static_assert(sizeof(PoseF) == 16 * sizeof(float), "PoseF is 16 floats");
+    GLIM_CUDA(ctx, cudaMemcpy(pose32_out, p->in_pose32(), size_t(p->npairs) * sizeof(PoseF), cudaMemcpyDeviceToHost));
+  }
   return GLIM_OK;
 }
 
@@ -629,10 +695,11 @@ extern "C" glim_status glim_plan_linearize(glim_plan* p, const double* poses12, 
     return set_error(ctx, GLIM_EINVAL, "plan_linearize: null output");
   const bool dev_out = p->npairs > 0 && is_device_ptr(e_out);
   GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  plan_pack_poses(p, poses12);
+  plan_stage_poses(p, poses12);
   if (dev_out || !p->use_graph) {
-    GLIM_CUDA(ctx, cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream));
-    glim_status st = plan_enqueue_kernels(p);
+    glim_status st = plan_enqueue_poses(p);
+    if (st != GLIM_OK) return st;
+    st = plan_enqueue_kernels(p);
     if (st != GLIM_OK) return st;
     if (dev_out) return copy_outputs(p, e_out, H_out, b_out, inliers_out, false);
     GLIM_CUDA(ctx, cudaMemcpyAsync(p->h_out, p->d_out, p->out_bytes, cudaMemcpyDeviceToHost, ctx->stream));
@@ -642,7 +709,7 @@ extern "C" glim_status glim_plan_linearize(glim_plan* p, const double* poses12, 
       if (st != GLIM_OK) return st;
     }
     GLIM_CUDA(ctx, cudaGraphLaunch(p->g_full, ctx->stream));
-    ctx->launches += glim_plan_kernels_per_launch(p);
+    ctx->launches += glim_plan_kernels_per_launch(p) + (p->npairs > 0 ? 1 : 0);
   }
   GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return copy_outputs(p, e_out, H_out, b_out, inliers_out, true);
@@ -654,17 +721,18 @@ extern "C" glim_status glim_plan_linearize_pinned(glim_plan* p, const double* po
   if (maps_current(p) != GLIM_OK) return GLIM_EINVAL;
   glim_ctx* ctx = p->ctx;
   GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  plan_pack_poses(p, poses12);
+  plan_stage_poses(p, poses12);
   if (p->use_graph) {
     if (!p->g_full) {
       glim_status st = capture(p, true, &p->g_full);
       if (st != GLIM_OK) return st;
     }
     GLIM_CUDA(ctx, cudaGraphLaunch(p->g_full, ctx->stream));
-    ctx->launches += glim_plan_kernels_per_launch(p);
+    ctx->launches += glim_plan_kernels_per_launch(p) + (p->npairs > 0 ? 1 : 0);
   } else {
-    GLIM_CUDA(ctx, cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream));
-    glim_status st = plan_enqueue_kernels(p);
+    glim_status st = plan_enqueue_poses(p);
+    if (st != GLIM_OK) return st;
+    st = plan_enqueue_kernels(p);
     if (st != GLIM_OK) return st;
     GLIM_CUDA(ctx, cudaMemcpyAsync(p->h_out, p->d_out, p->out_bytes, cudaMemcpyDeviceToHost, ctx->stream));
   }
@@ -764,8 +832,11 @@ extern "C" glim_status glim_linearize_factors_plain(glim_ctx* ctx, const glim_fr
   if (st != GLIM_OK) return st;
   o = p->opts;  // with the defaults filled in
   const bool dev_out = npairs > 0 && is_device_ptr(e_out);
-  plan_pack_poses(p, poses12);
-  GLIM_CUDA(ctx, cudaMemcpyAsync(p->d_in, p->h_in, p->in_bytes, cudaMemcpyHostToDevice, ctx->stream));
+  st = plan_upload_poses(p, poses12);
+  if (st != GLIM_OK) {
+    glim_plan_destroy(p);
+    return st;
+  }
   std::vector<int32_t> begin(npairs + 1);
   cudaMemcpy(begin.data(), p->d_item_begin, (npairs + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost);
   double* h = reinterpret_cast<double*>(p->h_out);

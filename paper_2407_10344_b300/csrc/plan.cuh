@@ -151,10 +151,14 @@ struct glim_plan {
   LinKernel kernel = nullptr;
   int lane_kernel = 0;  // 0: general kernel; 1: per-lane dense-grid kernel; 2: per-lane hash kernel
   size_t kernel_smem = 0;
-  // serialized input block: PoseF[npairs] then double[npairs * 12]
+  // pose block on the device: PoseF[npairs] then double[npairs * 12], formed by k_pack_poses
+  // from the frame poses, which are the only pose data that travel: pinned staging h_fposes ->
+  // d_fposes (nframes * 12 doubles)
   size_t in_bytes = 0;
   void* d_in = nullptr;
-  void* h_in = nullptr;
+  double* d_fposes = nullptr;
+  double* h_fposes = nullptr;
+  int2* d_pair_frames = nullptr;  // (source frame, target frame) per pair
   // serialized output block: e[npairs], H[npairs*144], b[npairs*12], inliers[npairs]
   size_t out_bytes = 0;
   void* d_out = nullptr;
@@ -175,7 +179,14 @@ struct glim_plan {
 
 
 // shared host helpers (linearize.cu)
-void plan_pack_poses(glim_plan* p, const double* poses12);
+// Stage the frame poses (host, into the pinned block), then enqueue their upload and the
+// pose-packing kernel on the context stream (also inside a graph capture).
+void plan_stage_poses(glim_plan* p, const double* poses12);
+glim_status plan_enqueue_poses(glim_plan* p);
+inline glim_status plan_upload_poses(glim_plan* p, const double* poses12) {
+  plan_stage_poses(p, poses12);
+  return plan_enqueue_poses(p);
+}
 bool plan_maps_current(const glim_plan* p);  // false once a target map changed since creation
 bool map_all_dense(const glim_vmap* m);     // every level a dense grid
 bool map_all_hash(const glim_vmap* m);      // every level a hash table

@@ -727,3 +727,44 @@ def test_process_exit_with_open_objects():
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
     assert r.stdout.strip().endswith("True")
+
+
+def test_plan_pose_packing_bits(G, ctx, corridor):
+    """The plan forms every pair's relative pose on the device from the uploaded frame poses:
+    T_rel = T_t^-1 T_s in FP64 with each product and sum rounded on its own, in a fixed order,
+    then rounded to FP32 with the target viewpoint v = -R^T t.  numpy's float64 arithmetic in
+    the same order gives the same bits."""
+    w = corridor.w
+    s = synth.Stream(21, "pose-bits")
+    poses = np.stack([synth.perturb_pose(T, 3.0, 0.4, s) for T in w.poses])
+    plan = G.Plan(ctx, corridor.gframes, corridor.gmaps, w.pairs)
+    plan.set_poses(poses)
+    T, p32 = plan.relative_poses()
+    for q, (si, ti) in enumerate(w.pairs):
+        S, Tt = poses[si], poses[ti]
+        R = np.zeros((3, 3))
+        for i in range(3):
+            for j in range(3):
+                v = 0.0
+                for k in range(3):
+                    v = v + Tt[k, i] * S[k, j]
+                R[i, j] = v
+        dt = S[:, 3] - Tt[:, 3]
+        tr = np.array([(Tt[0, i] * dt[0] + Tt[1, i] * dt[1]) + Tt[2, i] * dt[2] for i in range(3)])
+        assert np.array_equal(T[q, :, :3], R) and np.array_equal(T[q, :, 3], tr), q
+        v = np.zeros(3)
+        for i in range(3):
+            acc = 0.0
+            for k in range(3):
+                acc = acc + R[k, i] * tr[k]
+            v[i] = -acc
+        want = np.concatenate([R.reshape(-1), tr, v, [0.0]]).astype(np.float32)
+        assert np.array_equal(p32[q], want), q
+    # the packed poses are the ones linearized: the plan equals the one-shot call, whose
+    # relative poses are formed on the host
+    o = plan.opts()
+    e1, H1, b1, i1 = plan.linearize(poses)
+    e2, H2, b2, i2 = G.linearize(ctx, corridor.gframes, corridor.gmaps, w.pairs, poses, block=o["block"],
+                                 pts_per_thread=o["pts_per_thread"], accum_mode=o["accum_mode"])
+    for a, b_ in ((e1, e2), (H1, H2), (b1, b2), (i1, i2)):
+        assert np.array_equal(np.asarray(a), np.asarray(b_))
