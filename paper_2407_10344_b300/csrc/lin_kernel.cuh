@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize(const LinArgs 
 // table's longest probe sequence (rare at load 1/4).  A lane past the end of its tile reads
 // its tile's last point and is masked.  Because G = [-(u)x, I] is the same for all levels of
 // a point, the lane sums w Omega, w Omega d and e over the levels (a miss, or a term whose S
-// is not positive definite, adds exact zeros) and adds the G-form of the sums once: 28
+// is not positive definite, adds nothing) and adds the G-form of the sums once: 28
 // accumulator updates per point instead of per hit.  The weight enters as w adj(S)/det(S),
 // as in the general kernel; results agree up to FP32 rounding.
 
@@ -561,7 +561,7 @@ __device__ __forceinline__ void lane_point(const LaneView<typename std::conditio
     }
   }
   // per level: S = C~ + R C R^T, w Omega = w adj(S) / det(S), y = w Omega d, and the sums over
-  // levels (a term that is a miss or not positive definite adds zeros).  Skipping a level
+  // levels (a term that is a miss or not positive definite adds nothing).  Skipping a level
   // (or the whole point) when no lane of the warp hits it was measured slower: the vote has
   // to wait for the voxel reads, which stops R C R^T from overlapping their latency.
   float O00 = 0.f, O01 = 0.f, O02 = 0.f, O11 = 0.f, O12 = 0.f, O22 = 0.f;
@@ -575,17 +575,31 @@ __device__ __forceinline__ void lane_point(const LaneView<typename std::conditio
     const float A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
     const float det = a * A00 + b * A01 + c * A02;
     const bool ok = hit[l] && det > 0.f && det < INFINITY;
-    inl += ok ? 1 : 0;  // inliers: the terms that enter the sums
     const float id = __fdividef(w, det);
-    // selected, not multiplied by 0: adj(S) of a masked term need not be finite
-    const float o00 = ok ? A00 * id : 0.f, o01 = ok ? A01 * id : 0.f, o02 = ok ? A02 * id : 0.f;
-    const float o11 = ok ? A11 * id : 0.f, o12 = ok ? A12 * id : 0.f, o22 = ok ? A22 * id : 0.f;
-    const float y0 = o00 * dx + o01 * dy + o02 * dz;
-    const float y1 = o01 * dx + o11 * dy + o12 * dz;
-    const float y2 = o02 * dx + o12 * dy + o22 * dz;
-    es = __fmaf_rn(dx, y0, __fmaf_rn(dy, y1, __fmaf_rn(dz, y2, es)));
-    O00 += o00; O01 += o01; O02 += o02; O11 += o11; O12 += o12; O22 += o22;
-    g0 += y0; g1 += y1; g2 += y2;
+    // A d and d^T A d; the term enters the sums as w/det times these, by fused multiply-adds
+    // predicated on `ok` (a masked term's adj(S) need not be finite, so it is not multiplied
+    // by zero: its instructions do not execute), and counts as an inlier
+    const float a0 = A00 * dx + A01 * dy + A02 * dz;
+    const float a1 = A01 * dx + A11 * dy + A12 * dz;
+    const float a2 = A02 * dx + A12 * dy + A22 * dz;
+    const float el = dx * a0 + dy * a1 + dz * a2;
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %11, 0;\n\t"
+        "@p fma.rn.f32 %0, %13, %12, %0;\n\t"
+        "@p fma.rn.f32 %1, %14, %12, %1;\n\t"
+        "@p fma.rn.f32 %2, %15, %12, %2;\n\t"
+        "@p fma.rn.f32 %3, %16, %12, %3;\n\t"
+        "@p fma.rn.f32 %4, %17, %12, %4;\n\t"
+        "@p fma.rn.f32 %5, %18, %12, %5;\n\t"
+        "@p fma.rn.f32 %6, %19, %12, %6;\n\t"
+        "@p fma.rn.f32 %7, %20, %12, %7;\n\t"
+        "@p fma.rn.f32 %8, %21, %12, %8;\n\t"
+        "@p fma.rn.f32 %9, %22, %12, %9;\n\t"
+        "@p add.s32 %10, %10, 1;\n\t}"
+        : "+f"(O00), "+f"(O01), "+f"(O02), "+f"(O11), "+f"(O12), "+f"(O22), "+f"(g0), "+f"(g1), "+f"(g2),
+          "+f"(es), "+r"(inl)
+        : "r"(ok ? 1u : 0u), "f"(id), "f"(A00), "f"(A01), "f"(A02), "f"(A11), "f"(A12), "f"(A22), "f"(a0), "f"(a1),
+          "f"(a2), "f"(el));
   }
   // the G-form of the sums, G = [-(u)x, I] with u = R mu
   const float ux = q.x - R0.w, uy = q.y - R1.w, uz = q.z - R2.w;
