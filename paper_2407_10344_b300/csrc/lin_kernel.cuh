@@ -446,13 +446,29 @@ static_assert(sizeof(DenseLevelDev) == 32 && sizeof(HashLevelDev) == 32 && offse
                   offsetof(HashMapDev, inv_r) % 16 == 0,
               "lane-kernel descriptors must sit on 16-byte boundaries");
 
-template <int LMAX, bool HASH, class A>
-__device__ __forceinline__ void lane_point(const LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V,
-                                           const float4 m, bool live, int validate, A& acc, int& inl, int kk) {
+// What a lane has read for one point: the transformed point, its weight and covariance, and
+// the voxel records of every level (for a hash table the home slot).  Split from the
+// arithmetic so that one point's reads can be in flight while the previous point is computed.
+template <int LMAX>
+struct LaneFetch {
+  float3 q;
+  float w;
+  bool live;
+  float4 s0[LMAX];  // dense: {id, C~22, ., .} (8 bytes read); hash: {kx, ky, kz, C~22}
+  float4 s1[LMAX], s2[LMAX];
+  uint32_t slot[LMAX];  // hash: the first probe's slot
+  float2 ca, cb, cc;
+};
+
+template <int LMAX, bool HASH>
+__device__ __forceinline__ void lane_fetch(const LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V,
+                                           const float4 m, bool live, int validate, int kk, LaneFetch<LMAX>& F) {
   // the covariance is read here rather than a round ahead: it is needed only after the voxel
   // reads are in flight, and the registers it would hold are worth more as occupancy
   const float2* cp = V.cov + 3 * int64_t(kk);
-  const float2 ca = __ldg(cp), cb = __ldg(cp + 1), cc = __ldg(cp + 2);
+  F.ca = __ldg(cp);
+  F.cb = __ldg(cp + 1);
+  F.cc = __ldg(cp + 2);
   if (validate && V.nrm) {
     const float* nk = V.nrm + 3 * int64_t(kk);
     const float vv[3] = {V.v.x, V.v.y, V.v.z};
@@ -470,9 +486,6 @@ __device__ __forceinline__ void lane_point(const LaneView<typename std::conditio
   q.x = finite_q ? q.x : 0.f;
   q.y = finite_q ? q.y : 0.f;
   q.z = finite_q ? q.z : 0.f;
-  float4 s0[LMAX];  // dense: {id, C~22, ., .} (8 bytes read); hash: {kx, ky, kz, C~22}
-  float4 s1[LMAX], s2[LMAX];
-  uint32_t slot[LMAX];  // hash: the first probe's slot
   const float4 irq = *reinterpret_cast<const float4*>(V.M.inv_r);  // one 16-byte shared load
   const float irv[4] = {irq.x, irq.y, irq.z, irq.w};
 #pragma unroll
@@ -489,21 +502,40 @@ __device__ __forceinline__ void lane_point(const LaneView<typename std::conditio
     const int kz = __float2int_rd(__fmul_rn(q.z, ir));
     const VoxSlot* sl;
     if constexpr (HASH) {  // {slots, mask, log2cap} {max_probe, ...}
-      slot[l] = hash3(kx, ky, kz, la.w);
-      sl = base + slot[l];
-      s0[l] = ldg4(&sl->w0);
+      F.slot[l] = hash3(kx, ky, kz, la.w);
+      sl = base + F.slot[l];
+      F.s0[l] = ldg4(&sl->w0);
     } else {  // {cells, ox, oy} {oz, nx, ny, nz}
       const uint32_t x = uint32_t(kx) - uint32_t(la.z), y = uint32_t(ky) - uint32_t(la.w), z = uint32_t(kz) - lb.x;
       const bool in_box = live && x < lb.y && y < lb.z && z < lb.w;
       sl = base + (in_box ? int((x * lb.z + y) * lb.w + z) : -1);
       const float2 h = __ldg(reinterpret_cast<const float2*>(&sl->w0));
-      s0[l] = make_float4(h.x, h.y, 0.f, 0.f);
+      F.s0[l] = make_float4(h.x, h.y, 0.f, 0.f);
     }
-    s1[l] = ldg4(&sl->w1);  // {mean, C~00}
-    s2[l] = ldg4(&sl->w2);  // {C~01, C~02, C~11, C~12}
+    F.s1[l] = ldg4(&sl->w1);  // {mean, C~00}
+    F.s2[l] = ldg4(&sl->w2);  // {C~01, C~02, C~11, C~12}
   }
+  F.q = q;
+  F.w = m.w;
+  F.live = live;
+}
+
+template <int LMAX, bool HASH, class A>
+__device__ __forceinline__ void lane_compute(const LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V,
+                                             LaneFetch<LMAX>& F, A& acc, int& inl) {
+  const float4 R0 = V.Rt[0], R1 = V.Rt[1], R2 = V.Rt[2];
+  const float3 q = F.q;
+  const bool live = F.live;
+  float4(&s0)[LMAX] = F.s0;
+  float4(&s1)[LMAX] = F.s1;
+  float4(&s2)[LMAX] = F.s2;
+  const float4 irq = *reinterpret_cast<const float4*>(V.M.inv_r);
+  const float irv[4] = {irq.x, irq.y, irq.z, irq.w};
+  (void)live;
+  (void)irv;
+  const float2 ca = F.ca, cb = F.cb, cc = F.cc;
   // R C R^T (once for all levels)
-  const float w = m.w;
+  const float w = F.w;
   const float c00 = ca.x, c01 = ca.y, c02 = cb.x, c11 = cb.y, c12 = cc.x, c22 = cc.y;
   const float w00 = R0.x * c00 + R0.y * c01 + R0.z * c02;
   const float w01 = R0.x * c01 + R0.y * c11 + R0.z * c12;
@@ -538,7 +570,7 @@ __device__ __forceinline__ void lane_point(const LaneView<typename std::conditio
           const int max_probe = reinterpret_cast<const int4*>(&V.M.lv[l])[1].x;
           const VoxSlot* slots =
               reinterpret_cast<const VoxSlot*>(uint64_t(uint32_t(la.x)) | (uint64_t(uint32_t(la.y)) << 32));
-          uint32_t h = slot[l];
+          uint32_t h = F.slot[l];
           for (int p = 1; p < max_probe; ++p) {  // bounded by the longest probe sequence of the table
             h = (h + 1u) & uint32_t(la.z);
             const float4 w0 = ldg4(&slots[h].w0);
@@ -623,6 +655,14 @@ __device__ __forceinline__ void lane_point(const LaneView<typename std::conditio
   acc.add(27, es);
 }
 
+template <int LMAX, bool HASH, class A>
+__device__ __forceinline__ void lane_point(const LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V,
+                                           const float4 m, bool live, int validate, A& acc, int& inl, int kk) {
+  LaneFetch<LMAX> F;
+  lane_fetch<LMAX, HASH>(V, m, live, validate, kk, F);
+  lane_compute<LMAX, HASH>(V, F, acc, inl);
+}
+
 template <int BLOCK, int ACC, int LMAX, bool HASH>
 __device__ __forceinline__ void process_item_lane(const LinArgs& a, int item,
                                                   LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V) {
@@ -648,21 +688,45 @@ __device__ __forceinline__ void process_item_lane(const LinArgs& a, int item,
   const int last = V.end - 1;  // items are never empty
   const int first = it.start + int(threadIdx.x);
   const int rounds = min(a.ppt, (last - it.start) / BLOCK + 1);
-  // software pipeline of the point coordinates, unrolled twice so that the two buffers
-  // alternate without copies
-  float4 p0 = ldg4(V.pts + min(first, last));
-  int j = 0;
+  if constexpr (!HASH) {
+    // Dense grids: a software pipeline over the rounds, unrolled twice so that the two
+    // buffers alternate without copies.  A point's coordinates are read two rounds ahead, its
+    // voxel records and covariance one round ahead (lane_fetch), so the reads of the next
+    // point are in flight while the lane computes the current one (lane_compute): 9 % faster
+    // than reading a point's records at the start of its own round.
+    LaneFetch<LMAX> fa, fb;
+    lane_fetch<LMAX, HASH>(V, ldg4(V.pts + min(first, last)), first <= last, a.validate, min(first, last), fa);
+    float4 pn = ldg4(V.pts + min(first + BLOCK, last));
+    int j = 0;
 #pragma unroll 1
-  for (; j + 1 < rounds; j += 2) {
-    const int k = first + j * BLOCK;
-    const float4 p1 = ldg4(V.pts + min(k + BLOCK, last));
-    lane_point<LMAX, HASH>(V, p0, k <= last, a.validate, acc, inl, min(k, last));
-    p0 = ldg4(V.pts + min(k + 2 * BLOCK, last));
-    lane_point<LMAX, HASH>(V, p1, k + BLOCK <= last, a.validate, acc, inl, min(k + BLOCK, last));
-  }
-  if (j < rounds) {
-    const int k = first + j * BLOCK;
-    lane_point<LMAX, HASH>(V, p0, k <= last, a.validate, acc, inl, min(k, last));
+    for (; j + 1 < rounds; j += 2) {
+      const int k = first + j * BLOCK;
+      lane_fetch<LMAX, HASH>(V, pn, k + BLOCK <= last, a.validate, min(k + BLOCK, last), fb);
+      pn = ldg4(V.pts + min(k + 2 * BLOCK, last));
+      lane_compute<LMAX, HASH>(V, fa, acc, inl);
+      lane_fetch<LMAX, HASH>(V, pn, k + 2 * BLOCK <= last, a.validate, min(k + 2 * BLOCK, last), fa);
+      pn = ldg4(V.pts + min(k + 3 * BLOCK, last));
+      lane_compute<LMAX, HASH>(V, fb, acc, inl);
+    }
+    if (j < rounds) lane_compute<LMAX, HASH>(V, fa, acc, inl);
+  } else {
+    // Hash tables: the coordinates one round ahead only.  Holding a second point's home
+    // slots (48 bytes per level) costs the hash kernel more registers than the overlap
+    // gains: measured 34 % slower.
+    float4 p0 = ldg4(V.pts + min(first, last));
+    int j = 0;
+#pragma unroll 1
+    for (; j + 1 < rounds; j += 2) {
+      const int k = first + j * BLOCK;
+      const float4 p1 = ldg4(V.pts + min(k + BLOCK, last));
+      lane_point<LMAX, HASH>(V, p0, k <= last, a.validate, acc, inl, min(k, last));
+      p0 = ldg4(V.pts + min(k + 2 * BLOCK, last));
+      lane_point<LMAX, HASH>(V, p1, k + BLOCK <= last, a.validate, acc, inl, min(k + BLOCK, last));
+    }
+    if (j < rounds) {
+      const int k = first + j * BLOCK;
+      lane_point<LMAX, HASH>(V, p0, k <= last, a.validate, acc, inl, min(k, last));
+    }
   }
   block_reduce_store<BLOCK, ACC>(acc, inl, a.part + int64_t(item) * PSTRIDE);
 }
