@@ -36,7 +36,7 @@ BYTES_OUT_PER_PAIR = 157 * 8 + 8  # e, H (144), b (12) in FP64 and the inlier co
 # of this kernel version on the 40-submap urban case (k_linearize_dense_urban40_ncu_full.md
 # under profiles), scaled by the units of a launch.  None
 # when the kernel has changed since the capture.
-DRAM_BYTES_PER_PAIR_POINT = 11.22
+DRAM_BYTES_PER_PAIR_POINT = 12.17
 # Algorithmic FP32 flops of the linearization, counted on the per-term evaluation (a fused
 # multiply-add counts two): per (pair, point) the transform (18), 3 key products per level,
 # R C R^T (75) and u (3); per hit term S = C~ + R C R^T (6), d (3), the adjugate (18), det (5),
