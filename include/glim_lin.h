@@ -346,7 +346,12 @@ glim_status glim_backward(glim_ctx* ctx, const glim_frame* frames, int32_t nfram
  * block 256 and pts_per_thread 1 (GLIM_EINVAL otherwise); its validate_surface option
  * applies.  The gradient scratch (host tables, per-(pair, point) slots) is allocated at the
  * first call and kept until glim_plan_destroy.  The frames' point arrays may be rewritten in
- * place between calls.  Outputs as for glim_backward; synchronizes the stream. */
+ * place between calls, by work ordered on the context stream (or after synchronizing it).
+ * Outputs as for glim_backward, written by work enqueued on the context stream: the call does
+ * not wait for it (the first call waits once, to build the gradient tables).  When poses12
+ * equals the poses of the plan's last linearization or upload, the pose block on the device
+ * is reused and the call does not wait for the stream at all; otherwise it first waits for
+ * the stream's earlier work (the pinned pose staging block may still be in use). */
 glim_status glim_plan_backward(glim_plan* plan, const double* poses12, int32_t omega_grad_full,
                                double* dxi_out, float* dmu_out, float* dw_out);
 

@@ -3,8 +3,11 @@ weights, as a ``torch.autograd.Function``.
 
 Inputs: per-frame pose increments ``xi`` (nframes x 6, [omega; v], applied on the right,
 T_f <- T_f Exp(xi_f)), the source points' coordinates and their weights.  The forward pass
-is the library's batched linearization (the cost only is kept); the backward pass is
-``glim_backward``, which recomputes the per-point Jacobians instead of storing them.
+is the library's batched linearization (the cost only is kept).  The gradient comes from
+``glim_plan_backward``, which recomputes the per-point Jacobians instead of storing them.
+When an input needs a gradient, the forward pass enqueues that gradient pass right after
+the linearization, on the same point buffer and device pose block (no second upload, no
+host wait); the backward pass then only scales the three gradients by the incoming one.
 
 Conventions: the pose gradient is the gradient with respect to a right perturbation of the
 current pose T_f Exp(xi_f); it equals d/dxi exactly at xi = 0 (the usual parameterisation of a
@@ -108,9 +111,13 @@ class FactorProblem:
         return pts, w
 
     def _load(self, points, weights):
-        """Write the points and weights of an evaluation into the plan's buffer."""
-        self._p4[:, :3].copy_(points)
-        self._p4[:, 3].copy_(weights)
+        """Write the points and weights of an evaluation into the plan's buffer (one kernel)."""
+        buf = self._p4.untyped_storage().data_ptr()
+        if points.untyped_storage().data_ptr() == buf or weights.untyped_storage().data_ptr() == buf:
+            self._p4[:, :3].copy_(points)  # views of the buffer itself
+            self._p4[:, 3].copy_(weights)
+        else:
+            torch.cat((points, weights.unsqueeze(1)), dim=1, out=self._p4)
 
     def poses_at(self, xi):
         x = xi.detach().cpu().numpy().astype(np.float64).reshape(-1, 6)
@@ -124,24 +131,22 @@ class FactorProblem:
 class GlimFactorFn(torch.autograd.Function):
     @staticmethod
     def forward(fctx, xi, points, weights, problem: FactorProblem):
-        pts = points.detach().float()
-        wts = weights.detach().float()
-        problem._load(pts, wts)
+        problem._load(points.detach().float(), weights.detach().float())
         poses = problem.poses_at(xi)
         e, _, _, _ = problem._plan.linearize(poses, out=problem._out)
-        fctx.problem = problem
-        fctx.save_for_backward(pts, wts)
-        fctx.poses = poses
+        # The gradient pass reads the buffer as this evaluation wrote it, so later evaluations
+        # may reuse the buffer before this one's backward runs.
+        fctx.grads = (problem._plan.backward(poses, omega_grad_full=problem.full)
+                      if any(fctx.needs_input_grad[:3]) else None)
         fctx.xi_device = xi.device
         fctx.xi_dtype = xi.dtype
         return e.sum()
 
     @staticmethod
     def backward(fctx, grad_out):
-        p: FactorProblem = fctx.problem
-        pts, wts = fctx.saved_tensors
-        p._load(pts, wts)  # other evaluations may have used the buffer since this forward
-        dxi, dmu, dw = p._plan.backward(fctx.poses, omega_grad_full=p.full)
-        g = grad_out.to(torch.float64)
-        gxi = (g * dxi).to(device=fctx.xi_device, dtype=fctx.xi_dtype)
-        return gxi, (g * dmu.double()).float(), (g * dw.double()).float(), None
+        dxi, dmu, dw = fctx.grads
+        fctx.grads = None
+        need = fctx.needs_input_grad
+        # grad_out is a 0-dim FP64 tensor: the products keep the gradients' own dtypes
+        gxi = (dxi * grad_out).to(device=fctx.xi_device, dtype=fctx.xi_dtype) if need[0] else None
+        return gxi, dmu * grad_out if need[1] else None, dw * grad_out if need[2] else None, None

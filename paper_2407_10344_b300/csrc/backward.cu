@@ -297,9 +297,9 @@ glim_status bwd_run(glim_plan* p, const BwdScratch& sc, int32_t omega_grad_full,
         sc.pp, sc.pair_off, sc.src_list, sc.src_begin, sc.frame_off, nullptr, nframes, sc.ntot, dmu_out, dw_out);
     ctx->launches++;
   }
+  // the outputs are device arrays ordered on the context stream: no host wait here
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(ctx, e, "backward launch");
-  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return set_error(ctx, GLIM_ECUDA, "backward: sync failed");
   ctx->err.clear();
   return GLIM_OK;
 }
@@ -326,7 +326,8 @@ extern "C" glim_status glim_backward(glim_ctx* ctx, const glim_frame* frames, in
     st = plan_upload_poses(p, poses12);
   }
   if (st == GLIM_OK) st = bwd_run(p, sc, omega_grad_full, validate_surface, dxi_out, dmu_out, dw_out);
-  cudaStreamSynchronize(ctx->stream);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && st == GLIM_OK)
+    st = set_error(ctx, GLIM_ECUDA, "backward: sync failed");
   sc.release();
   glim_plan_destroy(p);
   return st;
@@ -341,7 +342,13 @@ extern "C" glim_status glim_plan_backward(glim_plan* p, const double* poses12, i
     return set_error(ctx, GLIM_EINVAL, "plan_backward: the plan needs block 256 and pts_per_thread 1");
   if (!plan_maps_current(p)) return set_error(ctx, GLIM_EINVAL, "plan_backward: a target voxelmap changed");
   GLIM_CUDA(ctx, cudaSetDevice(ctx->device));
-  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the pose block may still be in use
+  // The device pose block already holds these poses when the last linearization of the plan
+  // used them (the usual forward-then-gradient sequence): then nothing is uploaded and the
+  // call does not wait for the stream.  Otherwise the pinned staging block may still be read
+  // by an earlier upload, so the stream is drained before it is overwritten.
+  const bool same_poses = p->fposes_on_device && p->nframes > 0 &&
+                          std::memcmp(p->h_fposes, poses12, size_t(p->nframes) * 12 * sizeof(double)) == 0;
+  if (!same_poses) GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (!p->bwd) {
     BwdScratch* sc = new BwdScratch;
     const glim_status st = bwd_prepare(p, *sc);
@@ -351,7 +358,9 @@ extern "C" glim_status glim_plan_backward(glim_plan* p, const double* poses12, i
     }
     p->bwd = sc;
   }
-  const glim_status st = plan_upload_poses(p, poses12);
-  if (st != GLIM_OK) return st;
+  if (!same_poses) {
+    const glim_status st = plan_upload_poses(p, poses12);
+    if (st != GLIM_OK) return st;
+  }
   return bwd_run(p, *p->bwd, omega_grad_full, p->opts.validate_surface, dxi_out, dmu_out, dw_out);
 }

@@ -384,6 +384,7 @@ __global__ void k_pack_poses(const double* __restrict__ fposes, const int2* __re
 }  // namespace
 
 void plan_stage_poses(glim_plan* p, const double* poses12) {
+  p->fposes_on_device = false;
   std::memcpy(p->h_fposes, poses12, size_t(p->nframes) * 12 * sizeof(double));
 }
 
@@ -699,6 +700,7 @@ extern "C" glim_status glim_plan_linearize(glim_plan* p, const double* poses12, 
   if (dev_out || !p->use_graph) {
     glim_status st = plan_enqueue_poses(p);
     if (st != GLIM_OK) return st;
+    p->fposes_on_device = true;
     st = plan_enqueue_kernels(p);
     if (st != GLIM_OK) return st;
     if (dev_out) return copy_outputs(p, e_out, H_out, b_out, inliers_out, false);
@@ -709,6 +711,7 @@ extern "C" glim_status glim_plan_linearize(glim_plan* p, const double* poses12, 
       if (st != GLIM_OK) return st;
     }
     GLIM_CUDA(ctx, cudaGraphLaunch(p->g_full, ctx->stream));
+    p->fposes_on_device = true;
     ctx->launches += glim_plan_kernels_per_launch(p) + (p->npairs > 0 ? 1 : 0);
   }
   GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -728,10 +731,12 @@ extern "C" glim_status glim_plan_linearize_pinned(glim_plan* p, const double* po
       if (st != GLIM_OK) return st;
     }
     GLIM_CUDA(ctx, cudaGraphLaunch(p->g_full, ctx->stream));
+    p->fposes_on_device = true;
     ctx->launches += glim_plan_kernels_per_launch(p) + (p->npairs > 0 ? 1 : 0);
   } else {
     glim_status st = plan_enqueue_poses(p);
     if (st != GLIM_OK) return st;
+    p->fposes_on_device = true;
     st = plan_enqueue_kernels(p);
     if (st != GLIM_OK) return st;
     GLIM_CUDA(ctx, cudaMemcpyAsync(p->h_out, p->d_out, p->out_bytes, cudaMemcpyDeviceToHost, ctx->stream));

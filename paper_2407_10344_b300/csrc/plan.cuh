@@ -158,6 +158,7 @@ struct glim_plan {
   void* d_in = nullptr;
   double* d_fposes = nullptr;
   double* h_fposes = nullptr;
+  bool fposes_on_device = false;  // d_fposes and the pose block hold h_fposes (set after an upload)
   int2* d_pair_frames = nullptr;  // (source frame, target frame) per pair
   // serialized output block: e[npairs], H[npairs*144], b[npairs*12], inliers[npairs]
   size_t out_bytes = 0;
@@ -185,7 +186,9 @@ void plan_stage_poses(glim_plan* p, const double* poses12);
 glim_status plan_enqueue_poses(glim_plan* p);
 inline glim_status plan_upload_poses(glim_plan* p, const double* poses12) {
   plan_stage_poses(p, poses12);
-  return plan_enqueue_poses(p);
+  const glim_status st = plan_enqueue_poses(p);
+  p->fposes_on_device = st == GLIM_OK;
+  return st;
 }
 bool plan_maps_current(const glim_plan* p);  // false once a target map changed since creation
 bool map_all_dense(const glim_vmap* m);     // every level a dense grid

@@ -586,7 +586,8 @@ def test_plan_backward_equals_one_shot_and_reuses_scratch(G, ctx, full):
 
 def test_autograd_interleaved_evaluations(G, ctx):
     """Two evaluations at different points before the first one's backward: the gradient is
-    the first evaluation's (the problem's shared point buffer is reloaded for the backward)."""
+    the first evaluation's (its gradient pass read the shared point buffer before the second
+    evaluation rewrote it)."""
     from gpu_helpers import Prepared
     from paper_2407_10344_b300.autograd import FactorProblem
     P = Prepared(ctx, synth.corridor(n_cur=4000, kf_range=(3000, 5000), n_kf=3, weights=True))
