@@ -577,6 +577,9 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, _ = oracle_sample(w, budget_s=args.cpu_budget, single_thread=True)
         line["cpu_baseline"] = cb
+    for k in ("backward", "random_point_order"):  # legs that this workload does not run
+        if line.get(k) is None:
+            line.pop(k, None)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -598,6 +601,8 @@ def run_reference(args):
     cb["value"] = value
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * w.n_pair_points / value,
+            "ms_per_step_note": "one whole step (every pair) at the sampled rate; each timed step is a bounded sample",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_desc(w, args), "pairs": len(w.pairs)},
             "cpu_baseline": cb,
