@@ -527,7 +527,10 @@ def run_ours(args):
                    "accum_mode": args.accum, "block": opts["block"], "pts_per_thread": opts["pts_per_thread"],
                    "autotuned": tuned, "surface_validation": False,
                    "point_order": "Z-order of 0.5 m cells" if args.order == "morton" else "generator (random)",
-                   "l2": "inputs larger than L2: %.2f GB source stream per step (L2 126 MB)" % (BYTES_PER_POINT * n_pp / 1e9),
+                   "l2": ("inputs larger than L2: %.2f GB source stream per step (L2 126 MB)" % (BYTES_PER_POINT * n_pp / 1e9)
+                          if BYTES_PER_POINT * n_pp > 126e6 else
+                          "L2 not flushed: the %.3f GB source stream fits in L2 (126 MB), a warm-cache figure"
+                          % (BYTES_PER_POINT * n_pp / 1e9)),
                    "parallelism": f"replicas x{ws} (independent batches per GPU, no collective)",
                    "generation_s": round(gen_s, 1)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

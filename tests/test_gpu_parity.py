@@ -575,10 +575,21 @@ def test_plan_backward_equals_one_shot_and_reuses_scratch(G, ctx, full):
     w = P.w
     one = G.backward(ctx, P.gframes, P.gmaps, w.pairs, w.poses, omega_grad_full=full)
     plan = G.Plan(ctx, P.gframes, P.gmaps, w.pairs, block=256, pts_per_thread=1)
-    for _ in range(2):
+    for _ in range(2):  # the second call finds the poses on the device and uploads nothing
         got = plan.backward(w.poses, omega_grad_full=full)
         for a, b in zip(one, got):
             assert torch.equal(a, b)
+    # a linearization at other poses, then gradients at the first poses and at the other ones:
+    # each call uploads the poses it was given when the device holds different ones
+    poses2 = w.poses.copy()
+    poses2[0, :, 3] += np.array([0.05, -0.03, 0.02])
+    one2 = G.backward(ctx, P.gframes, P.gmaps, w.pairs, poses2, omega_grad_full=full)
+    plan.linearize(poses2)
+    for poses, ref in ((w.poses, one), (poses2, one2), (poses2, one2)):
+        got = plan.backward(poses, omega_grad_full=full)
+        for a, b in zip(ref, got):
+            assert torch.equal(a, b)
+    assert not torch.equal(one[0], one2[0])
     other = G.Plan(ctx, P.gframes, P.gmaps, w.pairs, block=128, pts_per_thread=16)
     with pytest.raises(G.GlimError, match="EINVAL"):
         other.backward(w.poses)
