@@ -388,6 +388,9 @@ def test_covariances_match_bruteforce_oracle(G, ctx):
         cov, nrm = G.estimate_covariances(ctx, p4, k=10)
         c64, n64, _, tie = O.estimate_covariances(pts, k=10)
         cov, nrm = cov.cpu().numpy().astype(np.float64), nrm.cpu().numpy().astype(np.float64)
+        # points whose two smallest eigenvalues are within 1e-4 of the largest have no stable
+        # normal; they are left out of the comparison and must stay rare (none in these frames)
+        assert tie.sum() <= 0.001 * len(pts), int(tie.sum())
         ok = ~tie
         Cg = cov[:, [0, 1, 2, 1, 3, 4, 2, 4, 5]].reshape(-1, 3, 3)
         Co = c64[:, [0, 1, 2, 1, 3, 4, 2, 4, 5]].reshape(-1, 3, 3)
