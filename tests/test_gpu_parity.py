@@ -783,3 +783,66 @@ def test_plan_pose_packing_bits(G, ctx, corridor):
                                  pts_per_thread=o["pts_per_thread"], accum_mode=o["accum_mode"])
     for a, b_ in ((e1, e2), (H1, H2), (b1, b2), (i1, i2)):
         assert np.array_equal(np.asarray(a), np.asarray(b_))
+
+
+# ---------------------------------------------------------------------------- key range edge
+@pytest.mark.parametrize("layout", ["dense", "hash"])
+def test_keys_at_the_edge_of_the_key_range(G, ctx, layout):
+    """Voxels at the largest and smallest valid keys (2^20 - 1 and -2^20 at 0.5 m, and their
+    level-1 keys at 1 m) and source points one key beyond them: the points inside hit their
+    voxels, the ones beyond miss, with ids bit-exact and e, H, b within the tolerance, at the
+    identity and after a shift that carries points across the boundary.
+
+    Near |x| = 2^20 r a binary32 coordinate has a spacing of r / 8, so every coordinate, voxel
+    mean and the shift are placed on multiples of 1/16 m: then the transform, the FP32 voxel
+    means and the differences d are exact and only the residual arithmetic rounds."""
+    res = [0.5, 1.0]
+    edge = 2 ** 20
+
+    def cluster(k0):  # 4 points symmetric about the centre of each voxel with x keys k0 - 1, k0
+        out = []
+        for kx in (k0 - 1, k0):
+            for ky in (-1, 0):
+                for kz in (-1, 0):
+                    c = np.array([kx + 0.5, ky + 0.5, kz + 0.5]) * res[0]
+                    for a in ([0.125, 0.0625, 0.0625], [0.0625, -0.125, 0.0625]):
+                        out += [c + a, c - np.array(a)]
+        return np.array(out)  # FP64
+
+    beyond = np.array([[(edge + 0.5) * res[0], 0.125, 0.125], [(-edge - 0.5) * res[0], -0.1875, 0.3125]])
+    src64 = np.concatenate([cluster(edge - 1), cluster(-edge + 1), beyond])
+    src = src64.astype(np.float32)
+    assert np.array_equal(src.astype(np.float64), src64)  # every coordinate is a binary32 value
+    m = len(src) // 2 - 1
+    tA, tB = src[:m], src[m:2 * m]
+    n = len(src)
+
+    def cov(k):
+        return np.tile(np.array([0.01, 0, 0, 0.01, 0, 0.01], np.float32), (k, 1))
+
+    pts = [src, tA, tB]
+    of = [O.Frame(O.as_pts4(p), cov(len(p))) for p in pts]
+    om = [None, O.VMap(of[1].pts4, of[1].cov6, res), O.VMap(of[2].pts4, of[2].cov6, res)]
+    gf = [G.FrameData(torch.as_tensor(f.pts4, device="cuda"), torch.as_tensor(f.cov6, device="cuda")) for f in of]
+    gm = [None] + [G.VoxelMap(ctx, gf[i].pts4, gf[i].cov6, res, layout=layout) for i in (1, 2)]
+    for i in (1, 2):
+        for l in range(2):
+            assert gm[i].is_dense(l) == (layout == "dense")
+            assert np.array_equal(gm[i].export(l)["keys"].cpu().numpy(), om[i].export(l)["keys"])
+    assert om[1].export(0)["keys"][:, 0].max() == edge - 1 and om[2].export(0)["keys"][:, 0].min() == -edge
+    pairs = np.array([[0, 1], [0, 2]], np.int32)
+    for shift in (0.0, 0.3125):
+        poses = np.stack([np.eye(3, 4)] * 3)
+        poses[0, 0, 3] = shift
+        ref = O.linearize(of, om, pairs, poses, want_ids=True, want_comp=True)
+        got = G.linearize(ctx, gf, gm, pairs, poses, kernel="auto")
+        _check(got, ref)
+        gid = np.concatenate([G.correspondences(ctx, gf[0], gm[t], poses[0], poses[t]).cpu().numpy().reshape(-1)
+                              for t in (1, 2)])
+        assert np.array_equal(gid, ref["ids"])
+        ids = gid.reshape(2, n, 2)
+        if shift == 0.0:  # every point inside the range hits at both levels; the two beyond miss
+            assert (ids[0, :m] >= 0).all() and (ids[1, m:2 * m] >= 0).all()
+            assert (ids[:, n - 2:] < 0).all()
+        else:  # the shift moves the last x-voxel of A past 2^20 - 1 at level 0
+            assert (ids[0, :m, 0] < 0).any() and (ids[0, :m, 0] >= 0).any()
