@@ -128,6 +128,13 @@ const char* glim_last_error(const glim_ctx* ctx);
 int32_t glim_num_sms(const glim_ctx* ctx);
 /* Number of kernels this context has launched since creation (for accounting). */
 int64_t glim_kernel_launches(const glim_ctx* ctx);
+/* Testing hook with no counterpart in the paper: the allocation n allocations from now
+ * (0 = the next one) among all device and pinned host allocations of the library, in any
+ * context and thread, fails once as if the device were out of memory, so that tests reach
+ * every GLIM_ENOMEM path without exhausting a GPU.  n < 0 disables it (the default).  The
+ * call that meets the failure returns GLIM_ENOMEM (GLIM_ECUDA where the failure surfaces
+ * through a CUDA call's own status) and leaves its objects as they were. */
+void glim_debug_fail_allocation(int64_t n);
 /* Measured FP32 multiply-add throughput of the context's device in TFLOP/s (two flops per
  * FMA): eight independent register-resident FMA chains per thread, eight 256-thread blocks
  * per SM, `iters` x 128 FMAs per thread, best of three timed launches after a warm-up.  The
@@ -319,7 +326,9 @@ glim_status glim_plan_launch_timed(glim_plan* plan, int32_t slot);
 glim_status glim_plan_kernel_ms(glim_plan* plan, int32_t nslots, float* ms_out);
 /* Autotuner: time every (block, pts_per_thread) candidate of the persistent kernel on this
  * plan's batch at poses12 with CUDA events (`iters` timed launches each, after one warm-up),
- * keep the fastest in the plan, and write it to best_out (may be NULL). */
+ * keep the fastest in the plan, and write it to best_out (may be NULL).  On an error the
+ * plan returns to its original configuration where that succeeds, and otherwise keeps the
+ * last configuration that did: it stays launchable either way. */
 glim_status glim_plan_autotune(glim_plan* plan, const double* poses12, int32_t iters,
                                glim_lin_opts* best_out, float* best_ms_out);
 /* The options the plan currently uses. */

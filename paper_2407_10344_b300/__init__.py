@@ -5,11 +5,12 @@ this package only marshals arguments to it.  See ``api`` for the calls and ``aut
 the differentiable cost.
 """
 from .api import (ACC_FP32, ACC_FP64, ACC_KAHAN, Context, FrameData, GlimError, Plan, VoxelMap, backward,
-                  correspondences, estimate_covariances, frames_needed, gn_solve, graph_step, linearize, overlap,
+                  correspondences, debug_fail_allocation, estimate_covariances, frames_needed, gn_solve, graph_step,
+                  linearize, overlap,
                   shard_pairs,
                   spatial_order, to_pts4)
 
 __all__ = ["ACC_FP32", "ACC_FP64", "ACC_KAHAN", "Context", "FrameData", "GlimError", "Plan", "VoxelMap",
-           "backward", "correspondences", "estimate_covariances", "frames_needed", "gn_solve", "graph_step", "linearize",
+           "backward", "correspondences", "debug_fail_allocation", "estimate_covariances", "frames_needed", "gn_solve", "graph_step", "linearize",
            "overlap",
            "shard_pairs", "spatial_order", "to_pts4"]

@@ -40,6 +40,7 @@ SIGNATURES = {
     "glim_last_error": (C.c_char_p, [_vp]),
     "glim_num_sms": (_i32, [_vp]),
     "glim_kernel_launches": (_i64, [_vp]),
+    "glim_debug_fail_allocation": (None, [_i64]),
     "glim_fp32_fma_peak": (_i32, [_vp, _i32, C.POINTER(C.c_double)]),
     "glim_fp64_fma_peak": (_i32, [_vp, _i32, C.POINTER(C.c_double)]),
     "glim_estimate_covariances": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _vp, _vp]),

@@ -137,6 +137,12 @@ class Context:
             pass
 
 
+def debug_fail_allocation(n: int) -> None:
+    """Testing hook: the library's allocation n allocations from now (0 = the next one) fails
+    once as if the device were out of memory; n < 0 disables it.  Process-wide."""
+    _abi.load().glim_debug_fail_allocation(int(n))
+
+
 def to_pts4(points, weights=None, device="cuda"):
     """(n, 3) points (+ optional (n,) weights) -> contiguous float32 (n, 4) CUDA tensor."""
     p = torch.as_tensor(np.asarray(points, dtype=np.float32)) if not isinstance(points, torch.Tensor) else points

@@ -1,8 +1,23 @@
 // api.cu -- context lifetime, error reporting and pose helpers of the C ABI.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
 #include "common.cuh"
+
+// Allocation-failure injection for tests: the countdown is the number of allocations that
+// still succeed before one fails; negative disables it.  Process-wide, shared by all threads.
+static std::atomic<long long> g_fail_countdown{-1};
+
+bool alloc_should_fail() {
+  long long c = g_fail_countdown.load(std::memory_order_relaxed);
+  while (c >= 0) {
+    if (g_fail_countdown.compare_exchange_weak(c, c - 1, std::memory_order_relaxed)) return c == 0;
+  }
+  return false;
+}
+
+extern "C" void glim_debug_fail_allocation(int64_t n) { g_fail_countdown.store(n < 0 ? -1 : n); }
 
 glim_status set_error(glim_ctx* ctx, glim_status st, const char* fmt, ...) {
   if (!ctx) return st;
@@ -85,7 +100,7 @@ extern "C" glim_status glim_create(glim_ctx** out, int device, void* cuda_stream
     }
     ctx->own_stream = true;
   }
-  if (cudaMalloc(&ctx->d_status, sizeof(unsigned int)) != cudaSuccess ||
+  if (dmalloc(&ctx->d_status, sizeof(unsigned int)) != cudaSuccess ||
       cudaMemset(ctx->d_status, 0, sizeof(unsigned int)) != cudaSuccess) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;

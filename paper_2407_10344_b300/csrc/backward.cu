@@ -241,14 +241,14 @@ glim_status bwd_prepare(glim_plan* p, BwdScratch& sc) {
   if (src_list.empty()) src_list.push_back(0);
   sc.npp = npp;
   sc.ntot = frame_off[nframes];
-  if (cudaMalloc(&sc.pair_off, pair_off.size() * sizeof(int64_t)) != cudaSuccess ||
-      cudaMalloc(&sc.frame_off, frame_off.size() * sizeof(int64_t)) != cudaSuccess ||
-      cudaMalloc(&sc.src_begin, src_begin.size() * sizeof(int32_t)) != cudaSuccess ||
-      cudaMalloc(&sc.src_list, src_list.size() * sizeof(int32_t)) != cudaSuccess ||
-      cudaMalloc(&sc.tgt, tgt.size() * sizeof(int32_t)) != cudaSuccess ||
-      cudaMalloc(&sc.pp, size_t(std::max<int64_t>(npp, 1)) * sizeof(float4)) != cudaSuccess ||
-      cudaMalloc(&sc.part, size_t(std::max(p->nitems, 1)) * BSTRIDE * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&sc.pair_grad, size_t(std::max(npairs, 1)) * 12 * sizeof(double)) != cudaSuccess) {
+  if (dmalloc(&sc.pair_off, pair_off.size() * sizeof(int64_t)) != cudaSuccess ||
+      dmalloc(&sc.frame_off, frame_off.size() * sizeof(int64_t)) != cudaSuccess ||
+      dmalloc(&sc.src_begin, src_begin.size() * sizeof(int32_t)) != cudaSuccess ||
+      dmalloc(&sc.src_list, src_list.size() * sizeof(int32_t)) != cudaSuccess ||
+      dmalloc(&sc.tgt, tgt.size() * sizeof(int32_t)) != cudaSuccess ||
+      dmalloc(&sc.pp, size_t(std::max<int64_t>(npp, 1)) * sizeof(float4)) != cudaSuccess ||
+      dmalloc(&sc.part, size_t(std::max(p->nitems, 1)) * BSTRIDE * sizeof(double)) != cudaSuccess ||
+      dmalloc(&sc.pair_grad, size_t(std::max(npairs, 1)) * 12 * sizeof(double)) != cudaSuccess) {
     sc.release();
     return set_error(ctx, GLIM_ENOMEM, "backward: scratch allocation failed");
   }

@@ -47,6 +47,36 @@ glim_status cuda_check(glim_ctx* ctx, cudaError_t e, const char* what);
 // read and clear the device status word; map to a status code
 glim_status take_device_status(glim_ctx* ctx, const char* where);
 
+// ------------------------------------------------------------------ allocations
+// Every device and pinned host allocation of the library goes through these wrappers, so
+// that a test can make one chosen allocation fail (glim_debug_fail_allocation) and reach each
+// error path on the host; a failed wrapper leaves *p null and allocates nothing.
+bool alloc_should_fail();
+template <class T>
+inline cudaError_t dmalloc(T** p, size_t bytes) {
+  if (alloc_should_fail()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+template <class T>
+inline cudaError_t dmalloc_async(T** p, size_t bytes, cudaStream_t s) {
+  if (alloc_should_fail()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, s);
+}
+template <class T>
+inline cudaError_t hmalloc(T** p, size_t bytes) {
+  if (alloc_should_fail()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(reinterpret_cast<void**>(p), bytes);
+}
+
 // stream-ordered temporary device buffer
 template <class T>
 struct DevBuf {
@@ -62,7 +92,7 @@ struct DevBuf {
     s = stream;
     n = count;
     if (count == 0) return cudaSuccess;
-    return cudaMallocAsync((void**)&p, count * sizeof(T), stream);
+    return dmalloc_async(&p, count * sizeof(T), stream);
   }
   void release() {
     if (p) cudaFreeAsync(p, s);

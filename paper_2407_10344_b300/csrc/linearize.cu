@@ -183,53 +183,70 @@ void drop_graphs(glim_plan* p) {
 
 glim_status plan_configure(glim_plan* p, const glim_lin_opts& o) {
   glim_ctx* ctx = p->ctx;
-  drop_graphs(p);
-  cudaFree(p->d_items);
-  cudaFree(p->d_item_begin);
-  cudaFree(p->d_part);
-  p->d_items = nullptr;
-  p->d_item_begin = nullptr;
-  p->d_part = nullptr;
-  p->opts = o;
-  p->tile = o.block * o.pts_per_thread;
+  // Everything that can fail comes first; the plan changes only once all of it succeeded, so
+  // a failed reconfiguration (an autotuner candidate that meets an out-of-memory condition)
+  // leaves a plan that still launches its previous configuration.
+  if (o.kernel == 2 && !p->d_dmaps)
+    return set_error(ctx, GLIM_EINVAL, "the dense-grid kernel needs every target level to be a dense grid");
+  if (o.kernel == 3 && !p->d_hmaps)
+    return set_error(ctx, GLIM_EINVAL, "the hash kernel needs every target level to be a hash table");
+  const int lane = o.kernel == 1 ? 0 : (p->d_dmaps ? 1 : (p->d_hmaps ? 2 : 0));
+  const LinKernelInfo ki = pick_kernel(o.block, o.accum_mode, p->lmax, lane);
+  if (!ki.fn) return set_error(ctx, GLIM_EINVAL, "no kernel for block=%d ppt=%d acc=%d", o.block, o.pts_per_thread, o.accum_mode);
+  GLIM_CUDA(ctx, cudaFuncSetAttribute(reinterpret_cast<const void*>(ki.fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(ki.smem)));
+  const int tile = o.block * o.pts_per_thread;
   std::vector<Item> items;
   std::vector<int32_t> begin(p->npairs + 1, 0);
   for (int q = 0; q < p->npairs; ++q) {
     begin[q] = int32_t(items.size());
     const int64_t n = p->frames[p->pairs[q].src_frame].n;
-    for (int64_t s = 0; s < n; s += p->tile) items.push_back(Item{q, int32_t(s)});
+    for (int64_t s = 0; s < n; s += tile) items.push_back(Item{q, int32_t(s)});
   }
   begin[p->npairs] = int32_t(items.size());
-  p->nitems = int(items.size());
-  const size_t ni = std::max<size_t>(items.size(), 1);
-  GLIM_CUDA(ctx, cudaMalloc(&p->d_items, ni * sizeof(Item)));
-  GLIM_CUDA(ctx, cudaMalloc(&p->d_item_begin, begin.size() * sizeof(int32_t)));
-  GLIM_CUDA(ctx, cudaMalloc(&p->d_part, ni * PSTRIDE * sizeof(double)));
-  if (!items.empty())
-    GLIM_CUDA(ctx, cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice));
-  GLIM_CUDA(ctx, cudaMemcpy(p->d_item_begin, begin.data(), begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  if (o.kernel == 2 && !p->d_dmaps)
-    return set_error(ctx, GLIM_EINVAL, "the dense-grid kernel needs every target level to be a dense grid");
-  if (o.kernel == 3 && !p->d_hmaps)
-    return set_error(ctx, GLIM_EINVAL, "the hash kernel needs every target level to be a hash table");
-  p->lane_kernel = o.kernel == 1 ? 0 : (p->d_dmaps ? 1 : (p->d_hmaps ? 2 : 0));
-  p->opts.kernel = p->lane_kernel == 1 ? 2 : (p->lane_kernel == 2 ? 3 : 1);  // the kernel actually used
-  const LinKernelInfo ki = pick_kernel(o.block, o.accum_mode, p->lmax, p->lane_kernel);
-  p->kernel = ki.fn;
-  p->kernel_smem = ki.smem;
-  if (!p->kernel) return set_error(ctx, GLIM_EINVAL, "no kernel for block=%d ppt=%d acc=%d", o.block, o.pts_per_thread, o.accum_mode);
-  GLIM_CUDA(ctx, cudaFuncSetAttribute(reinterpret_cast<const void*>(p->kernel),
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(p->kernel_smem)));
+  const int nitems = int(items.size());
+  int grid = std::max(1, nitems);
   if (o.persistent == 1) {
     int per_sm = o.blocks_per_sm;
     if (per_sm == 0) {
-      GLIM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kernel, o.block, p->kernel_smem));
+      GLIM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki.fn, o.block, ki.smem));
       per_sm = std::max(per_sm, 1);
     }
-    p->grid = std::max(1, std::min(per_sm * ctx->num_sms, p->nitems));
-  } else {
-    p->grid = std::max(1, p->nitems);
+    grid = std::max(1, std::min(per_sm * ctx->num_sms, nitems));
   }
+  const size_t ni = std::max<size_t>(items.size(), 1);
+  Item* d_items = nullptr;
+  int32_t* d_begin = nullptr;
+  double* d_part = nullptr;
+  cudaError_t e = dmalloc(&d_items, ni * sizeof(Item));
+  if (e == cudaSuccess) e = dmalloc(&d_begin, begin.size() * sizeof(int32_t));
+  if (e == cudaSuccess) e = dmalloc(&d_part, ni * PSTRIDE * sizeof(double));
+  if (e == cudaSuccess && !items.empty())
+    e = cudaMemcpy(d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_begin, begin.data(), begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d_items);
+    cudaFree(d_begin);
+    cudaFree(d_part);
+    return cuda_check(ctx, e, "plan: work list");
+  }
+  // commit; launches in flight may still read the previous work list
+  cudaStreamSynchronize(ctx->stream);
+  drop_graphs(p);
+  cudaFree(p->d_items);
+  cudaFree(p->d_item_begin);
+  cudaFree(p->d_part);
+  p->d_items = d_items;
+  p->d_item_begin = d_begin;
+  p->d_part = d_part;
+  p->opts = o;
+  p->tile = tile;
+  p->nitems = nitems;
+  p->lane_kernel = lane;
+  p->opts.kernel = lane == 1 ? 2 : (lane == 2 ? 3 : 1);  // the kernel actually used
+  p->kernel = ki.fn;
+  p->kernel_smem = ki.smem;
+  p->grid = grid;
   return GLIM_OK;
 }
 
@@ -532,7 +549,7 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
     for (size_t i = 0; i < maps.size(); ++i) fill_dense_map(maps[i], dmd[i]);
   std::vector<HashMapDev> hmd(std::max<size_t>(maps.size(), 1));
   if (all_hash) {
-    if (cudaMalloc(&p->d_empty_slots, 16 * sizeof(VoxSlot)) != cudaSuccess ||
+    if (dmalloc(&p->d_empty_slots, 16 * sizeof(VoxSlot)) != cudaSuccess ||
         cudaMemset(p->d_empty_slots, 0x80, 16 * sizeof(VoxSlot)) != cudaSuccess) {
       glim_plan_destroy(p);
       return set_error(ctx, GLIM_ENOMEM, "plan: device allocation failed");
@@ -547,32 +564,32 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
     glim_plan_destroy(p);
     return s;
   };
-  if (cudaMalloc(&p->d_frames, fd.size() * sizeof(FrameDev)) != cudaSuccess ||
-      cudaMalloc(&p->d_pairs, pd.size() * sizeof(PairDev)) != cudaSuccess ||
-      cudaMalloc(&p->d_maps, md.size() * sizeof(MapDev)) != cudaSuccess ||
-      cudaMalloc(&p->d_head, sizeof(int)) != cudaSuccess)
+  if (dmalloc(&p->d_frames, fd.size() * sizeof(FrameDev)) != cudaSuccess ||
+      dmalloc(&p->d_pairs, pd.size() * sizeof(PairDev)) != cudaSuccess ||
+      dmalloc(&p->d_maps, md.size() * sizeof(MapDev)) != cudaSuccess ||
+      dmalloc(&p->d_head, sizeof(int)) != cudaSuccess)
     return fail(set_error(ctx, GLIM_ENOMEM, "plan: device allocation failed"));
   cudaMemcpy(p->d_frames, fd.data(), fd.size() * sizeof(FrameDev), cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_pairs, pd.data(), pd.size() * sizeof(PairDev), cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_maps, md.data(), md.size() * sizeof(MapDev), cudaMemcpyHostToDevice);
   if (all_dense) {
-    if (cudaMalloc(&p->d_dmaps, dmd.size() * sizeof(DenseMapDev)) != cudaSuccess)
+    if (dmalloc(&p->d_dmaps, dmd.size() * sizeof(DenseMapDev)) != cudaSuccess)
       return fail(set_error(ctx, GLIM_ENOMEM, "plan: device allocation failed"));
     cudaMemcpy(p->d_dmaps, dmd.data(), dmd.size() * sizeof(DenseMapDev), cudaMemcpyHostToDevice);
   }
   if (all_hash) {
-    if (cudaMalloc(&p->d_hmaps, hmd.size() * sizeof(HashMapDev)) != cudaSuccess)
+    if (dmalloc(&p->d_hmaps, hmd.size() * sizeof(HashMapDev)) != cudaSuccess)
       return fail(set_error(ctx, GLIM_ENOMEM, "plan: device allocation failed"));
     cudaMemcpy(p->d_hmaps, hmd.data(), hmd.size() * sizeof(HashMapDev), cudaMemcpyHostToDevice);
   }
   p->in_bytes = std::max<size_t>(size_t(npairs) * (sizeof(PoseF) + 12 * sizeof(double)), 16);
   p->out_bytes = std::max<size_t>(size_t(npairs) * (157 * sizeof(double) + sizeof(int64_t)), 16);
   const size_t fpose_bytes = std::max<size_t>(size_t(nframes) * 12 * sizeof(double), 16);
-  if (cudaMalloc(&p->d_in, p->in_bytes) != cudaSuccess || cudaMalloc(&p->d_out, p->out_bytes) != cudaSuccess ||
-      cudaMalloc(&p->d_fposes, fpose_bytes) != cudaSuccess ||
-      cudaMalloc(&p->d_pair_frames, std::max(npairs, 1) * sizeof(int2)) != cudaSuccess ||
-      cudaMallocHost(&p->h_fposes, fpose_bytes) != cudaSuccess ||
-      cudaMallocHost(&p->h_out, p->out_bytes) != cudaSuccess)
+  if (dmalloc(&p->d_in, p->in_bytes) != cudaSuccess || dmalloc(&p->d_out, p->out_bytes) != cudaSuccess ||
+      dmalloc(&p->d_fposes, fpose_bytes) != cudaSuccess ||
+      dmalloc(&p->d_pair_frames, std::max(npairs, 1) * sizeof(int2)) != cudaSuccess ||
+      hmalloc(&p->h_fposes, fpose_bytes) != cudaSuccess ||
+      hmalloc(&p->h_out, p->out_bytes) != cudaSuccess)
     return fail(set_error(ctx, GLIM_ENOMEM, "plan: serialized block allocation failed"));
   {
     std::vector<int2> pf(std::max(npairs, 1), make_int2(0, 0));
@@ -770,36 +787,48 @@ extern "C" glim_status glim_plan_autotune(glim_plan* p, const double* poses12, i
   float best_ms = 1e30f;
   cudaEvent_t e0, e1;
   GLIM_CUDA(ctx, cudaEventCreate(&e0));
-  GLIM_CUDA(ctx, cudaEventCreate(&e1));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return set_error(ctx, GLIM_ECUDA, "plan_autotune: cudaEventCreate failed");
+  }
   const int blocks[] = {128, 256};
   const int ppts[] = {8, 16, 32, 64};
-  for (int bl : blocks)
-    for (int pp : ppts) {
-      glim_lin_opts o = base;
-      o.block = bl;
-      o.pts_per_thread = pp;
-      o.persistent = 1;
-      o.blocks_per_sm = 0;
-      st = plan_configure(p, o);
-      if (st != GLIM_OK) break;
-      st = plan_enqueue_kernels(p);  // warm-up
-      if (st != GLIM_OK) break;
-      cudaEventRecord(e0, ctx->stream);
-      for (int i = 0; i < iters && st == GLIM_OK; ++i) st = plan_enqueue_kernels(p);
-      cudaEventRecord(e1, ctx->stream);
-      if (st != GLIM_OK) break;
-      GLIM_CUDA(ctx, cudaEventSynchronize(e1));
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= iters;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = o;
-      }
+  for (int c = 0; c < 8 && st == GLIM_OK; ++c) {
+    glim_lin_opts o = base;
+    o.block = blocks[c / 4];
+    o.pts_per_thread = ppts[c % 4];
+    o.persistent = 1;
+    o.blocks_per_sm = 0;
+    st = plan_configure(p, o);
+    if (st == GLIM_OK) st = plan_enqueue_kernels(p);  // warm-up
+    if (st != GLIM_OK) break;
+    cudaEventRecord(e0, ctx->stream);
+    for (int i = 0; i < iters && st == GLIM_OK; ++i) st = plan_enqueue_kernels(p);
+    cudaEventRecord(e1, ctx->stream);
+    if (st != GLIM_OK) break;
+    const cudaError_t ce = cudaEventSynchronize(e1);
+    if (ce != cudaSuccess) {
+      st = cuda_check(ctx, ce, "plan_autotune: cudaEventSynchronize");
+      break;
     }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= iters;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = o;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (st != GLIM_OK) return st;
+  if (st != GLIM_OK) {
+    // keep the error, and go back to the original configuration where that is possible (a
+    // failed reconfiguration leaves the plan in the last one that succeeded)
+    const std::string msg = ctx->err;
+    plan_configure(p, base);
+    ctx->err = msg;
+    return st;
+  }
   st = plan_configure(p, best);
   if (st != GLIM_OK) return st;
   if (best_out) *best_out = best;

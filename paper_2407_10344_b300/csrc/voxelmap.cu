@@ -349,11 +349,11 @@ struct Canon {
 glim_status canon_alloc(glim_ctx* ctx, Canon& c, int64_t m) {
   c.m = m;
   const size_t mm = size_t(std::max<int64_t>(m, 1));
-  GLIM_CUDA(ctx, cudaMalloc(&c.key, mm * sizeof(unsigned long long)));
-  GLIM_CUDA(ctx, cudaMalloc(&c.sum, mm * 9 * sizeof(double)));
-  GLIM_CUDA(ctx, cudaMalloc(&c.count, mm * sizeof(int32_t)));
-  GLIM_CUDA(ctx, cudaMalloc(&c.mean, mm * 3 * sizeof(float)));
-  GLIM_CUDA(ctx, cudaMalloc(&c.cov, mm * 6 * sizeof(float)));
+  GLIM_CUDA(ctx, dmalloc(&c.key, mm * sizeof(unsigned long long)));
+  GLIM_CUDA(ctx, dmalloc(&c.sum, mm * 9 * sizeof(double)));
+  GLIM_CUDA(ctx, dmalloc(&c.count, mm * sizeof(int32_t)));
+  GLIM_CUDA(ctx, dmalloc(&c.mean, mm * 3 * sizeof(float)));
+  GLIM_CUDA(ctx, dmalloc(&c.cov, mm * 6 * sizeof(float)));
   return GLIM_OK;
 }
 
@@ -431,7 +431,7 @@ glim_status build_tables(glim_ctx* ctx, glim_vmap* vm, int l, int layout) {
     vm->log2cap[l] = 0;
     vm->max_probe[l] = 1;
     // one empty record before cell 0: lookups outside the box may read it instead of branching
-    GLIM_CUDA(ctx, cudaMalloc(&vm->slots_alloc[l], (ncell + 1) * sizeof(VoxSlot)));
+    GLIM_CUDA(ctx, dmalloc(&vm->slots_alloc[l], (ncell + 1) * sizeof(VoxSlot)));
     GLIM_CUDA(ctx, cudaMemsetAsync(vm->slots_alloc[l], 0x80, (ncell + 1) * sizeof(VoxSlot), ctx->stream));
     vm->slots[l] = vm->slots_alloc[l] + 1;
     k_dense_build<<<ceil_div_i(m, 256), 256, 0, ctx->stream>>>(vm->vkey[l], vm->vmean[l], vm->vcov[l], m,
@@ -443,9 +443,9 @@ glim_status build_tables(glim_ctx* ctx, glim_vmap* vm, int l, int layout) {
   const int64_t cap = std::max<int64_t>(16, int64_t(1) << log2_ceil(4 * m));  // load <= 1/4
   vm->cap[l] = cap;
   vm->log2cap[l] = log2_ceil(cap);
-  GLIM_CUDA(ctx, cudaMalloc(&vm->slots_alloc[l], cap * sizeof(VoxSlot)));
+  GLIM_CUDA(ctx, dmalloc(&vm->slots_alloc[l], cap * sizeof(VoxSlot)));
   vm->slots[l] = vm->slots_alloc[l];
-  GLIM_CUDA(ctx, cudaMalloc(&vm->slot_id[l], cap * sizeof(int32_t)));
+  GLIM_CUDA(ctx, dmalloc(&vm->slot_id[l], cap * sizeof(int32_t)));
   GLIM_CUDA(ctx, cudaMemsetAsync(vm->slots[l], 0x80, cap * sizeof(VoxSlot), ctx->stream));
   GLIM_CUDA(ctx, cudaMemsetAsync(vm->slot_id[l], 0xFF, cap * sizeof(int32_t), ctx->stream));
   if (m == 0) {
