@@ -309,6 +309,7 @@ glim_status bwd_run(glim_plan* p, const BwdScratch& sc, int32_t omega_grad_full,
 extern "C" glim_status glim_backward(glim_ctx* ctx, const glim_frame* frames, int32_t nframes, const glim_pair* pairs,
                                      int32_t npairs, const double* poses12, int32_t omega_grad_full,
                                      int32_t validate_surface, double* dxi_out, float* dmu_out, float* dw_out) {
+  GLIM_RANGE("glim_backward");
   if (!ctx) return GLIM_EINVAL;
   if (!poses12 || (nframes > 0 && !dxi_out)) return set_error(ctx, GLIM_EINVAL, "backward: null argument");
   glim_lin_opts o{};
@@ -335,6 +336,7 @@ extern "C" glim_status glim_backward(glim_ctx* ctx, const glim_frame* frames, in
 
 extern "C" glim_status glim_plan_backward(glim_plan* p, const double* poses12, int32_t omega_grad_full,
                                           double* dxi_out, float* dmu_out, float* dw_out) {
+  GLIM_RANGE("glim_plan_backward");
   if (!p || !poses12) return GLIM_EINVAL;
   glim_ctx* ctx = p->ctx;
   if (p->nframes > 0 && !dxi_out) return set_error(ctx, GLIM_EINVAL, "plan_backward: null argument");

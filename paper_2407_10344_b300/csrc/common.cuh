@@ -10,7 +10,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/glim_lin.h"
+
+// An NVTX range for the lifetime of a scope, named after the entry point: a profiler
+// (ncu --nvtx, Nsight Systems) attributes the call's launches to it; with no tool attached
+// a push and a pop cost a few nanoseconds.
+struct NvtxScope {
+  explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+  NvtxScope(const NvtxScope&) = delete;
+  NvtxScope& operator=(const NvtxScope&) = delete;
+};
+#define GLIM_RANGE(name) NvtxScope glim_nvtx_scope_(name)
 
 // ------------------------------------------------------------------ context
 struct glim_ctx {

@@ -441,6 +441,7 @@ glim_status knn_all_by_scan(glim_ctx* ctx, const GridArgs& a) {
 
 extern "C" glim_status glim_estimate_covariances(glim_ctx* ctx, const float* pts4, int64_t n, int32_t k,
                                                  int32_t reg_mode, float eps, float* cov6_out, float* normal3_out) {
+  GLIM_RANGE("glim_estimate_covariances");
   if (!ctx) return GLIM_EINVAL;
   if (n < 0 || k < 3 || k > 32 || k > n || (reg_mode != 0 && reg_mode != 1) || !(eps >= 0.f) ||
       (n > 0 && (!pts4 || !cov6_out)))

@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(1024) k_reduce_solve(const double* __restrict_
 extern "C" glim_status glim_graph_step(glim_ctx* ctx, const int32_t* pair_frames, int32_t npairs, int32_t nframes,
                                        const double* H, const double* b, int32_t fixed_frame, double lambda,
                                        double* xi_out, double* H_out, double* b_out) {
+  GLIM_RANGE("glim_graph_step");
   if (!ctx) return GLIM_EINVAL;
   if (nframes < 1 || nframes > MAX_FRAMES || npairs < 0 || (npairs > 0 && (!pair_frames || !H || !b)) || !xi_out ||
       fixed_frame < -1 || fixed_frame >= nframes || !(lambda >= 0.0) || !std::isfinite(lambda))

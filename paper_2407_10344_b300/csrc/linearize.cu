@@ -490,6 +490,7 @@ glim_status validate_batch(glim_ctx* ctx, const glim_frame* frames, int32_t nfra
 extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames, int32_t nframes,
                                         const glim_pair* pairs, int32_t npairs, const glim_lin_opts* opts,
                                         glim_plan** out) {
+  GLIM_RANGE("glim_plan_create");
   if (!ctx || !out) return GLIM_EINVAL;
   *out = nullptr;
   glim_status st = validate_batch(ctx, frames, nframes, pairs, npairs);
@@ -633,6 +634,7 @@ extern "C" void glim_plan_destroy(glim_plan* p) {
 }
 
 extern "C" glim_status glim_plan_set_poses(glim_plan* p, const double* poses12) {
+  GLIM_RANGE("glim_plan_set_poses");
   if (!p || !poses12) return GLIM_EINVAL;
   glim_ctx* ctx = p->ctx;
   // the pinned block may still be read by an earlier upload
@@ -655,6 +657,7 @@ extern "C" glim_status glim_plan_relative_poses(glim_plan* p, double* rt64_out, 
 }
 
 extern "C" glim_status glim_plan_launch(glim_plan* p) {
+  GLIM_RANGE("glim_plan_launch");
   if (!p) return GLIM_EINVAL;
   if (maps_current(p) != GLIM_OK) return GLIM_EINVAL;
   glim_ctx* ctx = p->ctx;
@@ -669,6 +672,7 @@ extern "C" glim_status glim_plan_launch(glim_plan* p) {
 }
 
 extern "C" glim_status glim_plan_launch_timed(glim_plan* p, int32_t slot) {
+  GLIM_RANGE("glim_plan_launch_timed");
   if (!p || slot < 0 || slot >= 4096) return GLIM_EINVAL;
   if (maps_current(p) != GLIM_OK) return GLIM_EINVAL;
   glim_ctx* ctx = p->ctx;
@@ -706,6 +710,7 @@ extern "C" glim_status glim_plan_device_outputs(glim_plan* p, double** e, double
 
 extern "C" glim_status glim_plan_linearize(glim_plan* p, const double* poses12, double* e_out, double* H_out,
                                            double* b_out, int64_t* inliers_out) {
+  GLIM_RANGE("glim_plan_linearize");
   if (!p || !poses12) return GLIM_EINVAL;
   if (maps_current(p) != GLIM_OK) return GLIM_EINVAL;
   glim_ctx* ctx = p->ctx;
@@ -737,6 +742,7 @@ extern "C" glim_status glim_plan_linearize(glim_plan* p, const double* poses12, 
 
 extern "C" glim_status glim_plan_linearize_pinned(glim_plan* p, const double* poses12, const double** e,
                                                   const double** H, const double** b, const int64_t** inl) {
+  GLIM_RANGE("glim_plan_linearize_pinned");
   if (!p || !poses12) return GLIM_EINVAL;
   if (maps_current(p) != GLIM_OK) return GLIM_EINVAL;
   glim_ctx* ctx = p->ctx;
@@ -777,6 +783,7 @@ extern "C" glim_status glim_plan_get_opts(const glim_plan* p, glim_lin_opts* out
 
 extern "C" glim_status glim_plan_autotune(glim_plan* p, const double* poses12, int32_t iters, glim_lin_opts* best_out,
                                           float* best_ms_out) {
+  GLIM_RANGE("glim_plan_autotune");
   if (!p || !poses12 || iters < 1) return GLIM_EINVAL;
   if (maps_current(p) != GLIM_OK) return GLIM_EINVAL;
   glim_ctx* ctx = p->ctx;
@@ -840,6 +847,7 @@ extern "C" glim_status glim_linearize_factors(glim_ctx* ctx, const glim_frame* f
                                               const glim_pair* pairs, int32_t npairs, const double* poses12,
                                               const glim_lin_opts* opts, double* e_out, double* H_out,
                                               double* b_out, int64_t* inliers_out) {
+  GLIM_RANGE("glim_linearize_factors");
   if (!ctx) return GLIM_EINVAL;
   if (!poses12 && nframes > 0) return set_error(ctx, GLIM_EINVAL, "linearize: null poses");
   glim_plan* p = nullptr;
@@ -856,6 +864,7 @@ extern "C" glim_status glim_linearize_factors_plain(glim_ctx* ctx, const glim_fr
                                                     const glim_pair* pairs, int32_t npairs, const double* poses12,
                                                     const glim_lin_opts* opts, double* e_out, double* H_out,
                                                     double* b_out, int64_t* inliers_out) {
+  GLIM_RANGE("glim_linearize_factors_plain");
   if (!ctx) return GLIM_EINVAL;
   glim_lin_opts o{};
   if (opts) o = *opts;

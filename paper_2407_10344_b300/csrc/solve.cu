@@ -56,6 +56,7 @@ __global__ void k_cholesky_solve(const double* __restrict__ H, int ldh, int64_t 
 extern "C" glim_status glim_gn_solve(glim_ctx* ctx, const double* H, int32_t ldh, int64_t stride_H, const double* b,
                                      int64_t stride_b, int32_t dim, int64_t count, double* xi_out,
                                      int32_t* status_out) {
+  GLIM_RANGE("glim_gn_solve");
   if (!ctx) return GLIM_EINVAL;
   if (dim < 1 || dim > MAXD || count < 0 || ldh < dim || (count > 0 && (!H || !b || !xi_out)))
     return set_error(ctx, GLIM_EINVAL, "gn_solve: bad arguments (dim=%d ldh=%d)", dim, ldh);

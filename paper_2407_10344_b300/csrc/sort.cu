@@ -224,6 +224,7 @@ __global__ void k_morton_keys(const float4* __restrict__ pts, int64_t n, float i
 
 extern "C" glim_status glim_spatial_order(glim_ctx* ctx, const float* pts4, int64_t n, float cell,
                                           int32_t* perm_out) {
+  GLIM_RANGE("glim_spatial_order");
   if (!ctx) return GLIM_EINVAL;
   if (n < 0 || n > 0x7FFFFFFFll || !(cell > 0.f) || (n > 0 && (!pts4 || !perm_out)))
     return set_error(ctx, GLIM_EINVAL, "spatial_order: bad arguments");

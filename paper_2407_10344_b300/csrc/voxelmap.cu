@@ -548,6 +548,7 @@ extern "C" glim_status glim_build_voxelmap(glim_ctx* ctx, const float* pts4, con
 extern "C" glim_status glim_build_voxelmap_ex(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n,
                                               const double* resolutions, int32_t levels, int32_t layout,
                                               glim_vmap** out) {
+  GLIM_RANGE("glim_build_voxelmap_ex");
   if (!ctx || !out) return GLIM_EINVAL;
   if (layout < 0 || layout > 2) return set_error(ctx, GLIM_EINVAL, "build_voxelmap: layout must be 0, 1 or 2");
   *out = nullptr;
@@ -581,6 +582,7 @@ extern "C" glim_status glim_build_voxelmap_ex(glim_ctx* ctx, const float* pts4, 
 
 extern "C" glim_status glim_vmap_insert(glim_ctx* ctx, glim_vmap* vm, const float* pts4, const float* cov6, int64_t n,
                                         int32_t layout) {
+  GLIM_RANGE("glim_vmap_insert");
   if (!ctx || !vm) return GLIM_EINVAL;
   if (layout < 0 || layout > 2) return set_error(ctx, GLIM_EINVAL, "vmap_insert: layout must be 0, 1 or 2");
   if (n < 0 || (n > 0 && (!pts4 || !cov6)))
@@ -647,6 +649,7 @@ extern "C" glim_status glim_vmap_export(glim_ctx* ctx, const glim_vmap* vm, int3
 extern "C" glim_status glim_correspondences(glim_ctx* ctx, const glim_frame* src, const glim_vmap* tgt,
                                             const double* pose_s12, const double* pose_t12,
                                             int32_t validate_surface, int32_t* ids_out) {
+  GLIM_RANGE("glim_correspondences");
   if (!ctx || !src || !tgt || !pose_s12 || !pose_t12 || (src->n > 0 && !ids_out))
     return ctx ? set_error(ctx, GLIM_EINVAL, "correspondences: null argument") : GLIM_EINVAL;
   if (src->n <= 0) return GLIM_OK;
@@ -665,6 +668,7 @@ extern "C" glim_status glim_correspondences(glim_ctx* ctx, const glim_frame* src
 
 extern "C" glim_status glim_overlap(glim_ctx* ctx, const glim_frame* frames, int32_t nframes, const glim_pair* pairs,
                                     int32_t npairs, const double* poses12, int32_t level, double* overlap_out) {
+  GLIM_RANGE("glim_overlap");
   if (!ctx || !frames || !pairs || !poses12 || !overlap_out || npairs < 0)
     return ctx ? set_error(ctx, GLIM_EINVAL, "overlap: null argument") : GLIM_EINVAL;
   if (npairs == 0) return GLIM_OK;
