@@ -328,6 +328,42 @@ def small_workloads(G, ctx, dev):
                             "ms_per_iteration": med(lm_iter, reps=10),
                             "note": "serialized upload, graph launch, download, device assembly + 66x66 Cholesky"}
 
+    # a submap grown by merging keyframes into it one at a time (incremental voxelmap
+    # insertion), against building the same map from all its points at once
+    wg = synth.corridor(seed=7)
+    res_g = [0.5, 1.0, 2.0]
+    pts_g, cov_g = [], []
+    for f in range(1, len(wg.points)):
+        T = np.asarray(wg.poses_true[f], np.float64)
+        p4 = G.to_pts4((wg.points[f] @ T[:, :3].T + T[:, 3]).astype(np.float32), device=dev)
+        c, _ = G.estimate_covariances(ctx, p4, k=10)
+        pts_g.append(p4)
+        cov_g.append(c)
+    torch.cuda.synchronize()
+
+    def grow():
+        gm = G.VoxelMap(ctx, pts_g[0], cov_g[0], res_g)
+        each = []
+        for p4, c in zip(pts_g[1:], cov_g[1:]):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            gm.insert(p4, c)
+            torch.cuda.synchronize()
+            each.append((time.perf_counter() - t0) * 1e3)
+        return gm, each
+
+    grow()  # warm-up
+    gm, each = grow()
+    P_all, C_all = torch.cat(pts_g), torch.cat(cov_g)
+    out["voxelmap_insert"] = {
+        "workload": "corridor keyframes (seed 7) in map coordinates merged one by one into a 0.5/1/2 m map",
+        "frames": len(pts_g), "points": int(P_all.shape[0]),
+        "voxels_level0": gm.info(0)["n_voxels"], "dense_grid": bool(gm.is_dense(0)),
+        "ms_per_insert_median": float(np.median(each)), "ms_per_insert_max": float(np.max(each)),
+        "ms_build_all_points": med(lambda: G.VoxelMap(ctx, P_all, C_all, res_g).free(), reps=5)}
+    gm.free()
+    del pts_g, cov_g, P_all, C_all
+
     # precision / scale batch: one 1M-point scan against a 20M-point terrain map at 0.25 m
     wt = synth.terrain()
     ft, mt = prep(wt)
