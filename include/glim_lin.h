@@ -193,6 +193,9 @@ glim_status glim_build_voxelmap(glim_ctx* ctx, const float* pts4, const float* c
 glim_status glim_build_voxelmap_ex(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n,
                                    const double* resolutions, int32_t levels, int32_t layout,
                                    glim_vmap** out);
+/* Free a voxelmap.  Waits for the device first, so that launches in flight on any stream that
+ * read its tables complete.  Plans created on the map keep pointers to its tables: destroy
+ * them before freeing the map. */
 void glim_vmap_free(glim_vmap* vmap);
 /* Incremental insertion (NEXT: submaps grow as frames are merged into them, Sec. V-A; the
  * voxel statistics are the running means of Sec. III-C).  Adds n map-frame points (pts4 /

@@ -173,6 +173,11 @@ def spatial_order(ctx: Context, pts4: torch.Tensor, cell: float = 0.5) -> torch.
     return perm.long()
 
 
+# Number of VoxelMap.free calls so far: a plan re-checks its target maps before a launch
+# only when a map was freed since its last check (a freed map's tables are gone).
+_FREED_MAPS = 0
+
+
 class VoxelMap:
     """Multi-resolution voxelmap of one frame (library-owned device tables)."""
 
@@ -231,6 +236,8 @@ class VoxelMap:
 
     def free(self):
         if getattr(self, "h", None):
+            global _FREED_MAPS
+            _FREED_MAPS += 1
             self.ctx.lib.glim_vmap_free(self.h)
             self.h = None
 
@@ -359,11 +366,21 @@ class Plan:
         self.h = h
         _LIVE["plans"].add(self)
         self._host = _outputs(P, "host")
+        self._freed_seen = _FREED_MAPS
+
+    def _maps_alive(self):
+        """Refuse to launch once a target map of the plan has been freed (its device tables
+        no longer exist)."""
+        if self._freed_seen != _FREED_MAPS:
+            if any(m is not None and not getattr(m, "h", None) for m in self.vmaps):
+                raise GlimError(-1, "a target voxelmap of this plan has been freed")
+            self._freed_seen = _FREED_MAPS
 
     def linearize(self, poses, out=None, copy=True):
         """One upload, one graph launch, one download; returns host arrays (e, H, b, inliers).
         copy=False returns read-only views of the plan's pinned output block instead (no host
         copy), valid until the plan's next launch."""
+        self._maps_alive()
         Pz = _poses(poses, self.nframes)
         if not copy and out is None:
             ptrs = [C.c_void_p() for _ in range(4)]
@@ -393,6 +410,7 @@ class Plan:
         return T, p32
 
     def set_poses(self, poses):
+        self._maps_alive()
         Pz = _poses(poses, self.nframes)
         self.ctx.call("plan_set_poses", self.ctx.lib.glim_plan_set_poses, self.h, _ptr(Pz))
 
@@ -403,6 +421,7 @@ class Plan:
     def backward(self, poses, omega_grad_full=True):
         """dE/dxi (nframes, 6) f64, dE/dmu (sum n, 3) f32, dE/dw (sum n,) f32 of the plan's
         batch (the plan must use block 256, pts_per_thread 1)."""
+        self._maps_alive()
         Pz = _poses(poses, self.nframes)
         dev = self.frames[0].pts4.device
         ntot = sum(f.n for f in self.frames)
@@ -414,10 +433,12 @@ class Plan:
         return dxi, dmu, dw
 
     def launch(self):
+        self._maps_alive()
         self.ctx.call("plan_launch", self.ctx.lib.glim_plan_launch, self.h)
 
     def launch_timed(self, slot):
         """Direct launches with CUDA events around the linearization kernel (timing slot)."""
+        self._maps_alive()
         self.ctx.call("plan_launch_timed", self.ctx.lib.glim_plan_launch_timed, self.h, slot)
 
     def kernel_ms(self, nslots):
@@ -437,6 +458,7 @@ class Plan:
         return e.value, H.value, b.value, inl.value
 
     def autotune(self, poses, iters=5):
+        self._maps_alive()
         Pz = _poses(poses, self.nframes)
         o = _abi.LinOpts()
         ms = C.c_float()

@@ -261,6 +261,15 @@ int log2_ceil(int64_t x) {
   return l;
 }
 
+// A map's arrays come from the stream-ordered allocator (cudaMallocAsync on the context
+// stream).  free_on returns one in the order of stream s; free_level releases a level's arrays
+// at once and does not wait for the device: every caller has made sure first that no launch
+// on any stream still reads them.
+template <class T>
+void free_on(T* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
 void free_level(glim_vmap* vm, int l) {
   cudaFree(vm->grid[l]);
   cudaFree(vm->slots_alloc[l]);
@@ -332,12 +341,13 @@ struct Canon {
   int32_t* count = nullptr;
   float* mean = nullptr;
   float* cov = nullptr;
+  cudaStream_t s = nullptr;  // the stream the arrays were allocated on (stream-ordered)
   void release() {
-    cudaFree(key);
-    cudaFree(sum);
-    cudaFree(count);
-    cudaFree(mean);
-    cudaFree(cov);
+    free_on(key, s);
+    free_on(sum, s);
+    free_on(count, s);
+    free_on(mean, s);
+    free_on(cov, s);
     key = nullptr;
     sum = nullptr;
     count = nullptr;
@@ -348,12 +358,13 @@ struct Canon {
 
 glim_status canon_alloc(glim_ctx* ctx, Canon& c, int64_t m) {
   c.m = m;
+  c.s = ctx->stream;
   const size_t mm = size_t(std::max<int64_t>(m, 1));
-  GLIM_CUDA(ctx, dmalloc(&c.key, mm * sizeof(unsigned long long)));
-  GLIM_CUDA(ctx, dmalloc(&c.sum, mm * 9 * sizeof(double)));
-  GLIM_CUDA(ctx, dmalloc(&c.count, mm * sizeof(int32_t)));
-  GLIM_CUDA(ctx, dmalloc(&c.mean, mm * 3 * sizeof(float)));
-  GLIM_CUDA(ctx, dmalloc(&c.cov, mm * 6 * sizeof(float)));
+  GLIM_CUDA(ctx, dmalloc_async(&c.key, mm * sizeof(unsigned long long), ctx->stream));
+  GLIM_CUDA(ctx, dmalloc_async(&c.sum, mm * 9 * sizeof(double), ctx->stream));
+  GLIM_CUDA(ctx, dmalloc_async(&c.count, mm * sizeof(int32_t), ctx->stream));
+  GLIM_CUDA(ctx, dmalloc_async(&c.mean, mm * 3 * sizeof(float), ctx->stream));
+  GLIM_CUDA(ctx, dmalloc_async(&c.cov, mm * 6 * sizeof(float), ctx->stream));
   return GLIM_OK;
 }
 
@@ -391,9 +402,10 @@ void adopt_canon(glim_vmap* vm, int l, Canon& c) {
 // Lookup tables of a level (dense grid or hash) from its canonical arrays; replaces any
 // existing tables of the level.
 glim_status build_tables(glim_ctx* ctx, glim_vmap* vm, int l, int layout) {
-  cudaFree(vm->slots_alloc[l]);
-  cudaFree(vm->slot_id[l]);
-  cudaFree(vm->grid[l]);
+  // the level belongs to a map under construction: only this stream has used its tables
+  free_on(vm->slots_alloc[l], ctx->stream);
+  free_on(vm->slot_id[l], ctx->stream);
+  free_on(vm->grid[l], ctx->stream);
   vm->slots[l] = nullptr;
   vm->slots_alloc[l] = nullptr;
   vm->slot_id[l] = nullptr;
@@ -431,7 +443,7 @@ glim_status build_tables(glim_ctx* ctx, glim_vmap* vm, int l, int layout) {
     vm->log2cap[l] = 0;
     vm->max_probe[l] = 1;
     // one empty record before cell 0: lookups outside the box may read it instead of branching
-    GLIM_CUDA(ctx, dmalloc(&vm->slots_alloc[l], (ncell + 1) * sizeof(VoxSlot)));
+    GLIM_CUDA(ctx, dmalloc_async(&vm->slots_alloc[l], (ncell + 1) * sizeof(VoxSlot), ctx->stream));
     GLIM_CUDA(ctx, cudaMemsetAsync(vm->slots_alloc[l], 0x80, (ncell + 1) * sizeof(VoxSlot), ctx->stream));
     vm->slots[l] = vm->slots_alloc[l] + 1;
     k_dense_build<<<ceil_div_i(m, 256), 256, 0, ctx->stream>>>(vm->vkey[l], vm->vmean[l], vm->vcov[l], m,
@@ -443,9 +455,9 @@ glim_status build_tables(glim_ctx* ctx, glim_vmap* vm, int l, int layout) {
   const int64_t cap = std::max<int64_t>(16, int64_t(1) << log2_ceil(4 * m));  // load <= 1/4
   vm->cap[l] = cap;
   vm->log2cap[l] = log2_ceil(cap);
-  GLIM_CUDA(ctx, dmalloc(&vm->slots_alloc[l], cap * sizeof(VoxSlot)));
+  GLIM_CUDA(ctx, dmalloc_async(&vm->slots_alloc[l], cap * sizeof(VoxSlot), ctx->stream));
   vm->slots[l] = vm->slots_alloc[l];
-  GLIM_CUDA(ctx, dmalloc(&vm->slot_id[l], cap * sizeof(int32_t)));
+  GLIM_CUDA(ctx, dmalloc_async(&vm->slot_id[l], cap * sizeof(int32_t), ctx->stream));
   GLIM_CUDA(ctx, cudaMemsetAsync(vm->slots[l], 0x80, cap * sizeof(VoxSlot), ctx->stream));
   GLIM_CUDA(ctx, cudaMemsetAsync(vm->slot_id[l], 0xFF, cap * sizeof(int32_t), ctx->stream));
   if (m == 0) {
@@ -621,6 +633,7 @@ extern "C" glim_status glim_vmap_insert(glim_ctx* ctx, glim_vmap* vm, const floa
 extern "C" void glim_vmap_free(glim_vmap* vm) {
   if (!vm) return;
   cudaSetDevice(vm->device);
+  cudaDeviceSynchronize();  // launches on any stream may still read the tables
   free_levels(vm);
   delete vm;
 }

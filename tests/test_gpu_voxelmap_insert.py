@@ -147,3 +147,23 @@ def test_insert_into_empty_map(G, ctx, room):
     assert gm.info(0)["n_voxels"] == 0
     gm.insert(g.pts4, g.cov6)
     _assert_same_map(gm, room.omaps[1], len(res))
+
+
+def test_plan_refuses_to_launch_on_a_freed_map(G, ctx, room):
+    """A plan whose target map has been freed raises instead of launching on tables that no
+    longer exist; the other plans of the context are unaffected."""
+    g = room.gframes[1]
+    vm = G.VoxelMap(ctx, g.pts4, g.cov6, room.w.resolutions)
+    other = G.Plan(ctx, room.gframes, room.gmaps, room.w.pairs)
+    plan = G.Plan(ctx, room.gframes, [None, vm], room.w.pairs)
+    first = plan.linearize(room.w.poses)
+    ref = [np.asarray(x).copy() for x in other.linearize(room.w.poses)]
+    vm.free()
+    for call in (lambda: plan.linearize(room.w.poses), plan.launch, lambda: plan.set_poses(room.w.poses)):
+        with pytest.raises(G.GlimError, match="freed"):
+            call()
+    for a, b in zip(other.linearize(room.w.poses), ref):
+        assert np.array_equal(np.asarray(a), b)
+    assert np.array_equal(np.asarray(first[3]), ref[3])
+    plan.close()
+    other.close()
