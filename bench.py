@@ -65,9 +65,11 @@ def dist_env():
 
 
 def make_workload(args, rank):
+    """The workload of one step.  Every rank generates the same global step (the pairs are
+    sharded, not replicated); `rank` seeds the replica batches of the smaller workloads."""
     import synth
     if args.workload == "urban":
-        return synth.urban(seed=3 + 1000 * rank, n_submaps=args.submaps, keep=args.keep)
+        return synth.urban(seed=3, n_submaps=args.submaps, keep=args.keep)
     if args.workload == "corridor":
         return synth.corridor(seed=2 + 1000 * rank)
     if args.workload == "corridor_weights":
@@ -399,6 +401,91 @@ def small_workloads(G, ctx, dev):
     return out
 
 
+# ---------------------------------------------------------------------------- sharded step
+def sharded_e2e_and_check(G, ctx, plan, recs, args, w, full_batch, idx, need, P_all, n_pp_all, block, ppt, acc, dev,
+                          rank, ws):
+    """N > 1: the end-to-end step through the public calls (host frame poses of this rank's
+    frames uploaded, its pairs linearized, records all-gathered, the full record block read
+    to the host on rank 0), and rank 0's check that the gathered records of pairs linearized
+    on other ranks are bit-identical to a single-GPU linearization of those pairs."""
+    import torch
+    import torch.distributed as dist
+    steps = max(10, min(args.steps, 20))
+
+    def step():
+        plan.set_poses(w.poses)
+        plan.launch()
+        full = G.gather_records(recs if args.dist_backend == "nccl" else recs.cpu(), idx, P_all)
+        return full.cpu() if rank == 0 else None
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        full = step()
+    torch.cuda.synchronize()
+    cdev = dev if args.dist_backend == "nccl" else torch.device("cpu")
+    t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=cdev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_s = float(t.item()) / steps
+    h2d = torch.tensor([len(need) * 12 * 8], dtype=torch.float64, device=cdev)
+    dist.all_reduce(h2d)
+    e2e = {"value": n_pp_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d.item()),
+           "d2h_bytes_per_step": P_all * 92 * 8, "steps": steps, "ms_per_step_mean": e2e_s * 1e3,
+           "note": "per rank: its frame poses uploaded, graph launch of its pairs, all-gather of the 92-double "
+                   "records, rank 0 reads the full record block to the host"}
+    check = None
+    if rank == 0:
+        # the first pair of every other rank, linearized again here on its own
+        pairs_g, points_g, poses_g = full_batch
+        others = [int(G.shard_pairs(pairs_g, r, ws)[0]) for r in range(1, ws) if len(G.shard_pairs(pairs_g, r, ws))]
+        same = True
+        for q in others:
+            s_, t_ = int(pairs_g[q, 0]), int(pairs_g[q, 1])
+            fr, mp = [], [None, None]
+            for j, f in enumerate((s_, t_)):
+                p4 = G.to_pts4(points_g[f], device=dev)
+                cov, nrm = G.estimate_covariances(ctx, p4, k=10)
+                perm = G.spatial_order(ctx, p4, 0.5)
+                p4, cov, nrm = p4[perm].contiguous(), cov[perm].contiguous(), nrm[perm].contiguous()
+                fr.append(G.FrameData(p4, cov, nrm))
+                if j == 1:
+                    mp[1] = G.VoxelMap(ctx, p4, cov, w.resolutions)
+            p1 = G.Plan(ctx, fr, mp, np.array([[0, 1]], np.int32), accum_mode=acc, block=block, pts_per_thread=ppt)
+            p1.linearize(np.stack([poses_g[s_], poses_g[t_]]))
+            same = same and bool(torch.equal(p1.device_records()[0].cpu(), full[q]))
+            p1.close()
+        check = {"pairs_checked": others, "bit_identical": same,
+                 "note": "records gathered from other ranks vs the same pairs linearized alone on rank 0"}
+    return e2e, check
+
+
+def sharded_line(w, args, ws, K, W, tmax, value, P_all, n_pp_all, plan, kern_ms, n_pp, e2e, check, launches, clk,
+                 gen_s):
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6400.0)
+    kavg = float(np.mean(kern_ms))
+    achieved = BYTES_PER_POINT * n_pp / (kavg / 1e3) / 1e9
+    opts = plan.opts()
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": tmax / K, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"urban global step: {args.submaps} submaps of log-U[50k,200k] pts, {P_all} pairs "
+                                   "(10 nearest), voxels 0.5/1/2 m", "pairs": P_all,
+                       "pair_points_per_step": n_pp_all, "accum_mode": args.accum, "block": opts["block"],
+                       "pts_per_thread": opts["pts_per_thread"],
+                       "parallelism": f"pairs sharded by source submap over {ws} GPUs; one all-gather of the "
+                                      "92-double per-pair records per step",
+                       "l2": "inputs larger than L2 (%.2f GB source stream per step)" % (BYTES_PER_POINT * n_pp_all / 1e9),
+                       "generation_s": round(gen_s, 1)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": "k_linearize_dense (rank 0's shard)", "kernel_ms": kavg,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk else "fallback"},
+            "e2e": e2e, "sharded_check": check, "gpu_launches": launches, "clocks": clk}
+
+
 # ---------------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -407,14 +494,36 @@ def run_ours(args):
     import paper_2407_10344_b300 as G
 
     ws, rank, local = dist_env()
+    if args.dist_backend == "gloo":
+        # exchange through host memory: ranks may share a GPU (none of their kernels waits on
+        # another rank), e.g. to run the sharded path on a one-GPU machine
+        local = local % torch.cuda.device_count()
     if ws > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if args.dist_backend == "gloo":
+            dist.init_process_group("gloo")
+        else:
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     t_gen = time.perf_counter()
     w = make_workload(args, rank)
     gen_s = time.perf_counter() - t_gen
     ctx = G.Context(local)
+    # The step is sharded by source submap (the pairs are independent units): each rank holds
+    # its source frames and the voxelmaps of their targets, linearizes its pairs, and one
+    # all-gather of the per-pair records is the exchange step.  Frames are numbered locally.
+    P_all = len(w.pairs)
+    n_pp_all = w.n_pair_points
+    sharded = ws > 1 and args.workload == "urban"
+    idx = G.shard_pairs(w.pairs, rank, ws) if sharded else np.arange(P_all)
+    need = G.frames_needed(w.pairs, idx) if sharded else list(range(len(w.points)))
+    local_of = {f: i for i, f in enumerate(need)}
+    pairs_g, points_g, poses_g = w.pairs, w.points, w.poses
+    w.pairs = np.array([[local_of[int(a)], local_of[int(b)]] for a, b in pairs_g[idx]], np.int32).reshape(-1, 2)
+    w.points = [w.points[f] for f in need]
+    w.poses = w.poses[need]
+    if w.weights:
+        w.weights = [w.weights[f] for f in need]
     # inputs resident in HBM: points, kNN covariances and normals, voxelmaps of every target
     # Frames in Z-order of 0.5 m cells (the spatially coherent order that voxel-grid
     # downsampling or a scan-line order gives); the synthetic generator's own order is random.
@@ -449,11 +558,15 @@ def run_ours(args):
     torch.cuda.synchronize()
     overlap_ms = (time.perf_counter() - t0) / 5 * 1e3
     acc = {"fp32": G.ACC_FP32, "kahan": G.ACC_KAHAN, "fp64": G.ACC_FP64}[args.accum]
-    plan = G.Plan(ctx, frames, maps, w.pairs, accum_mode=acc, block=args.block, pts_per_thread=args.ppt)
-    tuned = plan.autotune(w.poses, iters=2) if args.autotune else None
+    block, ppt = args.block, args.ppt
+    if sharded and block == 0 and ppt == 0:
+        block, ppt = 128, 64  # every rank uses the same tiles, so records are the single-GPU bits
+    plan = G.Plan(ctx, frames, maps, w.pairs, accum_mode=acc, block=block, pts_per_thread=ppt)
+    tuned = plan.autotune(w.poses, iters=2) if (args.autotune and not sharded) else None
     opts = plan.opts()
     plan.set_poses(w.poses)
-    n_pp = w.n_pair_points
+    n_pp = int(sum(len(w.points[int(a)]) for a in w.pairs[:, 0]))  # this rank's (pair, point) units
+    recs = plan.device_records()
     K, W = args.steps, args.warmup
     for _ in range(W):
         plan.launch_timed(0)
@@ -471,7 +584,10 @@ def run_ours(args):
     ev0.record(stream)
     for i in range(K):
         plan.launch_timed(i)
-    ev1.record(stream)
+        if sharded:  # the exchange step: every rank's per-pair records to every rank
+            full_rec = G.gather_records(recs if args.dist_backend == "nccl" else recs.cpu(), idx, P_all)
+    # sharded: the all-gather orders torch's current stream after itself
+    ev1.record(torch.cuda.current_stream() if sharded else stream)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -479,8 +595,18 @@ def run_ours(args):
     gpu_launches = ctx.kernel_launches - launches0
     clk = clocks.stop()
     kern_ms = plan.kernel_ms(K)
-    tmax, total_pp = aggregate_over_ranks(step_ms_total, n_pp, dev)
+    tmax, total_pp = aggregate_over_ranks(step_ms_total, n_pp, dev if args.dist_backend == "nccl" else torch.device("cpu"))
     value = total_pp * K / (tmax / 1e3)
+    sharded_check = None
+    if sharded:
+        e2e_line, sharded_check = sharded_e2e_and_check(G, ctx, plan, recs, args, w, (pairs_g, points_g, poses_g),
+                                                         idx, need, P_all, n_pp_all, block, ppt, acc, dev, rank, ws)
+        line = sharded_line(w, args, ws, K, W, tmax, value, P_all, n_pp_all, plan, kern_ms, n_pp, e2e_line,
+                            sharded_check, gpu_launches, clk, gen_s)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        dist.destroy_process_group()
+        return
     # e2e: public call with host poses in / host results out, copies in the timed region
     e2e_steps = max(10, min(K, 20))
     _, _, _, inl_out = plan.linearize(w.poses)  # capture the full graph outside the timing
@@ -570,8 +696,8 @@ def run_ours(args):
     kernel_name = "k_linearize_dense" if opts.get("kernel") == "dense" else "k_linearize"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
-        "ms_per_step": tmax / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+        "ms_per_step": tmax / K, "higher_is_better": True, "scaling": "strong" if args.workload == "urban" else "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_desc(w, args), "pairs": P, "frames": len(w.points),
                    "pair_points_per_step": n_pp, "levels": len(w.resolutions), "resolutions_m": w.resolutions,
                    "accum_mode": args.accum, "block": opts["block"], "pts_per_thread": opts["pts_per_thread"],
@@ -581,7 +707,7 @@ def run_ours(args):
                           if BYTES_PER_POINT * n_pp > 126e6 else
                           "L2 not flushed: the %.3f GB source stream fits in L2 (126 MB), a warm-cache figure"
                           % (BYTES_PER_POINT * n_pp / 1e9)),
-                   "parallelism": f"replicas x{ws} (independent batches per GPU, no collective)",
+                   "parallelism": "one GPU" if ws == 1 else f"replicas x{ws} (independent batches per GPU)",
                    "generation_s": round(gen_s, 1)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
@@ -683,6 +809,8 @@ def main():
     ap.add_argument("--no-small", action="store_true", help="skip the odometry / GN / autograd timings")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-points", type=int, default=3_000_000)
+    ap.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
+                    help="N > 1: nccl (one GPU per rank) or gloo (exchange through host memory)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

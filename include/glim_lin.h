@@ -59,6 +59,13 @@ typedef int32_t glim_status;
 
 #define GLIM_MAX_LEVELS 4
 
+/* A factor record: the linearization of one pair in GLIM_RECORD_DOUBLES doubles, for
+ * exchange between processes (the per-pair {e, H, b} that a multi-GPU global step gathers to
+ * the rank that assembles the system): [0] e; [1 .. 78] the upper triangle of the symmetric
+ * H, row-major (H[0][0..11], H[1][1..11], ..., H[11][11]); [79 .. 90] b; [91] the inlier
+ * count. */
+#define GLIM_RECORD_DOUBLES 92
+
 /* Accumulation modes of the per-point sums (precision of the partial sums of H, b, e). */
 #define GLIM_ACC_FP32 0  /* FP32 everywhere, including the cross-block sum (naive) */
 #define GLIM_ACC_KAHAN 1 /* FP32 with compensated (Kahan/Neumaier) per-thread and tree sums,
@@ -273,11 +280,17 @@ glim_status glim_linearize_factors_plain(glim_ctx* ctx, const glim_frame* frames
  * its scratch (descriptors, work list, queue head, partial sums) is one statically sized array
  * of about 4.5 MB that every device loading this library holds until the process exits.
  * Limits: at most 256 frames, 256 pairs and 16384 work items of block * pts_per_thread points
- * (GLIM_EINVAL with a message naming the limit otherwise).  The first call on a device looks
- * up that array's device address; make that first call before any stream capture.  Every call
- * shares the array and overwrites it (the queue head is cleared on each call), so calls that
+ * (GLIM_EINVAL with a message naming the limit otherwise).  The first call on a device sets it
+ * up (looks up that array's device address, fills a constant part of it and waits for that
+ * fill, creates an event, and once per process page-locks the library's host staging block
+ * with cudaHostRegister); make that first call before any stream capture.  The descriptors are
+ * staged in that one host block, which every call rewrites, so a call made while the context's
+ * stream is capturing returns GLIM_EINVAL without enqueuing anything.  Every call shares the
+ * device array and overwrites it (the queue head is cleared on each call), so calls that
  * overlap on the GPU, from any stream or thread, race: issue them one after another.  The work
- * is enqueued on the context's stream; the call does not synchronize. */
+ * is enqueued on the context's stream.  The call does not wait for that stream, except that it
+ * first waits until the previous call's upload of the staging block has been read, which is
+ * ordered after only the work that preceded the previous call. */
 glim_status glim_linearize_factors_noalloc(glim_ctx* ctx, const glim_frame* frames, int32_t nframes,
                                            const glim_pair* pairs, int32_t npairs,
                                            const double* poses12, const glim_lin_opts* opts,
@@ -315,9 +328,28 @@ glim_status glim_plan_set_poses(glim_plan* plan, const double* poses12);
  * doubles, [R row-major | t] of T_rel) and pose32_out (npairs x 16 floats: R, t, v, 0), either
  * may be NULL.  For inspection and tests of the pose packing. */
 glim_status glim_plan_relative_poses(glim_plan* plan, double* rt64_out, float* pose32_out);
+/* Correspondences as the plan's own kernel resolves them (Sec. III-C "Correspondence search":
+ * one voxel per level, key floor(q * inv_r) on the FP32 path).  Runs the id-recording
+ * instantiation of the linearization kernel that the plan uses (general, dense-grid or hash;
+ * the same lookup and hit code, block size, tile and work queue, accumulation mode
+ * GLIM_ACC_FP64) at poses12 (host, nframes x 12 doubles), and writes the canonical voxel id of
+ * every source point at every level of its pair's target map, or -1 (a miss, a point
+ * discarded by surface validation, a masked or non-finite point), to ids_out: device,
+ * int32, per pair n_src x levels (point-major), pairs concatenated in order.  The e, H, b and
+ * inlier counts of the same launch are copied to e_out, H_out, b_out, inliers_out (host
+ * arrays as for glim_plan_linearize; each may be NULL).  For inspection and parity tests;
+ * synchronizes.  GLIM_EINVAL for a null ids_out with pairs, or a plan whose maps changed. */
+glim_status glim_plan_correspondence_ids(glim_plan* plan, const double* poses12, int32_t* ids_out,
+                                         double* e_out, double* H_out, double* b_out,
+                                         int64_t* inliers_out);
 glim_status glim_plan_launch(glim_plan* plan);
 glim_status glim_plan_device_outputs(glim_plan* plan, double** e, double** H, double** b,
                                      int64_t** inliers);
+/* Device pointer to the plan's factor records (npairs x GLIM_RECORD_DOUBLES doubles, pair
+ * order), written by every linearization of the plan together with its other outputs; valid
+ * until the plan is destroyed.  H in every output of the library is exactly symmetric: its
+ * record holds every entry. */
+glim_status glim_plan_device_records(glim_plan* plan, double** rec);
 /* Kernels enqueued per glim_plan_launch (queue reset excluded). */
 int32_t glim_plan_kernels_per_launch(const glim_plan* plan);
 /* Timing support: enqueue like glim_plan_launch but with direct launches (no graph), and

@@ -776,6 +776,70 @@ int orc_gn_solve(const double* H, const double* b, int dim, double* xi_out) {
   return ORC_OK;
 }
 
+// One step of a small factor graph (Sec. V-A: the submaps of local mapping are optimised with
+// all-to-all matching-cost factors by Levenberg-Marquardt).  Each factor p contributes its
+// quadratic form over [xi_src; xi_tgt]: its 6 x 6 blocks are added to the blocks (src, src),
+// (src, tgt), (tgt, src), (tgt, tgt) of the global H and its two 6-vectors to the entries of b.
+// The variables of frame `fixed` (-1: none) are removed (the gauge of relative factors), the
+// remaining diagonal is damped by (1 + lambda), and (H_ff + lambda diag(H_ff)) xi_f = -b_f is
+// solved by Cholesky; xi of the fixed frame is zero.  Hg_out (6n x 6n) and bg_out (6n) receive
+// the undamped assembled system (nullable).  ORC_ENOTPD if the reduced system is not positive
+// definite.
+int orc_graph_step(const int32_t* pair_frames, int npairs, int nframes, const double* H, const double* b,
+                   int fixed, double lambda, double* xi_out, double* Hg_out, double* bg_out) {
+  if (nframes < 1 || npairs < 0 || fixed < -1 || fixed >= nframes) return ORC_EINVAL;
+  const int N = 6 * nframes;
+  std::vector<double> Hg(size_t(N) * N, 0.0), bg(N, 0.0);
+  for (int p = 0; p < npairs; ++p) {
+    const int f[2] = {pair_frames[2 * p], pair_frames[2 * p + 1]};
+    if (f[0] < 0 || f[0] >= nframes || f[1] < 0 || f[1] >= nframes) return ORC_EINVAL;
+    for (int u = 0; u < 2; ++u) {
+      for (int a = 0; a < 6; ++a) bg[6 * f[u] + a] += b[12 * p + 6 * u + a];
+      for (int v = 0; v < 2; ++v)
+        for (int a = 0; a < 6; ++a)
+          for (int c = 0; c < 6; ++c)
+            Hg[size_t(6 * f[u] + a) * N + 6 * f[v] + c] += H[144 * p + (6 * u + a) * 12 + 6 * v + c];
+    }
+  }
+  if (Hg_out) std::memcpy(Hg_out, Hg.data(), Hg.size() * sizeof(double));
+  if (bg_out) std::memcpy(bg_out, bg.data(), bg.size() * sizeof(double));
+  std::vector<int> free_vars;
+  for (int i = 0; i < N; ++i)
+    if (fixed < 0 || i / 6 != fixed) free_vars.push_back(i);
+  const int M = int(free_vars.size());
+  std::vector<double> A(size_t(M) * M), L(size_t(M) * M, 0.0), y(M), x(M);
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < M; ++j) {
+      double v = Hg[size_t(free_vars[i]) * N + free_vars[j]];
+      if (i == j) v += lambda * v;
+      A[size_t(i) * M + j] = v;
+    }
+  for (int j = 0; j < M; ++j) {  // A = L L^T
+    double d = A[size_t(j) * M + j];
+    for (int k = 0; k < j; ++k) d -= L[size_t(j) * M + k] * L[size_t(j) * M + k];
+    if (!(d > 0.0) || !std::isfinite(d)) return ORC_ENOTPD;
+    L[size_t(j) * M + j] = std::sqrt(d);
+    for (int i = j + 1; i < M; ++i) {
+      double t = A[size_t(i) * M + j];
+      for (int k = 0; k < j; ++k) t -= L[size_t(i) * M + k] * L[size_t(j) * M + k];
+      L[size_t(i) * M + j] = t / L[size_t(j) * M + j];
+    }
+  }
+  for (int i = 0; i < M; ++i) {  // L y = -b_f
+    double t = -bg[free_vars[i]];
+    for (int k = 0; k < i; ++k) t -= L[size_t(i) * M + k] * y[k];
+    y[i] = t / L[size_t(i) * M + i];
+  }
+  for (int i = M - 1; i >= 0; --i) {  // L^T x = y
+    double t = y[i];
+    for (int k = i + 1; k < M; ++k) t -= L[size_t(k) * M + i] * x[k];
+    x[i] = t / L[size_t(i) * M + i];
+  }
+  for (int i = 0; i < N; ++i) xi_out[i] = 0.0;
+  for (int i = 0; i < M; ++i) xi_out[free_vars[i]] = x[i];
+  return ORC_OK;
+}
+
 // Overlap rate: fraction of source points with a voxel of the target at level ``level``
 // under the relative pose (Sec. IV-B), surface test off.
 double orc_overlap(const orc_frame* src, const void* vmap, const double* pose_s12,

@@ -67,6 +67,8 @@ def lib():
         _lib.orc_gradient.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib.orc_gn_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+        _lib.orc_graph_step.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                        C.c_void_p, C.c_void_p, C.c_void_p]
         _lib.orc_overlap.restype = C.c_double
         _lib.orc_overlap.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
     return _lib
@@ -258,6 +260,24 @@ def gn_solve(H, b):
     if st != ORC_OK:
         raise np.linalg.LinAlgError(f"orc_gn_solve: {st}")
     return xi
+
+
+def graph_step(pair_frames, nframes, H, b, fixed=0, lam=0.0):
+    """Assembled global system and damped step of a factor graph: returns (xi (nframes, 6),
+    H_glob (6n, 6n), b_glob (6n)); raises LinAlgError if the reduced system is not PD."""
+    pf = np.ascontiguousarray(np.asarray(pair_frames, dtype=np.int32).reshape(-1, 2))
+    H = np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(-1, 144))
+    b = np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(-1, 12))
+    xi = np.zeros((nframes, 6))
+    Hg = np.zeros((6 * nframes, 6 * nframes))
+    bg = np.zeros(6 * nframes)
+    st = lib().orc_graph_step(_ptr(pf), len(pf), int(nframes), _ptr(H), _ptr(b), int(fixed), float(lam), _ptr(xi),
+                              _ptr(Hg), _ptr(bg))
+    if st == ORC_ENOTPD:
+        raise np.linalg.LinAlgError("orc_graph_step: reduced system not positive definite")
+    if st != ORC_OK:
+        raise ValueError(f"orc_graph_step failed: {st}")
+    return xi, Hg, bg
 
 
 def overlap(frame: Frame, vmap: VMap, pose_s, pose_t, level=0):

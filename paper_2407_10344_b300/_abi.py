@@ -16,6 +16,7 @@ STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EHASHFULL
                 -6: "ENOTPD", -7: "ETIMEOUT"}
 ACC_FP32, ACC_KAHAN, ACC_FP64 = 0, 1, 2
 MAX_LEVELS = 4
+RECORD_DOUBLES = 92  # GLIM_RECORD_DOUBLES: e, the upper triangle of H (78), b (12), inliers
 
 # every function the header declares, with (restype, argtypes)
 _vp, _i32, _i64, _f32, _f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double
@@ -66,8 +67,10 @@ SIGNATURES = {
     "glim_plan_linearize": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "glim_plan_set_poses": (_i32, [_vp, _vp]),
     "glim_plan_relative_poses": (_i32, [_vp, _vp, _vp]),
+    "glim_plan_correspondence_ids": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "glim_plan_launch": (_i32, [_vp]),
     "glim_plan_device_outputs": (_i32, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp)]),
+    "glim_plan_device_records": (_i32, [_vp, C.POINTER(_vp)]),
     "glim_plan_kernels_per_launch": (_i32, [_vp]),
     "glim_plan_launch_timed": (_i32, [_vp, _i32]),
     "glim_plan_kernel_ms": (_i32, [_vp, _i32, C.POINTER(_f32)]),

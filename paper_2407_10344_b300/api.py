@@ -360,6 +360,7 @@ class Plan:
         pr, P = _pairs(pairs, self.vmaps)
         self.npairs = P
         self.nframes = len(self.frames)
+        self._pairs_arr = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
         o = _opts(**opts)
         h = C.c_void_p()
         ctx.call("plan_create", ctx.lib.glim_plan_create, ctx.h, fr, self.nframes, pr, P, C.byref(o), C.byref(h))
@@ -409,10 +410,34 @@ class Plan:
         T[:, :, 3] = rt[:, 9:]
         return T, p32
 
+    def correspondence_ids(self, poses):
+        """Canonical voxel id of every (pair, source point, level) as the plan's own kernel
+        resolves it (-1: miss), through the kernel's id-recording instantiation: an int32 CUDA
+        tensor, per pair n_src x levels, pairs concatenated.  Also returns that launch's host
+        (e, H, b, inliers)."""
+        self._maps_alive()
+        Pz = _poses(poses, self.nframes)
+        lv = [self.vmaps[int(t)].levels for t in self._pairs_arr[:, 1]]
+        n = sum(self.frames[int(s_)].n * l for s_, l in zip(self._pairs_arr[:, 0], lv))
+        ids = torch.empty(max(n, 1), dtype=torch.int32, device=self.frames[0].pts4.device)
+        e, H, b, inl = _outputs(self.npairs, "host")
+        self.ctx.call("plan_correspondence_ids", self.ctx.lib.glim_plan_correspondence_ids, self.h, _ptr(Pz),
+                      _ptr(ids), _ptr(e), _ptr(H), _ptr(b), _ptr(inl))
+        return ids[:n], (e, H, b, inl)
+
     def set_poses(self, poses):
         self._maps_alive()
         Pz = _poses(poses, self.nframes)
         self.ctx.call("plan_set_poses", self.ctx.lib.glim_plan_set_poses, self.h, _ptr(Pz))
+
+    def device_records(self):
+        """The plan's factor records as a (npairs, 92) float64 CUDA tensor that shares the
+        plan's device memory (no copy): [e, the upper triangle of H row by row (78), b (12),
+        inliers] per pair, rewritten by every linearization of the plan.  Valid while the
+        plan is open."""
+        q = C.c_void_p()
+        self.ctx.call("plan_device_records", self.ctx.lib.glim_plan_device_records, self.h, C.byref(q))
+        return _device_view(q.value, (self.npairs, _abi.RECORD_DOUBLES), "<f8", self.frames[0].pts4.device)
 
     def device_outputs_alloc(self):
         """Device tensors (e, H, b, inliers) to pass as `out` to linearize."""
@@ -553,6 +578,86 @@ def shard_pairs(pairs, rank: int, world: int):
     group = np.minimum((cum - 1) * world // max(total, 1), world - 1) if total else np.zeros(0, int)
     mine = set(srcs[group == rank].tolist())
     return np.array([i for i, (s_, _) in enumerate(pairs) if int(s_) in mine], dtype=np.int64)
+
+
+class _DeviceArray:
+    """Library-owned device memory described by the CUDA array interface, so that torch can
+    view it without a copy (the library keeps ownership)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr or 0), False),
+                                         "version": 2, "strides": None}
+
+
+def _device_view(ptr, shape, typestr, device):
+    if int(np.prod(shape)) == 0:
+        return torch.empty(shape, dtype=torch.float64, device=device)
+    return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device=device)
+
+
+_TRIU = np.triu_indices(12)
+
+
+def pack_records(e, H, b, inliers):
+    """Factor records (P, 92) of (e, H, b, inliers) in the library's record layout: e, the
+    upper triangle of H row by row, b, the inlier count.  numpy in, numpy out; torch in,
+    torch out (same device)."""
+    if isinstance(e, torch.Tensor):
+        P = e.shape[0]
+        iu = torch.as_tensor(np.ravel_multi_index(_TRIU, (12, 12)), device=e.device)
+        return torch.cat([e.reshape(P, 1).double(), H.reshape(P, 144).double()[:, iu], b.reshape(P, 12).double(),
+                          inliers.reshape(P, 1).double()], dim=1)
+    e = np.asarray(e, np.float64)
+    P = len(e)
+    H = np.asarray(H, np.float64).reshape(P, 12, 12)
+    return np.concatenate([e.reshape(P, 1), H[:, _TRIU[0], _TRIU[1]], np.asarray(b, np.float64).reshape(P, 12),
+                           np.asarray(inliers, np.float64).reshape(P, 1)], axis=1)
+
+
+def unpack_records(rec):
+    """(e, H (P, 12, 12) symmetric, b, inliers int64) of factor records (numpy or torch)."""
+    is_t = isinstance(rec, torch.Tensor)
+    r = rec.cpu().numpy() if is_t else np.asarray(rec, np.float64)
+    P = r.shape[0]
+    H = np.zeros((P, 12, 12))
+    H[:, _TRIU[0], _TRIU[1]] = r[:, 1:79]
+    H[:, _TRIU[1], _TRIU[0]] = r[:, 1:79]
+    return r[:, 0].copy(), H, r[:, 79:91].copy(), np.rint(r[:, 91]).astype(np.int64)
+
+
+def gather_records(rec, idx, npairs, group=None):
+    """The exchange step of a factor batch sharded over ranks (shard_pairs): every rank holds
+    the records `rec` (n_local, 92) of its pairs `idx` (global pair indices); one all-gather
+    (torch.distributed: NCCL for CUDA tensors, gloo for CPU tensors) gives every rank the
+    records of all `npairs` pairs in pair order, on rec's device.  A world of one returns the
+    records placed in pair order."""
+    import torch.distributed as dist
+    rec_t = rec if isinstance(rec, torch.Tensor) else torch.as_tensor(np.asarray(rec, np.float64))
+    dev = rec_t.device
+    idx_t = torch.as_tensor(np.asarray(idx, np.int64), device=dev)
+    if rec_t.shape[0] != idx_t.shape[0]:
+        raise ValueError("records and pair indices differ in length")
+    out = torch.zeros((npairs, rec_t.shape[1]), dtype=torch.float64, device=dev)
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) == 1:
+        out[idx_t] = rec_t.double()
+        return out
+    world = dist.get_world_size(group)
+    n = torch.tensor([idx_t.shape[0]], dtype=torch.int64, device=dev)
+    counts = [torch.zeros_like(n) for _ in range(world)]
+    dist.all_gather(counts, n, group=group)
+    m = int(max(int(c.item()) for c in counts))
+    pad_r = torch.zeros((m, rec_t.shape[1]), dtype=torch.float64, device=dev)
+    pad_r[:rec_t.shape[0]] = rec_t
+    pad_i = torch.full((m,), -1, dtype=torch.int64, device=dev)
+    pad_i[:idx_t.shape[0]] = idx_t
+    all_r = [torch.empty_like(pad_r) for _ in range(world)]
+    all_i = [torch.empty_like(pad_i) for _ in range(world)]
+    dist.all_gather(all_r, pad_r, group=group)
+    dist.all_gather(all_i, pad_i, group=group)
+    for c, r_, i_ in zip(counts, all_r, all_i):
+        k = int(c.item())
+        out[i_[:k]] = r_[:k]
+    return out
 
 
 def frames_needed(pairs, idx):

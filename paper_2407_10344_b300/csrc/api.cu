@@ -1,5 +1,7 @@
 // api.cu -- context lifetime, error reporting and pose helpers of the C ABI.
 #include <atomic>
+#include <mutex>
+#include <unordered_map>
 #include <cmath>
 #include <cstring>
 
@@ -79,6 +81,36 @@ PoseF pose_to_f32(const RelPose& T) {
   return p;
 }
 
+namespace {
+std::mutex g_vmap_mu;
+std::unordered_map<const glim_vmap*, uint64_t> g_vmaps;  // live map -> serial
+uint64_t g_vmap_serial = 0;
+std::atomic<uint64_t> g_vmap_epoch{0};
+}  // namespace
+
+void vmap_register(glim_vmap* vm) {
+  std::lock_guard<std::mutex> lk(g_vmap_mu);
+  vm->serial = ++g_vmap_serial;
+  g_vmaps[vm] = vm->serial;
+}
+
+void vmap_unregister(glim_vmap* vm) {
+  {
+    std::lock_guard<std::mutex> lk(g_vmap_mu);
+    g_vmaps.erase(vm);
+  }
+  vmap_bump_epoch();
+}
+
+bool vmap_alive(const glim_vmap* vm, uint64_t serial) {
+  std::lock_guard<std::mutex> lk(g_vmap_mu);
+  const auto it = g_vmaps.find(vm);
+  return it != g_vmaps.end() && it->second == serial;
+}
+
+uint64_t vmap_epoch() { return g_vmap_epoch.load(std::memory_order_acquire); }
+void vmap_bump_epoch() { g_vmap_epoch.fetch_add(1, std::memory_order_acq_rel); }
+
 extern "C" glim_status glim_create(glim_ctx** out, int device, void* cuda_stream) {
   if (!out) return GLIM_EINVAL;
   *out = nullptr;
@@ -87,7 +119,8 @@ extern "C" glim_status glim_create(glim_ctx** out, int device, void* cuda_stream
     cudaGetLastError();
     return GLIM_EINVAL;
   }
-  if (cudaSetDevice(device) != cudaSuccess) return GLIM_ECUDA;
+  DeviceGuard device_guard;
+  if (device_guard.set(device) != cudaSuccess) return GLIM_ECUDA;
   glim_ctx* ctx = new glim_ctx;
   ctx->device = device;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
@@ -112,7 +145,8 @@ extern "C" glim_status glim_create(glim_ctx** out, int device, void* cuda_stream
 
 extern "C" void glim_destroy(glim_ctx* ctx) {
   if (!ctx) return;
-  cudaSetDevice(ctx->device);
+  DeviceGuard device_guard;
+  device_guard.set(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   cudaFree(ctx->d_status);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);

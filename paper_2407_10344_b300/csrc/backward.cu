@@ -343,7 +343,8 @@ extern "C" glim_status glim_plan_backward(glim_plan* p, const double* poses12, i
   if (p->opts.block != 256 || p->tile != 256)
     return set_error(ctx, GLIM_EINVAL, "plan_backward: the plan needs block 256 and pts_per_thread 1");
   if (!plan_maps_current(p)) return set_error(ctx, GLIM_EINVAL, "plan_backward: a target voxelmap changed");
-  GLIM_CUDA(ctx, cudaSetDevice(ctx->device));
+  DeviceGuard device_guard;
+  GLIM_CUDA(ctx, device_guard.set(ctx->device));
   // The device pose block already holds these poses when the last linearization of the plan
   // used them (the usual forward-then-gradient sequence): then nothing is uploaded and the
   // call does not wait for the stream.  Otherwise the pinned staging block may still be read

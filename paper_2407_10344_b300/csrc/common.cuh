@@ -25,6 +25,29 @@ struct NvtxScope {
 };
 #define GLIM_RANGE(name) NvtxScope glim_nvtx_scope_(name)
 
+// Makes a device current for the lifetime of a scope and restores the caller's current
+// device afterwards, so that an entry point leaves the calling thread's device as it found it.
+struct DeviceGuard {
+  int prev = -1;
+  DeviceGuard() = default;
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+  cudaError_t set(int dev) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+      cudaGetLastError();
+      cur = -1;
+    }
+    if (cur == dev) return cudaSuccess;
+    const cudaError_t e = cudaSetDevice(dev);
+    if (e == cudaSuccess) prev = cur;
+    return e;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 // ------------------------------------------------------------------ context
 struct glim_ctx {
   int device = 0;
@@ -204,6 +227,7 @@ struct glim_vmap {
   int32_t* vcount[GLIM_MAX_LEVELS] = {nullptr};
   double* vsum[GLIM_MAX_LEVELS] = {nullptr};              // n_vox x 9 FP64 sums (mean 3, cov 6)
   uint64_t version = 0;  // incremented whenever the tables are replaced (insertion)
+  uint64_t serial = 0;   // unique per map of the process (registry of live maps)
   LevelDev dev(int l) const {
     LevelDev d;
     d.slots = slots[l];
@@ -223,6 +247,16 @@ struct glim_vmap {
     return d;
   }
 };
+
+// Registry of the live voxelmaps of the process, so that a plan can tell, without touching a
+// freed map, whether its target maps still exist unchanged: every map gets a unique serial
+// when it is registered; freeing a map unregisters it.  The epoch changes whenever a map is
+// freed or its tables are replaced, so a plan re-checks its maps only after such a change.
+void vmap_register(glim_vmap* vm);
+void vmap_unregister(glim_vmap* vm);
+bool vmap_alive(const glim_vmap* vm, uint64_t serial);  // registered under that serial
+uint64_t vmap_epoch();
+void vmap_bump_epoch();
 
 // per-pair relative pose in FP32 as used by the point loop
 struct __align__(16) PoseF {

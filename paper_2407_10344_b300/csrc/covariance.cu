@@ -448,7 +448,8 @@ extern "C" glim_status glim_estimate_covariances(glim_ctx* ctx, const float* pts
     return set_error(ctx, GLIM_EINVAL, "estimate_covariances: bad arguments (n=%lld k=%d)", (long long)n, k);
   if (n > 0x7FFFFFFFll) return set_error(ctx, GLIM_EINVAL, "estimate_covariances: n too large");
   if (reinterpret_cast<uintptr_t>(pts4) & 15) return set_error(ctx, GLIM_EINVAL, "estimate_covariances: pts4 misaligned");
-  GLIM_CUDA(ctx, cudaSetDevice(ctx->device));
+  DeviceGuard device_guard;
+  GLIM_CUDA(ctx, device_guard.set(ctx->device));
   GridArgs a{};
   a.pts = reinterpret_cast<const float4*>(pts4);
   a.n = n;

@@ -138,11 +138,13 @@ struct WarpStage {
 // lane order within a level).  Phase 2 (the lanes share the term list): per hit
 // w Omega = adj(S')/det(S'), y = w Omega d, e = d^T y, and the G-form contribution
 // [G^T (w Omega) G, G^T y, e] with G = [-(u)x, I].  Misses and discarded points cost no
-// phase-2 lanes.
-template <int LMAX, class A>
+// phase-2 lanes.  With IDS (the id-recording instantiation) a real point (live on entry)
+// also writes the canonical id of the voxel each level resolved to, or -1, to ids[k idl + l].
+template <int LMAX, bool IDS, class A>
 __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in, bool live, int64_t k, int validate,
-                                           WarpStage<LMAX>& ws, A& acc, int& inl) {
+                                           WarpStage<LMAX>& ws, A& acc, int& inl, int32_t* ids, int idl) {
   const int lane = threadIdx.x & 31;
+  const bool real = live;
   const unsigned lt = (1u << lane) - 1u;
   const float4 m = in.m;
   if (live && validate && P.F.nrm) {
@@ -190,9 +192,14 @@ __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in,
     }
   }
   int nh = 0;
+  int vid[LMAX];  // IDS: canonical id of the voxel a level resolved to
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
-    if (hit[l] && P.M.lv[l].dense) hit[l] = __float_as_int(s0[l].x) >= 0;  // occupied cell
+    vid[l] = -1;
+    if (hit[l] && P.M.lv[l].dense) {
+      hit[l] = __float_as_int(s0[l].x) >= 0;  // occupied cell (its record starts with the id)
+      if constexpr (IDS) vid[l] = __float_as_int(s0[l].x);
+    }
     if (hit[l] && !P.M.lv[l].dense) {
       const int sx = __float_as_int(s0[l].x);
       if (!(sx == kx[l] && __float_as_int(s0[l].y) == ky[l] && __float_as_int(s0[l].z) == kz[l])) {
@@ -205,11 +212,21 @@ __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in,
             s0[l] = ldg4(&L.slots[s].w0);
             s1[l] = ldg4(&L.slots[s].w1);
             s2[l] = ldg4(&L.slots[s].w2);
+            if constexpr (IDS) vid[l] = L.slot_id[s];
           }
         }
+      } else if constexpr (IDS) {
+        vid[l] = P.M.lv[l].slot_id[hh[l]];
       }
     }
     nh += hit[l] ? 1 : 0;
+  }
+  if constexpr (IDS) {
+    if (real) {
+#pragma unroll
+      for (int l = 0; l < LMAX; ++l)
+        if (l < idl) ids[k * idl + l] = hit[l] ? vid[l] : -1;
+    }
   }
   // R C R^T and u, for the records of this lane's hits
   float r00 = 0.f, r01 = 0.f, r02 = 0.f, r11 = 0.f, r12 = 0.f, r22 = 0.f;
@@ -342,9 +359,15 @@ __device__ __forceinline__ void block_reduce_store(const typename AccOf<ACC>::ty
 }
 
 // ---------------------------------------------------------------- items and the kernel
-template <int BLOCK, int ACC, int LMAX>
+template <int BLOCK, int ACC, int LMAX, bool IDS>
 __device__ __forceinline__ void process_item(const LinArgs& a, int item, PairView& V, WarpStage<LMAX>& ws) {
   const Item it = a.items[item];
+  int32_t* ids = nullptr;
+  int idl = 0;
+  if constexpr (IDS) {
+    ids = a.ids + a.ids_off[it.pair];
+    idl = a.ids_lv[it.pair];
+  }
   if (threadIdx.x == 0) {
     const PairDev pd = a.pairs[it.pair];
     const PoseF pf = a.pose[it.pair];
@@ -375,7 +398,7 @@ __device__ __forceinline__ void process_item(const LinArgs& a, int item, PairVie
     PointIn nxt;
     const bool more = (j + 1 < rounds) && (k + BLOCK < end);
     if (more) nxt = load_point(V.F, k + BLOCK);
-    warp_round<LMAX>(V, cur, k < end, k, a.validate, ws, acc, inl);
+    warp_round<LMAX, IDS>(V, cur, k < end, k, a.validate, ws, acc, inl, ids, idl);
     if (more) cur = nxt;
   }
   // the reduction ends with a barrier, so V is free for the next item afterwards
@@ -389,15 +412,15 @@ constexpr size_t lin_dyn_smem() {
   return size_t(BLOCK / 32) * sizeof(WarpStage<LMAX>);
 }
 
-template <int BLOCK, int ACC, int LMAX>
-__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize(const LinArgs a) {
+template <int BLOCK, int ACC, int LMAX, bool IDS>
+__device__ __forceinline__ void general_kernel_body(const LinArgs& a) {
   __shared__ PairView V;
   __shared__ int s_item[2];
   extern __shared__ float4 dyn_smem[];
   WarpStage<LMAX>& ws = reinterpret_cast<WarpStage<LMAX>*>(dyn_smem)[threadIdx.x >> 5];
   if (a.head == nullptr) {
     const int item = a.item_base + blockIdx.x;
-    if (item < a.nitems) process_item<BLOCK, ACC, LMAX>(a, item, V, ws);
+    if (item < a.nitems) process_item<BLOCK, ACC, LMAX, IDS>(a, item, V, ws);
     return;
   }
   // the next item index is fetched one item ahead, so the queue's atomic latency overlaps work
@@ -407,9 +430,21 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize(const LinArgs 
   for (int b = 1;; b ^= 1) {
     if (cur >= a.nitems) break;
     if (threadIdx.x == 0) s_item[b] = atomicAdd(a.head, 1);
-    process_item<BLOCK, ACC, LMAX>(a, cur, V, ws);  // ends with a barrier
+    process_item<BLOCK, ACC, LMAX, IDS>(a, cur, V, ws);  // ends with a barrier
     cur = s_item[b];
   }
+}
+
+template <int BLOCK, int ACC, int LMAX>
+__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize(const LinArgs a) {
+  general_kernel_body<BLOCK, ACC, LMAX, false>(a);
+}
+
+// The id-recording instantiation of the general kernel (inspection and parity tests): the same
+// code plus the stores of the resolved voxel ids.
+template <int BLOCK, int ACC, int LMAX>
+__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize_ids(const LinArgs a) {
+  general_kernel_body<BLOCK, ACC, LMAX, true>(a);
 }
 
 // ---------------------------------------------------------------- per-lane kernels
@@ -456,13 +491,15 @@ struct LaneFetch {
   bool live;
   float4 s0[LMAX];  // dense: {id, C~22, ., .} (8 bytes read); hash: {kx, ky, kz, C~22}
   float4 s1[LMAX], s2[LMAX];
-  uint32_t slot[LMAX];  // hash: the first probe's slot
+  uint32_t slot[LMAX];  // hash: the first probe's slot (with IDS: the matching slot)
   float2 ca, cb, cc;
+  int idx;  // IDS: index of the point in its frame, -1 for a masked lane
 };
 
-template <int LMAX, bool HASH>
+template <int LMAX, bool HASH, bool IDS>
 __device__ __forceinline__ void lane_fetch(const LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V,
                                            const float4 m, bool live, int validate, int kk, LaneFetch<LMAX>& F) {
+  if constexpr (IDS) F.idx = live ? kk : -1;
   // the covariance is read here rather than a round ahead: it is needed only after the voxel
   // reads are in flight, and the registers it would hold are worth more as occupancy
   const float2* cp = V.cov + 3 * int64_t(kk);
@@ -520,9 +557,9 @@ __device__ __forceinline__ void lane_fetch(const LaneView<typename std::conditio
   F.live = live;
 }
 
-template <int LMAX, bool HASH, class A>
+template <int LMAX, bool HASH, bool IDS, class A>
 __device__ __forceinline__ void lane_compute(const LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V,
-                                             LaneFetch<LMAX>& F, A& acc, int& inl) {
+                                             LaneFetch<LMAX>& F, A& acc, int& inl, int32_t* ids, int idl) {
   const float4 R0 = V.Rt[0], R1 = V.Rt[1], R2 = V.Rt[2];
   const float3 q = F.q;
   const bool live = F.live;
@@ -579,6 +616,7 @@ __device__ __forceinline__ void lane_compute(const LaneView<typename std::condit
               s1[l] = ldg4(&slots[h].w1);
               s2[l] = ldg4(&slots[h].w2);
               match = true;
+              if constexpr (IDS) F.slot[l] = h;
               break;
             }
             if (__float_as_int(w0.x) == GLIM_EMPTY_COORD) break;
@@ -590,6 +628,20 @@ __device__ __forceinline__ void lane_compute(const LaneView<typename std::condit
     } else {
       hit[l] = __float_as_int(s0[l].x) >= 0;  // occupied cell (empty records hold 0x80808080)
       vc22[l] = s0[l].y;
+    }
+  }
+  if constexpr (IDS) {  // the canonical id of the voxel each level resolved to, or -1
+    if (F.idx >= 0) {
+#pragma unroll
+      for (int l = 0; l < LMAX; ++l) {
+        if (l >= idl) continue;
+        int id = -1;
+        if (hit[l]) {
+          if constexpr (HASH) id = V.M.lv[l].slot_id[F.slot[l]];
+          else id = __float_as_int(s0[l].x);  // a dense record starts with the id
+        }
+        ids[int64_t(F.idx) * idl + l] = id;
+      }
     }
   }
   // per level: S = C~ + R C R^T, w Omega = w adj(S) / det(S), y = w Omega d, and the sums over
@@ -655,18 +707,25 @@ __device__ __forceinline__ void lane_compute(const LaneView<typename std::condit
   acc.add(27, es);
 }
 
-template <int LMAX, bool HASH, class A>
+template <int LMAX, bool HASH, bool IDS, class A>
 __device__ __forceinline__ void lane_point(const LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V,
-                                           const float4 m, bool live, int validate, A& acc, int& inl, int kk) {
+                                           const float4 m, bool live, int validate, A& acc, int& inl, int kk,
+                                           int32_t* ids, int idl) {
   LaneFetch<LMAX> F;
-  lane_fetch<LMAX, HASH>(V, m, live, validate, kk, F);
-  lane_compute<LMAX, HASH>(V, F, acc, inl);
+  lane_fetch<LMAX, HASH, IDS>(V, m, live, validate, kk, F);
+  lane_compute<LMAX, HASH, IDS>(V, F, acc, inl, ids, idl);
 }
 
-template <int BLOCK, int ACC, int LMAX, bool HASH>
+template <int BLOCK, int ACC, int LMAX, bool HASH, bool IDS>
 __device__ __forceinline__ void process_item_lane(const LinArgs& a, int item,
                                                   LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V) {
   const Item it = a.items[item];
+  int32_t* ids = nullptr;
+  int idl = 0;
+  if constexpr (IDS) {
+    ids = a.ids + a.ids_off[it.pair];
+    idl = a.ids_lv[it.pair];
+  }
   if (threadIdx.x == 0) {
     const PairDev pd = a.pairs[it.pair];
     const PoseF pf = a.pose[it.pair];
@@ -695,20 +754,20 @@ __device__ __forceinline__ void process_item_lane(const LinArgs& a, int item,
     // point are in flight while the lane computes the current one (lane_compute): 9 % faster
     // than reading a point's records at the start of its own round.
     LaneFetch<LMAX> fa, fb;
-    lane_fetch<LMAX, HASH>(V, ldg4(V.pts + min(first, last)), first <= last, a.validate, min(first, last), fa);
+    lane_fetch<LMAX, HASH, IDS>(V, ldg4(V.pts + min(first, last)), first <= last, a.validate, min(first, last), fa);
     float4 pn = ldg4(V.pts + min(first + BLOCK, last));
     int j = 0;
 #pragma unroll 1
     for (; j + 1 < rounds; j += 2) {
       const int k = first + j * BLOCK;
-      lane_fetch<LMAX, HASH>(V, pn, k + BLOCK <= last, a.validate, min(k + BLOCK, last), fb);
+      lane_fetch<LMAX, HASH, IDS>(V, pn, k + BLOCK <= last, a.validate, min(k + BLOCK, last), fb);
       pn = ldg4(V.pts + min(k + 2 * BLOCK, last));
-      lane_compute<LMAX, HASH>(V, fa, acc, inl);
-      lane_fetch<LMAX, HASH>(V, pn, k + 2 * BLOCK <= last, a.validate, min(k + 2 * BLOCK, last), fa);
+      lane_compute<LMAX, HASH, IDS>(V, fa, acc, inl, ids, idl);
+      lane_fetch<LMAX, HASH, IDS>(V, pn, k + 2 * BLOCK <= last, a.validate, min(k + 2 * BLOCK, last), fa);
       pn = ldg4(V.pts + min(k + 3 * BLOCK, last));
-      lane_compute<LMAX, HASH>(V, fb, acc, inl);
+      lane_compute<LMAX, HASH, IDS>(V, fb, acc, inl, ids, idl);
     }
-    if (j < rounds) lane_compute<LMAX, HASH>(V, fa, acc, inl);
+    if (j < rounds) lane_compute<LMAX, HASH, IDS>(V, fa, acc, inl, ids, idl);
   } else {
     // Hash tables: the coordinates one round ahead only.  Holding a second point's home
     // slots (48 bytes per level) costs the hash kernel more registers than the overlap
@@ -719,25 +778,25 @@ __device__ __forceinline__ void process_item_lane(const LinArgs& a, int item,
     for (; j + 1 < rounds; j += 2) {
       const int k = first + j * BLOCK;
       const float4 p1 = ldg4(V.pts + min(k + BLOCK, last));
-      lane_point<LMAX, HASH>(V, p0, k <= last, a.validate, acc, inl, min(k, last));
+      lane_point<LMAX, HASH, IDS>(V, p0, k <= last, a.validate, acc, inl, min(k, last), ids, idl);
       p0 = ldg4(V.pts + min(k + 2 * BLOCK, last));
-      lane_point<LMAX, HASH>(V, p1, k + BLOCK <= last, a.validate, acc, inl, min(k + BLOCK, last));
+      lane_point<LMAX, HASH, IDS>(V, p1, k + BLOCK <= last, a.validate, acc, inl, min(k + BLOCK, last), ids, idl);
     }
     if (j < rounds) {
       const int k = first + j * BLOCK;
-      lane_point<LMAX, HASH>(V, p0, k <= last, a.validate, acc, inl, min(k, last));
+      lane_point<LMAX, HASH, IDS>(V, p0, k <= last, a.validate, acc, inl, min(k, last), ids, idl);
     }
   }
   block_reduce_store<BLOCK, ACC>(acc, inl, a.part + int64_t(item) * PSTRIDE);
 }
 
-template <int BLOCK, int ACC, int LMAX, bool HASH>
+template <int BLOCK, int ACC, int LMAX, bool HASH, bool IDS>
 __device__ __forceinline__ void lane_kernel_body(const LinArgs& a) {
   __shared__ LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type> V;
   __shared__ int s_item[2];
   if (a.head == nullptr) {
     const int item = a.item_base + blockIdx.x;
-    if (item < a.nitems) process_item_lane<BLOCK, ACC, LMAX, HASH>(a, item, V);
+    if (item < a.nitems) process_item_lane<BLOCK, ACC, LMAX, HASH, IDS>(a, item, V);
     return;
   }
   if (threadIdx.x == 0) s_item[0] = atomicAdd(a.head, 1);
@@ -746,19 +805,31 @@ __device__ __forceinline__ void lane_kernel_body(const LinArgs& a) {
   for (int b = 1;; b ^= 1) {
     if (cur >= a.nitems) break;
     if (threadIdx.x == 0) s_item[b] = atomicAdd(a.head, 1);
-    process_item_lane<BLOCK, ACC, LMAX, HASH>(a, cur, V);  // ends with a barrier
+    process_item_lane<BLOCK, ACC, LMAX, HASH, IDS>(a, cur, V);  // ends with a barrier
     cur = s_item[b];
   }
 }
 
 template <int BLOCK, int ACC, int LMAX>
 __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize_dense(const LinArgs a) {
-  lane_kernel_body<BLOCK, ACC, LMAX, false>(a);
+  lane_kernel_body<BLOCK, ACC, LMAX, false, false>(a);
 }
 
 template <int BLOCK, int ACC, int LMAX>
 __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize_hash(const LinArgs a) {
-  lane_kernel_body<BLOCK, ACC, LMAX, true>(a);
+  lane_kernel_body<BLOCK, ACC, LMAX, true, false>(a);
+}
+
+// The id-recording instantiations of the per-lane kernels (inspection and parity tests): the
+// same code plus the stores of the resolved voxel ids.
+template <int BLOCK, int ACC, int LMAX>
+__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize_dense_ids(const LinArgs a) {
+  lane_kernel_body<BLOCK, ACC, LMAX, false, true>(a);
+}
+
+template <int BLOCK, int ACC, int LMAX>
+__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize_hash_ids(const LinArgs a) {
+  lane_kernel_body<BLOCK, ACC, LMAX, true, true>(a);
 }
 
 // Kernel and its dynamic shared memory (bytes) for a configuration; the attribute allowing
@@ -816,6 +887,43 @@ LinKernelInfo pick_lin_lane(int block, int lmax) {
   return LinKernelInfo{};
 }
 
+// The id-recording instantiations (accumulation mode GLIM_ACC_FP64; the lookup and the hit
+// decisions are the same code in every mode): LANE 0 general, 1 dense grid, 2 hash.
+template <int B, int L, int LANE>
+LinKernelInfo lin_ids_info() {
+  LinKernelInfo k;
+  if constexpr (LANE == 1) {
+    k.fn = k_linearize_dense_ids<B, GLIM_ACC_FP64, L>;
+  } else if constexpr (LANE == 2) {
+    k.fn = k_linearize_hash_ids<B, GLIM_ACC_FP64, L>;
+  } else {
+    k.fn = k_linearize_ids<B, GLIM_ACC_FP64, L>;
+    k.smem = lin_dyn_smem<B, L>();
+  }
+  return k;
+}
+
+template <int LANE>
+LinKernelInfo pick_lin_ids_lane(int block, int lmax) {
+#define GLIM_PICK_IDS_L(B)                          \
+  switch (lmax) {                                   \
+    case 1: return lin_ids_info<B, 1, LANE>();      \
+    case 2: return lin_ids_info<B, 2, LANE>();      \
+    case 3: return lin_ids_info<B, 3, LANE>();      \
+    case 4: return lin_ids_info<B, 4, LANE>();      \
+  }                                                 \
+  return LinKernelInfo{};
+  switch (block) {
+    case 128: { GLIM_PICK_IDS_L(128) }
+    case 256: { GLIM_PICK_IDS_L(256) }
+  }
+#undef GLIM_PICK_IDS_L
+  return LinKernelInfo{};
+}
+
+LinKernelInfo pick_lin_ids_general(int block, int lmax);
+LinKernelInfo pick_lin_ids_dense(int block, int lmax);
+LinKernelInfo pick_lin_ids_hash(int block, int lmax);
 LinKernelInfo pick_lin_fp32(int block, int lmax);
 LinKernelInfo pick_lin_kahan(int block, int lmax);
 LinKernelInfo pick_lin_fp64(int block, int lmax);

@@ -40,6 +40,7 @@ struct ReduceArgs {
   double* H;
   double* b;
   long long* inl;
+  double* rec = nullptr;  // optional: per pair the GLIM_RECORD_DOUBLES-double factor record
 };
 
 __global__ void __launch_bounds__(128) k_reduce_expand(const ReduceArgs a) {
@@ -102,22 +103,38 @@ __global__ void __launch_bounds__(128) k_reduce_expand(const ReduceArgs a) {
     T[r][c] = v;
   }
   __syncthreads();
-  for (int i = tid; i < 144; i += blockDim.x) {  // H = Lift^T T
-    const int r = i / 12, c = i % 12;
+  // H = Lift^T T: the 78 entries of the upper triangle (row-major, r <= c), each mirrored,
+  // so that H is exactly symmetric and its record holds every entry
+  double* rec = a.rec ? a.rec + int64_t(p) * GLIM_RECORD_DOUBLES : nullptr;
+  for (int i = tid; i < 78; i += blockDim.x) {
+    int r = 0, rem = i;
+    while (rem >= 12 - r) {  // i-th entry of the row-major upper triangle
+      rem -= 12 - r;
+      ++r;
+    }
+    const int c = r + rem;
     double v = 0.0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) v += L[k][r] * T[k][c];
-    a.H[int64_t(p) * 144 + i] = v;
+    a.H[int64_t(p) * 144 + r * 12 + c] = v;
+    a.H[int64_t(p) * 144 + c * 12 + r] = v;
+    if (rec) rec[1 + i] = v;
   }
   if (tid < 12) {  // b = Lift^T g
     double v = 0.0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) v += L[k][tid] * g[k];
     a.b[int64_t(p) * 12 + tid] = v;
+    if (rec) rec[79 + tid] = v;
   }
   if (tid == 0) {
     a.e[p] = s[27];
-    if (a.inl) a.inl[p] = (long long)(s[NACC] + 0.5);
+    const long long n_in = (long long)(s[NACC] + 0.5);
+    if (a.inl) a.inl[p] = n_in;
+    if (rec) {
+      rec[0] = s[27];
+      rec[91] = double(n_in);
+    }
   }
 }
 
@@ -289,6 +306,7 @@ glim_status plan_enqueue_kernels(glim_plan* p, int slot = -1) {
   r.H = p->out_H();
   r.b = p->out_b();
   r.inl = p->out_inl();
+  r.rec = p->d_rec;
   if (p->npairs > 0) {
     k_reduce_expand<<<p->npairs, 128, 0, ctx->stream>>>(r);
     GLIM_LAUNCHED(ctx);
@@ -341,6 +359,7 @@ void fill_hash_map(const glim_vmap* m, const VoxSlot* empty16, HashMapDev& d) {
       v.mask = uint32_t(m->cap[l] - 1);
       v.log2cap = m->log2cap[l];
       v.max_probe = m->max_probe[l];
+      v.slot_id = m->slot_id[l];
       d.inv_r[l] = m->inv_r[l];
     } else {  // an absent level probes an all-empty table of 16 slots
       v.slots = empty16;
@@ -352,11 +371,16 @@ void fill_hash_map(const glim_vmap* m, const VoxSlot* empty16, HashMapDev& d) {
   }
 }
 
-// The plan holds device pointers to its maps' tables; a map changed since (an insertion
-// frees and replaces them) makes the plan unusable.
-bool plan_maps_current(const glim_plan* p) {
+// The plan holds device pointers to its maps' tables; a map freed since, or changed (an
+// insertion frees and replaces its tables), makes the plan unusable.  A freed map is
+// recognised through the registry of live maps, without reading the freed object; the
+// per-map check runs only when the registry's epoch moved since the last check.
+bool plan_maps_current(glim_plan* p) {
+  const uint64_t epoch = vmap_epoch();
+  if (epoch == p->maps_checked_epoch) return true;
   for (const auto& mv : p->map_versions)
-    if (mv.first->version != mv.second) return false;
+    if (!vmap_alive(mv.m, mv.serial) || mv.m->version != mv.version) return false;
+  p->maps_checked_epoch = epoch;
   return true;
 }
 
@@ -499,7 +523,8 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
   if (opts) o = *opts;
   fill_defaults(o);
   if (!opts_valid(o)) return set_error(ctx, GLIM_EINVAL, "linearize: invalid options");
-  GLIM_CUDA(ctx, cudaSetDevice(ctx->device));
+  DeviceGuard device_guard;
+  GLIM_CUDA(ctx, device_guard.set(ctx->device));
   glim_plan* p = new glim_plan;
   p->ctx = ctx;
   p->nframes = nframes;
@@ -558,7 +583,11 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
     for (size_t i = 0; i < maps.size(); ++i) fill_hash_map(maps[i], p->d_empty_slots, hmd[i]);
   }
   p->nmaps = int(maps.size());
-  for (const glim_vmap* m : maps) p->map_versions.emplace_back(m, m->version);
+  for (const glim_vmap* m : maps) p->map_versions.push_back(glim_plan::MapSeen{m, m->serial, m->version});
+  if (!plan_maps_current(p)) {
+    glim_plan_destroy(p);
+    return set_error(ctx, GLIM_EINVAL, "plan: a target voxelmap is not a live map of this library");
+  }
   p->lmax = 1;
   for (const glim_vmap* m : maps) p->lmax = std::max(p->lmax, m->levels);
   auto fail = [&](glim_status s) {
@@ -589,6 +618,7 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
   if (dmalloc(&p->d_in, p->in_bytes) != cudaSuccess || dmalloc(&p->d_out, p->out_bytes) != cudaSuccess ||
       dmalloc(&p->d_fposes, fpose_bytes) != cudaSuccess ||
       dmalloc(&p->d_pair_frames, std::max(npairs, 1) * sizeof(int2)) != cudaSuccess ||
+      dmalloc(&p->d_rec, std::max<size_t>(size_t(npairs) * GLIM_RECORD_DOUBLES, 1) * sizeof(double)) != cudaSuccess ||
       hmalloc(&p->h_fposes, fpose_bytes) != cudaSuccess ||
       hmalloc(&p->h_out, p->out_bytes) != cudaSuccess)
     return fail(set_error(ctx, GLIM_ENOMEM, "plan: serialized block allocation failed"));
@@ -606,7 +636,8 @@ extern "C" glim_status glim_plan_create(glim_ctx* ctx, const glim_frame* frames,
 
 extern "C" void glim_plan_destroy(glim_plan* p) {
   if (!p) return;
-  cudaSetDevice(p->ctx->device);
+  DeviceGuard device_guard;
+  device_guard.set(p->ctx->device);
   cudaStreamSynchronize(p->ctx->stream);
   drop_graphs(p);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
@@ -627,6 +658,7 @@ extern "C" void glim_plan_destroy(glim_plan* p) {
   cudaFree(p->d_in);
   cudaFree(p->d_fposes);
   cudaFree(p->d_pair_frames);
+  cudaFree(p->d_rec);
   if (p->h_fposes) cudaFreeHost(p->h_fposes);
   cudaFree(p->d_out);
   if (p->h_out) cudaFreeHost(p->h_out);
@@ -708,6 +740,12 @@ extern "C" glim_status glim_plan_device_outputs(glim_plan* p, double** e, double
   return GLIM_OK;
 }
 
+extern "C" glim_status glim_plan_device_records(glim_plan* p, double** rec) {
+  if (!p || !rec) return GLIM_EINVAL;
+  *rec = p->d_rec;
+  return GLIM_OK;
+}
+
 extern "C" glim_status glim_plan_linearize(glim_plan* p, const double* poses12, double* e_out, double* H_out,
                                            double* b_out, int64_t* inliers_out) {
   GLIM_RANGE("glim_plan_linearize");
@@ -771,6 +809,85 @@ extern "C" glim_status glim_plan_linearize_pinned(glim_plan* p, const double* po
   if (H) *H = base + P;
   if (b) *b = base + size_t(P) * 145;
   if (inl) *inl = reinterpret_cast<const int64_t*>(base + size_t(P) * 157);
+  ctx->err.clear();
+  return GLIM_OK;
+}
+
+// Inspection of the correspondences that the plan's own kernel resolves (Sec. III-C
+// "Correspondence search"): the id-recording instantiation of the kernel the plan runs (same
+// lookup and hit code, same launch configuration) linearizes the batch at poses12 and writes
+// the canonical voxel id of every (pair, point, level), or -1.
+extern "C" glim_status glim_plan_correspondence_ids(glim_plan* p, const double* poses12, int32_t* ids_out,
+                                                    double* e_out, double* H_out, double* b_out,
+                                                    int64_t* inliers_out) {
+  GLIM_RANGE("glim_plan_correspondence_ids");
+  if (!p || !poses12) return GLIM_EINVAL;
+  if (maps_current(p) != GLIM_OK) return GLIM_EINVAL;
+  glim_ctx* ctx = p->ctx;
+  if (p->npairs > 0 && !ids_out) return set_error(ctx, GLIM_EINVAL, "plan_correspondence_ids: null ids_out");
+  const int P = p->npairs;
+  std::vector<int64_t> off(std::max(P, 1), 0);
+  std::vector<int32_t> lv(std::max(P, 1), 0);
+  int64_t tot = 0;
+  for (int q = 0; q < P; ++q) {
+    off[q] = tot;
+    lv[q] = p->pairs[q].tgt->levels;
+    tot += p->frames[p->pairs[q].src_frame].n * lv[q];
+  }
+  LinKernelInfo ki;
+  if (p->lane_kernel == 1) ki = pick_lin_ids_dense(p->opts.block, p->lmax);
+  else if (p->lane_kernel == 2) ki = pick_lin_ids_hash(p->opts.block, p->lmax);
+  else ki = pick_lin_ids_general(p->opts.block, p->lmax);
+  if (!ki.fn) return set_error(ctx, GLIM_EINVAL, "plan_correspondence_ids: no kernel for this configuration");
+  GLIM_CUDA(ctx, cudaFuncSetAttribute(reinterpret_cast<const void*>(ki.fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(ki.smem)));
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the pinned pose block may still be read
+  glim_status st = plan_upload_poses(p, poses12);
+  if (st != GLIM_OK) return st;
+  DevBuf<int64_t> d_off;
+  DevBuf<int32_t> d_lv;
+  GLIM_CUDA(ctx, d_off.alloc(off.size(), ctx->stream));
+  GLIM_CUDA(ctx, d_lv.alloc(lv.size(), ctx->stream));
+  GLIM_CUDA(ctx, cudaMemcpyAsync(d_off.p, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+  GLIM_CUDA(ctx, cudaMemcpyAsync(d_lv.p, lv.data(), lv.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+  if (p->nitems > 0) {
+    LinArgs a;
+    a.items = p->d_items;
+    a.nitems = p->nitems;
+    a.item_base = 0;
+    a.pairs = p->d_pairs;
+    a.frames = p->d_frames;
+    a.maps = p->d_maps;
+    a.dmaps = p->lane_kernel == 1 ? p->d_dmaps : nullptr;
+    a.hmaps = p->lane_kernel == 2 ? p->d_hmaps : nullptr;
+    a.pose = p->in_pose32();
+    a.head = p->opts.persistent == 1 ? p->d_head : nullptr;
+    a.part = p->d_part;
+    a.tile = p->tile;
+    a.ppt = p->opts.pts_per_thread;
+    a.validate = p->opts.validate_surface;
+    a.ids = ids_out;
+    a.ids_off = d_off.p;
+    a.ids_lv = d_lv.p;
+    if (p->opts.persistent == 1) GLIM_CUDA(ctx, cudaMemsetAsync(p->d_head, 0, sizeof(int), ctx->stream));
+    ki.fn<<<p->grid, p->opts.block, ki.smem, ctx->stream>>>(a);
+    GLIM_LAUNCHED(ctx);
+  }
+  st = enqueue_reduce_expand(ctx, p->d_part, p->d_item_begin, p->in_pose64(), P,
+                             p->opts.accum_mode == GLIM_ACC_FP32 ? 1 : 0, p->out_e(), p->out_H(), p->out_b(),
+                             p->out_inl());
+  if (st != GLIM_OK) return st;
+  const bool want = e_out || H_out || b_out || inliers_out;
+  if (want && P > 0)
+    GLIM_CUDA(ctx, cudaMemcpyAsync(p->h_out, p->d_out, p->out_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (want && P > 0) {
+    const char* base = reinterpret_cast<const char*>(p->h_out);
+    if (e_out) std::memcpy(e_out, base, P * sizeof(double));
+    if (H_out) std::memcpy(H_out, base + P * sizeof(double), size_t(P) * 144 * sizeof(double));
+    if (b_out) std::memcpy(b_out, base + size_t(P) * 145 * sizeof(double), size_t(P) * 12 * sizeof(double));
+    if (inliers_out) std::memcpy(inliers_out, base + size_t(P) * 157 * sizeof(double), P * sizeof(int64_t));
+  }
   ctx->err.clear();
   return GLIM_OK;
 }

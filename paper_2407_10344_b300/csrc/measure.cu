@@ -35,7 +35,8 @@ __global__ void __launch_bounds__(256) k_fma_chains(T* __restrict__ sink, int it
 template <typename T>
 glim_status fma_peak(glim_ctx* ctx, int32_t iters, double* tflops_out, const char* what) {
   if (!ctx || !tflops_out || iters < 1) return GLIM_EINVAL;
-  GLIM_CUDA(ctx, cudaSetDevice(ctx->device));
+  DeviceGuard device_guard;
+  GLIM_CUDA(ctx, device_guard.set(ctx->device));
   const int blocks = 8 * ctx->num_sms, threads = 256;
   DevBuf<T> sink;
   GLIM_CUDA(ctx, sink.alloc(blocks, ctx->stream));

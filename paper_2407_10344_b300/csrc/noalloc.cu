@@ -40,11 +40,40 @@ struct NoAllocScratch {
 // The scratch array: about 4.5 MB on every device that loads this library, held until exit.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
-// Host staging of the descriptor block (calls must not overlap, see the header).
+// Host staging of the descriptor block (calls must not overlap, see the header).  It is
+// page-locked once per process (cudaHostRegister pins this existing array; nothing is
+// allocated), so that its upload is an asynchronous copy that does not wait for the
+// stream's earlier work.
 static NoAllocHostPart g_stage;
+static bool g_stage_pinned = false;
+static bool g_stage_register_tried = false;
 
-// Device address of g_noalloc_scratch per device, resolved on the first call on that device.
+// Per device, set up on the first call on that device: the device address of
+// g_noalloc_scratch, and an event recorded after each upload of g_stage, so that the next
+// call rewrites g_stage only once that upload has been read.
 static void* g_scratch_addr[NA_MAX_DEVICES] = {nullptr};
+static cudaEvent_t g_stage_read[NA_MAX_DEVICES] = {nullptr};
+static int g_last_device = -1;  // device of the last upload of g_stage (-1: none yet)
+
+// First call on a device (that device current): look up the scratch array's device address,
+// fill the all-empty hash table, wait for that fill, create the upload event.  The address is
+// stored last, so that a failure leaves the device to be set up again by the next call.
+glim_status noalloc_setup(glim_ctx* ctx) {
+  void* ptr = nullptr;
+  GLIM_CUDA(ctx, cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+  NoAllocScratch* d0 = static_cast<NoAllocScratch*>(ptr);
+  GLIM_CUDA(ctx, cudaMemsetAsync(d0->empty16, 0x80, sizeof(d0->empty16), ctx->stream));
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (!g_stage_read[ctx->device])
+    GLIM_CUDA(ctx, cudaEventCreateWithFlags(&g_stage_read[ctx->device], cudaEventDisableTiming));
+  if (!g_stage_register_tried) {
+    g_stage_register_tried = true;
+    g_stage_pinned = cudaHostRegister(&g_stage, sizeof(g_stage), cudaHostRegisterDefault) == cudaSuccess;
+    if (!g_stage_pinned) cudaGetLastError();  // the uploads then stay correct, only synchronous
+  }
+  g_scratch_addr[ctx->device] = ptr;
+  return GLIM_OK;
+}
 
 }  // namespace
 
@@ -75,17 +104,23 @@ extern "C" glim_status glim_linearize_factors_noalloc(glim_ctx* ctx, const glim_
         (reinterpret_cast<uintptr_t>(F.pts4) & 15) || (reinterpret_cast<uintptr_t>(F.cov6) & 7))
       return set_error(ctx, GLIM_EINVAL, "linearize_noalloc: frame %d is invalid", f);
   }
-  GLIM_CUDA(ctx, cudaSetDevice(ctx->device));
+  DeviceGuard device_guard;
+  GLIM_CUDA(ctx, device_guard.set(ctx->device));
+  // The descriptors travel through g_stage, which every call rewrites: a captured call would
+  // replay whatever the latest call left there, so capture is refused.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  GLIM_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return set_error(ctx, GLIM_EINVAL, "linearize_noalloc: the context's stream is capturing a graph");
   // set-up, once per device, with that device current
   if (!g_scratch_addr[ctx->device]) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "linearize_noalloc: cudaGetSymbolAddress");
-    g_scratch_addr[ctx->device] = ptr;
-    NoAllocScratch* d0 = static_cast<NoAllocScratch*>(ptr);
-    GLIM_CUDA(ctx, cudaMemsetAsync(d0->empty16, 0x80, sizeof(d0->empty16), ctx->stream));
+    const glim_status st = noalloc_setup(ctx);
+    if (st != GLIM_OK) return st;
   }
   NoAllocScratch* dev = static_cast<NoAllocScratch*>(g_scratch_addr[ctx->device]);
+  // the previous upload of g_stage (on whichever device) must have been read before it is
+  // rewritten; this waits for no work enqueued after that upload
+  if (g_last_device >= 0) GLIM_CUDA(ctx, cudaEventSynchronize(g_stage_read[g_last_device]));
 
   // descriptors, poses and work list, staged on the host
   NoAllocHostPart& h = g_stage;
@@ -138,6 +173,8 @@ extern "C" glim_status glim_linearize_factors_noalloc(glim_ctx* ctx, const glim_
   }
   h.item_begin[npairs] = nitems;
   GLIM_CUDA(ctx, cudaMemcpyAsync(&dev->host, &h, sizeof(NoAllocHostPart), cudaMemcpyHostToDevice, ctx->stream));
+  GLIM_CUDA(ctx, cudaEventRecord(g_stage_read[ctx->device], ctx->stream));
+  g_last_device = ctx->device;
 
   if (nitems > 0) {
     const LinKernelInfo ki = pick_lin_kernel(o.block, o.accum_mode, lmax, lane);

@@ -42,13 +42,15 @@ struct DenseMapDev {
 };
 
 // One hash level as the per-lane hash kernel sees it (32 bytes, two 16-byte words):
-// {slots, mask, log2cap} {max_probe, ...}.
+// {slots, mask, log2cap} {max_probe, pad, slot_id}.  slot_id (the canonical id of each slot)
+// is read only by the id-recording instantiations.
 struct HashLevelDev {
   const VoxSlot* slots;
   uint32_t mask;
   int32_t log2cap;
   int32_t max_probe;
-  int32_t pad[3];
+  int32_t pad;
+  const int32_t* slot_id;
 };
 
 struct HashMapDev {
@@ -81,6 +83,12 @@ struct LinArgs {
   int32_t tile;      // points per item = blockDim.x * ppt
   int32_t ppt;       // rounds per item (points per thread)
   int32_t validate;
+  // Read only by the id-recording instantiations (*_ids kernels): the canonical voxel id (or
+  // -1) that the kernel resolved for point k of pair p at level l goes to
+  // ids[ids_off[p] + k * ids_lv[p] + l], ids_lv[p] being the levels of the pair's map.
+  int32_t* ids = nullptr;
+  const int64_t* ids_off = nullptr;
+  const int32_t* ids_lv = nullptr;
 };
 
 struct PairView {
@@ -138,7 +146,14 @@ struct glim_plan {
   DenseMapDev* d_dmaps = nullptr;  // set when every level of every target map is a dense grid
   HashMapDev* d_hmaps = nullptr;   // set when every level of every target map is a hash table
   VoxSlot* d_empty_slots = nullptr;  // an all-empty table for the levels a hash map lacks
-  std::vector<std::pair<const glim_vmap*, uint64_t>> map_versions;  // target maps as the plan saw them
+  // target maps as the plan saw them (address, registry serial, table version), and the map
+  // registry's epoch at the last check that found them all unchanged
+  struct MapSeen {
+    const glim_vmap* m;
+    uint64_t serial, version;
+  };
+  std::vector<MapSeen> map_versions;
+  uint64_t maps_checked_epoch = ~0ull;
   int lmax = 1;  // most levels of any target map (kernel template parameter)
   // work list (depends on the tile size)
   Item* d_items = nullptr;
@@ -164,6 +179,8 @@ struct glim_plan {
   size_t out_bytes = 0;
   void* d_out = nullptr;
   void* h_out = nullptr;
+  double* d_rec = nullptr;  // per pair its factor record (GLIM_RECORD_DOUBLES doubles), for exchange
+
   std::vector<cudaEvent_t> ev;       // timing slots: ev[2 s], ev[2 s + 1]
   bool use_graph = true;
   cudaGraphExec_t g_full = nullptr;  // upload + kernels + download
@@ -190,7 +207,8 @@ inline glim_status plan_upload_poses(glim_plan* p, const double* poses12) {
   p->fposes_on_device = st == GLIM_OK;
   return st;
 }
-bool plan_maps_current(const glim_plan* p);  // false once a target map changed since creation
+// false once a target map was freed or had its tables replaced since the plan was created
+bool plan_maps_current(glim_plan* p);
 bool map_all_dense(const glim_vmap* m);     // every level a dense grid
 bool map_all_hash(const glim_vmap* m);      // every level a hash table
 void fill_dense_map(const glim_vmap* m, DenseMapDev& d);

@@ -230,7 +230,8 @@ extern "C" glim_status glim_spatial_order(glim_ctx* ctx, const float* pts4, int6
     return set_error(ctx, GLIM_EINVAL, "spatial_order: bad arguments");
   if (reinterpret_cast<uintptr_t>(pts4) & 15) return set_error(ctx, GLIM_EINVAL, "spatial_order: pts4 misaligned");
   if (n == 0) return GLIM_OK;
-  GLIM_CUDA(ctx, cudaSetDevice(ctx->device));
+  DeviceGuard device_guard;
+  GLIM_CUDA(ctx, device_guard.set(ctx->device));
   DevBuf<unsigned long long> keys, ks;
   DevBuf<uint32_t> idx;
   GLIM_CUDA(ctx, keys.alloc(n, ctx->stream));

@@ -572,7 +572,8 @@ extern "C" glim_status glim_build_voxelmap_ex(glim_ctx* ctx, const float* pts4, 
   for (int l = 0; l < levels; ++l)
     if (!(resolutions[l] > 0.0) || !std::isfinite(resolutions[l]))
       return set_error(ctx, GLIM_EINVAL, "build_voxelmap: resolution %d is not positive", l);
-  GLIM_CUDA(ctx, cudaSetDevice(ctx->device));
+  DeviceGuard device_guard;
+  GLIM_CUDA(ctx, device_guard.set(ctx->device));
   glim_vmap* vm = new glim_vmap;
   vm->device = ctx->device;
   vm->levels = levels;
@@ -587,6 +588,7 @@ extern "C" glim_status glim_build_voxelmap_ex(glim_ctx* ctx, const float* pts4, 
       return st;
     }
   }
+  vmap_register(vm);
   *out = vm;
   ctx->err.clear();
   return GLIM_OK;
@@ -603,7 +605,8 @@ extern "C" glim_status glim_vmap_insert(glim_ctx* ctx, glim_vmap* vm, const floa
   if ((reinterpret_cast<uintptr_t>(pts4) & 15) || (reinterpret_cast<uintptr_t>(cov6) & 7))
     return set_error(ctx, GLIM_EINVAL, "vmap_insert: pts4 must be 16-byte and cov6 8-byte aligned");
   if (vm->device != ctx->device) return set_error(ctx, GLIM_EINVAL, "vmap_insert: map and context devices differ");
-  GLIM_CUDA(ctx, cudaSetDevice(ctx->device));
+  DeviceGuard device_guard;
+  GLIM_CUDA(ctx, device_guard.set(ctx->device));
   // every level is rebuilt into a scratch map first, so that a failure leaves vm unchanged
   glim_vmap tmp;
   tmp.device = vm->device;
@@ -626,13 +629,16 @@ extern "C" glim_status glim_vmap_insert(glim_ctx* ctx, glim_vmap* vm, const floa
   }
   for (int l = 0; l < vm->levels; ++l) move_level(vm, &tmp, l);
   ++vm->version;
+  vmap_bump_epoch();
   ctx->err.clear();
   return GLIM_OK;
 }
 
 extern "C" void glim_vmap_free(glim_vmap* vm) {
   if (!vm) return;
-  cudaSetDevice(vm->device);
+  vmap_unregister(vm);  // plans on this map refuse to launch from now on
+  DeviceGuard device_guard;
+  device_guard.set(vm->device);
   cudaDeviceSynchronize();  // launches on any stream may still read the tables
   free_levels(vm);
   delete vm;

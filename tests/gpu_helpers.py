@@ -65,3 +65,10 @@ def rel_errors(e, H, b, ref):
 
 def numpy_of(x):
     return x.cpu().numpy() if isinstance(x, torch.Tensor) else np.asarray(x)
+
+
+def b_rel_plain(b, ref):
+    """|b - b*|_2 / |b*|_2 per pair: the plain relative error of b, reported beside the P7
+    measure (whose denominator also admits the cancellation-free scale)."""
+    b = np.asarray(b, dtype=np.float64).reshape(-1, 12)
+    return np.linalg.norm(b - ref["b"], axis=1) / np.maximum(np.linalg.norm(ref["b"], axis=1), 1e-300)

@@ -4,7 +4,9 @@
   whole batch runs as one plan (dense-grid kernel, block 128, 64 points per thread, FP64
   cross-block sums, Z-ordered points, persistent work queue); a seeded sample of pairs is
   recomputed by the oracle one pair at a time on the same float32 inputs, and each sampled
-  pair must match (inliers exactly, e / H / b within 1e-4).
+  pair must match (inliers exactly, e / H / b within 1e-4, and the correspondence ids that the
+  kernel's id-recording instantiation resolved, in the same launch configuration, bit for
+  bit).  The plain relative error of b, |b - b*| / |b*|, is bounded as well.
 * Odometry window at its full size (30k-point frame, 10 keyframes, per-point weights): the
   gradient of the batch against the oracle's analytic gradient.
 """
@@ -32,7 +34,7 @@ def ctx(G):
 
 
 def test_urban_global_step_full_size_sampled_pairs(G, ctx):
-    from gpu_helpers import rel_errors
+    from gpu_helpers import b_rel_plain, rel_errors
     w = synth.urban(n_submaps=400)
     dev = torch.device("cuda", ctx.device)
     frames, maps = [], [None] * len(w.points)
@@ -47,20 +49,28 @@ def test_urban_global_step_full_size_sampled_pairs(G, ctx):
             maps[i] = G.VoxelMap(ctx, p4, cov, w.resolutions)
     plan = G.Plan(ctx, frames, maps, w.pairs, accum_mode=G.ACC_FP64, block=128, pts_per_thread=64)
     assert plan.opts()["kernel"] == "dense"
-    e, H, b, inl = plan.linearize(w.poses)
+    e, H, b, inl = [np.array(x) for x in plan.linearize(w.poses)]
     assert np.isfinite(e).all() and np.isfinite(H).all() and np.isfinite(b).all()
+    ids, (e_i, H_i, b_i, inl_i) = plan.correspondence_ids(w.poses)
+    assert np.array_equal(e_i, e) and np.array_equal(H_i, H) and np.array_equal(b_i, b)
+    L = len(w.resolutions)
+    off = np.concatenate([[0], np.cumsum([frames[int(s_)].n * L for s_ in w.pairs[:, 0]])])
     sample = np.sort(synth.Stream(11, "urban-sample").integers(8, 0, len(w.pairs)))
-    worst = [0.0, 0.0, 0.0]
+    worst = [0.0, 0.0, 0.0, 0.0]
     for q in sample:
         s, t = int(w.pairs[q, 0]), int(w.pairs[q, 1])
         fs = O.Frame(frames[s].pts4.cpu().numpy(), frames[s].cov6.cpu().numpy(), frames[s].normal3.cpu().numpy())
         ft = O.Frame(frames[t].pts4.cpu().numpy(), frames[t].cov6.cpu().numpy())
         vm = O.VMap(ft.pts4, ft.cov6, w.resolutions)
         ref = O.linearize([fs, ft], [None, vm], np.array([[0, 1]], np.int32), np.stack([w.poses[s], w.poses[t]]),
-                          want_comp=True)
+                          want_comp=True, want_ids=True)
         assert inl[q] == ref["inliers"][0], (q, inl[q], ref["inliers"][0])
+        got = ids[int(off[q]):int(off[q + 1])].cpu().numpy()
+        assert np.array_equal(got, ref["ids"]), (q, int((got != ref["ids"]).sum()))
         ee, eH, eb = rel_errors(e[q:q + 1], H[q:q + 1], b[q:q + 1], ref)
-        worst = [max(worst[0], ee[0]), max(worst[1], eH[0]), max(worst[2], eb[0])]
+        ebp = b_rel_plain(b[q:q + 1], ref)
+        worst = [max(worst[0], ee[0]), max(worst[1], eH[0]), max(worst[2], eb[0]), max(worst[3], ebp[0])]
+    print("urban full size, worst over sampled pairs: e %.2e  H %.2e  b (P7) %.2e  b plain %.2e" % tuple(worst))
     assert max(worst) <= TOL, worst
 
 

@@ -627,7 +627,10 @@ def test_autograd_interleaved_evaluations(G, ctx):
 
 
 # ---------------------------------------------------------------------------- small factor graph
-def test_graph_step_assembly_and_solve_against_numpy(G, ctx):
+def test_graph_step_assembly_and_solve_against_oracle(G, ctx):
+    """glim_graph_step (device assembly + damped FP64 Cholesky) against the oracle's
+    orc_graph_step on a random graph, for a fixed frame and plain GN, a fixed frame with LM
+    damping, and no fixed frame with damping."""
     s = synth.Stream(77, "graph")
     n, P = 7, 18
     pairs = []
@@ -644,21 +647,10 @@ def test_graph_step_assembly_and_solve_against_numpy(G, ctx):
     b = torch.as_tensor(np.stack(bs), device="cuda")
     for fixed, lam in ((0, 0.0), (3, 1e-3), (-1, 0.5)):
         xi, Hg, bg = G.graph_step(ctx, pairs, n, H, b, fixed_frame=fixed, lam=lam, want_system=True)
-        Hn = np.zeros((6 * n, 6 * n))
-        bn = np.zeros(6 * n)
-        for p, (a, c) in enumerate(pairs):  # the global system, block by block, pairs in order
-            for (ra, fa) in ((0, a), (6, c)):
-                bn[6 * fa:6 * fa + 6] += bs[p][ra:ra + 6]
-                for (cb, fb) in ((0, a), (6, c)):
-                    Hn[6 * fa:6 * fa + 6, 6 * fb:6 * fb + 6] += Hs[p][ra:ra + 6, cb:cb + 6]
-        np.testing.assert_allclose(Hg.cpu().numpy(), Hn, rtol=1e-14, atol=1e-12)
-        np.testing.assert_allclose(bg.cpu().numpy(), bn, rtol=1e-14, atol=1e-12)
-        free = [i for i in range(6 * n) if fixed < 0 or not (6 * fixed <= i < 6 * fixed + 6)]
-        A = Hn[np.ix_(free, free)]
-        A = A + lam * np.diag(np.diag(A))
-        x = np.zeros(6 * n)
-        x[free] = np.linalg.solve(A, -bn[free])
-        np.testing.assert_allclose(xi.cpu().numpy().reshape(-1), x, rtol=1e-9, atol=1e-9 * np.abs(x).max())
+        oxi, oHg, obg = O.graph_step(pairs, n, Hs, bs, fixed=fixed, lam=lam)
+        np.testing.assert_allclose(Hg.cpu().numpy(), oHg, rtol=1e-14, atol=1e-12)
+        np.testing.assert_allclose(bg.cpu().numpy(), obg, rtol=1e-14, atol=1e-12)
+        np.testing.assert_allclose(xi.cpu().numpy(), oxi, rtol=1e-9, atol=1e-9 * np.abs(oxi).max())
     # relative-pose factors alone leave the gauge free: not positive definite without a fixed frame
     with pytest.raises(G.GlimError, match="ENOTPD"):
         gh = torch.zeros((1, 144), dtype=torch.float64, device="cuda")
@@ -846,3 +838,31 @@ def test_keys_at_the_edge_of_the_key_range(G, ctx, layout):
             assert (ids[:, n - 2:] < 0).all()
         else:  # the shift moves the last x-voxel of A past 2^20 - 1 at level 0
             assert (ids[0, :m, 0] < 0).any() and (ids[0, :m, 0] >= 0).any()
+
+
+# ---------------------------------------------------------------------------- C-level guards
+def test_plan_on_a_map_freed_through_the_c_abi_is_refused(G, ctx, corridor):
+    """A plan whose target map was freed with glim_vmap_free (bypassing the Python binding's
+    own guard) returns GLIM_EINVAL from its launch entry points instead of reading freed
+    tables; a plan on live maps is unaffected, and the caller's current device is kept."""
+    import ctypes as C
+    w = corridor.w
+    t = int(w.pairs[0, 1])
+    g = corridor.gframes[t]
+    vm = G.VoxelMap(ctx, g.pts4, g.cov6, w.resolutions)
+    maps = list(corridor.gmaps)
+    maps[t] = vm
+    plan = G.Plan(ctx, corridor.gframes, maps, w.pairs)
+    other = G.Plan(ctx, corridor.gframes, corridor.gmaps, w.pairs)
+    plan.linearize(w.poses)
+    ctx.lib.glim_vmap_free(vm.h)  # the C call alone: the binding does not see it
+    poses = np.ascontiguousarray(w.poses.reshape(-1, 12))
+    assert ctx.lib.glim_plan_launch(plan.h) == -1
+    assert ctx.lib.glim_plan_set_poses(plan.h, poses.ctypes.data_as(C.c_void_p)) in (0, -1)
+    assert ctx.lib.glim_plan_launch_timed(plan.h, 0) == -1
+    e, H, b, inl = other.linearize(w.poses)
+    assert np.isfinite(H).all() and (inl > 0).all()
+    vm.h = None  # already freed
+    plan.close()
+    other.close()
+    assert torch.cuda.current_device() == 0

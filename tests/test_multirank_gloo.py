@@ -1,6 +1,8 @@
-"""Multi-rank host logic on the CPU with the gloo backend (world size 2): sharding the pair
-list by source frame and gathering the per-rank (e, H, b) records reproduces the single-rank
-result bit for bit (the oracle stands in for the per-rank compute; no GPU), and the bench's
+"""Multi-rank host logic on the CPU with the gloo backend: the global step sharded by source
+frame (shard_pairs, frames_needed), each rank's factors packed into records (pack_records)
+and exchanged with one all-gather (gather_records) reproduces the single-rank result bit for
+bit.  The oracle stands in for each rank's GPU compute (no GPU here); the packing, the
+exchange and the placement in pair order are the package's own.  Also: the bench's
 cross-rank aggregation takes the slowest time and the total work."""
 import os
 import socket
@@ -18,7 +20,7 @@ def _free_port():
     return port
 
 
-def _worker(rank, world, port, out):
+def _worker(rank, world, port, keep, out):
     import torch
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
@@ -28,48 +30,70 @@ def _worker(rank, world, port, out):
         import bench
         import synth
         from oracle import oracle as O
-        from paper_2407_10344_b300.api import frames_needed, shard_pairs
-        w = synth.urban(n_submaps=400, keep=8, neighbours=3, point_scale=0.02)
+        from paper_2407_10344_b300.api import frames_needed, gather_records, pack_records, shard_pairs, unpack_records
+        w = synth.urban(n_submaps=400, keep=keep, neighbours=3, point_scale=0.02)
+        P = len(w.pairs)
         idx = shard_pairs(w.pairs, rank, world)
         need = frames_needed(w.pairs, idx)
         cov = [np.tile(np.array([1.0, 0, 0, 1.0, 0, 1e-3], np.float32), (len(p), 1)) for p in w.points]
         frames = [O.Frame(O.as_pts4(p), c) for p, c in zip(w.points, cov)]
         vmaps = [O.VMap(frames[f].pts4, frames[f].cov6, w.resolutions) if f in need else None
                  for f in range(len(frames))]
-        r = O.linearize(frames, vmaps, w.pairs[idx], w.poses) if len(idx) else dict(e=[], H=[], b=[])
-        gathered = [None] * world
-        dist.all_gather_object(gathered, (idx.tolist(), np.asarray(r["e"]), np.asarray(r["H"]), np.asarray(r["b"])))
+        if len(idx):
+            r = O.linearize(frames, vmaps, w.pairs[idx], w.poses)
+            rec = pack_records(r["e"], r["H"], r["b"], r["inliers"])
+        else:
+            rec = np.zeros((0, 92))
+        full_rec = gather_records(torch.as_tensor(rec), idx, P)  # every rank gets all records
         tmax, total = bench.aggregate_over_ranks(10.0 + rank, 100 * (rank + 1), torch.device("cpu"))
         if rank == 0:
             all_vm = [O.VMap(f.pts4, f.cov6, w.resolutions) for f in frames]
             full = O.linearize(frames, all_vm, w.pairs, w.poses)
-            e = np.zeros(len(w.pairs))
-            H = np.zeros((len(w.pairs), 12, 12))
-            b = np.zeros((len(w.pairs), 12))
-            seen = []
-            for ids, ee, HH, bb in gathered:
-                seen += ids
-                if len(ids):
-                    e[ids], H[ids], b[ids] = ee, HH, bb
-            ok = (sorted(seen) == list(range(len(w.pairs))) and np.array_equal(e, full["e"])
-                  and np.array_equal(H, full["H"]) and np.array_equal(b, full["b"])
-                  and tmax == 11.0 and total == 300.0 and all(len(g[0]) > 0 for g in gathered))
-            out.put(bool(ok))
+            ref = pack_records(full["e"], full["H"], full["b"], full["inliers"])
+            e, H, b, inl = unpack_records(full_rec)
+            iu = np.triu_indices(12)
+            sizes = [len(shard_pairs(w.pairs, q, world)) for q in range(world)]
+            ok = (np.array_equal(full_rec.numpy(), ref) and np.array_equal(e, full["e"])
+                  and np.array_equal(H[:, iu[0], iu[1]], full["H"][:, iu[0], iu[1]])
+                  and np.array_equal(H, np.transpose(H, (0, 2, 1))) and np.array_equal(b, full["b"])
+                  and np.array_equal(inl, full["inliers"]) and sum(sizes) == P
+                  and tmax == 10.0 + world - 1 and total == 100.0 * world * (world + 1) / 2)
+            out.put((bool(ok), sizes))
     finally:
         dist.destroy_process_group()
 
 
-def test_sharded_pairs_gather_to_the_full_result():
+@pytest.mark.parametrize("world,keep", [(2, 8), (3, 2)])
+def test_sharded_pairs_gather_to_the_full_result(world, keep):
+    """world 2 over 8 source submaps; world 3 over 2 source submaps (one rank holds no pair)."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, keep, q)) for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
         p.join(timeout=300)
     assert all(p.exitcode == 0 for p in procs)
-    assert q.get(timeout=10) is True
+    ok, sizes = q.get(timeout=10)
+    assert ok, sizes
+    if keep == 2:
+        assert 0 in sizes
+
+
+def test_records_round_trip():
+    from paper_2407_10344_b300.api import pack_records, unpack_records
+    rng = np.random.default_rng(1)
+    A = rng.normal(size=(5, 12, 12))
+    H = A + np.transpose(A, (0, 2, 1))
+    e, b, inl = rng.normal(size=5), rng.normal(size=(5, 12)), np.arange(5) * 1000
+    rec = pack_records(e, H, b, inl)
+    assert rec.shape == (5, 92)
+    e2, H2, b2, inl2 = unpack_records(rec)
+    assert np.array_equal(e2, e) and np.array_equal(H2, H) and np.array_equal(b2, b) and np.array_equal(inl2, inl)
+    import torch
+    rt = pack_records(torch.as_tensor(e), torch.as_tensor(H), torch.as_tensor(b), torch.as_tensor(inl))
+    assert np.array_equal(rt.numpy(), rec)
 
 
 def test_shard_pairs_partitions_by_source():

@@ -57,6 +57,24 @@ def test_single_point_hand_computed():
     np.testing.assert_allclose(r["H"][0], np.array(g["H"], float), atol=1e-12)
 
 
+def test_b_scale_of_cancelling_terms():
+    """The cancellation-free scale of b (the second denominator of the b parity measure) is
+    the sum over terms of |w J^T Omega d|: two terms whose contributions cancel give b = 0
+    and a scale of sqrt(29/8), not 0 (the norm of the sum) and not sqrt(29/32) (without w)."""
+    g = json.load(open(os.path.join(GOLD, "cancelling_b_terms.json")))
+    pts = np.array(g["points"])
+    cov = np.array([g["cov"]] * len(pts), np.float32)
+    src = O.Frame(O.as_pts4(pts, np.full(len(pts), g["weight"])), cov)
+    tgt = O.Frame(O.as_pts4(pts), cov)
+    vm = O.VMap(tgt.pts4, tgt.cov6, [g["resolution"]])
+    r = O.linearize([src, tgt], [None, vm], [[0, 1]], np.stack([np.eye(3, 4), np.eye(3, 4)]), want_comp=True)
+    assert r["inliers"][0] == g["inliers"]
+    assert abs(r["e"][0] - g["e"]) < 1e-15
+    np.testing.assert_array_equal(r["b"][0], np.array(g["b"]))
+    assert abs(r["b_scale"][0] - g["b_scale"]) < 1e-14
+    assert abs(g["b_scale"] - np.sqrt(29 / 8)) < 1e-15
+
+
 def test_voxel_statistics_closed_form():
     g = json.load(open(os.path.join(GOLD, "two_point_voxel.json")))
     vm = O.VMap(O.as_pts4(np.array(g["points"])), np.array(g["covs"], np.float32), [g["resolution"]])
@@ -510,3 +528,88 @@ def test_overlap_rate_counts_hits(room):
     for l in range(L):
         ov = O.overlap(fr[0], vms[1], w.poses[0], w.poses[1], level=l)
         assert ov == pytest.approx((ids[:, l] >= 0).mean(), abs=0)
+
+
+# ---------------------------------------------------------------------------- graph step (Sec. V-A)
+def _random_graph(seed, n, P):
+    s = synth.Stream(seed, "graph-pin")
+    pairs = []
+    while len(pairs) < P:
+        a, b_ = (int(v) for v in s.integers(2, 0, n))
+        if a != b_:
+            pairs.append((a, b_))
+    return s, pairs
+
+
+def test_graph_step_recovers_a_consistent_linear_model():
+    """Each factor p is the Gauss-Newton form of the residual r_p(x) = A_p x_s + B_p x_t + c_p
+    (H = J^T J, b = J^T c with J = [A_p, B_p]), where c_p = -(A_p x*_s + B_p x*_t) for fixed
+    per-frame offsets x* with x*_0 = 0.  The stacked least-squares problem then has the exact
+    solution x*, so the undamped step with frame 0 fixed must return x* (to rounding),
+    whatever the pair order and directions."""
+    n = 6
+    s, pairs = _random_graph(3, n, 16)
+    xs = s.normal(6 * n).reshape(n, 6)
+    xs[0] = 0.0
+    H, b = [], []
+    for a, c in pairs:
+        A = s.normal(3 * 6 * 3).reshape(9, 6)
+        B = s.normal(3 * 6 * 3).reshape(9, 6)
+        J = np.hstack([A, B])
+        r = -(A @ xs[a] + B @ xs[c])
+        H.append(J.T @ J)
+        b.append(J.T @ r)
+    xi, Hg, bg = O.graph_step(pairs, n, H, b, fixed=0)
+    np.testing.assert_allclose(xi, xs, atol=1e-10)
+    assert (xi[0] == 0).all()
+    # the same graph with the pairs reversed (source and target swapped, blocks swapped)
+    perm = np.r_[6:12, 0:6]
+    H2 = [h[np.ix_(perm, perm)] for h in H[::-1]]
+    b2 = [v[perm] for v in b[::-1]]
+    xi2, Hg2, bg2 = O.graph_step([(c, a) for a, c in pairs[::-1]], n, H2, b2, fixed=0)
+    np.testing.assert_allclose(xi2, xs, atol=1e-10)
+    np.testing.assert_allclose(Hg2, Hg, rtol=1e-14, atol=1e-12)
+
+
+def test_graph_step_assembly_is_the_sum_of_selected_blocks():
+    """H_glob = sum_p E_p^T H_p E_p and b_glob = sum_p E_p^T b_p, with E_p the 12 x 6n matrix
+    that selects the source and target variables of pair p; integer-valued factors make both
+    sides exact."""
+    n = 5
+    s, pairs = _random_graph(4, n, 11)
+    H = [np.round(s.normal(144).reshape(12, 12) * 8) for _ in pairs]
+    b = [np.round(s.normal(12) * 8) for _ in pairs]
+    Hn = np.zeros((6 * n, 6 * n))
+    bn = np.zeros(6 * n)
+    for (a, c), h, v in zip(pairs, H, b):
+        E = np.zeros((12, 6 * n))
+        E[0:6, 6 * a:6 * a + 6] = np.eye(6)
+        E[6:12, 6 * c:6 * c + 6] = np.eye(6)
+        Hn += E.T @ h @ E
+        bn += E.T @ v
+    # make the system positive definite so that the step exists; the assembly is checked as is
+    Hpd = [h @ h.T + 12 * np.eye(12) for h in H]
+    _, Hg, bg = O.graph_step(pairs, n, Hpd, b, fixed=2)
+    Hn_pd = sum(np.block([[np.eye(6 * n)[:, 6 * a:6 * a + 6], np.eye(6 * n)[:, 6 * c:6 * c + 6]]]) @ h @
+                np.block([[np.eye(6 * n)[:, 6 * a:6 * a + 6], np.eye(6 * n)[:, 6 * c:6 * c + 6]]]).T
+                for (a, c), h in zip(pairs, Hpd))
+    assert np.array_equal(Hg, Hn_pd)
+    assert np.array_equal(bg, bn)
+
+
+def test_graph_step_damping_closed_form_and_gauge():
+    """One factor between two frames with a diagonal H, frame 0 fixed: the step of frame 1 is
+    -b_t / ((1 + lambda) h_t) per variable.  Relative factors alone leave the gauge free: with
+    no frame fixed the system is singular and the step is refused."""
+    h = np.arange(1.0, 13.0)
+    bvec = np.linspace(-3.0, 2.5, 12)
+    for lam in (0.0, 0.5, 1e-3):
+        xi, _, _ = O.graph_step([(0, 1)], 2, [np.diag(h)], [bvec], fixed=0, lam=lam)
+        assert (xi[0] == 0).all()
+        np.testing.assert_allclose(xi[1], -bvec[6:] / ((1 + lam) * h[6:]), rtol=1e-15)
+    K = np.arange(1.0, 37.0).reshape(6, 6) + 6 * np.eye(6)
+    J = np.hstack([K, -K])  # a relative residual: moving both frames together changes nothing
+    with pytest.raises(np.linalg.LinAlgError):
+        O.graph_step([(0, 1)], 2, [J.T @ J], [np.zeros(12)], fixed=-1)
+    xi, _, _ = O.graph_step([(0, 1)], 2, [J.T @ J], [J.T @ np.ones(6)], fixed=0)
+    np.testing.assert_allclose(K @ xi[1], np.ones(6), atol=1e-9)  # r = K x_0 - K x_1 + 1 = 0 with x_0 = 0

@@ -84,3 +84,30 @@ def test_noalloc_rejects_batches_beyond_its_limits():
     too_many = np.repeat(w.pairs, 26, axis=0)  # 260 pairs > 256
     with pytest.raises(G.GlimError, match="exceed the limits"):
         _call_noalloc(G, _abi, ctx, w, frames, maps, too_many)
+
+
+def test_noalloc_refuses_stream_capture():
+    """Every call stages its descriptors in one host block that the next call rewrites, so a
+    call made while the context's stream captures a graph is refused (GLIM_EINVAL) and
+    enqueues nothing; a call after the capture works as before."""
+    G, _abi, ctx, w, frames, maps = _setup()
+    ref = _call_noalloc(G, _abi, ctx, w, frames, maps, w.pairs)  # the set-up happens before any capture
+    fr = (_abi.Frame * len(frames))(*[f.c() for f in frames])
+    pr = (_abi.Pair * len(w.pairs))(*[_abi.Pair(int(s), int(t), maps[int(t)].h.value) for s, t in w.pairs])
+    poses = np.ascontiguousarray(w.poses.reshape(-1, 12))
+    P = len(w.pairs)
+    shapes = [((P,), torch.float64), ((P * 144,), torch.float64), ((P * 12,), torch.float64), ((P,), torch.int64)]
+    out = [torch.empty(n, dtype=dt, device="cuda") for n, dt in shapes]
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(ctx.stream):
+        g.capture_begin()
+        try:
+            st = ctx.lib.glim_linearize_factors_noalloc(ctx.h, fr, len(frames), pr, P, poses.ctypes.data_as(C.c_void_p),
+                                                        None, *[C.c_void_p(t.data_ptr()) for t in out])
+        finally:
+            g.capture_end()
+    assert st == -1
+    assert b"capturing" in ctx.lib.glim_last_error(ctx.h)
+    e, H, b, inl = _call_noalloc(G, _abi, ctx, w, frames, maps, w.pairs)
+    assert np.array_equal(inl, ref[3]) and np.array_equal(H, ref[1])
