@@ -32,14 +32,38 @@ UNIT = "points/s"
 BYTES_PER_POINT = 40  # float4 point + 6 floats covariance, read once per (pair, point)
 BYTES_PER_TOUCHED_VOXEL = 56  # 8-byte key + 48-byte statistics, each voxel a pair hits, once
 BYTES_OUT_PER_PAIR = 157 * 8 + 8  # e, H (144), b (12) in FP64 and the inlier count
-# DRAM bytes (read + write) per (pair, point) of the linearization kernel, from one ncu capture
-# of this kernel version on the 40-submap urban case (k_linearize_dense_urban40_ncu_full.md
-# under profiles), scaled by the units of a launch.  None
-# when the kernel has changed since the capture.
-DRAM_BYTES_PER_PAIR_POINT = 12.17
-# ncu DRAM bytes (read + write) per (pair, point) of the terrain launch (1M-point scan vs the
-# 282 MB dense grid of a 20M-point map), from the one-pass capture of that batch
-TERRAIN_DRAM_BYTES_PER_PAIR_POINT = 77.9
+# DRAM bytes (read + write) per (pair, point) of a kernel come from committed ncu capture
+# summaries: a line "traffic per (pair, point): <bytes> B; kernel source digest: <digest>" in
+# the summary named below.  The figure is used only while the digest of the kernel's sources
+# still matches the one it was captured with; otherwise `traffic` is null.
+KERNEL_SOURCES = ["lin_kernel.cuh", "lookup.cuh", "plan.cuh", "common.cuh", "lin_dense_fp64.cu"]
+TRAFFIC_SUMMARIES = {"urban": "k_linearize_dense_urban40_ncu_full.md", "terrain": "k_linearize_dense_terrain_ncu.md"}
+
+
+def kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2407_10344_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(workload):
+    """(bytes per (pair, point), digest) from the capture summary, or (None, reason)."""
+    import re
+    path = os.path.join(ROOT, "profiles", TRAFFIC_SUMMARIES.get(workload, ""))
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None, "no capture summary"
+    m = re.search(r"traffic per \(pair, point\): ([0-9.]+) B; kernel source digest: ([0-9a-f]+)", txt)
+    if not m:
+        return None, "no traffic line in the capture summary"
+    if m.group(2) != kernel_digest():
+        return None, "the kernel changed since the capture (digest %s, now %s)" % (m.group(2), kernel_digest())
+    return float(m.group(1)), m.group(2)
+
+
 # Algorithmic FP32 flops of the linearization, counted on the per-term evaluation (a fused
 # multiply-add counts two): per (pair, point) the transform (18), 3 key products per level,
 # R C R^T (75) and u (3); per hit term S = C~ + R C R^T (6), d (3), the adjugate (18), det (5),
@@ -94,6 +118,18 @@ def workload_desc(w, args):
     return "corridor odometry window: 30k-pt frame vs 10 keyframes of 15k-40k pts, 0.5 m voxels" + extra
 
 
+def workload_config(w, args, ws):
+    """The `config` of the JSON line: the workload alone, identical in both arms."""
+    n_pp = w.n_pair_points
+    src = BYTES_PER_POINT * n_pp
+    return {"workload": workload_desc(w, args), "pairs": int(len(w.pairs)), "frames": len(w.points),
+            "pair_points_per_step": int(n_pp), "levels": len(w.resolutions), "resolutions_m": list(w.resolutions),
+            "l2": ("inputs larger than L2: %.2f GB source stream per step (L2 126 MB)" % (src / 1e9) if src > 126e6
+                   else "L2 not flushed: the %.3f GB source stream fits in L2 (126 MB), a warm-cache figure"
+                   % (src / 1e9)),
+            "parallelism": "one worker" if ws == 1 else f"pairs sharded by source submap over {ws} workers"}
+
+
 # ---------------------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -145,9 +181,15 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------- CPU oracle leg
+COV_STANDIN = ("covariances are a stand-in (one plane covariance diag(1, 1, 1e-3) for every point): the oracle's "
+               "brute-force kNN is quadratic in the frame size; the oracle's lookups and per-term FP64 arithmetic "
+               "do not depend on the covariance values")
+
+
 def oracle_sample(w, budget_s=15.0, nthreads=None, target_points=30_000_000, single_thread=False):
     """Time the FP64 oracle on the first pairs of the workload (about budget_s of CPU work).
-    Covariances here are a plain stand-in (identity-plane) since only linearization is timed."""
+    Covariances here are a plain stand-in (one plane covariance for every point), since only
+    the linearization is timed."""
     from oracle import oracle as O
     nthreads = nthreads or os.cpu_count()
     pairs = []
@@ -174,9 +216,9 @@ def oracle_sample(w, budget_s=15.0, nthreads=None, target_points=30_000_000, sin
     t0 = time.perf_counter()
     O.linearize(fr, vm, pr, poses, nthreads=nthreads)
     dt = time.perf_counter() - t0
-    out = dict(value=pts / dt, unit=UNIT, cores=nthreads, kind="oracle",
+    out = dict(value=pts / dt, unit=UNIT, cores=nthreads, kind="oracle", pair_points=int(pts), seconds=dt,
                sample=f"first {len(pairs)} of {len(w.pairs)} pairs ({pts} pair-points), std::map voxelmaps prebuilt, "
-                      f"{dt:.1f} s wall on {nthreads} threads")
+                      f"{dt:.1f} s wall on {nthreads} threads; " + COV_STANDIN)
     if single_thread:  # the same oracle on one thread, on the first pair only
         n1 = len(fr[pr[0, 0]].pts4)
         t0 = time.perf_counter()
@@ -373,10 +415,19 @@ def small_workloads(G, ctx, dev):
     plant.set_poses(wt.poses)
     for i in range(8):
         plant.launch_timed(i)
+    t_warm = float(np.median(plant.kernel_ms(8)[3:]))  # back to back: the 40 MB source stays in L2
+    # cold L2: before each timed launch, write a 256 MB buffer (twice the L2) on the stream the
+    # launch waits for; only the linearization kernel is inside the events
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for i in range(8):
+        flush.fill_(float(i))
+        plant.launch_timed(i)
     t_ms = float(np.median(plant.kernel_ms(8)[3:]))
+    del flush
     out["terrain"] = {"workload": "terrain: 1M-pt scan vs 20M-pt map (0.25 m, one level), unary factor",
                       "pair_points": wt.n_pair_points, "kernel": plant.opts()["kernel"],
-                      "kernel_ms": t_ms, "points_per_s": wt.n_pair_points / (t_ms / 1e3),
+                      "kernel_ms": t_ms, "kernel_ms_note": "cold L2 (256 MB written before each launch)",
+                      "kernel_ms_back_to_back": t_warm, "points_per_s": wt.n_pair_points / (t_ms / 1e3),
                       "e2e_plan_linearize_ms": med(lambda: plant.linearize(wt.poses), reps=10),
                       "voxels": mt[int(wt.pairs[0, 1])].info(0)["n_voxels"],
                       "dense_grid": bool(mt[int(wt.pairs[0, 1])].is_dense(0))}
@@ -384,12 +435,14 @@ def small_workloads(G, ctx, dev):
     hbm = pk.get("hbm_gbs", 6400.0)
     n_t = wt.n_pair_points
     alg_gbs = BYTES_PER_POINT * n_t / (t_ms / 1e3) / 1e9
-    dram_gbs = TERRAIN_DRAM_BYTES_PER_PAIR_POINT * n_t / (t_ms / 1e3) / 1e9
+    t_bpp, t_src = captured_traffic("terrain")
+    dram_gbs = None if t_bpp is None else t_bpp * n_t / (t_ms / 1e3) / 1e9
     out["terrain"]["roofline"] = {
         "bound": "hbm", "achieved": alg_gbs, "peak": hbm, "unit": "GB/s", "frac": alg_gbs / hbm,
-        "traffic": TERRAIN_DRAM_BYTES_PER_PAIR_POINT * n_t, "dram_achieved": dram_gbs, "dram_frac": dram_gbs / hbm,
-        "note": "achieved: 40 B of source stream per point; traffic: ncu DRAM bytes of this launch (the grid "
-                "gathered from HBM); a warm-L2, ~20 us launch dominated by ramp and drain",
+        "traffic": None if t_bpp is None else t_bpp * n_t, "traffic_source": t_src, "dram_achieved": dram_gbs,
+        "dram_frac": None if dram_gbs is None else dram_gbs / hbm,
+        "note": "achieved: 40 B of source stream per point over the cold-L2 launch time; traffic: ncu DRAM bytes "
+                "of this launch (the grid gathered from HBM)",
         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk else "fallback"}
     del ft, mt, plant
     poses = gn10()
@@ -462,7 +515,7 @@ def sharded_e2e_and_check(G, ctx, plan, recs, args, w, full_batch, idx, need, P_
     return e2e, check
 
 
-def sharded_line(w, args, ws, K, W, tmax, value, P_all, n_pp_all, plan, kern_ms, n_pp, e2e, check, launches, clk,
+def sharded_line(cfg, args, ws, K, W, tmax, value, P_all, n_pp_all, plan, kern_ms, n_pp, e2e, check, launches, clk,
                  gen_s):
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6400.0)
@@ -472,14 +525,10 @@ def sharded_line(w, args, ws, K, W, tmax, value, P_all, n_pp_all, plan, kern_ms,
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
             "ms_per_step": tmax / K, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"urban global step: {args.submaps} submaps of log-U[50k,200k] pts, {P_all} pairs "
-                                   "(10 nearest), voxels 0.5/1/2 m", "pairs": P_all,
-                       "pair_points_per_step": n_pp_all, "accum_mode": args.accum, "block": opts["block"],
-                       "pts_per_thread": opts["pts_per_thread"],
-                       "parallelism": f"pairs sharded by source submap over {ws} GPUs; one all-gather of the "
-                                      "92-double per-pair records per step",
-                       "l2": "inputs larger than L2 (%.2f GB source stream per step)" % (BYTES_PER_POINT * n_pp_all / 1e9),
-                       "generation_s": round(gen_s, 1)},
+            "config": cfg,
+            "launch": {"accum_mode": args.accum, "block": opts["block"], "pts_per_thread": opts["pts_per_thread"],
+                       "kernel": opts["kernel"], "exchange": "one all-gather of the 92-double per-pair records per "
+                       "step (%s)" % args.dist_backend, "generation_s": round(gen_s, 1)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": None, "kernel": "k_linearize_dense (rank 0's shard)", "kernel_ms": kavg,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk else "fallback"},
@@ -509,6 +558,7 @@ def run_ours(args):
     w = make_workload(args, rank)
     gen_s = time.perf_counter() - t_gen
     ctx = G.Context(local)
+    cfg = workload_config(w, args, ws)
     # The step is sharded by source submap (the pairs are independent units): each rank holds
     # its source frames and the voxelmaps of their targets, linearizes its pairs, and one
     # all-gather of the per-pair records is the exchange step.  Frames are numbered locally.
@@ -601,7 +651,7 @@ def run_ours(args):
     if sharded:
         e2e_line, sharded_check = sharded_e2e_and_check(G, ctx, plan, recs, args, w, (pairs_g, points_g, poses_g),
                                                          idx, need, P_all, n_pp_all, block, ppt, acc, dev, rank, ws)
-        line = sharded_line(w, args, ws, K, W, tmax, value, P_all, n_pp_all, plan, kern_ms, n_pp, e2e_line,
+        line = sharded_line(cfg, args, ws, K, W, tmax, value, P_all, n_pp_all, plan, kern_ms, n_pp, e2e_line,
                             sharded_check, gpu_launches, clk, gen_s)
         if rank == 0:
             print(json.dumps(line), flush=True)
@@ -666,22 +716,26 @@ def run_ours(args):
     plan_h.close()
     del plan_h, hmaps
     torch.cuda.synchronize()
-    # per-point weights: the backward pass of the same batch (dE/dxi, dE/dmu, dE/dw)
-    backward_line = None
-    if w.weights:
-        plan_b = G.Plan(ctx, frames, maps, w.pairs, accum_mode=acc, block=256, pts_per_thread=1)
-        for _ in range(3):
-            plan_b.backward(w.poses)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(10):
-            plan_b.backward(w.poses)
-        torch.cuda.synchronize()
-        backward_line = {"ms_per_call": (time.perf_counter() - t0) / 10 * 1e3,
-                         "note": "glim_plan_backward with Omega differentiated through R, host poses in"}
-        plan_b.close()
+    # the gradient pass of the same batch (dE/dxi per frame, dE/dmu and dE/dw per point; Omega
+    # differentiated through R), on the plan's own device pose block (no upload, no host wait)
+    plan.set_poses(w.poses)
+    for _ in range(2):
+        plan.backward(w.poses)
+    torch.cuda.synchronize()
+    bw_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    bw_ev[0].record(stream)
+    for _ in range(5):
+        g_xi, g_mu, g_w = plan.backward(w.poses)
+    bw_ev[1].record(stream)
+    torch.cuda.synchronize()
+    backward_line = {"ms_per_call": bw_ev[0].elapsed_time(bw_ev[1]) / 5, "pair_points": n_pp,
+                     "note": "glim_plan_backward: persistent (source frame, 1024-point tile) items over all pairs of "
+                             "the source, per-point gradients summed in registers, no per-(pair, point) scratch; "
+                             "device-timed on the library stream, the plan's poses already on the device"}
+    del g_xi, g_mu, g_w
     pk = peaks()
     hbm_peak = pk.get("hbm_gbs", 6400.0)
+    u_bpp, u_src = captured_traffic("urban") if args.workload == "urban" else (None, "no capture of this workload")
     kavg_ms = float(np.mean(kern_ms))
     achieved = BYTES_PER_POINT * n_pp / (kavg_ms / 1e3) / 1e9
     # the full algorithmic count: the source stream, plus every voxel a pair hits read once,
@@ -698,21 +752,16 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": tmax / K, "higher_is_better": True, "scaling": "strong" if args.workload == "urban" else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_desc(w, args), "pairs": P, "frames": len(w.points),
-                   "pair_points_per_step": n_pp, "levels": len(w.resolutions), "resolutions_m": w.resolutions,
-                   "accum_mode": args.accum, "block": opts["block"], "pts_per_thread": opts["pts_per_thread"],
-                   "autotuned": tuned, "surface_validation": False,
+        "config": cfg,
+        "launch": {"accum_mode": args.accum, "block": opts["block"], "pts_per_thread": opts["pts_per_thread"],
+                   "kernel": opts["kernel"], "autotuned": tuned, "surface_validation": False,
                    "point_order": "Z-order of 0.5 m cells" if args.order == "morton" else "generator (random)",
-                   "l2": ("inputs larger than L2: %.2f GB source stream per step (L2 126 MB)" % (BYTES_PER_POINT * n_pp / 1e9)
-                          if BYTES_PER_POINT * n_pp > 126e6 else
-                          "L2 not flushed: the %.3f GB source stream fits in L2 (126 MB), a warm-cache figure"
-                          % (BYTES_PER_POINT * n_pp / 1e9)),
-                   "parallelism": "one GPU" if ws == 1 else f"replicas x{ws} (independent batches per GPU)",
                    "generation_s": round(gen_s, 1)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
-                     "traffic": DRAM_BYTES_PER_PAIR_POINT * n_pp if args.workload == "urban" else None,
-                     "traffic_note": "ncu dram bytes of a 40-submap capture scaled by (pair, point) units",
+                     "traffic": None if u_bpp is None else u_bpp * n_pp,
+                     "traffic_note": "ncu dram bytes per (pair, point) of a 40-submap capture of this kernel version, "
+                                     "scaled by the launch's (pair, point) units (%s)" % u_src,
                      "kernel": kernel_name + " (persistent work queue)", "kernel_ms": kavg_ms,
                      "algorithmic_bytes_per_launch": BYTES_PER_POINT * n_pp,
                      "with_touched_voxels": {
@@ -766,24 +815,30 @@ def run_ours(args):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the host cores.  Each step is one bounded
+    sample of the workload (its first pairs, about --ref-points (pair, point) units); the
+    line reports the sample's own time and size, and the rate measured on it."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     w = make_workload(args, 0)
-    vals = []
+    vals, secs = [], []
     cb = None
     for i in range(args.warmup + args.steps):
         cb, dt = oracle_sample(w, budget_s=args.cpu_budget, target_points=args.ref_points)
         if i >= args.warmup:
             vals.append(cb["value"])
+            secs.append(dt)
     value = float(np.median(vals))
     cb["value"] = value
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "ms_per_step": 1e3 * w.n_pair_points / value,
-            "ms_per_step_note": "one whole step (every pair) at the sampled rate; each timed step is a bounded sample",
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "strong" if args.workload == "urban" else "weak",
+            "ms_per_step": 1e3 * float(np.median(secs)),
+            "ms_per_step_note": "one timed step = one bounded sample of %d (pair, point) units (the first pairs "
+                                "of the batch); the whole batch has %d" % (cb["pair_points"], w.n_pair_points),
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(w, args), "pairs": len(w.pairs)},
+            "config": workload_config(w, args, 1),
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

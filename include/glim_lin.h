@@ -166,6 +166,13 @@ glim_status glim_estimate_covariances(glim_ctx* ctx, const float* pts4, int64_t 
                                       int32_t reg_mode, float eps, float* cov6_out,
                                       float* normal3_out);
 
+/* The same, also writing the neighbour sets: knn_out (device, n x k int32, or NULL) receives
+ * the indices of every point's k nearest neighbours in (squared distance in FP64, index)
+ * order, nearest first (the point itself included).  For inspection and parity tests. */
+glim_status glim_estimate_covariances_knn(glim_ctx* ctx, const float* pts4, int64_t n, int32_t k,
+                                          int32_t reg_mode, float eps, float* cov6_out,
+                                          float* normal3_out, int32_t* knn_out);
+
 /* ---------------------------------------------------------------- point order */
 
 /* Permutation that orders a frame's points along a Z-order (Morton) curve of cubic cells of
@@ -386,10 +393,11 @@ glim_status glim_backward(glim_ctx* ctx, const glim_frame* frames, int32_t nfram
                           int32_t omega_grad_full, int32_t validate_surface, double* dxi_out,
                           float* dmu_out, float* dw_out);
 /* The same gradient for the batch of a plan, so that repeated evaluations (an optimiser's
- * iterations, autograd) reuse the plan's descriptors: the plan must have been created with
- * block 256 and pts_per_thread 1 (GLIM_EINVAL otherwise); its validate_surface option
- * applies.  The gradient scratch (host tables, per-(pair, point) slots) is allocated at the
- * first call and kept until glim_plan_destroy.  The frames' point arrays may be rewritten in
+ * iterations, autograd) reuse the plan's descriptors; its validate_surface option applies
+ * (its tile options do not: the gradient pass has its own work list of (source frame, point
+ * tile) items that walk all pairs of their source).  The gradient scratch (host tables, one
+ * slot of 9 sums per (item, pair), per-pair gradients; no per-(pair, point) storage) is
+ * allocated at the first call and kept until glim_plan_destroy.  The frames' point arrays may be rewritten in
  * place between calls, by work ordered on the context stream (or after synchronizing it).
  * Outputs as for glim_backward, written by work enqueued on the context stream: the call does
  * not wait for it (the first call waits once, to build the gradient tables).  When poses12

@@ -37,6 +37,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <queue>
 #include <thread>
 #include <vector>
 
@@ -256,6 +257,54 @@ typedef struct {
 
 int orc_abi_version() { return 1; }
 
+// Covariance of point i from its k nearest neighbours nb (nearest first, the point itself
+// included): mean and 1/k sample covariance in FP64, eigenvector n of the smallest eigenvalue
+// (cyclic Jacobi), n oriented so that n . mu <= 0; reg_mode 0: C + eps I, reg_mode 1:
+// C = I - (1 - eps) n n^T (GICP plane regularisation, Segal et al. 2009).
+void point_covariance(const float* pts4, int64_t i, const std::vector<int64_t>& nb, int reg_mode, double eps,
+                      double* cov6, double* normal3, int32_t* knn, uint8_t* near_tie) {
+  const int k = int(nb.size());
+  const double px = pts4[4 * i], py = pts4[4 * i + 1], pz = pts4[4 * i + 2];
+  double m[3] = {0, 0, 0};
+  for (int a = 0; a < k; ++a)
+    for (int c = 0; c < 3; ++c) m[c] += pts4[4 * nb[a] + c];
+  for (int c = 0; c < 3; ++c) m[c] /= k;
+  M3 C{};
+  for (int a = 0; a < k; ++a) {
+    double v[3];
+    for (int c = 0; c < 3; ++c) v[c] = pts4[4 * nb[a] + c] - m[c];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) C[r][c] += v[r] * v[c];
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) C[r][c] /= k;
+  double w[3];
+  M3 V;
+  jacobi_eigen(C, w, V);
+  int order[3] = {0, 1, 2};
+  std::sort(order, order + 3, [&](int a, int b) { return w[a] < w[b]; });
+  V3 nrm = {V[0][order[0]], V[1][order[0]], V[2][order[0]]};
+  double nn = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+  for (int c = 0; c < 3; ++c) nrm[c] /= nn;
+  if (nrm[0] * px + nrm[1] * py + nrm[2] * pz > 0)
+    for (int c = 0; c < 3; ++c) nrm[c] = -nrm[c];
+  M3 out;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      if (reg_mode == 0)
+        out[r][c] = C[r][c] + (r == c ? eps : 0.0);
+      else
+        out[r][c] = (r == c ? 1.0 : 0.0) - (1.0 - eps) * nrm[r] * nrm[c];
+    }
+  cov6[0] = out[0][0]; cov6[1] = out[0][1]; cov6[2] = out[0][2];
+  cov6[3] = out[1][1]; cov6[4] = out[1][2]; cov6[5] = out[2][2];
+  if (normal3)
+    for (int c = 0; c < 3; ++c) normal3[c] = nrm[c];
+  if (knn)
+    for (int a = 0; a < k; ++a) knn[a] = int32_t(nb[a]);
+  if (near_tie) *near_tie = (w[order[1]] - w[order[0]]) <= 1e-4 * std::fabs(w[order[2]]);
+}
+
 // ---------------------------------------------------------------- covariances (brute-force kNN)
 // For each point: its k nearest neighbours (itself included; ties broken by
 // (squared distance, index), distances in FP64), their sample covariance with
@@ -280,50 +329,56 @@ int orc_estimate_covariances(const float* pts4, int64_t n, int k, int reg_mode, 
         d[j] = {dx * dx + dy * dy + dz * dz, j};
       }
       std::partial_sort(d.begin(), d.begin() + k, d.end());
-      double m[3] = {0, 0, 0};
-      for (int a = 0; a < k; ++a)
-        for (int c = 0; c < 3; ++c) m[c] += pts4[4 * d[a].second + c];
-      for (int c = 0; c < 3; ++c) m[c] /= k;
-      M3 C{};
-      for (int a = 0; a < k; ++a) {
-        double v[3];
-        for (int c = 0; c < 3; ++c) v[c] = pts4[4 * d[a].second + c] - m[c];
-        for (int r = 0; r < 3; ++r)
-          for (int c = 0; c < 3; ++c) C[r][c] += v[r] * v[c];
-      }
-      for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) C[r][c] /= k;
-      double w[3];
-      M3 V;
-      jacobi_eigen(C, w, V);
-      int order[3] = {0, 1, 2};
-      std::sort(order, order + 3, [&](int a, int b) { return w[a] < w[b]; });
-      V3 nrm = {V[0][order[0]], V[1][order[0]], V[2][order[0]]};
-      double nn = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
-      for (int c = 0; c < 3; ++c) nrm[c] /= nn;
-      if (nrm[0] * px + nrm[1] * py + nrm[2] * pz > 0)
-        for (int c = 0; c < 3; ++c) nrm[c] = -nrm[c];
-      M3 out;
-      for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) {
-          if (reg_mode == 0)
-            out[r][c] = C[r][c] + (r == c ? eps : 0.0);
-          else
-            out[r][c] = (r == c ? 1.0 : 0.0) - (1.0 - eps) * nrm[r] * nrm[c];
-        }
-      double* o = cov6_out + 6 * i;
-      o[0] = out[0][0]; o[1] = out[0][1]; o[2] = out[0][2];
-      o[3] = out[1][1]; o[4] = out[1][2]; o[5] = out[2][2];
-      if (normal3_out)
-        for (int c = 0; c < 3; ++c) normal3_out[3 * i + c] = nrm[c];
-      if (knn_out)
-        for (int a = 0; a < k; ++a) knn_out[int64_t(k) * i + a] = int32_t(d[a].second);
-      if (near_tie_out) near_tie_out[i] = (w[order[1]] - w[order[0]]) <= 1e-4 * std::fabs(w[order[2]]);
+      std::vector<int64_t> nb(k);
+      for (int a = 0; a < k; ++a) nb[a] = d[a].second;
+      point_covariance(pts4, i, nb, reg_mode, eps, cov6_out + 6 * i, normal3_out ? normal3_out + 3 * i : nullptr,
+                       knn_out ? knn_out + int64_t(k) * i : nullptr, near_tie_out ? near_tie_out + i : nullptr);
     }
   };
   int T = std::max(1, nthreads);
   std::vector<std::thread> th;
   for (int t = 0; t < T; ++t) th.emplace_back(work, n * t / T, n * (t + 1) / T);
+  for (auto& x : th) x.join();
+  return ORC_OK;
+}
+
+// The same for the listed query points only (nq indices into the frame): every query scans
+// all n points, keeping the k smallest (squared distance in FP64, index) pairs.  Outputs are
+// per query (nq x 6, nq x 3, nq x k, nq).  For parity tests on large frames.
+int orc_covariances_at(const float* pts4, int64_t n, const int64_t* queries, int64_t nq, int k, int reg_mode,
+                       double eps, double* cov6_out, double* normal3_out, int32_t* knn_out, uint8_t* near_tie_out,
+                       int nthreads) {
+  if (n < 0 || nq < 0 || k < 3 || k > n || (reg_mode != 0 && reg_mode != 1)) return ORC_EINVAL;
+  for (int64_t q = 0; q < nq; ++q)
+    if (queries[q] < 0 || queries[q] >= n) return ORC_EINVAL;
+  auto work = [&](int64_t begin, int64_t end) {
+    for (int64_t q = begin; q < end; ++q) {
+      const int64_t i = queries[q];
+      const double px = pts4[4 * i], py = pts4[4 * i + 1], pz = pts4[4 * i + 2];
+      std::priority_queue<std::pair<double, int64_t>> best;  // the k best so far, worst on top
+      for (int64_t j = 0; j < n; ++j) {
+        double dx = double(pts4[4 * j]) - px, dy = double(pts4[4 * j + 1]) - py,
+               dz = double(pts4[4 * j + 2]) - pz;
+        const std::pair<double, int64_t> c{dx * dx + dy * dy + dz * dz, j};
+        if (int(best.size()) < k) {
+          best.push(c);
+        } else if (c < best.top()) {
+          best.pop();
+          best.push(c);
+        }
+      }
+      std::vector<int64_t> nb(k);
+      for (int a = k - 1; a >= 0; --a) {
+        nb[a] = best.top().second;
+        best.pop();
+      }
+      point_covariance(pts4, i, nb, reg_mode, eps, cov6_out + 6 * q, normal3_out ? normal3_out + 3 * q : nullptr,
+                       knn_out ? knn_out + int64_t(k) * q : nullptr, near_tie_out ? near_tie_out + q : nullptr);
+    }
+  };
+  int T = std::max<int64_t>(1, std::min<int64_t>(nthreads, std::max<int64_t>(nq, 1)));
+  std::vector<std::thread> th;
+  for (int t = 0; t < T; ++t) th.emplace_back(work, nq * t / T, nq * (t + 1) / T);
   for (auto& x : th) x.join();
   return ORC_OK;
 }

@@ -60,6 +60,8 @@ def lib():
         _lib.orc_vmap_free.argtypes = [C.c_void_p]
         _lib.orc_estimate_covariances.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_double,
                                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        _lib.orc_covariances_at.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_double,
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
         _lib.orc_linearize.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                        C.c_void_p] + [C.c_void_p] * 8
         _lib.orc_energy.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
@@ -102,6 +104,23 @@ def estimate_covariances(pts, k: int = 10, reg_mode: int = 1, eps: float = 1e-3,
                                         _ptr(tie), nthreads or os.cpu_count())
     if st != ORC_OK:
         raise ValueError(f"orc_estimate_covariances failed: {st}")
+    return cov, nrm, knn, tie.astype(bool)
+
+
+def covariances_at(pts, queries, k: int = 10, reg_mode: int = 1, eps: float = 1e-3, nthreads: int = 0):
+    """Brute-force kNN covariances of the listed query points only (each scans the whole frame);
+    returns (cov6 f64 (nq, 6), normals (nq, 3), knn int32 (nq, k), near_tie bool (nq,))."""
+    p4 = as_pts4(pts)
+    qi = np.ascontiguousarray(queries, dtype=np.int64)
+    nq = len(qi)
+    cov = np.zeros((nq, 6))
+    nrm = np.zeros((nq, 3))
+    knn = np.zeros((nq, k), dtype=np.int32)
+    tie = np.zeros(nq, dtype=np.uint8)
+    st = lib().orc_covariances_at(_ptr(p4), len(p4), _ptr(qi), nq, k, reg_mode, eps, _ptr(cov), _ptr(nrm), _ptr(knn),
+                                  _ptr(tie), nthreads or os.cpu_count())
+    if st != ORC_OK:
+        raise ValueError(f"orc_covariances_at failed: {st}")
     return cov, nrm, knn, tie.astype(bool)
 
 

@@ -45,6 +45,7 @@ SIGNATURES = {
     "glim_fp32_fma_peak": (_i32, [_vp, _i32, C.POINTER(C.c_double)]),
     "glim_fp64_fma_peak": (_i32, [_vp, _i32, C.POINTER(C.c_double)]),
     "glim_estimate_covariances": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _vp, _vp]),
+    "glim_estimate_covariances_knn": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _vp, _vp, _vp]),
     "glim_spatial_order": (_i32, [_vp, _vp, _i64, _f32, _vp]),
     "glim_build_voxelmap": (_i32, [_vp, _vp, _vp, _i64, _vp, _i32, C.POINTER(_vp)]),
     "glim_build_voxelmap_ex": (_i32, [_vp, _vp, _vp, _i64, _vp, _i32, _i32, C.POINTER(_vp)]),

@@ -165,6 +165,19 @@ def estimate_covariances(ctx: Context, pts4: torch.Tensor, k: int = 10, reg_mode
     return cov, nrm
 
 
+def estimate_covariances_knn(ctx: Context, pts4: torch.Tensor, k: int = 10, reg_mode: int = 1, eps: float = 1e-3):
+    """kNN covariances (n, 6), normals (n, 3) and the neighbour indices (n, k) int32, nearest
+    first, of one frame."""
+    _dev(pts4, torch.float32, 4, "pts4")
+    n = pts4.shape[0]
+    cov = torch.empty((n, 6), dtype=torch.float32, device=pts4.device)
+    nrm = torch.empty((n, 3), dtype=torch.float32, device=pts4.device)
+    knn = torch.empty((n, k), dtype=torch.int32, device=pts4.device)
+    ctx.call("estimate_covariances_knn", ctx.lib.glim_estimate_covariances_knn, ctx.h, _ptr(pts4), n, k, reg_mode, eps,
+             _ptr(cov), _ptr(nrm), _ptr(knn))
+    return cov, nrm, knn
+
+
 def spatial_order(ctx: Context, pts4: torch.Tensor, cell: float = 0.5) -> torch.Tensor:
     """Permutation (int64 CUDA tensor) ordering the points along a Z-order curve of cells."""
     _dev(pts4, torch.float32, 4, "pts4")
@@ -445,7 +458,7 @@ class Plan:
 
     def backward(self, poses, omega_grad_full=True):
         """dE/dxi (nframes, 6) f64, dE/dmu (sum n, 3) f32, dE/dw (sum n,) f32 of the plan's
-        batch (the plan must use block 256, pts_per_thread 1)."""
+        batch."""
         self._maps_alive()
         Pz = _poses(poses, self.nframes)
         dev = self.frames[0].pts4.device

@@ -83,8 +83,8 @@ class FactorProblem:
     base poses, and the split of the concatenated point array into frames.
 
     The problem owns one packed (n, 4) point buffer (the frames are row ranges of it) and one
-    plan over it (block 256, one point per thread, as the gradient pass needs), so that an
-    evaluation only writes the current points and weights into the buffer and launches."""
+    plan over it, so that an evaluation only writes the current points and weights into the
+    buffer and launches."""
 
     def __init__(self, ctx: api.Context, frames, vmaps, pairs, poses, validate_surface=False,
                  omega_grad_full=True):
@@ -100,8 +100,7 @@ class FactorProblem:
         self._p4 = torch.cat([f.pts4 for f in self.frames]).contiguous()
         self._bufs = [api.FrameData(self._p4[int(self.offsets[i]):int(self.offsets[i + 1])], f.cov6, f.normal3)
                       for i, f in enumerate(self.frames)]
-        self._plan = api.Plan(ctx, self._bufs, self.vmaps, self.pairs, validate_surface=self.validate,
-                              block=256, pts_per_thread=1)
+        self._plan = api.Plan(ctx, self._bufs, self.vmaps, self.pairs, validate_surface=self.validate)
         self._out = self._plan.device_outputs_alloc()
 
     def points(self):

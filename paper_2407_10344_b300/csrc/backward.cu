@@ -11,10 +11,13 @@
 // The Omega terms follow from dE/dS = -w y y^T and dS/domega_s,a = R (e_a x C - C e_a x) R^T,
 // dS/domega_t,a = -(e_a x) S' + S' (e_a x) with S' = R C R^T.
 //
-// Pipeline: per work item (pair, tile) the 9 sums (g: 6, a: 3) are block-reduced into the
-// item's slot, and each point writes its (dE/dmu, dE/dw) for that pair into a per-(pair,
-// point) slot; then fixed-order FP64 sums per pair, per frame, and per point.  No float
-// atomics, so the gradient repeats bit for bit.
+// Work decomposition: an item is a tile of BWD_TILE points of one source frame; a persistent
+// kernel takes items from an atomic queue and walks every pair of that source in pair order.
+// Per pair, the points' contributions to the 9 pose sums (g: 6, the Omega term: 3) are
+// block-reduced into the (item, pair) slot, while each point keeps its dE/dmu and dE/dw summed
+// over the pairs in registers and writes them once.  Then fixed-order FP64 sums per pair and
+// per frame.  No float atomics, so the gradient repeats bit for bit; no per-(pair, point)
+// scratch.
 #include <algorithm>
 #include <cstring>
 
@@ -22,138 +25,197 @@
 
 namespace {
 
-constexpr int BSTRIDE = 12;  // doubles per item slot: g (6), a (3), 3 spare
+constexpr int BWD_BLOCK = 256;
+constexpr int BWD_PPT = 4;  // points per thread of an item
+constexpr int BWD_TILE = BWD_BLOCK * BWD_PPT;
+constexpr int BSTRIDE = 9;  // doubles per partial slot: g (6), Omega term (3)
 
 struct BwdArgs {
-  const Item* items;
+  const int2* items;
   int32_t nitems;
+  int* head;
   const PairDev* pairs;
   const FrameDev* frames;
   const MapDev* maps;
   const PoseF* pose;
-  int32_t tile;
+  const int32_t* frame_item_begin;
+  const int32_t* src_begin;
+  const int32_t* src_list;
+  const int64_t* frame_off;
+  const int64_t* slot_base;
   int32_t validate;
   int32_t full;
-  const int64_t* pair_pt_off;  // npairs: offset of the pair's points in pp
-  float4* pp;                  // per (pair, point): dE/dmu (xyz), dE/dw
-  double* part;                // nitems x BSTRIDE
+  double* part;
+  float* dmu;
+  float* dw;
 };
 
-__global__ void __launch_bounds__(256) k_backward_items(const BwdArgs a) {
-  const int item = blockIdx.x;
-  if (item >= a.nitems) return;
-  const Item it = a.items[item];
-  __shared__ PairView V;
-  __shared__ float s_red[8][9];
-  if (threadIdx.x == 0) {
-    const PairDev pd = a.pairs[it.pair];
-    const PoseF pf = a.pose[it.pair];
-    for (int i = 0; i < 9; ++i) V.R[i] = pf.R[i];
-    for (int i = 0; i < 3; ++i) {
-      V.t[i] = pf.t[i];
-      V.v[i] = pf.v[i];
+// One point against one pair: adds its 9 pose sums to acc and its (dE/dmu, dE/dw) to out.
+__device__ __forceinline__ void point_gradient(const PairView& V, int64_t k, int validate, int full, float (&acc)[9],
+                                               float4& out) {
+  const float4 m = V.F.pts[k];
+  if (validate && V.F.nrm &&
+      behind_surface(m.x, m.y, m.z, V.v, V.F.nrm[3 * k], V.F.nrm[3 * k + 1], V.F.nrm[3 * k + 2]))
+    return;
+  const float2 ca = V.F.cov[3 * k], cb = V.F.cov[3 * k + 1], cc = V.F.cov[3 * k + 2];
+  const float c00 = ca.x, c01 = ca.y, c02 = cb.x, c11 = cb.y, c12 = cc.x, c22 = cc.y;
+  const float* R = V.R;
+  const float3 q = transform_pinned(R, V.t, m.x, m.y, m.z);
+  const float3 u = make_float3(q.x - V.t[0], q.y - V.t[1], q.z - V.t[2]);
+  // R C R^T
+  float W[3][3], S[3][3];
+  const float C[3][3] = {{c00, c01, c02}, {c01, c11, c12}, {c02, c12, c22}};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) W[i][j] = R[3 * i] * C[0][j] + R[3 * i + 1] * C[1][j] + R[3 * i + 2] * C[2][j];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) S[i][j] = W[i][0] * R[3 * j] + W[i][1] * R[3 * j + 1] + W[i][2] * R[3 * j + 2];
+  float Y[3] = {0, 0, 0}, E = 0.f, av[3] = {0, 0, 0};
+  for (int l = 0; l < V.M.levels; ++l) {
+    const LevelDev& L = V.M.lv[l];
+    int kx, ky, kz;
+    if (!level_key3(q, L.inv_r, kx, ky, kz)) continue;
+    int vid;
+    const int s = find_voxel(L, kx, ky, kz, &vid);
+    if (s < 0) continue;
+    const float4 v0 = L.slots[s].w0, v1 = L.slots[s].w1, v2 = L.slots[s].w2;
+    const float sa = v1.w + S[0][0], sb = v2.x + S[0][1], sc = v2.y + S[0][2], sd = v2.z + S[1][1],
+                se = v2.w + S[1][2], sf = v0.w + S[2][2];
+    const float A00 = sd * sf - se * se, A01 = sc * se - sb * sf, A02 = sb * se - sc * sd;
+    const float A11 = sa * sf - sc * sc, A12 = sb * sc - sa * se, A22 = sa * sd - sb * sb;
+    const float det = sa * A00 + sb * A01 + sc * A02;
+    if (!(det > 0.f) || !isfinite(det)) continue;
+    const float id = __frcp_rn(det);
+    const float O[3][3] = {{A00 * id, A01 * id, A02 * id}, {A01 * id, A11 * id, A12 * id},
+                           {A02 * id, A12 * id, A22 * id}};
+    const float d[3] = {v1.x - q.x, v1.y - q.y, v1.z - q.z};
+    float y[3];
+    for (int i = 0; i < 3; ++i) y[i] = O[i][0] * d[0] + O[i][1] * d[1] + O[i][2] * d[2];
+    E += d[0] * y[0] + d[1] * y[1] + d[2] * y[2];
+    for (int i = 0; i < 3; ++i) Y[i] += y[i];
+    if (full) {
+      float z[3], Cz[3];
+      for (int i = 0; i < 3; ++i) z[i] = R[i] * y[0] + R[3 + i] * y[1] + R[6 + i] * y[2];  // R^T y
+      for (int i = 0; i < 3; ++i) Cz[i] = C[i][0] * z[0] + C[i][1] * z[1] + C[i][2] * z[2];
+      av[0] += z[1] * Cz[2] - z[2] * Cz[1];
+      av[1] += z[2] * Cz[0] - z[0] * Cz[2];
+      av[2] += z[0] * Cz[1] - z[1] * Cz[0];
     }
-    V.F = a.frames[pd.src];
-    V.M = a.maps[pd.map];
   }
-  __syncthreads();
-  float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  const int64_t k = int64_t(it.start) + threadIdx.x;
-  if (k < V.F.n && threadIdx.x < a.tile) {
-    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 m = V.F.pts[k];
-    bool visible = true;
-    if (a.validate && V.F.nrm)
-      visible = !behind_surface(m.x, m.y, m.z, V.v, V.F.nrm[3 * k], V.F.nrm[3 * k + 1], V.F.nrm[3 * k + 2]);
-    if (visible) {
-      const float2 ca = V.F.cov[3 * k], cb = V.F.cov[3 * k + 1], cc = V.F.cov[3 * k + 2];
-      const float c00 = ca.x, c01 = ca.y, c02 = cb.x, c11 = cb.y, c12 = cc.x, c22 = cc.y;
-      const float* R = V.R;
-      const float3 q = transform_pinned(R, V.t, m.x, m.y, m.z);
-      const float3 u = make_float3(q.x - V.t[0], q.y - V.t[1], q.z - V.t[2]);
-      // R C R^T
-      float W[3][3], S[3][3];
-      const float C[3][3] = {{c00, c01, c02}, {c01, c11, c12}, {c02, c12, c22}};
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) W[i][j] = R[3 * i] * C[0][j] + R[3 * i + 1] * C[1][j] + R[3 * i + 2] * C[2][j];
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) S[i][j] = W[i][0] * R[3 * j] + W[i][1] * R[3 * j + 1] + W[i][2] * R[3 * j + 2];
-      float Y[3] = {0, 0, 0}, E = 0.f, av[3] = {0, 0, 0};
-      for (int l = 0; l < V.M.levels; ++l) {
-        const LevelDev& L = V.M.lv[l];
-        int kx, ky, kz;
-        if (!level_key3(q, L.inv_r, kx, ky, kz)) continue;
-        int vid;
-        const int s = find_voxel(L, kx, ky, kz, &vid);
-        if (s < 0) continue;
-        const float4 v0 = L.slots[s].w0, v1 = L.slots[s].w1, v2 = L.slots[s].w2;
-        const float sa = v1.w + S[0][0], sb = v2.x + S[0][1], sc = v2.y + S[0][2], sd = v2.z + S[1][1],
-                    se = v2.w + S[1][2], sf = v0.w + S[2][2];
-        const float A00 = sd * sf - se * se, A01 = sc * se - sb * sf, A02 = sb * se - sc * sd;
-        const float A11 = sa * sf - sc * sc, A12 = sb * sc - sa * se, A22 = sa * sd - sb * sb;
-        const float det = sa * A00 + sb * A01 + sc * A02;
-        if (!(det > 0.f) || !isfinite(det)) continue;
-        const float id = __frcp_rn(det);
-        const float O[3][3] = {{A00 * id, A01 * id, A02 * id}, {A01 * id, A11 * id, A12 * id},
-                               {A02 * id, A12 * id, A22 * id}};
-        const float d[3] = {v1.x - q.x, v1.y - q.y, v1.z - q.z};
-        float y[3];
-        for (int i = 0; i < 3; ++i) y[i] = O[i][0] * d[0] + O[i][1] * d[1] + O[i][2] * d[2];
-        E += d[0] * y[0] + d[1] * y[1] + d[2] * y[2];
-        for (int i = 0; i < 3; ++i) Y[i] += y[i];
-        if (a.full) {
-          float z[3], Cz[3];
-          for (int i = 0; i < 3; ++i) z[i] = R[i] * y[0] + R[3 + i] * y[1] + R[6 + i] * y[2];  // R^T y
-          for (int i = 0; i < 3; ++i) Cz[i] = C[i][0] * z[0] + C[i][1] * z[1] + C[i][2] * z[2];
-          av[0] += z[1] * Cz[2] - z[2] * Cz[1];
-          av[1] += z[2] * Cz[0] - z[0] * Cz[2];
-          av[2] += z[0] * Cz[1] - z[1] * Cz[0];
-        }
-      }
-      const float w = m.w;
-      // dE/dmu = -2 w R^T Y, dE/dw = E
-      out.x = -2.f * w * (R[0] * Y[0] + R[3] * Y[1] + R[6] * Y[2]);
-      out.y = -2.f * w * (R[1] * Y[0] + R[4] * Y[1] + R[7] * Y[2]);
-      out.z = -2.f * w * (R[2] * Y[0] + R[5] * Y[1] + R[8] * Y[2]);
-      out.w = E;
-      const float wy[3] = {w * Y[0], w * Y[1], w * Y[2]};
-      acc[0] = u.y * wy[2] - u.z * wy[1];
-      acc[1] = u.z * wy[0] - u.x * wy[2];
-      acc[2] = u.x * wy[1] - u.y * wy[0];
-      acc[3] = wy[0];
-      acc[4] = wy[1];
-      acc[5] = wy[2];
-      acc[6] = 2.f * w * av[0];
-      acc[7] = 2.f * w * av[1];
-      acc[8] = 2.f * w * av[2];
-    }
-    a.pp[a.pair_pt_off[it.pair] + k] = out;
-  }
-  // block reduction: warp trees in FP32, warps summed in FP64 (fixed order)
+  const float w = m.w;
+  // dE/dmu = -2 w R^T Y, dE/dw = E
+  out.x += -2.f * w * (R[0] * Y[0] + R[3] * Y[1] + R[6] * Y[2]);
+  out.y += -2.f * w * (R[1] * Y[0] + R[4] * Y[1] + R[7] * Y[2]);
+  out.z += -2.f * w * (R[2] * Y[0] + R[5] * Y[1] + R[8] * Y[2]);
+  out.w += E;
+  const float wy[3] = {w * Y[0], w * Y[1], w * Y[2]};
+  acc[0] += u.y * wy[2] - u.z * wy[1];
+  acc[1] += u.z * wy[0] - u.x * wy[2];
+  acc[2] += u.x * wy[1] - u.y * wy[0];
+  acc[3] += wy[0];
+  acc[4] += wy[1];
+  acc[5] += wy[2];
+  acc[6] += 2.f * w * av[0];
+  acc[7] += 2.f * w * av[1];
+  acc[8] += 2.f * w * av[2];
+}
+
+__device__ __forceinline__ void backward_item(const BwdArgs& a, int g, PairView& V, float (&s_red)[BWD_BLOCK / 32][9]) {
+  const int2 it = a.items[g];
+  const int f = it.x;
+  const int64_t start = it.y;
+  const int pb = a.src_begin[f], npf = a.src_begin[f + 1] - pb;
+  const int64_t slot0 = a.slot_base[f] + int64_t(g - a.frame_item_begin[f]) * npf;
+  const int64_t n = a.frames[f].n;
+  const int64_t end = min(start + int64_t(BWD_TILE), n);
+  float4 pacc[BWD_PPT];
+#pragma unroll
+  for (int r = 0; r < BWD_PPT; ++r) pacc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 1
+  for (int j = 0; j < npf; ++j) {
+    if (threadIdx.x == 0) {
+      const int p = a.src_list[pb + j];
+      const PairDev pd = a.pairs[p];
+      const PoseF pf = a.pose[p];
+      for (int i = 0; i < 9; ++i) V.R[i] = pf.R[i];
+      for (int i = 0; i < 3; ++i) {
+        V.t[i] = pf.t[i];
+        V.v[i] = pf.v[i];
+      }
+      V.F = a.frames[f];
+      V.M = a.maps[pd.map];
+    }
+    __syncthreads();
+    float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    float v = acc[i];
+    for (int r = 0; r < BWD_PPT; ++r) {
+      const int64_t k = start + int64_t(r) * BWD_BLOCK + threadIdx.x;
+      if (k < end) point_gradient(V, k, a.validate, a.full, acc, pacc[r]);
+    }
+    // block reduction: warp trees in FP32, warps summed in FP64 (fixed order)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) s_red[warp][i] = v;
+    for (int i = 0; i < 9; ++i) {
+      float v = acc[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) s_red[warp][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < BWD_BLOCK / 32; ++w) t += double(s_red[w][threadIdx.x]);
+      a.part[(slot0 + j) * BSTRIDE + threadIdx.x] = t;
+    }
+    __syncthreads();  // V and s_red are rewritten for the next pair
   }
-  __syncthreads();
-  if (threadIdx.x < 9) {
-    double t = 0.0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += double(s_red[w][threadIdx.x]);
-    a.part[int64_t(item) * BSTRIDE + threadIdx.x] = t;
+  const int64_t base = a.frame_off[f];
+#pragma unroll
+  for (int r = 0; r < BWD_PPT; ++r) {
+    const int64_t k = start + int64_t(r) * BWD_BLOCK + threadIdx.x;
+    if (k < end) {
+      if (a.dmu) {
+        a.dmu[3 * (base + k)] = pacc[r].x;
+        a.dmu[3 * (base + k) + 1] = pacc[r].y;
+        a.dmu[3 * (base + k) + 2] = pacc[r].z;
+      }
+      if (a.dw) a.dw[base + k] = pacc[r].w;
+    }
   }
 }
 
-// per pair: dxi_pair (12) = 2 Lift^T g + [a; 0; -R a; 0]
-__global__ void k_backward_pairs(const double* __restrict__ part, const int32_t* __restrict__ item_begin,
+// Persistent blocks over the item queue (the next item fetched one item ahead).
+__global__ void __launch_bounds__(BWD_BLOCK) k_backward_items(const BwdArgs a) {
+  __shared__ PairView V;
+  __shared__ float s_red[BWD_BLOCK / 32][9];
+  __shared__ int s_item[2];
+  if (threadIdx.x == 0) s_item[0] = atomicAdd(a.head, 1);
+  __syncthreads();
+  int cur = s_item[0];
+  for (int b = 1;; b ^= 1) {
+    if (cur >= a.nitems) break;
+    if (threadIdx.x == 0) s_item[b] = atomicAdd(a.head, 1);
+    backward_item(a, cur, V, s_red);  // ends with a barrier
+    cur = s_item[b];
+  }
+}
+
+// per pair: dxi_pair (12) = 2 Lift^T g + [a; 0; -R a; 0], g and a summed over the items of
+// the pair's source frame in item order
+__global__ void k_backward_pairs(const double* __restrict__ part, const PairDev* __restrict__ pairs,
+                                 const int32_t* __restrict__ pair_pos, const int32_t* __restrict__ src_begin,
+                                 const int32_t* __restrict__ frame_item_begin, const int64_t* __restrict__ slot_base,
                                  const double* __restrict__ pose64, int npairs, double* __restrict__ pair_grad) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npairs) return;
+  const int f = pairs[p].src;
+  const int npf = src_begin[f + 1] - src_begin[f], j = pair_pos[p];
+  const int nit = frame_item_begin[f + 1] - frame_item_begin[f];
   double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for (int i = item_begin[p]; i < item_begin[p + 1]; ++i)
-    for (int c = 0; c < 9; ++c) s[c] += part[int64_t(i) * BSTRIDE + c];
+  for (int i = 0; i < nit; ++i) {
+    const double* sl = part + (slot_base[f] + int64_t(i) * npf + j) * BSTRIDE;
+    for (int c = 0; c < 9; ++c) s[c] += sl[c];
+  }
   const double* P = pose64 + 12 * int64_t(p);
   const double* R = P;
   const double t[3] = {P[9], P[10], P[11]};
@@ -186,120 +248,119 @@ __global__ void k_backward_frames(const double* __restrict__ pair_grad, const Pa
   for (int c = 0; c < 6; ++c) dxi[6 * int64_t(f) + c] = s[c];
 }
 
-// per point of every frame: sum over the pairs that have the frame as source, in pair order
-__global__ void k_backward_points(const float4* __restrict__ pp, const int64_t* __restrict__ pair_pt_off,
-                                  const int32_t* __restrict__ src_list, const int32_t* __restrict__ src_begin,
-                                  const int64_t* __restrict__ frame_off, const int32_t* __restrict__ point_frame_hint,
-                                  int nframes, int64_t ntot, float* __restrict__ dmu, float* __restrict__ dw) {
-  const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (g >= ntot) return;
-  // frame of global point g (binary search over frame offsets)
-  int lo = 0, hi = nframes - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (frame_off[mid] <= g) lo = mid;
-    else hi = mid - 1;
-  }
-  (void)point_frame_hint;
-  const int f = lo;
-  const int64_t k = g - frame_off[f];
-  float sx = 0.f, sy = 0.f, sz = 0.f, sw = 0.f;
-  for (int j = src_begin[f]; j < src_begin[f + 1]; ++j) {
-    const float4 v = pp[pair_pt_off[src_list[j]] + k];
-    sx += v.x;
-    sy += v.y;
-    sz += v.z;
-    sw += v.w;
-  }
-  if (dmu) {
-    dmu[3 * g] = sx;
-    dmu[3 * g + 1] = sy;
-    dmu[3 * g + 2] = sz;
-  }
-  if (dw) dw[g] = sw;
-}
-
 // Host tables of a batch, uploaded into freshly allocated scratch (synchronous copies).
 glim_status bwd_prepare(glim_plan* p, BwdScratch& sc) {
   glim_ctx* ctx = p->ctx;
   const int npairs = p->npairs, nframes = p->nframes;
-  std::vector<int64_t> pair_off(std::max(npairs, 1), 0), frame_off(nframes + 1, 0);
-  int64_t npp = 0;
-  for (int q = 0; q < npairs; ++q) {
-    pair_off[q] = npp;
-    npp += p->frames[p->pairs[q].src_frame].n;
-  }
-  for (int f = 0; f < nframes; ++f) frame_off[f + 1] = frame_off[f] + p->frames[f].n;
-  std::vector<int32_t> src_begin(nframes + 1, 0), src_list, tgt(std::max(npairs, 1), 0);
+  std::vector<int32_t> src_begin(nframes + 1, 0), src_list, pair_pos(std::max(npairs, 1), 0),
+      tgt(std::max(npairs, 1), 0);
   for (int f = 0; f < nframes; ++f) {
     src_begin[f] = int32_t(src_list.size());
     for (int q = 0; q < npairs; ++q)
-      if (p->pairs[q].src_frame == f) src_list.push_back(q);
+      if (p->pairs[q].src_frame == f) {
+        pair_pos[q] = int32_t(src_list.size()) - src_begin[f];
+        src_list.push_back(q);
+      }
   }
   src_begin[nframes] = int32_t(src_list.size());
   for (int q = 0; q < npairs; ++q) tgt[q] = p->pairs[q].tgt_frame;
+  std::vector<int64_t> frame_off(nframes + 1, 0), slot_base(std::max(nframes, 1), 0);
+  std::vector<int2> items;
+  std::vector<int32_t> frame_item_begin(nframes + 1, 0);
+  int64_t nslots = 0;
+  for (int f = 0; f < nframes; ++f) {
+    const int64_t n = p->frames[f].n;
+    frame_off[f + 1] = frame_off[f] + n;
+    frame_item_begin[f] = int32_t(items.size());
+    slot_base[f] = nslots;
+    for (int64_t s0 = 0; s0 < n; s0 += BWD_TILE) items.push_back(make_int2(f, int32_t(s0)));
+    nslots += int64_t(items.size() - frame_item_begin[f]) * (src_begin[f + 1] - src_begin[f]);
+  }
+  frame_item_begin[nframes] = int32_t(items.size());
   if (src_list.empty()) src_list.push_back(0);
-  sc.npp = npp;
+  if (items.empty()) items.push_back(make_int2(0, 0));
+  sc.nitems = frame_item_begin[nframes];
   sc.ntot = frame_off[nframes];
-  if (dmalloc(&sc.pair_off, pair_off.size() * sizeof(int64_t)) != cudaSuccess ||
-      dmalloc(&sc.frame_off, frame_off.size() * sizeof(int64_t)) != cudaSuccess ||
+  sc.nslots = nslots;
+  int per_sm = 1;
+  GLIM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_items, BWD_BLOCK, 0));
+  sc.grid = std::max(1, std::min(std::max(per_sm, 1) * ctx->num_sms, std::max(sc.nitems, 1)));
+  if (dmalloc(&sc.items, items.size() * sizeof(int2)) != cudaSuccess ||
+      dmalloc(&sc.frame_item_begin, frame_item_begin.size() * sizeof(int32_t)) != cudaSuccess ||
       dmalloc(&sc.src_begin, src_begin.size() * sizeof(int32_t)) != cudaSuccess ||
       dmalloc(&sc.src_list, src_list.size() * sizeof(int32_t)) != cudaSuccess ||
+      dmalloc(&sc.pair_pos, pair_pos.size() * sizeof(int32_t)) != cudaSuccess ||
       dmalloc(&sc.tgt, tgt.size() * sizeof(int32_t)) != cudaSuccess ||
-      dmalloc(&sc.pp, size_t(std::max<int64_t>(npp, 1)) * sizeof(float4)) != cudaSuccess ||
-      dmalloc(&sc.part, size_t(std::max(p->nitems, 1)) * BSTRIDE * sizeof(double)) != cudaSuccess ||
-      dmalloc(&sc.pair_grad, size_t(std::max(npairs, 1)) * 12 * sizeof(double)) != cudaSuccess) {
+      dmalloc(&sc.frame_off, frame_off.size() * sizeof(int64_t)) != cudaSuccess ||
+      dmalloc(&sc.slot_base, slot_base.size() * sizeof(int64_t)) != cudaSuccess ||
+      dmalloc(&sc.part, size_t(std::max<int64_t>(nslots, 1)) * BSTRIDE * sizeof(double)) != cudaSuccess ||
+      dmalloc(&sc.pair_grad, size_t(std::max(npairs, 1)) * 12 * sizeof(double)) != cudaSuccess ||
+      dmalloc(&sc.head, sizeof(int)) != cudaSuccess) {
     sc.release();
     return set_error(ctx, GLIM_ENOMEM, "backward: scratch allocation failed");
   }
-  GLIM_CUDA(ctx, cudaMemcpy(sc.pair_off, pair_off.data(), pair_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
-  GLIM_CUDA(ctx, cudaMemcpy(sc.frame_off, frame_off.data(), frame_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
-  GLIM_CUDA(ctx, cudaMemcpy(sc.src_begin, src_begin.data(), src_begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  GLIM_CUDA(ctx, cudaMemcpy(sc.src_list, src_list.data(), src_list.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  GLIM_CUDA(ctx, cudaMemcpy(sc.tgt, tgt.data(), tgt.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  cudaError_t e = cudaMemcpy(sc.items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(sc.frame_item_begin, frame_item_begin.data(), frame_item_begin.size() * sizeof(int32_t),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(sc.src_begin, src_begin.data(), src_begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(sc.src_list, src_list.data(), src_list.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(sc.pair_pos, pair_pos.data(), pair_pos.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(sc.tgt, tgt.data(), tgt.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(sc.frame_off, frame_off.data(), frame_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(sc.slot_base, slot_base.data(), slot_base.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    sc.release();
+    return cuda_check(ctx, e, "backward: table upload");
+  }
   return GLIM_OK;
 }
 
-// The gradient kernels of a batch whose poses are already uploaded into p->d_in; synchronizes.
+// The gradient kernels of a batch whose poses are already uploaded into p->d_in (no wait).
 glim_status bwd_run(glim_plan* p, const BwdScratch& sc, int32_t omega_grad_full, int32_t validate_surface,
                     double* dxi_out, float* dmu_out, float* dw_out) {
   glim_ctx* ctx = p->ctx;
   const int npairs = p->npairs, nframes = p->nframes;
-  if (p->nitems > 0) {
+  if (sc.nitems > 0) {
     BwdArgs a;
-    a.items = p->d_items;
-    a.nitems = p->nitems;
+    a.items = sc.items;
+    a.nitems = sc.nitems;
+    a.head = sc.head;
     a.pairs = p->d_pairs;
     a.frames = p->d_frames;
     a.maps = p->d_maps;
     a.pose = p->in_pose32();
-    a.tile = p->tile;
+    a.frame_item_begin = sc.frame_item_begin;
+    a.src_begin = sc.src_begin;
+    a.src_list = sc.src_list;
+    a.frame_off = sc.frame_off;
+    a.slot_base = sc.slot_base;
     a.validate = validate_surface;
     a.full = omega_grad_full;
-    a.pair_pt_off = sc.pair_off;
-    a.pp = sc.pp;
     a.part = sc.part;
-    k_backward_items<<<p->nitems, 256, 0, ctx->stream>>>(a);
-    ctx->launches++;
+    a.dmu = dmu_out;
+    a.dw = dw_out;
+    GLIM_CUDA(ctx, cudaMemsetAsync(sc.head, 0, sizeof(int), ctx->stream));
+    k_backward_items<<<sc.grid, BWD_BLOCK, 0, ctx->stream>>>(a);
+    GLIM_LAUNCHED(ctx);
   }
   if (npairs > 0) {
-    k_backward_pairs<<<ceil_div_i(npairs, 64), 64, 0, ctx->stream>>>(sc.part, p->d_item_begin, p->in_pose64(),
+    k_backward_pairs<<<ceil_div_i(npairs, 64), 64, 0, ctx->stream>>>(sc.part, p->d_pairs, sc.pair_pos, sc.src_begin,
+                                                                     sc.frame_item_begin, sc.slot_base, p->in_pose64(),
                                                                      npairs, sc.pair_grad);
-    ctx->launches++;
+    GLIM_LAUNCHED(ctx);
   }
   if (nframes > 0) {
     k_backward_frames<<<ceil_div_i(nframes, 64), 64, 0, ctx->stream>>>(sc.pair_grad, p->d_pairs, sc.tgt, npairs,
                                                                        nframes, dxi_out);
-    ctx->launches++;
-  }
-  if (sc.ntot > 0 && (dmu_out || dw_out)) {
-    k_backward_points<<<ceil_div_i(sc.ntot, 256), 256, 0, ctx->stream>>>(
-        sc.pp, sc.pair_off, sc.src_list, sc.src_begin, sc.frame_off, nullptr, nframes, sc.ntot, dmu_out, dw_out);
-    ctx->launches++;
+    GLIM_LAUNCHED(ctx);
   }
   // the outputs are device arrays ordered on the context stream: no host wait here
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_check(ctx, e, "backward launch");
   ctx->err.clear();
   return GLIM_OK;
 }
@@ -313,9 +374,6 @@ extern "C" glim_status glim_backward(glim_ctx* ctx, const glim_frame* frames, in
   if (!ctx) return GLIM_EINVAL;
   if (!poses12 || (nframes > 0 && !dxi_out)) return set_error(ctx, GLIM_EINVAL, "backward: null argument");
   glim_lin_opts o{};
-  o.block = 256;
-  o.pts_per_thread = 1;
-  o.persistent = 2;
   o.accum_mode = GLIM_ACC_FP64;
   o.validate_surface = validate_surface;
   glim_plan* p = nullptr;
@@ -340,8 +398,6 @@ extern "C" glim_status glim_plan_backward(glim_plan* p, const double* poses12, i
   if (!p || !poses12) return GLIM_EINVAL;
   glim_ctx* ctx = p->ctx;
   if (p->nframes > 0 && !dxi_out) return set_error(ctx, GLIM_EINVAL, "plan_backward: null argument");
-  if (p->opts.block != 256 || p->tile != 256)
-    return set_error(ctx, GLIM_EINVAL, "plan_backward: the plan needs block 256 and pts_per_thread 1");
   if (!plan_maps_current(p)) return set_error(ctx, GLIM_EINVAL, "plan_backward: a target voxelmap changed");
   DeviceGuard device_guard;
   GLIM_CUDA(ctx, device_guard.set(ctx->device));

@@ -158,6 +158,7 @@ struct GridArgs {
   float eps;
   float* cov6;
   float* normal3;
+  int32_t* knn = nullptr;  // optional: the k neighbour indices of every point, nearest first
 };
 
 __device__ __forceinline__ bool find_cell(const GridArgs& a, unsigned long long key, uint32_t& start, uint32_t& count) {
@@ -266,6 +267,11 @@ __device__ __forceinline__ void finish_point(const GridArgs& a, int32_t self, do
   if (a.normal3) {
     float* nn = a.normal3 + 3 * int64_t(self);
     nn[0] = float(nv[0]); nn[1] = float(nv[1]); nn[2] = float(nv[2]);
+  }
+  if (a.knn) {
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < a.k) a.knn[int64_t(self) * a.k + j] = top.i[j];
   }
 }
 
@@ -441,6 +447,12 @@ glim_status knn_all_by_scan(glim_ctx* ctx, const GridArgs& a) {
 
 extern "C" glim_status glim_estimate_covariances(glim_ctx* ctx, const float* pts4, int64_t n, int32_t k,
                                                  int32_t reg_mode, float eps, float* cov6_out, float* normal3_out) {
+  return glim_estimate_covariances_knn(ctx, pts4, n, k, reg_mode, eps, cov6_out, normal3_out, nullptr);
+}
+
+extern "C" glim_status glim_estimate_covariances_knn(glim_ctx* ctx, const float* pts4, int64_t n, int32_t k,
+                                                     int32_t reg_mode, float eps, float* cov6_out,
+                                                     float* normal3_out, int32_t* knn_out) {
   GLIM_RANGE("glim_estimate_covariances");
   if (!ctx) return GLIM_EINVAL;
   if (n < 0 || k < 3 || k > 32 || k > n || (reg_mode != 0 && reg_mode != 1) || !(eps >= 0.f) ||
@@ -458,6 +470,7 @@ extern "C" glim_status glim_estimate_covariances(glim_ctx* ctx, const float* pts
   a.eps = eps;
   a.cov6 = cov6_out;
   a.normal3 = normal3_out;
+  a.knn = knn_out;
   // reject non-finite input before any neighbour search (a NaN distance would never enter
   // the k-best list)
   k_check_finite<<<std::min(ceil_div_i(n, 256), 8 * ctx->num_sms), 256, 0, ctx->stream>>>(a.pts, n, ctx->d_status);

@@ -97,27 +97,35 @@ struct PairView {
   MapDev M;
 };
 
-// Scratch of the gradient pass of a plan (host tables uploaded once, per-(pair, point)
-// gradient slots), created at the first glim_plan_backward and kept by the plan.
+// Scratch of the gradient pass of a plan, created at the first glim_plan_backward and kept by
+// the plan: the work list of (source frame, point tile) items, the pairs grouped by source
+// frame, one partial slot of 9 sums per (item, pair of its frame), and the per-pair gradients.
 struct BwdScratch {
-  int64_t* pair_off = nullptr;   // npairs: offset of the pair's points in pp
-  int64_t* frame_off = nullptr;  // nframes + 1
-  int32_t* src_begin = nullptr;  // nframes + 1
-  int32_t* src_list = nullptr;   // pairs grouped by source frame
-  int32_t* tgt = nullptr;        // npairs
-  float4* pp = nullptr;          // per (pair, point)
-  double* part = nullptr;        // nitems x 12
-  double* pair_grad = nullptr;   // npairs x 12
-  int64_t npp = 0, ntot = 0;
+  int2* items = nullptr;               // nitems: (frame, first point of the tile)
+  int32_t* frame_item_begin = nullptr; // nframes + 1
+  int32_t* src_begin = nullptr;        // nframes + 1: pairs grouped by source frame
+  int32_t* src_list = nullptr;
+  int32_t* pair_pos = nullptr;         // npairs: position of the pair in its source's group
+  int32_t* tgt = nullptr;              // npairs: target frame
+  int64_t* frame_off = nullptr;        // nframes + 1: first point of each frame in the outputs
+  int64_t* slot_base = nullptr;        // nframes: first partial slot of the frame's items
+  double* part = nullptr;              // nslots x 9
+  double* pair_grad = nullptr;         // npairs x 12
+  int* head = nullptr;                 // work-queue head
+  int nitems = 0, grid = 0;
+  int64_t ntot = 0, nslots = 0;
   void release() {
-    cudaFree(pair_off);
-    cudaFree(frame_off);
+    cudaFree(items);
+    cudaFree(frame_item_begin);
     cudaFree(src_begin);
     cudaFree(src_list);
+    cudaFree(pair_pos);
     cudaFree(tgt);
-    cudaFree(pp);
+    cudaFree(frame_off);
+    cudaFree(slot_base);
     cudaFree(part);
     cudaFree(pair_grad);
+    cudaFree(head);
     *this = BwdScratch{};
   }
 };

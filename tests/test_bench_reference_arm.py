@@ -21,3 +21,8 @@ def test_reference_arm_prints_one_complete_json_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    # the step is the measured sample, the config names the workload as the GPU arm does
+    cb = d["cpu_baseline"]
+    assert abs(d["ms_per_step"] - 1e3 * cb["seconds"]) < 0.5 * d["ms_per_step"] and cb["pair_points"] > 0
+    assert set(d["config"]) >= {"workload", "pairs", "frames", "pair_points_per_step", "l2", "parallelism"}
+    assert "stand-in" in cb["sample"]

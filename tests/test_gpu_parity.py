@@ -570,9 +570,9 @@ def test_autograd_function_against_fd(G, ctx, full):
 
 @pytest.mark.parametrize("full", [False, True])
 def test_plan_backward_equals_one_shot_and_reuses_scratch(G, ctx, full):
-    """glim_plan_backward on a plan (block 256, one point per thread) gives the one-shot
-    glim_backward's gradient bit for bit, again on a second call with the kept scratch, and
-    refuses a plan with another tile."""
+    """glim_plan_backward on a plan gives the one-shot glim_backward's gradient bit for bit,
+    again on a second call with the kept scratch, and on a plan with other linearization tiles
+    (the gradient pass has its own work list)."""
     from gpu_helpers import Prepared
     P = Prepared(ctx, synth.corridor(n_cur=4000, kf_range=(3000, 5000), n_kf=3, weights=True))
     w = P.w
@@ -594,8 +594,8 @@ def test_plan_backward_equals_one_shot_and_reuses_scratch(G, ctx, full):
             assert torch.equal(a, b)
     assert not torch.equal(one[0], one2[0])
     other = G.Plan(ctx, P.gframes, P.gmaps, w.pairs, block=128, pts_per_thread=16)
-    with pytest.raises(G.GlimError, match="EINVAL"):
-        other.backward(w.poses)
+    for a, b in zip(one, other.backward(w.poses, omega_grad_full=full)):
+        assert torch.equal(a, b)
 
 
 def test_autograd_interleaved_evaluations(G, ctx):
@@ -866,3 +866,23 @@ def test_plan_on_a_map_freed_through_the_c_abi_is_refused(G, ctx, corridor):
     plan.close()
     other.close()
     assert torch.cuda.current_device() == 0
+
+
+def test_factor_records_and_symmetric_H(G, ctx, corridor):
+    """Every linearization of a plan also writes one 92-double record per pair (e, the upper
+    triangle of H, b, inliers): it equals the packing of the plan's own outputs bit for bit,
+    H is exactly symmetric, and unpacking the records gives those outputs back; gathering the
+    records of a split pair list (world of one) puts them back in pair order."""
+    w = corridor.w
+    plan = G.Plan(ctx, corridor.gframes, corridor.gmaps, w.pairs)
+    e, H, b, inl = [np.array(x) for x in plan.linearize(w.poses)]
+    rec = plan.device_records()
+    assert rec.shape == (len(w.pairs), 92) and rec.is_cuda
+    assert np.array_equal(H, np.transpose(H, (0, 2, 1)))
+    assert np.array_equal(rec.cpu().numpy(), G.pack_records(e, H, b, inl))
+    e2, H2, b2, inl2 = G.unpack_records(rec)
+    assert np.array_equal(e2, e) and np.array_equal(H2, H) and np.array_equal(b2, b) and np.array_equal(inl2, inl)
+    idx = np.arange(len(w.pairs))[::-1].copy()
+    full = G.gather_records(rec[torch.as_tensor(idx, device=rec.device)], idx, len(w.pairs))
+    assert torch.equal(full, rec)
+    plan.close()

@@ -613,3 +613,19 @@ def test_graph_step_damping_closed_form_and_gauge():
         O.graph_step([(0, 1)], 2, [J.T @ J], [np.zeros(12)], fixed=-1)
     xi, _, _ = O.graph_step([(0, 1)], 2, [J.T @ J], [J.T @ np.ones(6)], fixed=0)
     np.testing.assert_allclose(K @ xi[1], np.ones(6), atol=1e-9)  # r = K x_0 - K x_1 + 1 = 0 with x_0 = 0
+
+
+def test_covariances_at_queries_equal_the_full_brute_force():
+    """The query-subset kNN (a k-heap over all points per query) gives, for every listed point,
+    the same neighbour list, covariance, normal and near-tie flag as the full brute force (a
+    partial sort of all distances), including points with exactly tied distances."""
+    s = synth.Stream(21, "cov-at")
+    pts = s.uniform(3 * 700, -2, 2).reshape(700, 3)
+    pts[:100] = np.round(pts[:100] * 4) / 4  # a lattice patch: many exact distance ties
+    for reg in (1, 0):
+        c, n, knn, tie = O.estimate_covariances(pts, k=10, reg_mode=reg, eps=1e-3)
+        q = np.array([0, 1, 5, 50, 99, 100, 333, 699])
+        cq, nq, kq, tq = O.covariances_at(pts, q, k=10, reg_mode=reg, eps=1e-3)
+        assert np.array_equal(kq, knn[q]) and np.array_equal(cq, c[q]) and np.array_equal(nq, n[q])
+        assert np.array_equal(tq, tie[q])
+    assert (kq[:, 0] == q).all()  # the point itself is its own nearest neighbour
