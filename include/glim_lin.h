@@ -188,8 +188,8 @@ glim_status glim_spatial_order(glim_ctx* ctx, const float* pts4, int64_t n, floa
 /* ---------------------------------------------------------------- voxelmaps */
 
 /* Build the multi-resolution voxelmap of one frame (Sec. III-C "Preprocessing"): for each
- * level, the occupied voxels with the mean of their points and covariances, in an
- * open-addressing hash table keyed by the packed voxel key.  pts4 / cov6 are device
+ * level, the occupied voxels with the mean of their points and covariances, stored in a dense
+ * grid or in hashed voxel blocks (see glim_build_voxelmap_ex).  pts4 / cov6 are device
  * arrays (n x float4, n x 6); resolutions is a host array of `levels` voxel sizes.
  * Returns GLIM_ERANGE if a key is outside [-2^20, 2^20), GLIM_EINVAL on non-finite input.
  * Synchronizes the stream.  The voxelmap keeps no reference to the input arrays. */
@@ -198,12 +198,14 @@ glim_status glim_build_voxelmap(glim_ctx* ctx, const float* pts4, const float* c
 /* As glim_build_voxelmap, choosing the table layout of every level:
  *   layout 0 (default): a dense grid over the bounding box of the occupied keys whose cells
  *            hold the voxel records (48 bytes per cell) when the box has at most 256 cells
- *            per voxel plus 2^22 cells and needs at most 32 GiB, else an open-addressing hash
- *            table (linear probing, load <= 1/4);
+ *            per voxel plus 2^22 cells and needs at most 32 GiB, else hashed voxel blocks;
  *   layout 1: dense grid (GLIM_EINVAL if the bounding box exceeds the limit);
- *   layout 2: hash table.
+ *   layout 2: hashed voxel blocks: blocks of 2 x 2 x 2 voxels whose 8 cells hold the records,
+ *            found through an open-addressing table of the block keys (linear probing, load
+ *            <= 1/4), as voxel hashing stores voxel blocks.
  * Both layouts give identical correspondences and results; the dense grid resolves every
- * lookup, hit or miss, with one 48-byte read, the hash table with one read per probe. */
+ * lookup, hit or miss, with one 48-byte read, the hashed layout with one table-entry read of
+ * the block (one per probe) and one 48-byte read. */
 glim_status glim_build_voxelmap_ex(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n,
                                    const double* resolutions, int32_t levels, int32_t layout,
                                    glim_vmap** out);
@@ -226,8 +228,9 @@ void glim_vmap_free(glim_vmap* vmap);
  * box exceeds the dense limit, GLIM_ENOMEM. */
 glim_status glim_vmap_insert(glim_ctx* ctx, glim_vmap* vmap, const float* pts4, const float* cov6,
                              int64_t n, int32_t layout);
-/* Number of occupied voxels, table capacity (hash slots, or grid cells for a dense level)
- * and longest probe sequence (1 for a dense level) of a level. */
+/* Number of occupied voxels, capacity in cells (grid cells of a dense level, the cells of the
+ * allocated blocks of a hashed level) and longest probe sequence of the block table (1 for a
+ * dense level) of a level. */
 glim_status glim_vmap_info(const glim_vmap* vmap, int32_t level, int64_t* n_voxels,
                            int64_t* capacity, int32_t* max_probe);
 /* 1 if the level uses a dense index grid, 0 for a hash table, -1 for a bad argument. */

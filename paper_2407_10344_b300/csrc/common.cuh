@@ -178,26 +178,38 @@ __device__ __forceinline__ bool voxel_coord(float c, float inv_r, int& k) {
   return true;
 }
 
-// ------------------------------------------------------------------ hash slot (48 bytes)
-// One open-addressing slot holds the key and the voxel statistics, so a probe that matches
-// returns the voxel with the same 48-byte read:  w0 = {kx, ky, kz (int bits), c22},
-// w1 = {mean x, mean y, mean z, c00}, w2 = {c01, c02, c11, c12}.  Empty slots have every
-// byte 0x80.
+// ------------------------------------------------------------------ voxel record (48 bytes)
+// The record of one voxel cell: w0 = {canonical id (int bits), c22, kx (int bits), c22},
+// w1 = {mean x, mean y, mean z, c00}, w2 = {c01, c02, c11, c12}.  An empty cell has every byte
+// 0x80, so its id reads negative.  c22 sits next to the id (one 8-byte read gives both) and
+// again at w0.w.
 struct __align__(16) VoxSlot {
   float4 w0, w1, w2;
 };
 
-// One resolution level of a voxelmap as the kernels see it.  Either a dense grid over the
-// bounding box of the occupied keys whose cells hold the voxel records directly (empty cells
-// have every byte 0x80; an occupied cell has w0 = {canonical id, kx, ky, c22}), or, when
-// that box is too large, an open-addressing hash table whose slots carry key and statistics.
+// Voxel blocks of the hashed layout: 2 x 2 x 2 cells.  Block key (kx >> 1, ky >> 1, kz >> 1)
+// (arithmetic shifts, i.e. floor division), cell kx & 1, ky & 1, kz & 1 inside it.
+#define GLIM_BLOCK_SHIFT 1
+#define GLIM_BLOCK_CELLS 8
+
+__host__ __device__ inline int block_local(int kx, int ky, int kz) {
+  return ((kx & 1) << 2) | ((ky & 1) << 1) | (kz & 1);
+}
+
+// One resolution level of a voxelmap as the kernels see it: the voxel records live in cells
+// (empty cells all 0x80, and one empty record just before cell 0 that a miss reads), either
+//   dense: a grid over the bounding box of the occupied keys, cell ((kx - ox) ny + ky - oy)
+//          nz + kz - oz; or
+//   hashed: voxel blocks (spatial hashing of voxel blocks, as in voxel hashing): an
+//          open-addressing table (linear probing) of entries {bx, by, bz, block} maps a block
+//          key to its block, whose 8 cells hold the records, cell block * 8 + local.
 struct LevelDev {
-  const VoxSlot* slots;    // hash: table slots; dense: nx * ny * nz cells, z fastest
-  const int32_t* slot_id;  // hash: canonical voxel id of each slot (-1 = empty)
-  const int32_t* grid;     // unused (kept for layout stability)
-  uint32_t mask;           // hash: capacity - 1
+  const VoxSlot* slots;    // cell records: grid cells (dense) or block cells (hashed)
+  const int4* btab;        // hashed: block table {bx, by, bz, block index}, empty = 0x80 bytes
+  const int32_t* unused;   // null (keeps the descriptor's layout)
+  uint32_t mask;           // hashed: block-table capacity - 1
   int32_t log2cap;
-  int32_t max_probe;       // hash: longest probe sequence of any stored key
+  int32_t max_probe;       // hashed: longest probe sequence of any block in the table
   float inv_r;
   int32_t dense;
   int32_t ox, oy, oz;      // dense: key of grid cell (0, 0, 0)
@@ -214,11 +226,11 @@ struct glim_vmap {
   int64_t cap[GLIM_MAX_LEVELS] = {0};
   int32_t log2cap[GLIM_MAX_LEVELS] = {0};
   int32_t max_probe[GLIM_MAX_LEVELS] = {0};
-  VoxSlot* slots[GLIM_MAX_LEVELS] = {nullptr};       // hash slots, or dense cell (0, 0, 0)
-  VoxSlot* slots_alloc[GLIM_MAX_LEVELS] = {nullptr}; // allocation; a dense grid has an empty record at slots - 1
-  int32_t* slot_id[GLIM_MAX_LEVELS] = {nullptr};
+  VoxSlot* slots[GLIM_MAX_LEVELS] = {nullptr};       // cell 0 (grid or block cells)
+  VoxSlot* slots_alloc[GLIM_MAX_LEVELS] = {nullptr}; // allocation: an empty record at slots - 1
+  int4* btab[GLIM_MAX_LEVELS] = {nullptr};           // hashed: block table (cap entries)
+  int64_t nblk[GLIM_MAX_LEVELS] = {0};               // hashed: number of blocks
   int32_t dense[GLIM_MAX_LEVELS] = {0};
-  int32_t* grid[GLIM_MAX_LEVELS] = {nullptr};
   int32_t org[GLIM_MAX_LEVELS][3] = {};
   uint32_t dim[GLIM_MAX_LEVELS][3] = {};
   unsigned long long* vkey[GLIM_MAX_LEVELS] = {nullptr};  // canonical order
@@ -231,13 +243,13 @@ struct glim_vmap {
   LevelDev dev(int l) const {
     LevelDev d;
     d.slots = slots[l];
-    d.slot_id = slot_id[l];
+    d.btab = btab[l];
+    d.unused = nullptr;
     d.mask = uint32_t(cap[l] - 1);
     d.log2cap = log2cap[l];
     d.max_probe = max_probe[l];
     d.inv_r = inv_r[l];
     d.dense = dense[l];
-    d.grid = grid[l];
     d.ox = org[l][0];
     d.oy = org[l][1];
     d.oz = org[l][2];

@@ -156,13 +156,15 @@ __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in,
 
   int kx[LMAX], ky[LMAX], kz[LMAX];
   bool hit[LMAX];
-  uint32_t hh[LMAX];  // hash level: first slot
+  uint32_t hh[LMAX];  // hashed level: first probe of the block table
+  int4 be[LMAX];      // hashed level: that entry
+  int64_t cell[LMAX];
   float4 s0[LMAX], s1[LMAX], s2[LMAX];
   // keys: shifts of the level-0 key when the resolutions double per level, else per level
   int k0x, k0y, k0z;
   const bool shifted = P.M.pow2 && level0_key3(q, P.M.lv[0].inv_r, k0x, k0y, k0z);
-  // one read of every level, all in flight together: a dense level reads its grid cell (the
-  // record itself), a hash level its first slot (key and statistics)
+  // first reads of every level in flight together: a dense level's cell index is known from
+  // its key, a hashed level reads its block's table entry
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
     const LevelDev& L = P.M.lv[l];
@@ -174,21 +176,37 @@ __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in,
     } else {
       hit[l] = live && (l < P.M.levels) && level_key3(q, L.inv_r, kx[l], ky[l], kz[l]);
     }
+    cell[l] = -1;
     if (hit[l]) {
-      int64_t c;
       if (L.dense) {
-        c = dense_cell(L, kx[l], ky[l], kz[l]);
-        hit[l] = c >= 0;
+        cell[l] = dense_cell(L, kx[l], ky[l], kz[l]);
       } else {
-        hh[l] = hash3(kx[l], ky[l], kz[l], L.log2cap);
-        c = hh[l];
+        hh[l] = block_hash(kx[l], ky[l], kz[l], L.log2cap);
+        be[l] = ldg4i(&L.btab[hh[l]]);
       }
-      if (hit[l]) {
-        const VoxSlot* sl = L.slots + c;
-        s0[l] = ldg4(&sl->w0);
-        s1[l] = ldg4(&sl->w1);
-        s2[l] = ldg4(&sl->w2);
-      }
+    }
+  }
+  // hashed levels: the entry of the block, or a bounded continuation of the probe
+#pragma unroll
+  for (int l = 0; l < LMAX; ++l) {
+    const LevelDev& L = P.M.lv[l];
+    if (hit[l] && !L.dense) {
+      const int bx = kx[l] >> GLIM_BLOCK_SHIFT, by = ky[l] >> GLIM_BLOCK_SHIFT, bz = kz[l] >> GLIM_BLOCK_SHIFT;
+      if (be[l].x == bx && be[l].y == by && be[l].z == bz)
+        cell[l] = int64_t(be[l].w) * GLIM_BLOCK_CELLS + block_local(kx[l], ky[l], kz[l]);
+      else if (be[l].x != GLIM_EMPTY_COORD)
+        cell[l] = block_cell_from(L, kx[l], ky[l], kz[l], (hh[l] + 1u) & L.mask, 1);
+    }
+  }
+  // the records of every level in flight together
+#pragma unroll
+  for (int l = 0; l < LMAX; ++l) {
+    hit[l] = cell[l] >= 0;
+    if (hit[l]) {
+      const VoxSlot* sl = P.M.lv[l].slots + cell[l];
+      s0[l] = ldg4(&sl->w0);
+      s1[l] = ldg4(&sl->w1);
+      s2[l] = ldg4(&sl->w2);
     }
   }
   int nh = 0;
@@ -196,28 +214,9 @@ __device__ __forceinline__ void warp_round(const PairView& P, const PointIn& in,
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
     vid[l] = -1;
-    if (hit[l] && P.M.lv[l].dense) {
+    if (hit[l]) {
       hit[l] = __float_as_int(s0[l].x) >= 0;  // occupied cell (its record starts with the id)
       if constexpr (IDS) vid[l] = __float_as_int(s0[l].x);
-    }
-    if (hit[l] && !P.M.lv[l].dense) {
-      const int sx = __float_as_int(s0[l].x);
-      if (!(sx == kx[l] && __float_as_int(s0[l].y) == ky[l] && __float_as_int(s0[l].z) == kz[l])) {
-        hit[l] = false;
-        if (sx != GLIM_EMPTY_COORD) {  // collision: continue the probe sequence
-          const LevelDev& L = P.M.lv[l];
-          const int s = probe_from(L, kx[l], ky[l], kz[l], (hh[l] + 1u) & L.mask, 1);
-          if (s >= 0) {
-            hit[l] = true;
-            s0[l] = ldg4(&L.slots[s].w0);
-            s1[l] = ldg4(&L.slots[s].w1);
-            s2[l] = ldg4(&L.slots[s].w2);
-            if constexpr (IDS) vid[l] = L.slot_id[s];
-          }
-        }
-      } else if constexpr (IDS) {
-        vid[l] = P.M.lv[l].slot_id[hh[l]];
-      }
     }
     nh += hit[l] ? 1 : 0;
   }
@@ -448,18 +447,19 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) k_linearize_ids(const LinA
 }
 
 // ---------------------------------------------------------------- per-lane kernels
-// Every target level is a dense grid (k_linearize_dense) or every one a hash table
+// Every target level is a dense grid (k_linearize_dense) or every one is hashed
 // (k_linearize_hash): a lane handles its own point from start to end.  Dense grid: a lookup
-// is an index computation and one read, without divergent branches; a key outside the
-// grid's box reads the empty record before cell 0.  Hash table: the first probe (one
-// 48-byte slot with key and statistics) is read the same way, unconditionally; the lanes
-// whose first slot holds another key continue the linear probe in a loop bounded by the
-// table's longest probe sequence (rare at load 1/4).  A lane past the end of its tile reads
-// its tile's last point and is masked.  Because G = [-(u)x, I] is the same for all levels of
-// a point, the lane sums w Omega, w Omega d and e over the levels (a miss, or a term whose S
-// is not positive definite, adds nothing) and adds the G-form of the sums once: 28
-// accumulator updates per point instead of per hit.  The weight enters as w adj(S)/det(S),
-// as in the general kernel; results agree up to FP32 rounding.
+// is an index computation and one record read, without divergent branches; a key outside the
+// grid's box reads the empty record before cell 0.  Hashed: the lookup first reads the
+// block's table entry (the lanes of a warp mostly share a few 2 x 2 x 2 blocks, so the entries
+// are warp-coherent and cached); a lane whose entry holds another block continues the probe in
+// a loop bounded by the table's longest probe sequence (a warp-uniform branch skips it when
+// no lane needs it); then the cell record is read as on a dense grid.  A lane past the end of
+// its tile reads its tile's last point and is masked.  Because G = [-(u)x, I] is the same for
+// all levels of a point, the lane sums w Omega, w Omega d and e over the levels (a miss, or a
+// term whose S is not positive definite, adds nothing) and adds the G-form of the sums once:
+// 28 accumulator updates per point instead of per hit.  The weight enters as
+// w adj(S)/det(S), as in the general kernel; results agree up to FP32 rounding.
 
 template <class MapT>
 struct LaneView {  // per-item constants, written by thread 0
@@ -489,9 +489,8 @@ struct LaneFetch {
   float3 q;
   float w;
   bool live;
-  float4 s0[LMAX];  // dense: {id, C~22, ., .} (8 bytes read); hash: {kx, ky, kz, C~22}
+  float4 s0[LMAX];  // {id, C~22, ., .} (8 bytes read)
   float4 s1[LMAX], s2[LMAX];
-  uint32_t slot[LMAX];  // hash: the first probe's slot (with IDS: the matching slot)
   float2 ca, cb, cc;
   int idx;  // IDS: index of the point in its frame, -1 for a masked lane
 };
@@ -525,32 +524,79 @@ __device__ __forceinline__ void lane_fetch(const LaneView<typename std::conditio
   q.z = finite_q ? q.z : 0.f;
   const float4 irq = *reinterpret_cast<const float4*>(V.M.inv_r);  // one 16-byte shared load
   const float irv[4] = {irq.x, irq.y, irq.z, irq.w};
+  if constexpr (!HASH) {
+    // dense: per level the key, the cell inside the grid's box and the record reads, the
+    // levels interleaved (kept in this form: splitting it into per-stage loops measured 6 %
+    // slower); descriptor {cells, ox, oy} {oz, nx, ny, nz}
 #pragma unroll
-  for (int l = 0; l < LMAX; ++l) {
-    // the level's descriptor as two 16-byte shared loads
-    const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
-    const uint4 lb = reinterpret_cast<const uint4*>(&V.M.lv[l])[1];
-    const float ir = irv[l];
-    const VoxSlot* base =
-        reinterpret_cast<const VoxSlot*>(uint64_t(uint32_t(la.x)) | (uint64_t(uint32_t(la.y)) << 32));
-    // keys floor(q * inv_r) (FP32 product); a key outside [-2^20, 2^20) is in no table
-    const int kx = __float2int_rd(__fmul_rn(q.x, ir));
-    const int ky = __float2int_rd(__fmul_rn(q.y, ir));
-    const int kz = __float2int_rd(__fmul_rn(q.z, ir));
-    const VoxSlot* sl;
-    if constexpr (HASH) {  // {slots, mask, log2cap} {max_probe, ...}
-      F.slot[l] = hash3(kx, ky, kz, la.w);
-      sl = base + F.slot[l];
-      F.s0[l] = ldg4(&sl->w0);
-    } else {  // {cells, ox, oy} {oz, nx, ny, nz}
+    for (int l = 0; l < LMAX; ++l) {
+      const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
+      const uint4 lb = reinterpret_cast<const uint4*>(&V.M.lv[l])[1];
+      const VoxSlot* base =
+          reinterpret_cast<const VoxSlot*>(uint64_t(uint32_t(la.x)) | (uint64_t(uint32_t(la.y)) << 32));
+      // keys floor(q * inv_r) (FP32 product); a key outside [-2^20, 2^20) is in no table
+      const int kx = __float2int_rd(__fmul_rn(q.x, irv[l]));
+      const int ky = __float2int_rd(__fmul_rn(q.y, irv[l]));
+      const int kz = __float2int_rd(__fmul_rn(q.z, irv[l]));
       const uint32_t x = uint32_t(kx) - uint32_t(la.z), y = uint32_t(ky) - uint32_t(la.w), z = uint32_t(kz) - lb.x;
       const bool in_box = live && x < lb.y && y < lb.z && z < lb.w;
-      sl = base + (in_box ? int((x * lb.z + y) * lb.w + z) : -1);
-      const float2 h = __ldg(reinterpret_cast<const float2*>(&sl->w0));
-      F.s0[l] = make_float4(h.x, h.y, 0.f, 0.f);
+      const VoxSlot* sl = base + (in_box ? int((x * lb.z + y) * lb.w + z) : -1);  // -1: the empty record
+      const float2 h2 = __ldg(reinterpret_cast<const float2*>(&sl->w0));
+      F.s0[l] = make_float4(h2.x, h2.y, 0.f, 0.f);
+      F.s1[l] = ldg4(&sl->w1);  // {mean, C~00}
+      F.s2[l] = ldg4(&sl->w2);  // {C~01, C~02, C~11, C~12}
     }
-    F.s1[l] = ldg4(&sl->w1);  // {mean, C~00}
-    F.s2[l] = ldg4(&sl->w2);  // {C~01, C~02, C~11, C~12}
+  } else {
+    // hashed: the keys of every level, the table entries of every level's block in flight
+    // together (the lanes of a warp mostly share a few blocks), then per level the lanes whose
+    // first entry holds another block continue the probe, bounded by the table's longest
+    // probe sequence, and the records of every level; descriptor {slots, btab}
+    // {mask, log2cap, max_probe, pad}
+    int kx[LMAX], ky[LMAX], kz[LMAX], cell[LMAX];
+    int4 e[LMAX];
+    uint32_t h[LMAX];
+#pragma unroll
+    for (int l = 0; l < LMAX; ++l) {
+      kx[l] = __float2int_rd(__fmul_rn(q.x, irv[l]));
+      ky[l] = __float2int_rd(__fmul_rn(q.y, irv[l]));
+      kz[l] = __float2int_rd(__fmul_rn(q.z, irv[l]));
+      const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
+      const int4 lb = reinterpret_cast<const int4*>(&V.M.lv[l])[1];
+      const int4* btab = reinterpret_cast<const int4*>(uint64_t(uint32_t(la.z)) | (uint64_t(uint32_t(la.w)) << 32));
+      h[l] = hash3(kx[l] >> GLIM_BLOCK_SHIFT, ky[l] >> GLIM_BLOCK_SHIFT, kz[l] >> GLIM_BLOCK_SHIFT, lb.y);
+      e[l] = ldg4i(btab + h[l]);
+    }
+#pragma unroll
+    for (int l = 0; l < LMAX; ++l) {
+      const int bx = kx[l] >> GLIM_BLOCK_SHIFT, by = ky[l] >> GLIM_BLOCK_SHIFT, bz = kz[l] >> GLIM_BLOCK_SHIFT;
+      bool match = e[l].x == bx && e[l].y == by && e[l].z == bz;
+      const bool more = live && !match && e[l].x != GLIM_EMPTY_COORD;
+      if (__any_sync(0xffffffffu, more)) {
+        if (more) {
+          const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
+          const int4 lb = reinterpret_cast<const int4*>(&V.M.lv[l])[1];
+          const int4* btab = reinterpret_cast<const int4*>(uint64_t(uint32_t(la.z)) | (uint64_t(uint32_t(la.w)) << 32));
+          uint32_t hh = h[l];
+          for (int p = 1; p < lb.z; ++p) {
+            hh = (hh + 1u) & uint32_t(lb.x);
+            e[l] = ldg4i(btab + hh);
+            match = e[l].x == bx && e[l].y == by && e[l].z == bz;
+            if (match || e[l].x == GLIM_EMPTY_COORD) break;
+          }
+        }
+      }
+      cell[l] = (live && match) ? e[l].w * GLIM_BLOCK_CELLS + block_local(kx[l], ky[l], kz[l]) : -1;
+    }
+#pragma unroll
+    for (int l = 0; l < LMAX; ++l) {
+      const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
+      const VoxSlot* sl =  // cell -1 is the empty record before cell 0
+          reinterpret_cast<const VoxSlot*>(uint64_t(uint32_t(la.x)) | (uint64_t(uint32_t(la.y)) << 32)) + cell[l];
+      const float2 h2 = __ldg(reinterpret_cast<const float2*>(&sl->w0));
+      F.s0[l] = make_float4(h2.x, h2.y, 0.f, 0.f);
+      F.s1[l] = ldg4(&sl->w1);  // {mean, C~00}
+      F.s2[l] = ldg4(&sl->w2);  // {C~01, C~02, C~11, C~12}
+    }
   }
   F.q = q;
   F.w = m.w;
@@ -594,52 +640,15 @@ __device__ __forceinline__ void lane_compute(const LaneView<typename std::condit
   float vc22[LMAX];  // C~22 of the level's voxel
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
-    if constexpr (HASH) {
-      const int kx = __float2int_rd(__fmul_rn(q.x, irv[l]));
-      const int ky = __float2int_rd(__fmul_rn(q.y, irv[l]));
-      const int kz = __float2int_rd(__fmul_rn(q.z, irv[l]));
-      bool match = live && __float_as_int(s0[l].x) == kx && __float_as_int(s0[l].y) == ky &&
-                   __float_as_int(s0[l].z) == kz;
-      const bool more = live && !match && __float_as_int(s0[l].x) != GLIM_EMPTY_COORD;
-      if (__any_sync(0xffffffffu, more)) {  // some first slot held another key
-        if (more) {
-          const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
-          const int max_probe = reinterpret_cast<const int4*>(&V.M.lv[l])[1].x;
-          const VoxSlot* slots =
-              reinterpret_cast<const VoxSlot*>(uint64_t(uint32_t(la.x)) | (uint64_t(uint32_t(la.y)) << 32));
-          uint32_t h = F.slot[l];
-          for (int p = 1; p < max_probe; ++p) {  // bounded by the longest probe sequence of the table
-            h = (h + 1u) & uint32_t(la.z);
-            const float4 w0 = ldg4(&slots[h].w0);
-            if (__float_as_int(w0.x) == kx && __float_as_int(w0.y) == ky && __float_as_int(w0.z) == kz) {
-              s0[l] = w0;
-              s1[l] = ldg4(&slots[h].w1);
-              s2[l] = ldg4(&slots[h].w2);
-              match = true;
-              if constexpr (IDS) F.slot[l] = h;
-              break;
-            }
-            if (__float_as_int(w0.x) == GLIM_EMPTY_COORD) break;
-          }
-        }
-      }
-      hit[l] = match;
-      vc22[l] = s0[l].w;
-    } else {
-      hit[l] = __float_as_int(s0[l].x) >= 0;  // occupied cell (empty records hold 0x80808080)
-      vc22[l] = s0[l].y;
-    }
+    hit[l] = __float_as_int(s0[l].x) >= 0;  // occupied cell (empty records hold 0x80808080)
+    vc22[l] = s0[l].y;
   }
   if constexpr (IDS) {  // the canonical id of the voxel each level resolved to, or -1
     if (F.idx >= 0) {
 #pragma unroll
       for (int l = 0; l < LMAX; ++l) {
         if (l >= idl) continue;
-        int id = -1;
-        if (hit[l]) {
-          if constexpr (HASH) id = V.M.lv[l].slot_id[F.slot[l]];
-          else id = __float_as_int(s0[l].x);  // a dense record starts with the id
-        }
+        const int id = hit[l] ? __float_as_int(s0[l].x) : -1;  // a record starts with the id
         ids[int64_t(F.idx) * idl + l] = id;
       }
     }
@@ -707,15 +716,6 @@ __device__ __forceinline__ void lane_compute(const LaneView<typename std::condit
   acc.add(27, es);
 }
 
-template <int LMAX, bool HASH, bool IDS, class A>
-__device__ __forceinline__ void lane_point(const LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V,
-                                           const float4 m, bool live, int validate, A& acc, int& inl, int kk,
-                                           int32_t* ids, int idl) {
-  LaneFetch<LMAX> F;
-  lane_fetch<LMAX, HASH, IDS>(V, m, live, validate, kk, F);
-  lane_compute<LMAX, HASH, IDS>(V, F, acc, inl, ids, idl);
-}
-
 template <int BLOCK, int ACC, int LMAX, bool HASH, bool IDS>
 __device__ __forceinline__ void process_item_lane(const LinArgs& a, int item,
                                                   LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V) {
@@ -747,46 +747,27 @@ __device__ __forceinline__ void process_item_lane(const LinArgs& a, int item,
   const int last = V.end - 1;  // items are never empty
   const int first = it.start + int(threadIdx.x);
   const int rounds = min(a.ppt, (last - it.start) / BLOCK + 1);
-  if constexpr (!HASH) {
-    // Dense grids: a software pipeline over the rounds, unrolled twice so that the two
-    // buffers alternate without copies.  A point's coordinates are read two rounds ahead, its
-    // voxel records and covariance one round ahead (lane_fetch), so the reads of the next
-    // point are in flight while the lane computes the current one (lane_compute): 9 % faster
-    // than reading a point's records at the start of its own round.
-    LaneFetch<LMAX> fa, fb;
-    lane_fetch<LMAX, HASH, IDS>(V, ldg4(V.pts + min(first, last)), first <= last, a.validate, min(first, last), fa);
-    float4 pn = ldg4(V.pts + min(first + BLOCK, last));
-    int j = 0;
+  // A software pipeline over the rounds, unrolled twice so that the two buffers alternate
+  // without copies.  A point's coordinates are read two rounds ahead, its voxel records
+  // (after the block-table lookup of a hashed level) and covariance one round ahead
+  // (lane_fetch), so the reads of the next point are in flight while the lane computes the
+  // current one (lane_compute): 9 % faster on dense grids than reading a point's records at
+  // the start of its own round.
+  LaneFetch<LMAX> fa, fb;
+  lane_fetch<LMAX, HASH, IDS>(V, ldg4(V.pts + min(first, last)), first <= last, a.validate, min(first, last), fa);
+  float4 pn = ldg4(V.pts + min(first + BLOCK, last));
+  int j = 0;
 #pragma unroll 1
-    for (; j + 1 < rounds; j += 2) {
-      const int k = first + j * BLOCK;
-      lane_fetch<LMAX, HASH, IDS>(V, pn, k + BLOCK <= last, a.validate, min(k + BLOCK, last), fb);
-      pn = ldg4(V.pts + min(k + 2 * BLOCK, last));
-      lane_compute<LMAX, HASH, IDS>(V, fa, acc, inl, ids, idl);
-      lane_fetch<LMAX, HASH, IDS>(V, pn, k + 2 * BLOCK <= last, a.validate, min(k + 2 * BLOCK, last), fa);
-      pn = ldg4(V.pts + min(k + 3 * BLOCK, last));
-      lane_compute<LMAX, HASH, IDS>(V, fb, acc, inl, ids, idl);
-    }
-    if (j < rounds) lane_compute<LMAX, HASH, IDS>(V, fa, acc, inl, ids, idl);
-  } else {
-    // Hash tables: the coordinates one round ahead only.  Holding a second point's home
-    // slots (48 bytes per level) costs the hash kernel more registers than the overlap
-    // gains: measured 34 % slower.
-    float4 p0 = ldg4(V.pts + min(first, last));
-    int j = 0;
-#pragma unroll 1
-    for (; j + 1 < rounds; j += 2) {
-      const int k = first + j * BLOCK;
-      const float4 p1 = ldg4(V.pts + min(k + BLOCK, last));
-      lane_point<LMAX, HASH, IDS>(V, p0, k <= last, a.validate, acc, inl, min(k, last), ids, idl);
-      p0 = ldg4(V.pts + min(k + 2 * BLOCK, last));
-      lane_point<LMAX, HASH, IDS>(V, p1, k + BLOCK <= last, a.validate, acc, inl, min(k + BLOCK, last), ids, idl);
-    }
-    if (j < rounds) {
-      const int k = first + j * BLOCK;
-      lane_point<LMAX, HASH, IDS>(V, p0, k <= last, a.validate, acc, inl, min(k, last), ids, idl);
-    }
+  for (; j + 1 < rounds; j += 2) {
+    const int k = first + j * BLOCK;
+    lane_fetch<LMAX, HASH, IDS>(V, pn, k + BLOCK <= last, a.validate, min(k + BLOCK, last), fb);
+    pn = ldg4(V.pts + min(k + 2 * BLOCK, last));
+    lane_compute<LMAX, HASH, IDS>(V, fa, acc, inl, ids, idl);
+    lane_fetch<LMAX, HASH, IDS>(V, pn, k + 2 * BLOCK <= last, a.validate, min(k + 2 * BLOCK, last), fa);
+    pn = ldg4(V.pts + min(k + 3 * BLOCK, last));
+    lane_compute<LMAX, HASH, IDS>(V, fb, acc, inl, ids, idl);
   }
+  if (j < rounds) lane_compute<LMAX, HASH, IDS>(V, fa, acc, inl, ids, idl);
   block_reduce_store<BLOCK, ACC>(acc, inl, a.part + int64_t(item) * PSTRIDE);
 }
 

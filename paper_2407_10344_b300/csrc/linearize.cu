@@ -326,7 +326,7 @@ bool map_all_dense(const glim_vmap* m) {
 
 bool map_all_hash(const glim_vmap* m) {
   for (int l = 0; l < m->levels; ++l)
-    if (m->dense[l] || !m->slots[l] || m->max_probe[l] < 1) return false;
+    if (m->dense[l] || !m->slots[l] || !m->btab[l] || m->max_probe[l] < 1) return false;
   return true;
 }
 
@@ -356,13 +356,14 @@ void fill_hash_map(const glim_vmap* m, const VoxSlot* empty16, HashMapDev& d) {
     HashLevelDev& v = d.lv[l];
     if (l < m->levels) {
       v.slots = m->slots[l];
+      v.btab = m->btab[l];
       v.mask = uint32_t(m->cap[l] - 1);
       v.log2cap = m->log2cap[l];
       v.max_probe = m->max_probe[l];
-      v.slot_id = m->slot_id[l];
       d.inv_r[l] = m->inv_r[l];
-    } else {  // an absent level probes an all-empty table of 16 slots
-      v.slots = empty16;
+    } else {  // an absent level: an all-empty table of 16 entries, and its empty record
+      v.slots = empty16 + 1;
+      v.btab = reinterpret_cast<const int4*>(empty16);
       v.mask = 15u;
       v.log2cap = 4;
       v.max_probe = 1;

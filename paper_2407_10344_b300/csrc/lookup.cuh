@@ -42,21 +42,27 @@ __device__ __forceinline__ bool level_key3(const float3& q, float inv_r, int& kx
   return a && b && c;
 }
 
-// Linear probe for key (kx, ky, kz) starting at slot h; returns the slot index or -1.  The
-// loop is bounded by the longest probe sequence recorded when the table was built.
-__device__ __forceinline__ int probe_from(const LevelDev& L, int kx, int ky, int kz, uint32_t h, int first) {
+__device__ __forceinline__ int4 ldg4i(const int4* p) { return __ldg(p); }
+
+// Cell of key (kx, ky, kz) in a hashed level, or -1: the block key's entry is looked up by a
+// linear probe from slot h, bounded by the table's longest probe sequence.
+__device__ __forceinline__ int block_cell_from(const LevelDev& L, int kx, int ky, int kz, uint32_t h, int first) {
+  const int bx = kx >> GLIM_BLOCK_SHIFT, by = ky >> GLIM_BLOCK_SHIFT, bz = kz >> GLIM_BLOCK_SHIFT;
   for (int p = first; p < L.max_probe; ++p) {
-    const float4 w0 = ldg4(&L.slots[h].w0);
-    const int sx = __float_as_int(w0.x);
-    if (sx == kx && __float_as_int(w0.y) == ky && __float_as_int(w0.z) == kz) return int(h);
-    if (sx == GLIM_EMPTY_COORD) return -1;
+    const int4 e = ldg4i(&L.btab[h]);
+    if (e.x == bx && e.y == by && e.z == bz) return e.w * GLIM_BLOCK_CELLS + block_local(kx, ky, kz);
+    if (e.x == GLIM_EMPTY_COORD) return -1;
     h = (h + 1u) & L.mask;
   }
   return -1;
 }
 
-__device__ __forceinline__ int probe_slot3(const LevelDev& L, int kx, int ky, int kz) {
-  return probe_from(L, kx, ky, kz, hash3(kx, ky, kz, L.log2cap), 0);
+__device__ __forceinline__ uint32_t block_hash(int kx, int ky, int kz, int log2cap) {
+  return hash3(kx >> GLIM_BLOCK_SHIFT, ky >> GLIM_BLOCK_SHIFT, kz >> GLIM_BLOCK_SHIFT, log2cap);
+}
+
+__device__ __forceinline__ int block_cell(const LevelDev& L, int kx, int ky, int kz) {
+  return block_cell_from(L, kx, ky, kz, block_hash(kx, ky, kz, L.log2cap), 0);
 }
 
 // Dense grid cell of key (kx, ky, kz), or -1 outside the grid (grids have < 2^31 cells).
@@ -85,16 +91,11 @@ __device__ __forceinline__ bool level0_key3(const float3& q, float inv_r0, int& 
   return level0_ok(px) && level0_ok(py) && level0_ok(pz);
 }
 
-// Voxel of key (kx, ky, kz) at a level: the index of its record in L.slots (dense: grid cell;
-// hash: slot) or -1, and the canonical id through *id.
+// Voxel of key (kx, ky, kz) at a level: the index of its record in L.slots (a grid cell or a
+// block cell) or -1, and the canonical id through *id.
 __device__ __forceinline__ int find_voxel(const LevelDev& L, int kx, int ky, int kz, int* id) {
-  if (L.dense) {
-    const int64_t c = dense_cell(L, kx, ky, kz);
-    const int v = c < 0 ? -1 : __float_as_int(ldg4(&L.slots[c].w0).x);
-    *id = v < 0 ? -1 : v;
-    return v < 0 ? -1 : int(c);
-  }
-  const int s = probe_slot3(L, kx, ky, kz);
-  *id = s < 0 ? -1 : L.slot_id[s];
-  return s;
+  const int64_t c = L.dense ? dense_cell(L, kx, ky, kz) : int64_t(block_cell(L, kx, ky, kz));
+  const int v = c < 0 ? -1 : __float_as_int(ldg4(&L.slots[c].w0).x);
+  *id = v < 0 ? -1 : v;
+  return v < 0 ? -1 : int(c);
 }

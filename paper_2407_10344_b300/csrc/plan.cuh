@@ -41,16 +41,15 @@ struct DenseMapDev {
   float inv_r[GLIM_MAX_LEVELS];
 };
 
-// One hash level as the per-lane hash kernel sees it (32 bytes, two 16-byte words):
-// {slots, mask, log2cap} {max_probe, pad, slot_id}.  slot_id (the canonical id of each slot)
-// is read only by the id-recording instantiations.
+// One hashed level as the per-lane hash kernel sees it (32 bytes, two 16-byte words):
+// {cell records, block table} {mask, log2cap, max_probe, pad}.
 struct HashLevelDev {
   const VoxSlot* slots;
+  const int4* btab;
   uint32_t mask;
   int32_t log2cap;
   int32_t max_probe;
   int32_t pad;
-  const int32_t* slot_id;
 };
 
 struct HashMapDev {

@@ -6,9 +6,10 @@
 //      stable radix sort, so the members of a voxel are contiguous and in point order;
 //   2. one thread per voxel sums its members' means and covariances in FP64 in that order
 //      and stores the averages (canonical id = rank of the key = position in sorted order);
-//   3. the voxels are written into a dense grid over their key box (48-byte records) when it
-//      is small enough, else inserted into an open-addressing table (linear probing, load
-//      <= 1/4) whose 48-byte slots carry the key and the statistics together.
+//   3. the voxel records (48 bytes) are written into a dense grid over their key box when it
+//      is small enough, else into voxel blocks (2 x 2 x 2 cells) found through an
+//      open-addressing table of block keys (linear probing, load <= 1/4): spatial hashing of
+//      voxel blocks, as voxel hashing does.
 #include <climits>
 
 #include "lookup.cuh"
@@ -50,40 +51,65 @@ __global__ void k_voxel_stats(const float4* __restrict__ pts, const float* __res
   vcount[v] = int32_t(e - b);
 }
 
-__global__ void k_hash_insert(const unsigned long long* __restrict__ vkey, const float* __restrict__ vmean,
-                              const float* __restrict__ vcov, const int32_t* __restrict__ vcount, int64_t m,
-                              VoxSlot* __restrict__ slots, int32_t* __restrict__ slot_id, int log2cap,
-                              uint32_t mask, int* __restrict__ max_probe, unsigned int* __restrict__ status) {
+// Block key of every voxel (its key >> 1 per axis, packed), with the voxel's index.
+__global__ void k_block_keys(const unsigned long long* __restrict__ vkey, int64_t m, unsigned long long* __restrict__ bkey,
+                             uint32_t* __restrict__ idx) {
   const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (v >= m) return;
-  const unsigned long long key = vkey[v];
-  const int kx = unpack_x(key), ky = unpack_y(key), kz = unpack_z(key);
-  // claim the slot through its first 8 bytes (kx, ky); keys are unique, so a claimed slot is
-  // never claimed again
-  const unsigned long long xy = (unsigned long long)(uint32_t)kx | ((unsigned long long)(uint32_t)ky << 32);
-  uint32_t h = hash3(kx, ky, kz, log2cap);
+  const unsigned long long k = vkey[v];
+  bkey[v] = pack_key(unpack_x(k) >> GLIM_BLOCK_SHIFT, unpack_y(k) >> GLIM_BLOCK_SHIFT, unpack_z(k) >> GLIM_BLOCK_SHIFT);
+  idx[v] = uint32_t(v);
+}
+
+// One thread per block (blocks in sorted block-key order; the block index is the rank): its
+// entry {bx, by, bz, block} goes into the table by linear probing, claimed through its first
+// 8 bytes (bx, by); block keys are unique, so a claimed slot is never claimed again.
+__global__ void k_block_table(const unsigned long long* __restrict__ bkey_unique, int64_t nblk, int4* __restrict__ btab,
+                              int log2cap, uint32_t mask, int* __restrict__ max_probe,
+                              unsigned int* __restrict__ status) {
+  const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b >= nblk) return;
+  const unsigned long long key = bkey_unique[b];
+  const int bx = unpack_x(key), by = unpack_y(key), bz = unpack_z(key);
+  const unsigned long long xy = (unsigned long long)(uint32_t)bx | ((unsigned long long)(uint32_t)by << 32);
+  uint32_t h = hash3(bx, by, bz, log2cap);
   for (uint32_t p = 0; p <= mask; ++p) {
-    unsigned long long* kp = reinterpret_cast<unsigned long long*>(&slots[h].w0);
-    const unsigned long long old = atomicCAS(kp, GLIM_EMPTY_XY, xy);
-    if (old == GLIM_EMPTY_XY) {
-      float* w = reinterpret_cast<float*>(&slots[h]);
-      w[2] = __int_as_float(kz);
-      w[3] = vcov[6 * v + 5];                                    // c22
-      w[4] = vmean[3 * v];
-      w[5] = vmean[3 * v + 1];
-      w[6] = vmean[3 * v + 2];
-      w[7] = vcov[6 * v + 0];                                    // c00
-      w[8] = vcov[6 * v + 1];                                    // c01
-      w[9] = vcov[6 * v + 2];                                    // c02
-      w[10] = vcov[6 * v + 3];                                   // c11
-      w[11] = vcov[6 * v + 4];                                   // c12
-      slot_id[h] = int32_t(v);
+    unsigned long long* kp = reinterpret_cast<unsigned long long*>(&btab[h]);
+    if (atomicCAS(kp, GLIM_EMPTY_XY, xy) == GLIM_EMPTY_XY) {
+      int* e = reinterpret_cast<int*>(&btab[h]);
+      e[2] = bz;
+      e[3] = int(b);
       atomicMax(max_probe, int(p + 1));
       return;
     }
     h = (h + 1u) & mask;
   }
   atomicOr(status, GLIM_DS_HASHFULL);
+}
+
+// The voxel record {id, C~22, kx, C~22} {mean, C~00} {C~01, C~02, C~11, C~12} of voxel v.
+__device__ __forceinline__ VoxSlot voxel_record(const unsigned long long* __restrict__ vkey, const float* __restrict__ vmean,
+                                                const float* __restrict__ vcov, int64_t v) {
+  const int kx = unpack_x(vkey[v]);
+  VoxSlot r;
+  r.w0 = make_float4(__int_as_float(int(v)), vcov[6 * v + 5], __int_as_float(kx), vcov[6 * v + 5]);
+  r.w1 = make_float4(vmean[3 * v], vmean[3 * v + 1], vmean[3 * v + 2], vcov[6 * v + 0]);
+  r.w2 = make_float4(vcov[6 * v + 1], vcov[6 * v + 2], vcov[6 * v + 3], vcov[6 * v + 4]);
+  return r;
+}
+
+// One thread per block: the records of its voxels (sorted positions start[b] .. start[b+1]-1,
+// at most 8) into its cells.
+__global__ void k_block_scatter(const uint32_t* __restrict__ start, const uint32_t* __restrict__ idx_sorted, int64_t nblk,
+                                const unsigned long long* __restrict__ vkey, const float* __restrict__ vmean,
+                                const float* __restrict__ vcov, VoxSlot* __restrict__ cells) {
+  const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b >= nblk) return;
+  for (uint32_t j = start[b]; j < start[b + 1]; ++j) {
+    const int64_t v = idx_sorted[j];
+    const unsigned long long k = vkey[v];
+    cells[b * GLIM_BLOCK_CELLS + block_local(unpack_x(k), unpack_y(k), unpack_z(k))] = voxel_record(vkey, vmean, vcov, v);
+  }
 }
 
 // Merge of two canonical voxel sets: entries [0, m_old) are the existing voxels, [m_old, ...)
@@ -142,12 +168,7 @@ __global__ void k_dense_build(const unsigned long long* __restrict__ vkey, const
   if (v >= m) return;
   const unsigned long long key = vkey[v];
   const int kx = unpack_x(key), ky = unpack_y(key), kz = unpack_z(key);
-  VoxSlot r;
-  // {id, C~22, kx, C~22}: C~22 at .w as in a hash slot, and next to the id for one 8-byte read
-  r.w0 = make_float4(__int_as_float(int(v)), vcov[6 * v + 5], __int_as_float(kx), vcov[6 * v + 5]);
-  r.w1 = make_float4(vmean[3 * v], vmean[3 * v + 1], vmean[3 * v + 2], vcov[6 * v + 0]);
-  r.w2 = make_float4(vcov[6 * v + 1], vcov[6 * v + 2], vcov[6 * v + 3], vcov[6 * v + 4]);
-  cells[(int64_t(kx - ox) * ny + (ky - oy)) * nz + (kz - oz)] = r;
+  cells[(int64_t(kx - ox) * ny + (ky - oy)) * nz + (kz - oz)] = voxel_record(vkey, vmean, vcov, v);
 }
 
 __global__ void k_export(const unsigned long long* __restrict__ vkey, const float* __restrict__ vmean,
@@ -271,18 +292,16 @@ void free_on(T* p, cudaStream_t s) {
 }
 
 void free_level(glim_vmap* vm, int l) {
-  cudaFree(vm->grid[l]);
   cudaFree(vm->slots_alloc[l]);
-  cudaFree(vm->slot_id[l]);
+  cudaFree(vm->btab[l]);
   cudaFree(vm->vkey[l]);
   cudaFree(vm->vmean[l]);
   cudaFree(vm->vcov[l]);
   cudaFree(vm->vcount[l]);
   cudaFree(vm->vsum[l]);
-  vm->grid[l] = nullptr;
   vm->slots[l] = nullptr;
   vm->slots_alloc[l] = nullptr;
-  vm->slot_id[l] = nullptr;
+  vm->btab[l] = nullptr;
   vm->vkey[l] = nullptr;
   vm->vmean[l] = nullptr;
   vm->vcov[l] = nullptr;
@@ -308,8 +327,8 @@ void move_level(glim_vmap* dst, glim_vmap* src, int l) {
   }
   dst->slots[l] = src->slots[l];
   dst->slots_alloc[l] = src->slots_alloc[l];
-  dst->slot_id[l] = src->slot_id[l];
-  dst->grid[l] = src->grid[l];
+  dst->btab[l] = src->btab[l];
+  dst->nblk[l] = src->nblk[l];
   dst->vkey[l] = src->vkey[l];
   dst->vmean[l] = src->vmean[l];
   dst->vcov[l] = src->vcov[l];
@@ -317,8 +336,7 @@ void move_level(glim_vmap* dst, glim_vmap* src, int l) {
   dst->vsum[l] = src->vsum[l];
   src->slots[l] = nullptr;
   src->slots_alloc[l] = nullptr;
-  src->slot_id[l] = nullptr;
-  src->grid[l] = nullptr;
+  src->btab[l] = nullptr;
   src->vkey[l] = nullptr;
   src->vmean[l] = nullptr;
   src->vcov[l] = nullptr;
@@ -404,12 +422,11 @@ void adopt_canon(glim_vmap* vm, int l, Canon& c) {
 glim_status build_tables(glim_ctx* ctx, glim_vmap* vm, int l, int layout) {
   // the level belongs to a map under construction: only this stream has used its tables
   free_on(vm->slots_alloc[l], ctx->stream);
-  free_on(vm->slot_id[l], ctx->stream);
-  free_on(vm->grid[l], ctx->stream);
+  free_on(vm->btab[l], ctx->stream);
   vm->slots[l] = nullptr;
   vm->slots_alloc[l] = nullptr;
-  vm->slot_id[l] = nullptr;
-  vm->grid[l] = nullptr;
+  vm->btab[l] = nullptr;
+  vm->nblk[l] = 0;
   vm->dense[l] = 0;
   const int64_t m = vm->n_vox[l];
   // dense grid over the key bounding box when it is small enough (or requested)
@@ -452,30 +469,59 @@ glim_status build_tables(glim_ctx* ctx, glim_vmap* vm, int l, int layout) {
     GLIM_LAUNCHED(ctx);
     return take_device_status(ctx, "voxel statistics / dense grid");
   }
-  const int64_t cap = std::max<int64_t>(16, int64_t(1) << log2_ceil(4 * m));  // load <= 1/4
+  // voxel blocks: the voxels' block keys sorted (stable, so a block's voxels stay in id order)
+  // and segmented; a block's index is its rank
+  int64_t nblk = 0;
+  SortedCells blk;
+  {
+    DevBuf<unsigned long long> bkey;
+    DevBuf<uint32_t> bidx;
+    GLIM_CUDA(ctx, bkey.alloc(std::max<int64_t>(m, 1), ctx->stream));
+    GLIM_CUDA(ctx, bidx.alloc(std::max<int64_t>(m, 1), ctx->stream));
+    GLIM_CUDA(ctx, blk.key_sorted.alloc(std::max<int64_t>(m, 1), ctx->stream));
+    GLIM_CUDA(ctx, blk.idx_sorted.alloc(std::max<int64_t>(m, 1), ctx->stream));
+    if (m > 0) {
+      k_block_keys<<<ceil_div_i(m, 256), 256, 0, ctx->stream>>>(vm->vkey[l], m, bkey.p, bidx.p);
+      GLIM_LAUNCHED(ctx);
+      unsigned long long varying = 0;
+      glim_status st = key_varying_bits(ctx, bkey.p, m, &varying);
+      if (st != GLIM_OK) return st;
+      st = radix_sort_pairs(ctx, bkey.p, bidx.p, blk.key_sorted.p, blk.idx_sorted.p, m, varying);
+      if (st != GLIM_OK) return st;
+      st = segment_sorted(ctx, blk.key_sorted.p, m, blk);
+      if (st != GLIM_OK) return st;
+      nblk = blk.m;
+    }
+  }
+  const int64_t cap = std::max<int64_t>(16, int64_t(1) << log2_ceil(4 * nblk));  // load <= 1/4
   vm->cap[l] = cap;
   vm->log2cap[l] = log2_ceil(cap);
-  GLIM_CUDA(ctx, dmalloc_async(&vm->slots_alloc[l], cap * sizeof(VoxSlot), ctx->stream));
-  vm->slots[l] = vm->slots_alloc[l];
-  GLIM_CUDA(ctx, dmalloc_async(&vm->slot_id[l], cap * sizeof(int32_t), ctx->stream));
-  GLIM_CUDA(ctx, cudaMemsetAsync(vm->slots[l], 0x80, cap * sizeof(VoxSlot), ctx->stream));
-  GLIM_CUDA(ctx, cudaMemsetAsync(vm->slot_id[l], 0xFF, cap * sizeof(int32_t), ctx->stream));
+  vm->nblk[l] = nblk;
+  GLIM_CUDA(ctx, dmalloc_async(&vm->btab[l], cap * sizeof(int4), ctx->stream));
+  GLIM_CUDA(ctx, cudaMemsetAsync(vm->btab[l], 0x80, cap * sizeof(int4), ctx->stream));
+  // cell records: one empty record before cell 0, then 8 cells per block
+  const int64_t nbcell = nblk * GLIM_BLOCK_CELLS;
+  GLIM_CUDA(ctx, dmalloc_async(&vm->slots_alloc[l], (nbcell + 1) * sizeof(VoxSlot), ctx->stream));
+  GLIM_CUDA(ctx, cudaMemsetAsync(vm->slots_alloc[l], 0x80, (nbcell + 1) * sizeof(VoxSlot), ctx->stream));
+  vm->slots[l] = vm->slots_alloc[l] + 1;
   if (m == 0) {
-    vm->max_probe[l] = 0;
+    vm->max_probe[l] = 1;
     return GLIM_OK;
   }
   DevBuf<int> maxp;
   GLIM_CUDA(ctx, maxp.alloc(1, ctx->stream));
   GLIM_CUDA(ctx, cudaMemsetAsync(maxp.p, 0, sizeof(int), ctx->stream));
-  k_hash_insert<<<ceil_div_i(m, 256), 256, 0, ctx->stream>>>(vm->vkey[l], vm->vmean[l], vm->vcov[l], vm->vcount[l],
-                                                             m, vm->slots[l], vm->slot_id[l], vm->log2cap[l],
-                                                             uint32_t(cap - 1), maxp.p, ctx->d_status);
+  k_block_table<<<ceil_div_i(nblk, 256), 256, 0, ctx->stream>>>(blk.cell_key.p, nblk, vm->btab[l], vm->log2cap[l],
+                                                                uint32_t(cap - 1), maxp.p, ctx->d_status);
+  GLIM_LAUNCHED(ctx);
+  k_block_scatter<<<ceil_div_i(nblk, 256), 256, 0, ctx->stream>>>(blk.cell_start.p, blk.idx_sorted.p, nblk, vm->vkey[l],
+                                                                  vm->vmean[l], vm->vcov[l], vm->slots[l]);
   GLIM_LAUNCHED(ctx);
   int mp = 0;
   GLIM_CUDA(ctx, cudaMemcpyAsync(&mp, maxp.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   vm->max_probe[l] = mp;
-  return take_device_status(ctx, "voxel statistics / hash insert");
+  return take_device_status(ctx, "voxel statistics / block table");
 }
 
 glim_status build_level(glim_ctx* ctx, const float* pts4, const float* cov6, int64_t n, glim_vmap* vm, int l,
@@ -648,7 +694,7 @@ extern "C" glim_status glim_vmap_info(const glim_vmap* vm, int32_t level, int64_
                                       int32_t* max_probe) {
   if (!vm || level < 0 || level >= vm->levels) return GLIM_EINVAL;
   if (n_voxels) *n_voxels = vm->n_vox[level];
-  if (capacity) *capacity = vm->cap[level];
+  if (capacity) *capacity = vm->dense[level] ? vm->cap[level] : vm->nblk[level] * GLIM_BLOCK_CELLS;
   if (max_probe) *max_probe = vm->max_probe[level];
   return GLIM_OK;
 }
