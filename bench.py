@@ -759,6 +759,9 @@ def run_ours(args):
                    "generation_s": round(gen_s, 1)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak,
+                     "achieved_full": achieved_full, "frac_full": achieved_full / hbm_peak,
+                     "frac_full_note": "the full algorithmic count: 40 B per (pair, point) + 56 B per distinct "
+                                       "(pair, level, voxel) hit + 1264 B of output per pair",
                      "traffic": None if u_bpp is None else u_bpp * n_pp,
                      "traffic_note": "ncu dram bytes per (pair, point) of a 40-submap capture of this kernel version, "
                                      "scaled by the launch's (pair, point) units (%s)" % u_src,

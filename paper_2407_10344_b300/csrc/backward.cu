@@ -11,13 +11,15 @@
 // The Omega terms follow from dE/dS = -w y y^T and dS/domega_s,a = R (e_a x C - C e_a x) R^T,
 // dS/domega_t,a = -(e_a x) S' + S' (e_a x) with S' = R C R^T.
 //
-// Work decomposition: an item is a tile of BWD_TILE points of one source frame; a persistent
-// kernel takes items from an atomic queue and walks every pair of that source in pair order.
-// Per pair, the points' contributions to the 9 pose sums (g: 6, the Omega term: 3) are
-// block-reduced into the (item, pair) slot, while each point keeps its dE/dmu and dE/dw summed
-// over the pairs in registers and writes them once.  Then fixed-order FP64 sums per pair and
-// per frame.  No float atomics, so the gradient repeats bit for bit; no per-(pair, point)
-// scratch.
+// Work decomposition: an item is a tile of BWD_TILE points of one source frame and a group of
+// that frame's pairs (all of them, unless the batch has too few tiles to fill the GPU: then a
+// frame's pairs are split into up to `groups` contiguous groups); a persistent kernel takes
+// items from an atomic queue and walks the pairs of its group in pair order.  Per pair, the
+// points' contributions to the 9 pose sums (g: 6, the Omega term: 3) are block-reduced into
+// the (item, pair) slot, while each point keeps its dE/dmu and dE/dw summed over the group's
+// pairs in registers and writes them once (directly, or into its group's slot, summed over the
+// groups in order afterwards).  Then fixed-order FP64 sums per pair and per frame.  No float
+// atomics, so the gradient repeats bit for bit; no per-(pair, point) scratch.
 #include <algorithm>
 #include <cstring>
 
@@ -31,21 +33,22 @@ constexpr int BWD_TILE = BWD_BLOCK * BWD_PPT;
 constexpr int BSTRIDE = 9;  // doubles per partial slot: g (6), Omega term (3)
 
 struct BwdArgs {
-  const int2* items;
+  const int4* items;
+  const int32_t* item_grp;
+  const int64_t* item_slot;
   int32_t nitems;
   int* head;
   const PairDev* pairs;
   const FrameDev* frames;
   const MapDev* maps;
   const PoseF* pose;
-  const int32_t* frame_item_begin;
-  const int32_t* src_begin;
   const int32_t* src_list;
   const int64_t* frame_off;
-  const int64_t* slot_base;
+  int64_t ntot;
   int32_t validate;
   int32_t full;
   double* part;
+  float4* pp;  // groups > 1: per-point slots of the groups; else null
   float* dmu;
   float* dw;
 };
@@ -120,11 +123,11 @@ __device__ __forceinline__ void point_gradient(const PairView& V, int64_t k, int
 }
 
 __device__ __forceinline__ void backward_item(const BwdArgs& a, int g, PairView& V, float (&s_red)[BWD_BLOCK / 32][9]) {
-  const int2 it = a.items[g];
+  const int4 it = a.items[g];
   const int f = it.x;
   const int64_t start = it.y;
-  const int pb = a.src_begin[f], npf = a.src_begin[f + 1] - pb;
-  const int64_t slot0 = a.slot_base[f] + int64_t(g - a.frame_item_begin[f]) * npf;
+  const int pb = it.z, npf = it.w;
+  const int64_t slot0 = a.item_slot[g];
   const int64_t n = a.frames[f].n;
   const int64_t end = min(start + int64_t(BWD_TILE), n);
   float4 pacc[BWD_PPT];
@@ -173,7 +176,9 @@ __device__ __forceinline__ void backward_item(const BwdArgs& a, int g, PairView&
 #pragma unroll
   for (int r = 0; r < BWD_PPT; ++r) {
     const int64_t k = start + int64_t(r) * BWD_BLOCK + threadIdx.x;
-    if (k < end) {
+    if (k < end && a.pp) {
+      a.pp[int64_t(a.item_grp[g]) * a.ntot + base + k] = pacc[r];
+    } else if (k < end) {
       if (a.dmu) {
         a.dmu[3 * (base + k)] = pacc[r].x;
         a.dmu[3 * (base + k) + 1] = pacc[r].y;
@@ -201,19 +206,17 @@ __global__ void __launch_bounds__(BWD_BLOCK) k_backward_items(const BwdArgs a) {
 }
 
 // per pair: dxi_pair (12) = 2 Lift^T g + [a; 0; -R a; 0], g and a summed over the items of
-// the pair's source frame in item order
-__global__ void k_backward_pairs(const double* __restrict__ part, const PairDev* __restrict__ pairs,
-                                 const int32_t* __restrict__ pair_pos, const int32_t* __restrict__ src_begin,
-                                 const int32_t* __restrict__ frame_item_begin, const int64_t* __restrict__ slot_base,
-                                 const double* __restrict__ pose64, int npairs, double* __restrict__ pair_grad) {
+// the pair's group in item order
+__global__ void k_backward_pairs(const double* __restrict__ part, const int64_t* __restrict__ item_slot,
+                                 const int32_t* __restrict__ pair_item0, const int32_t* __restrict__ pair_nitems,
+                                 const int32_t* __restrict__ pair_jj, const double* __restrict__ pose64, int npairs,
+                                 double* __restrict__ pair_grad) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npairs) return;
-  const int f = pairs[p].src;
-  const int npf = src_begin[f + 1] - src_begin[f], j = pair_pos[p];
-  const int nit = frame_item_begin[f + 1] - frame_item_begin[f];
+  const int i0 = pair_item0[p], ni = pair_nitems[p], jj = pair_jj[p];
   double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for (int i = 0; i < nit; ++i) {
-    const double* sl = part + (slot_base[f] + int64_t(i) * npf + j) * BSTRIDE;
+  for (int i = i0; i < i0 + ni; ++i) {
+    const double* sl = part + (item_slot[i] + jj) * BSTRIDE;
     for (int c = 0; c < 9; ++c) s[c] += sl[c];
   }
   const double* P = pose64 + 12 * int64_t(p);
@@ -248,72 +251,137 @@ __global__ void k_backward_frames(const double* __restrict__ pair_grad, const Pa
   for (int c = 0; c < 6; ++c) dxi[6 * int64_t(f) + c] = s[c];
 }
 
+// groups > 1: per point, the sum of its frame's group slots in group order.
+__global__ void k_backward_points(const float4* __restrict__ pp, const int64_t* __restrict__ frame_off,
+                                  const int32_t* __restrict__ frame_groups, int nframes, int64_t ntot,
+                                  float* __restrict__ dmu, float* __restrict__ dw) {
+  const int64_t gi = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gi >= ntot) return;
+  int lo = 0, hi = nframes - 1;  // the frame of point gi
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (frame_off[mid] <= gi) lo = mid;
+    else hi = mid - 1;
+  }
+  float4 t = pp[gi];
+  for (int g = 1; g < frame_groups[lo]; ++g) {
+    const float4 v = pp[int64_t(g) * ntot + gi];
+    t.x += v.x;
+    t.y += v.y;
+    t.z += v.z;
+    t.w += v.w;
+  }
+  if (dmu) {
+    dmu[3 * gi] = t.x;
+    dmu[3 * gi + 1] = t.y;
+    dmu[3 * gi + 2] = t.z;
+  }
+  if (dw) dw[gi] = t.w;
+}
+
 // Host tables of a batch, uploaded into freshly allocated scratch (synchronous copies).
 glim_status bwd_prepare(glim_plan* p, BwdScratch& sc) {
   glim_ctx* ctx = p->ctx;
   const int npairs = p->npairs, nframes = p->nframes;
-  std::vector<int32_t> src_begin(nframes + 1, 0), src_list, pair_pos(std::max(npairs, 1), 0),
-      tgt(std::max(npairs, 1), 0);
+  std::vector<int32_t> src_begin(nframes + 1, 0), src_list, pos(std::max(npairs, 1), 0), tgt(std::max(npairs, 1), 0);
   for (int f = 0; f < nframes; ++f) {
     src_begin[f] = int32_t(src_list.size());
     for (int q = 0; q < npairs; ++q)
       if (p->pairs[q].src_frame == f) {
-        pair_pos[q] = int32_t(src_list.size()) - src_begin[f];
+        pos[q] = int32_t(src_list.size()) - src_begin[f];
         src_list.push_back(q);
       }
   }
   src_begin[nframes] = int32_t(src_list.size());
   for (int q = 0; q < npairs; ++q) tgt[q] = p->pairs[q].tgt_frame;
-  std::vector<int64_t> frame_off(nframes + 1, 0), slot_base(std::max(nframes, 1), 0);
-  std::vector<int2> items;
-  std::vector<int32_t> frame_item_begin(nframes + 1, 0);
-  int64_t nslots = 0;
+  // groups: enough items (tiles x groups) to fill the GPU about eight times over
+  std::vector<int64_t> frame_off(nframes + 1, 0), ntiles(std::max(nframes, 1), 0);
+  int64_t base_work = 0;
+  int max_npf = 1;
   for (int f = 0; f < nframes; ++f) {
     const int64_t n = p->frames[f].n;
     frame_off[f + 1] = frame_off[f] + n;
-    frame_item_begin[f] = int32_t(items.size());
-    slot_base[f] = nslots;
-    for (int64_t s0 = 0; s0 < n; s0 += BWD_TILE) items.push_back(make_int2(f, int32_t(s0)));
-    nslots += int64_t(items.size() - frame_item_begin[f]) * (src_begin[f + 1] - src_begin[f]);
+    ntiles[f] = (n + BWD_TILE - 1) / BWD_TILE;
+    const int npf = src_begin[f + 1] - src_begin[f];
+    if (npf > 0) base_work += ntiles[f];
+    max_npf = std::max(max_npf, npf);
   }
-  frame_item_begin[nframes] = int32_t(items.size());
+  const int64_t target = 8 * int64_t(ctx->num_sms);
+  const int G = int(std::max<int64_t>(1, std::min<int64_t>(max_npf, base_work > 0 ? (target + base_work - 1) / base_work : 1)));
+  std::vector<int4> items;
+  std::vector<int32_t> item_grp, frame_groups(std::max(nframes, 1), 1);
+  std::vector<int64_t> item_slot;
+  std::vector<int32_t> pair_item0(std::max(npairs, 1), 0), pair_nitems(std::max(npairs, 1), 0),
+      pair_jj(std::max(npairs, 1), 0);
+  int64_t nslots = 0;
+  for (int f = 0; f < nframes; ++f) {
+    const int npf = src_begin[f + 1] - src_begin[f];
+    const int Gf = std::max(1, std::min(G, npf));
+    frame_groups[f] = Gf;
+    for (int g = 0; g < Gf; ++g) {
+      const int jb = int(int64_t(g) * npf / Gf), je = int(int64_t(g + 1) * npf / Gf);
+      const int32_t it0 = int32_t(items.size());
+      for (int64_t t = 0; t < ntiles[f]; ++t) {
+        items.push_back(make_int4(f, int32_t(t * BWD_TILE), src_begin[f] + jb, je - jb));
+        item_grp.push_back(g);
+        item_slot.push_back(nslots);
+        nslots += je - jb;
+      }
+      for (int j = jb; j < je; ++j) {
+        const int q = src_list[src_begin[f] + j];
+        pair_item0[q] = it0;
+        pair_nitems[q] = int32_t(ntiles[f]);
+        pair_jj[q] = j - jb;
+      }
+    }
+  }
+  (void)pos;
   if (src_list.empty()) src_list.push_back(0);
-  if (items.empty()) items.push_back(make_int2(0, 0));
-  sc.nitems = frame_item_begin[nframes];
+  sc.nitems = int(items.size());
+  if (items.empty()) {
+    items.push_back(make_int4(0, 0, 0, 0));
+    item_grp.push_back(0);
+    item_slot.push_back(0);
+  }
   sc.ntot = frame_off[nframes];
   sc.nslots = nslots;
+  sc.groups = G;
   int per_sm = 1;
   GLIM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_items, BWD_BLOCK, 0));
   sc.grid = std::max(1, std::min(std::max(per_sm, 1) * ctx->num_sms, std::max(sc.nitems, 1)));
-  if (dmalloc(&sc.items, items.size() * sizeof(int2)) != cudaSuccess ||
-      dmalloc(&sc.frame_item_begin, frame_item_begin.size() * sizeof(int32_t)) != cudaSuccess ||
+  const size_t npp = G > 1 ? size_t(G) * size_t(std::max<int64_t>(sc.ntot, 1)) : 0;
+  if (dmalloc(&sc.items, items.size() * sizeof(int4)) != cudaSuccess ||
+      dmalloc(&sc.item_grp, item_grp.size() * sizeof(int32_t)) != cudaSuccess ||
+      dmalloc(&sc.item_slot, item_slot.size() * sizeof(int64_t)) != cudaSuccess ||
       dmalloc(&sc.src_begin, src_begin.size() * sizeof(int32_t)) != cudaSuccess ||
       dmalloc(&sc.src_list, src_list.size() * sizeof(int32_t)) != cudaSuccess ||
-      dmalloc(&sc.pair_pos, pair_pos.size() * sizeof(int32_t)) != cudaSuccess ||
+      dmalloc(&sc.pair_item0, pair_item0.size() * sizeof(int32_t)) != cudaSuccess ||
+      dmalloc(&sc.pair_nitems, pair_nitems.size() * sizeof(int32_t)) != cudaSuccess ||
+      dmalloc(&sc.pair_jj, pair_jj.size() * sizeof(int32_t)) != cudaSuccess ||
       dmalloc(&sc.tgt, tgt.size() * sizeof(int32_t)) != cudaSuccess ||
       dmalloc(&sc.frame_off, frame_off.size() * sizeof(int64_t)) != cudaSuccess ||
-      dmalloc(&sc.slot_base, slot_base.size() * sizeof(int64_t)) != cudaSuccess ||
+      dmalloc(&sc.frame_groups, frame_groups.size() * sizeof(int32_t)) != cudaSuccess ||
+      (npp > 0 && dmalloc(&sc.pp, npp * sizeof(float4)) != cudaSuccess) ||
       dmalloc(&sc.part, size_t(std::max<int64_t>(nslots, 1)) * BSTRIDE * sizeof(double)) != cudaSuccess ||
       dmalloc(&sc.pair_grad, size_t(std::max(npairs, 1)) * 12 * sizeof(double)) != cudaSuccess ||
       dmalloc(&sc.head, sizeof(int)) != cudaSuccess) {
     sc.release();
     return set_error(ctx, GLIM_ENOMEM, "backward: scratch allocation failed");
   }
-  cudaError_t e = cudaMemcpy(sc.items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(sc.frame_item_begin, frame_item_begin.data(), frame_item_begin.size() * sizeof(int32_t),
-                   cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(sc.src_begin, src_begin.data(), src_begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(sc.src_list, src_list.data(), src_list.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(sc.pair_pos, pair_pos.data(), pair_pos.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(sc.tgt, tgt.data(), tgt.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(sc.frame_off, frame_off.data(), frame_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(sc.slot_base, slot_base.data(), slot_base.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMemcpy(sc.items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  up(sc.item_grp, item_grp.data(), item_grp.size() * sizeof(int32_t));
+  up(sc.item_slot, item_slot.data(), item_slot.size() * sizeof(int64_t));
+  up(sc.src_begin, src_begin.data(), src_begin.size() * sizeof(int32_t));
+  up(sc.src_list, src_list.data(), src_list.size() * sizeof(int32_t));
+  up(sc.pair_item0, pair_item0.data(), pair_item0.size() * sizeof(int32_t));
+  up(sc.pair_nitems, pair_nitems.data(), pair_nitems.size() * sizeof(int32_t));
+  up(sc.pair_jj, pair_jj.data(), pair_jj.size() * sizeof(int32_t));
+  up(sc.tgt, tgt.data(), tgt.size() * sizeof(int32_t));
+  up(sc.frame_off, frame_off.data(), frame_off.size() * sizeof(int64_t));
+  up(sc.frame_groups, frame_groups.data(), frame_groups.size() * sizeof(int32_t));
   if (e != cudaSuccess) {
     sc.release();
     return cuda_check(ctx, e, "backward: table upload");
@@ -329,30 +397,36 @@ glim_status bwd_run(glim_plan* p, const BwdScratch& sc, int32_t omega_grad_full,
   if (sc.nitems > 0) {
     BwdArgs a;
     a.items = sc.items;
+    a.item_grp = sc.item_grp;
+    a.item_slot = sc.item_slot;
     a.nitems = sc.nitems;
     a.head = sc.head;
     a.pairs = p->d_pairs;
     a.frames = p->d_frames;
     a.maps = p->d_maps;
     a.pose = p->in_pose32();
-    a.frame_item_begin = sc.frame_item_begin;
-    a.src_begin = sc.src_begin;
     a.src_list = sc.src_list;
     a.frame_off = sc.frame_off;
-    a.slot_base = sc.slot_base;
+    a.ntot = sc.ntot;
     a.validate = validate_surface;
     a.full = omega_grad_full;
     a.part = sc.part;
+    a.pp = sc.groups > 1 ? sc.pp : nullptr;
     a.dmu = dmu_out;
     a.dw = dw_out;
     GLIM_CUDA(ctx, cudaMemsetAsync(sc.head, 0, sizeof(int), ctx->stream));
     k_backward_items<<<sc.grid, BWD_BLOCK, 0, ctx->stream>>>(a);
     GLIM_LAUNCHED(ctx);
   }
+  if (sc.groups > 1 && sc.ntot > 0 && (dmu_out || dw_out)) {
+    k_backward_points<<<ceil_div_i(sc.ntot, 256), 256, 0, ctx->stream>>>(sc.pp, sc.frame_off, sc.frame_groups, nframes,
+                                                                         sc.ntot, dmu_out, dw_out);
+    GLIM_LAUNCHED(ctx);
+  }
   if (npairs > 0) {
-    k_backward_pairs<<<ceil_div_i(npairs, 64), 64, 0, ctx->stream>>>(sc.part, p->d_pairs, sc.pair_pos, sc.src_begin,
-                                                                     sc.frame_item_begin, sc.slot_base, p->in_pose64(),
-                                                                     npairs, sc.pair_grad);
+    k_backward_pairs<<<ceil_div_i(npairs, 64), 64, 0, ctx->stream>>>(sc.part, sc.item_slot, sc.pair_item0,
+                                                                     sc.pair_nitems, sc.pair_jj, p->in_pose64(), npairs,
+                                                                     sc.pair_grad);
     GLIM_LAUNCHED(ctx);
   }
   if (nframes > 0) {

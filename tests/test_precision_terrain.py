@@ -22,7 +22,7 @@ TOL = 1e-4
 
 def test_terrain_precision_all_accumulation_modes():
     import paper_2407_10344_b300 as G
-    from gpu_helpers import rel_errors
+    from gpu_helpers import b_rel_plain, rel_errors
     t0 = time.time()
     w = synth.terrain()
     t_gen = time.time() - t0
@@ -56,6 +56,7 @@ def test_terrain_precision_all_accumulation_modes():
     for name, (e, H, b, inl) in res.items():
         ee, eH, eb = rel_errors(e, H, b, ref)
         table[name] = {"e": float(ee[0]), "H": float(eH[0]), "b": float(eb[0]),
+                       "b_plain": float(b_rel_plain(b, ref)[0]),
                        "H_max_elementwise_rel": float(np.abs(H[0] - ref["H"][0]).max() / np.abs(ref["H"][0]).max())}
         assert np.array_equal(inl, ref["inliers"])
         assert ee.max() <= TOL and eH.max() <= TOL and eb.max() <= TOL, (name, table[name])
