@@ -495,16 +495,17 @@ struct LaneFetch {
   int idx;  // IDS: index of the point in its frame, -1 for a masked lane
 };
 
-template <int LMAX, bool HASH, bool IDS>
-__device__ __forceinline__ void lane_fetch(const LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V,
-                                           const float4 m, bool live, int validate, int kk, LaneFetch<LMAX>& F) {
-  if constexpr (IDS) F.idx = live ? kk : -1;
+// The part of a fetch that every layout shares: the covariance reads, the surface test, the
+// FP32 transform and the masking of non-finite points.
+template <class View>
+__device__ __forceinline__ float3 lane_transform(const View& V, const float4 m, bool& live, int validate, int kk,
+                                                 float2& ca, float2& cb, float2& cc) {
   // the covariance is read here rather than a round ahead: it is needed only after the voxel
   // reads are in flight, and the registers it would hold are worth more as occupancy
   const float2* cp = V.cov + 3 * int64_t(kk);
-  F.ca = __ldg(cp);
-  F.cb = __ldg(cp + 1);
-  F.cc = __ldg(cp + 2);
+  ca = __ldg(cp);
+  cb = __ldg(cp + 1);
+  cc = __ldg(cp + 2);
   if (validate && V.nrm) {
     const float* nk = V.nrm + 3 * int64_t(kk);
     const float vv[3] = {V.v.x, V.v.y, V.v.z};
@@ -522,85 +523,124 @@ __device__ __forceinline__ void lane_fetch(const LaneView<typename std::conditio
   q.x = finite_q ? q.x : 0.f;
   q.y = finite_q ? q.y : 0.f;
   q.z = finite_q ? q.z : 0.f;
+  return q;
+}
+
+// Dense grids: per level the key, the cell inside the grid's box and the record reads, the
+// levels interleaved (kept in this form: splitting it into per-stage loops measured 6 %
+// slower); descriptor {cells, ox, oy} {oz, nx, ny, nz}.
+template <int LMAX, bool IDS>
+__device__ __forceinline__ void lane_fetch(const DenseView& V, const float4 m, bool live, int validate, int kk,
+                                           LaneFetch<LMAX>& F) {
+  if constexpr (IDS) F.idx = live ? kk : -1;
+  const float3 q = lane_transform(V, m, live, validate, kk, F.ca, F.cb, F.cc);
   const float4 irq = *reinterpret_cast<const float4*>(V.M.inv_r);  // one 16-byte shared load
   const float irv[4] = {irq.x, irq.y, irq.z, irq.w};
-  if constexpr (!HASH) {
-    // dense: per level the key, the cell inside the grid's box and the record reads, the
-    // levels interleaved (kept in this form: splitting it into per-stage loops measured 6 %
-    // slower); descriptor {cells, ox, oy} {oz, nx, ny, nz}
 #pragma unroll
-    for (int l = 0; l < LMAX; ++l) {
-      const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
-      const uint4 lb = reinterpret_cast<const uint4*>(&V.M.lv[l])[1];
-      const VoxSlot* base =
-          reinterpret_cast<const VoxSlot*>(uint64_t(uint32_t(la.x)) | (uint64_t(uint32_t(la.y)) << 32));
-      // keys floor(q * inv_r) (FP32 product); a key outside [-2^20, 2^20) is in no table
-      const int kx = __float2int_rd(__fmul_rn(q.x, irv[l]));
-      const int ky = __float2int_rd(__fmul_rn(q.y, irv[l]));
-      const int kz = __float2int_rd(__fmul_rn(q.z, irv[l]));
-      const uint32_t x = uint32_t(kx) - uint32_t(la.z), y = uint32_t(ky) - uint32_t(la.w), z = uint32_t(kz) - lb.x;
-      const bool in_box = live && x < lb.y && y < lb.z && z < lb.w;
-      const VoxSlot* sl = base + (in_box ? int((x * lb.z + y) * lb.w + z) : -1);  // -1: the empty record
-      const float2 h2 = __ldg(reinterpret_cast<const float2*>(&sl->w0));
-      F.s0[l] = make_float4(h2.x, h2.y, 0.f, 0.f);
-      F.s1[l] = ldg4(&sl->w1);  // {mean, C~00}
-      F.s2[l] = ldg4(&sl->w2);  // {C~01, C~02, C~11, C~12}
-    }
-  } else {
-    // hashed: the keys of every level, the table entries of every level's block in flight
-    // together (the lanes of a warp mostly share a few blocks), then per level the lanes whose
-    // first entry holds another block continue the probe, bounded by the table's longest
-    // probe sequence, and the records of every level; descriptor {slots, btab}
-    // {mask, log2cap, max_probe, pad}
-    int kx[LMAX], ky[LMAX], kz[LMAX], cell[LMAX];
-    int4 e[LMAX];
-    uint32_t h[LMAX];
-#pragma unroll
-    for (int l = 0; l < LMAX; ++l) {
-      kx[l] = __float2int_rd(__fmul_rn(q.x, irv[l]));
-      ky[l] = __float2int_rd(__fmul_rn(q.y, irv[l]));
-      kz[l] = __float2int_rd(__fmul_rn(q.z, irv[l]));
-      const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
-      const int4 lb = reinterpret_cast<const int4*>(&V.M.lv[l])[1];
-      const int4* btab = reinterpret_cast<const int4*>(uint64_t(uint32_t(la.z)) | (uint64_t(uint32_t(la.w)) << 32));
-      h[l] = hash3(kx[l] >> GLIM_BLOCK_SHIFT, ky[l] >> GLIM_BLOCK_SHIFT, kz[l] >> GLIM_BLOCK_SHIFT, lb.y);
-      e[l] = ldg4i(btab + h[l]);
-    }
-#pragma unroll
-    for (int l = 0; l < LMAX; ++l) {
-      const int bx = kx[l] >> GLIM_BLOCK_SHIFT, by = ky[l] >> GLIM_BLOCK_SHIFT, bz = kz[l] >> GLIM_BLOCK_SHIFT;
-      bool match = e[l].x == bx && e[l].y == by && e[l].z == bz;
-      const bool more = live && !match && e[l].x != GLIM_EMPTY_COORD;
-      if (__any_sync(0xffffffffu, more)) {
-        if (more) {
-          const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
-          const int4 lb = reinterpret_cast<const int4*>(&V.M.lv[l])[1];
-          const int4* btab = reinterpret_cast<const int4*>(uint64_t(uint32_t(la.z)) | (uint64_t(uint32_t(la.w)) << 32));
-          uint32_t hh = h[l];
-          for (int p = 1; p < lb.z; ++p) {
-            hh = (hh + 1u) & uint32_t(lb.x);
-            e[l] = ldg4i(btab + hh);
-            match = e[l].x == bx && e[l].y == by && e[l].z == bz;
-            if (match || e[l].x == GLIM_EMPTY_COORD) break;
-          }
-        }
-      }
-      cell[l] = (live && match) ? e[l].w * GLIM_BLOCK_CELLS + block_local(kx[l], ky[l], kz[l]) : -1;
-    }
-#pragma unroll
-    for (int l = 0; l < LMAX; ++l) {
-      const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
-      const VoxSlot* sl =  // cell -1 is the empty record before cell 0
-          reinterpret_cast<const VoxSlot*>(uint64_t(uint32_t(la.x)) | (uint64_t(uint32_t(la.y)) << 32)) + cell[l];
-      const float2 h2 = __ldg(reinterpret_cast<const float2*>(&sl->w0));
-      F.s0[l] = make_float4(h2.x, h2.y, 0.f, 0.f);
-      F.s1[l] = ldg4(&sl->w1);  // {mean, C~00}
-      F.s2[l] = ldg4(&sl->w2);  // {C~01, C~02, C~11, C~12}
-    }
+  for (int l = 0; l < LMAX; ++l) {
+    const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
+    const uint4 lb = reinterpret_cast<const uint4*>(&V.M.lv[l])[1];
+    const VoxSlot* base =
+        reinterpret_cast<const VoxSlot*>(uint64_t(uint32_t(la.x)) | (uint64_t(uint32_t(la.y)) << 32));
+    // keys floor(q * inv_r) (FP32 product); a key outside [-2^20, 2^20) is in no table
+    const int kx = __float2int_rd(__fmul_rn(q.x, irv[l]));
+    const int ky = __float2int_rd(__fmul_rn(q.y, irv[l]));
+    const int kz = __float2int_rd(__fmul_rn(q.z, irv[l]));
+    const uint32_t x = uint32_t(kx) - uint32_t(la.z), y = uint32_t(ky) - uint32_t(la.w), z = uint32_t(kz) - lb.x;
+    const bool in_box = live && x < lb.y && y < lb.z && z < lb.w;
+    const VoxSlot* sl = base + (in_box ? int((x * lb.z + y) * lb.w + z) : -1);  // -1: the empty record
+    const float2 h2 = __ldg(reinterpret_cast<const float2*>(&sl->w0));
+    F.s0[l] = make_float4(h2.x, h2.y, 0.f, 0.f);
+    F.s1[l] = ldg4(&sl->w1);  // {mean, C~00}
+    F.s2[l] = ldg4(&sl->w2);  // {C~01, C~02, C~11, C~12}
   }
   F.q = q;
   F.w = m.w;
   F.live = live;
+}
+
+// Hashed levels take a lookup in two dependent reads (the block's table entry, then the cell
+// record), so their pipeline has one more stage: a point's table entries are read one round
+// ahead (hash_fetch), and its records at the start of its own round (hash_resolve), where
+// the next point's transform and the current point's R C R^T cover their latency.  What a
+// lane holds between the two stages:
+template <int LMAX>
+struct HashFetch {
+  float3 q;
+  float w;
+  bool live;
+  float2 ca, cb, cc;
+  int kx[LMAX], ky[LMAX], kz[LMAX];
+  int4 e[LMAX];  // the table entry at each level's home slot, {bx, by, bz, block}
+  int idx;       // IDS: index of the point in its frame, -1 for a masked lane
+};
+
+// First stage: transform, the keys of every level and the home-slot table entries of every
+// level's block, all in flight together; descriptor {slots, btab} {mask, log2cap, max_probe, pad}.
+template <int LMAX, bool IDS>
+__device__ __forceinline__ void hash_fetch(const HashView& V, const float4 m, bool live, int validate, int kk,
+                                           HashFetch<LMAX>& H) {
+  if constexpr (IDS) H.idx = live ? kk : -1;
+  const float3 q = lane_transform(V, m, live, validate, kk, H.ca, H.cb, H.cc);
+  const float4 irq = *reinterpret_cast<const float4*>(V.M.inv_r);
+  const float irv[4] = {irq.x, irq.y, irq.z, irq.w};
+#pragma unroll
+  for (int l = 0; l < LMAX; ++l) {
+    H.kx[l] = __float2int_rd(__fmul_rn(q.x, irv[l]));
+    H.ky[l] = __float2int_rd(__fmul_rn(q.y, irv[l]));
+    H.kz[l] = __float2int_rd(__fmul_rn(q.z, irv[l]));
+    const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
+    const int4 lb = reinterpret_cast<const int4*>(&V.M.lv[l])[1];
+    const int4* btab = reinterpret_cast<const int4*>(uint64_t(uint32_t(la.z)) | (uint64_t(uint32_t(la.w)) << 32));
+    H.e[l] = ldg4i(btab + hash3(H.kx[l] >> GLIM_BLOCK_SHIFT, H.ky[l] >> GLIM_BLOCK_SHIFT, H.kz[l] >> GLIM_BLOCK_SHIFT,
+                                lb.y));
+  }
+  H.q = q;
+  H.w = m.w;
+  H.live = live;
+}
+
+// Second stage: per level the lanes whose home entry holds another block continue the probe
+// (a warp-uniform branch skips it when no lane needs it), bounded by the table's longest
+// probe sequence; then the records of every level, read as on a dense grid (cell -1 is the
+// empty record before cell 0).
+template <int LMAX, bool IDS>
+__device__ __forceinline__ void hash_resolve(const HashView& V, HashFetch<LMAX>& H, LaneFetch<LMAX>& F) {
+#pragma unroll
+  for (int l = 0; l < LMAX; ++l) {
+    const int bx = H.kx[l] >> GLIM_BLOCK_SHIFT, by = H.ky[l] >> GLIM_BLOCK_SHIFT, bz = H.kz[l] >> GLIM_BLOCK_SHIFT;
+    int4 e = H.e[l];
+    bool match = e.x == bx && e.y == by && e.z == bz;
+    const bool more = H.live && !match && e.x != GLIM_EMPTY_COORD;
+    const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
+    if (__any_sync(0xffffffffu, more)) {
+      if (more) {
+        const int4 lb = reinterpret_cast<const int4*>(&V.M.lv[l])[1];
+        const int4* btab = reinterpret_cast<const int4*>(uint64_t(uint32_t(la.z)) | (uint64_t(uint32_t(la.w)) << 32));
+        uint32_t hh = hash3(bx, by, bz, lb.y);
+        for (int p = 1; p < lb.z; ++p) {
+          hh = (hh + 1u) & uint32_t(lb.x);
+          e = ldg4i(btab + hh);
+          match = e.x == bx && e.y == by && e.z == bz;
+          if (match || e.x == GLIM_EMPTY_COORD) break;
+        }
+      }
+    }
+    const int cell = (H.live && match) ? e.w * GLIM_BLOCK_CELLS + block_local(H.kx[l], H.ky[l], H.kz[l]) : -1;
+    const VoxSlot* sl =
+        reinterpret_cast<const VoxSlot*>(uint64_t(uint32_t(la.x)) | (uint64_t(uint32_t(la.y)) << 32)) + cell;
+    const float2 h2 = __ldg(reinterpret_cast<const float2*>(&sl->w0));
+    F.s0[l] = make_float4(h2.x, h2.y, 0.f, 0.f);
+    F.s1[l] = ldg4(&sl->w1);  // {mean, C~00}
+    F.s2[l] = ldg4(&sl->w2);  // {C~01, C~02, C~11, C~12}
+  }
+  F.q = H.q;
+  F.w = H.w;
+  F.live = H.live;
+  F.ca = H.ca;
+  F.cb = H.cb;
+  F.cc = H.cc;
+  if constexpr (IDS) F.idx = H.idx;
 }
 
 template <int LMAX, bool HASH, bool IDS, class A>
@@ -748,26 +788,51 @@ __device__ __forceinline__ void process_item_lane(const LinArgs& a, int item,
   const int first = it.start + int(threadIdx.x);
   const int rounds = min(a.ppt, (last - it.start) / BLOCK + 1);
   // A software pipeline over the rounds, unrolled twice so that the two buffers alternate
-  // without copies.  A point's coordinates are read two rounds ahead, its voxel records
-  // (after the block-table lookup of a hashed level) and covariance one round ahead
-  // (lane_fetch), so the reads of the next point are in flight while the lane computes the
-  // current one (lane_compute): 9 % faster on dense grids than reading a point's records at
-  // the start of its own round.
-  LaneFetch<LMAX> fa, fb;
-  lane_fetch<LMAX, HASH, IDS>(V, ldg4(V.pts + min(first, last)), first <= last, a.validate, min(first, last), fa);
-  float4 pn = ldg4(V.pts + min(first + BLOCK, last));
+  // without copies.  Dense grids: a point's coordinates are read two rounds ahead, its voxel
+  // records and covariance one round ahead (lane_fetch), so the reads of the next point are
+  // in flight while the lane computes the current one (lane_compute): 9 % faster than reading
+  // a point's records at the start of its own round.  Hashed levels: the coordinates two
+  // rounds ahead, the covariance and the block-table entries one round ahead (hash_fetch),
+  // the records at the start of the point's own round (hash_resolve).
+  float4 pn;
   int j = 0;
+  if constexpr (!HASH) {
+    LaneFetch<LMAX> fa, fb;
+    lane_fetch<LMAX, IDS>(V, ldg4(V.pts + min(first, last)), first <= last, a.validate, min(first, last), fa);
+    pn = ldg4(V.pts + min(first + BLOCK, last));
 #pragma unroll 1
-  for (; j + 1 < rounds; j += 2) {
-    const int k = first + j * BLOCK;
-    lane_fetch<LMAX, HASH, IDS>(V, pn, k + BLOCK <= last, a.validate, min(k + BLOCK, last), fb);
-    pn = ldg4(V.pts + min(k + 2 * BLOCK, last));
-    lane_compute<LMAX, HASH, IDS>(V, fa, acc, inl, ids, idl);
-    lane_fetch<LMAX, HASH, IDS>(V, pn, k + 2 * BLOCK <= last, a.validate, min(k + 2 * BLOCK, last), fa);
-    pn = ldg4(V.pts + min(k + 3 * BLOCK, last));
-    lane_compute<LMAX, HASH, IDS>(V, fb, acc, inl, ids, idl);
+    for (; j + 1 < rounds; j += 2) {
+      const int k = first + j * BLOCK;
+      lane_fetch<LMAX, IDS>(V, pn, k + BLOCK <= last, a.validate, min(k + BLOCK, last), fb);
+      pn = ldg4(V.pts + min(k + 2 * BLOCK, last));
+      lane_compute<LMAX, HASH, IDS>(V, fa, acc, inl, ids, idl);
+      lane_fetch<LMAX, IDS>(V, pn, k + 2 * BLOCK <= last, a.validate, min(k + 2 * BLOCK, last), fa);
+      pn = ldg4(V.pts + min(k + 3 * BLOCK, last));
+      lane_compute<LMAX, HASH, IDS>(V, fb, acc, inl, ids, idl);
+    }
+    if (j < rounds) lane_compute<LMAX, HASH, IDS>(V, fa, acc, inl, ids, idl);
+  } else {
+    HashFetch<LMAX> ha, hb;
+    LaneFetch<LMAX> f;
+    hash_fetch<LMAX, IDS>(V, ldg4(V.pts + min(first, last)), first <= last, a.validate, min(first, last), ha);
+    pn = ldg4(V.pts + min(first + BLOCK, last));
+#pragma unroll 1
+    for (; j + 1 < rounds; j += 2) {
+      const int k = first + j * BLOCK;
+      hash_resolve<LMAX, IDS>(V, ha, f);
+      hash_fetch<LMAX, IDS>(V, pn, k + BLOCK <= last, a.validate, min(k + BLOCK, last), hb);
+      pn = ldg4(V.pts + min(k + 2 * BLOCK, last));
+      lane_compute<LMAX, HASH, IDS>(V, f, acc, inl, ids, idl);
+      hash_resolve<LMAX, IDS>(V, hb, f);
+      hash_fetch<LMAX, IDS>(V, pn, k + 2 * BLOCK <= last, a.validate, min(k + 2 * BLOCK, last), ha);
+      pn = ldg4(V.pts + min(k + 3 * BLOCK, last));
+      lane_compute<LMAX, HASH, IDS>(V, f, acc, inl, ids, idl);
+    }
+    if (j < rounds) {
+      hash_resolve<LMAX, IDS>(V, ha, f);
+      lane_compute<LMAX, HASH, IDS>(V, f, acc, inl, ids, idl);
+    }
   }
-  if (j < rounds) lane_compute<LMAX, HASH, IDS>(V, fa, acc, inl, ids, idl);
   block_reduce_store<BLOCK, ACC>(acc, inl, a.part + int64_t(item) * PSTRIDE);
 }
 
