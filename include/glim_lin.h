@@ -202,7 +202,7 @@ glim_status glim_build_voxelmap(glim_ctx* ctx, const float* pts4, const float* c
  *   layout 1: dense grid (GLIM_EINVAL if the bounding box exceeds the limit);
  *   layout 2: hashed voxel blocks: blocks of 2 x 2 x 2 voxels whose 8 cells hold the records,
  *            found through an open-addressing table of the block keys (linear probing, load
- *            <= 1/4), as voxel hashing stores voxel blocks.
+ *            <= 1/16), as voxel hashing stores voxel blocks.
  * Both layouts give identical correspondences and results; the dense grid resolves every
  * lookup, hit or miss, with one 48-byte read, the hashed layout with one table-entry read of
  * the block (one per probe) and one 48-byte read. */

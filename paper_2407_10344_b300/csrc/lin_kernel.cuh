@@ -570,7 +570,8 @@ struct HashFetch {
   float w;
   bool live;
   float2 ca, cb, cc;
-  int kx[LMAX], ky[LMAX], kz[LMAX];
+  int kx[LMAX], ky[LMAX], kz[LMAX];  // keys of each level (holding the block keys and the
+                                     // cells inside the blocks instead measured 2 % slower)
   int4 e[LMAX];  // the table entry at each level's home slot, {bx, by, bz, block}
   int idx;       // IDS: index of the point in its frame, -1 for a masked lane
 };
@@ -586,14 +587,16 @@ __device__ __forceinline__ void hash_fetch(const HashView& V, const float4 m, bo
   const float irv[4] = {irq.x, irq.y, irq.z, irq.w};
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
-    H.kx[l] = __float2int_rd(__fmul_rn(q.x, irv[l]));
-    H.ky[l] = __float2int_rd(__fmul_rn(q.y, irv[l]));
-    H.kz[l] = __float2int_rd(__fmul_rn(q.z, irv[l]));
+    const int kx = __float2int_rd(__fmul_rn(q.x, irv[l]));
+    const int ky = __float2int_rd(__fmul_rn(q.y, irv[l]));
+    const int kz = __float2int_rd(__fmul_rn(q.z, irv[l]));
+    H.kx[l] = kx;
+    H.ky[l] = ky;
+    H.kz[l] = kz;
     const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
     const int4 lb = reinterpret_cast<const int4*>(&V.M.lv[l])[1];
     const int4* btab = reinterpret_cast<const int4*>(uint64_t(uint32_t(la.z)) | (uint64_t(uint32_t(la.w)) << 32));
-    H.e[l] = ldg4i(btab + hash3(H.kx[l] >> GLIM_BLOCK_SHIFT, H.ky[l] >> GLIM_BLOCK_SHIFT, H.kz[l] >> GLIM_BLOCK_SHIFT,
-                                lb.y));
+    H.e[l] = ldg4i(btab + hash3(kx >> GLIM_BLOCK_SHIFT, ky >> GLIM_BLOCK_SHIFT, kz >> GLIM_BLOCK_SHIFT, lb.y));
   }
   H.q = q;
   H.w = m.w;

@@ -8,7 +8,7 @@
 //      and stores the averages (canonical id = rank of the key = position in sorted order);
 //   3. the voxel records (48 bytes) are written into a dense grid over their key box when it
 //      is small enough, else into voxel blocks (2 x 2 x 2 cells) found through an
-//      open-addressing table of block keys (linear probing, load <= 1/4): spatial hashing of
+//      open-addressing table of block keys (linear probing, load <= 1/16): spatial hashing of
 //      voxel blocks, as voxel hashing does.
 #include <climits>
 
@@ -493,7 +493,7 @@ glim_status build_tables(glim_ctx* ctx, glim_vmap* vm, int l, int layout) {
       nblk = blk.m;
     }
   }
-  const int64_t cap = std::max<int64_t>(16, int64_t(1) << log2_ceil(4 * nblk));  // load <= 1/4
+  const int64_t cap = std::max<int64_t>(16, int64_t(1) << log2_ceil(16 * nblk));  // load <= 1/16
   vm->cap[l] = cap;
   vm->log2cap[l] = log2_ceil(cap);
   vm->nblk[l] = nblk;
