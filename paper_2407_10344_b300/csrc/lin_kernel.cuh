@@ -559,96 +559,15 @@ __device__ __forceinline__ void lane_fetch(const DenseView& V, const float4 m, b
   F.live = live;
 }
 
-// Hashed levels take a lookup in two dependent reads (the block's table entry, then the cell
-// record), so their pipeline has one more stage: a point's table entries are read one round
-// ahead (hash_fetch), and its records at the start of its own round (hash_resolve), where
-// the next point's transform and the current point's R C R^T cover their latency.  What a
-// lane holds between the two stages:
-template <int LMAX>
-struct HashFetch {
-  float3 q;
-  float w;
-  bool live;
-  float2 ca, cb, cc;
-  int kx[LMAX], ky[LMAX], kz[LMAX];  // keys of each level (holding the block keys and the
-                                     // cells inside the blocks instead measured 2 % slower)
-  int4 e[LMAX];  // the table entry at each level's home slot, {bx, by, bz, block}
-  int idx;       // IDS: index of the point in its frame, -1 for a masked lane
+// A point's sums over its levels (w Omega, w Omega d, e) and u = R mu, between the level
+// arithmetic and the G-form.
+struct LaneSums {
+  float O00, O01, O02, O11, O12, O22, g0, g1, g2, es, ux, uy, uz;
 };
 
-// First stage: transform, the keys of every level and the home-slot table entries of every
-// level's block, all in flight together; descriptor {slots, btab} {mask, log2cap, max_probe, pad}.
-template <int LMAX, bool IDS>
-__device__ __forceinline__ void hash_fetch(const HashView& V, const float4 m, bool live, int validate, int kk,
-                                           HashFetch<LMAX>& H) {
-  if constexpr (IDS) H.idx = live ? kk : -1;
-  const float3 q = lane_transform(V, m, live, validate, kk, H.ca, H.cb, H.cc);
-  const float4 irq = *reinterpret_cast<const float4*>(V.M.inv_r);
-  const float irv[4] = {irq.x, irq.y, irq.z, irq.w};
-#pragma unroll
-  for (int l = 0; l < LMAX; ++l) {
-    const int kx = __float2int_rd(__fmul_rn(q.x, irv[l]));
-    const int ky = __float2int_rd(__fmul_rn(q.y, irv[l]));
-    const int kz = __float2int_rd(__fmul_rn(q.z, irv[l]));
-    H.kx[l] = kx;
-    H.ky[l] = ky;
-    H.kz[l] = kz;
-    const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
-    const int4 lb = reinterpret_cast<const int4*>(&V.M.lv[l])[1];
-    const int4* btab = reinterpret_cast<const int4*>(uint64_t(uint32_t(la.z)) | (uint64_t(uint32_t(la.w)) << 32));
-    H.e[l] = ldg4i(btab + hash3(kx >> GLIM_BLOCK_SHIFT, ky >> GLIM_BLOCK_SHIFT, kz >> GLIM_BLOCK_SHIFT, lb.y));
-  }
-  H.q = q;
-  H.w = m.w;
-  H.live = live;
-}
-
-// Second stage: per level the lanes whose home entry holds another block continue the probe
-// (a warp-uniform branch skips it when no lane needs it), bounded by the table's longest
-// probe sequence; then the records of every level, read as on a dense grid (cell -1 is the
-// empty record before cell 0).
-template <int LMAX, bool IDS>
-__device__ __forceinline__ void hash_resolve(const HashView& V, HashFetch<LMAX>& H, LaneFetch<LMAX>& F) {
-#pragma unroll
-  for (int l = 0; l < LMAX; ++l) {
-    const int bx = H.kx[l] >> GLIM_BLOCK_SHIFT, by = H.ky[l] >> GLIM_BLOCK_SHIFT, bz = H.kz[l] >> GLIM_BLOCK_SHIFT;
-    int4 e = H.e[l];
-    bool match = e.x == bx && e.y == by && e.z == bz;
-    const bool more = H.live && !match && e.x != GLIM_EMPTY_COORD;
-    const int4 la = reinterpret_cast<const int4*>(&V.M.lv[l])[0];
-    if (__any_sync(0xffffffffu, more)) {
-      if (more) {
-        const int4 lb = reinterpret_cast<const int4*>(&V.M.lv[l])[1];
-        const int4* btab = reinterpret_cast<const int4*>(uint64_t(uint32_t(la.z)) | (uint64_t(uint32_t(la.w)) << 32));
-        uint32_t hh = hash3(bx, by, bz, lb.y);
-        for (int p = 1; p < lb.z; ++p) {
-          hh = (hh + 1u) & uint32_t(lb.x);
-          e = ldg4i(btab + hh);
-          match = e.x == bx && e.y == by && e.z == bz;
-          if (match || e.x == GLIM_EMPTY_COORD) break;
-        }
-      }
-    }
-    const int cell = (H.live && match) ? e.w * GLIM_BLOCK_CELLS + block_local(H.kx[l], H.ky[l], H.kz[l]) : -1;
-    const VoxSlot* sl =
-        reinterpret_cast<const VoxSlot*>(uint64_t(uint32_t(la.x)) | (uint64_t(uint32_t(la.y)) << 32)) + cell;
-    const float2 h2 = __ldg(reinterpret_cast<const float2*>(&sl->w0));
-    F.s0[l] = make_float4(h2.x, h2.y, 0.f, 0.f);
-    F.s1[l] = ldg4(&sl->w1);  // {mean, C~00}
-    F.s2[l] = ldg4(&sl->w2);  // {C~01, C~02, C~11, C~12}
-  }
-  F.q = H.q;
-  F.w = H.w;
-  F.live = H.live;
-  F.ca = H.ca;
-  F.cb = H.cb;
-  F.cc = H.cc;
-  if constexpr (IDS) F.idx = H.idx;
-}
-
-template <int LMAX, bool HASH, bool IDS, class A>
-__device__ __forceinline__ void lane_compute(const LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V,
-                                             LaneFetch<LMAX>& F, A& acc, int& inl, int32_t* ids, int idl) {
+template <int LMAX, bool HASH, bool IDS>
+__device__ __forceinline__ void lane_levels(const LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V,
+                                            LaneFetch<LMAX>& F, LaneSums& S, int& inl, int32_t* ids, int idl) {
   const float4 R0 = V.Rt[0], R1 = V.Rt[1], R2 = V.Rt[2];
   const float3 q = F.q;
   const bool live = F.live;
@@ -737,8 +656,27 @@ __device__ __forceinline__ void lane_compute(const LaneView<typename std::condit
         : "r"(ok ? 1u : 0u), "f"(id), "f"(A00), "f"(A01), "f"(A02), "f"(A11), "f"(A12), "f"(A22), "f"(a0), "f"(a1),
           "f"(a2), "f"(el));
   }
-  // the G-form of the sums, G = [-(u)x, I] with u = R mu
-  const float ux = q.x - R0.w, uy = q.y - R1.w, uz = q.z - R2.w;
+  S.O00 = O00;
+  S.O01 = O01;
+  S.O02 = O02;
+  S.O11 = O11;
+  S.O12 = O12;
+  S.O22 = O22;
+  S.g0 = g0;
+  S.g1 = g1;
+  S.g2 = g2;
+  S.es = es;
+  S.ux = q.x - R0.w;
+  S.uy = q.y - R1.w;
+  S.uz = q.z - R2.w;
+}
+
+// The G-form of a point's level sums, G = [-(u)x, I] with u = R mu: 28 accumulator updates.
+template <class A>
+__device__ __forceinline__ void lane_gform(const LaneSums& S, A& acc) {
+  const float O00 = S.O00, O01 = S.O01, O02 = S.O02, O11 = S.O11, O12 = S.O12, O22 = S.O22;
+  const float g0 = S.g0, g1 = S.g1, g2 = S.g2, es = S.es;
+  const float ux = S.ux, uy = S.uy, uz = S.uz;
   const float W00 = -uz * O01 + uy * O02, W01 = -uz * O11 + uy * O12, W02 = -uz * O12 + uy * O22;
   const float W10 = uz * O00 - ux * O02, W11 = uz * O01 - ux * O12, W12 = uz * O02 - ux * O22;
   const float W20 = -uy * O00 + ux * O01, W21 = -uy * O01 + ux * O11, W22 = -uy * O02 + ux * O12;
@@ -758,6 +696,16 @@ __device__ __forceinline__ void lane_compute(const LaneView<typename std::condit
   acc.add(24, g0); acc.add(25, g1); acc.add(26, g2);
   acc.add(27, es);
 }
+
+template <int LMAX, bool HASH, bool IDS, class A>
+__device__ __forceinline__ void lane_compute(const LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>& V,
+                                             LaneFetch<LMAX>& F, A& acc, int& inl, int32_t* ids, int idl) {
+  LaneSums S;
+  lane_levels<LMAX, HASH, IDS>(V, F, S, inl, ids, idl);
+  lane_gform(S, acc);
+}
+
+#include "lane_hash.cuh"
 
 template <int BLOCK, int ACC, int LMAX, bool HASH, bool IDS>
 __device__ __forceinline__ void process_item_lane(const LinArgs& a, int item,
@@ -794,15 +742,12 @@ __device__ __forceinline__ void process_item_lane(const LinArgs& a, int item,
   // without copies.  Dense grids: a point's coordinates are read two rounds ahead, its voxel
   // records and covariance one round ahead (lane_fetch), so the reads of the next point are
   // in flight while the lane computes the current one (lane_compute): 9 % faster than reading
-  // a point's records at the start of its own round.  Hashed levels: the coordinates two
-  // rounds ahead, the covariance and the block-table entries one round ahead (hash_fetch),
-  // the records at the start of the point's own round (hash_resolve).
-  float4 pn;
-  int j = 0;
+  // a point's records at the start of its own round.  Hashed levels: hash_rounds.
   if constexpr (!HASH) {
     LaneFetch<LMAX> fa, fb;
     lane_fetch<LMAX, IDS>(V, ldg4(V.pts + min(first, last)), first <= last, a.validate, min(first, last), fa);
-    pn = ldg4(V.pts + min(first + BLOCK, last));
+    float4 pn = ldg4(V.pts + min(first + BLOCK, last));
+    int j = 0;
 #pragma unroll 1
     for (; j + 1 < rounds; j += 2) {
       const int k = first + j * BLOCK;
@@ -815,26 +760,7 @@ __device__ __forceinline__ void process_item_lane(const LinArgs& a, int item,
     }
     if (j < rounds) lane_compute<LMAX, HASH, IDS>(V, fa, acc, inl, ids, idl);
   } else {
-    HashFetch<LMAX> ha, hb;
-    LaneFetch<LMAX> f;
-    hash_fetch<LMAX, IDS>(V, ldg4(V.pts + min(first, last)), first <= last, a.validate, min(first, last), ha);
-    pn = ldg4(V.pts + min(first + BLOCK, last));
-#pragma unroll 1
-    for (; j + 1 < rounds; j += 2) {
-      const int k = first + j * BLOCK;
-      hash_resolve<LMAX, IDS>(V, ha, f);
-      hash_fetch<LMAX, IDS>(V, pn, k + BLOCK <= last, a.validate, min(k + BLOCK, last), hb);
-      pn = ldg4(V.pts + min(k + 2 * BLOCK, last));
-      lane_compute<LMAX, HASH, IDS>(V, f, acc, inl, ids, idl);
-      hash_resolve<LMAX, IDS>(V, hb, f);
-      hash_fetch<LMAX, IDS>(V, pn, k + 2 * BLOCK <= last, a.validate, min(k + 2 * BLOCK, last), ha);
-      pn = ldg4(V.pts + min(k + 3 * BLOCK, last));
-      lane_compute<LMAX, HASH, IDS>(V, f, acc, inl, ids, idl);
-    }
-    if (j < rounds) {
-      hash_resolve<LMAX, IDS>(V, ha, f);
-      lane_compute<LMAX, HASH, IDS>(V, f, acc, inl, ids, idl);
-    }
+    hash_rounds<BLOCK, LMAX, IDS>(V, a.validate, first, last, rounds, acc, inl, ids, idl);
   }
   block_reduce_store<BLOCK, ACC>(acc, inl, a.part + int64_t(item) * PSTRIDE);
 }
