@@ -289,9 +289,14 @@ def small_workloads(G, ctx, dev):
         torch.cuda.synchronize()
         return frames, maps
 
-    def med(f, reps=20, warm=3):
-        for _ in range(warm):
+    def med(f, reps=20, warm=3, warm_s=0.3):
+        # warm-up: at least `warm` calls and `warm_s` seconds of calls; after an idle stretch the
+        # first few hundred microsecond-scale calls run up to several times slower
+        t_end = time.perf_counter() + warm_s
+        i = 0
+        while i < warm or time.perf_counter() < t_end:
             f()
+            i += 1
         ts = []
         for _ in range(reps):
             torch.cuda.synchronize()
@@ -329,9 +334,27 @@ def small_workloads(G, ctx, dev):
         E = prob.energy(xi, pts, wts)
         E.backward()
 
+    class _EmptyFn(torch.autograd.Function):
+        """The same inputs and outputs with no work: what torch.autograd itself costs."""
+        @staticmethod
+        def forward(fctx, x, p, q):
+            return x.new_zeros(())
+
+        @staticmethod
+        def backward(fctx, g):
+            return zgrads  # preallocated: the leaves' gradient accumulation still runs
+
+    zgrads = (torch.zeros_like(xi), torch.zeros_like(pts), torch.zeros_like(wts))
+
+    def empty_fwd_bwd():
+        _EmptyFn.apply(xi, pts, wts).backward()
+
     out["autograd"] = {"workload": "corridor with per-point weights, E and dE/d(xi, xyz, w)",
-                       "forward_backward_ms": med(fwd_bwd, reps=10),
-                       "forward_ms": med(lambda: prob.energy(xi, pts, wts), reps=10)}
+                       "forward_backward_ms": med(fwd_bwd, reps=20),
+                       "forward_ms": med(lambda: prob.energy(xi, pts, wts), reps=20),
+                       "empty_function_forward_backward_ms": med(empty_fwd_bwd, reps=20),
+                       "note": "host-bound: E.backward() hands the graph to torch's CUDA autograd thread; "
+                               "empty_function_* is the same call pattern with no work, on the same box"}
     # unary factor + 10 Gauss-Newton iterations
     wb = synth.box_room()
     fb, mb = prep(wb)
@@ -411,40 +434,67 @@ def small_workloads(G, ctx, dev):
     # precision / scale batch: one 1M-point scan against a 20M-point terrain map at 0.25 m
     wt = synth.terrain()
     ft, mt = prep(wt)
+    tgt = int(wt.pairs[0, 1])
+
+    def terrain_times(plan):
+        for i in range(8):
+            plan.launch_timed(i)
+        warm = float(np.median(plan.kernel_ms(8)[3:]))  # back to back: the 40 MB source stays in L2
+        # cold L2: before each timed launch, write a 256 MB buffer (twice the L2) on the stream the
+        # launch waits for; only the linearization kernel is inside the events
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        for i in range(8):
+            flush.fill_(float(i))
+            plan.launch_timed(i)
+        cold = float(np.median(plan.kernel_ms(8)[3:]))
+        del flush
+        return cold, warm
+
     plant = G.Plan(ctx, ft, mt, wt.pairs)
     plant.set_poses(wt.poses)
-    for i in range(8):
-        plant.launch_timed(i)
-    t_warm = float(np.median(plant.kernel_ms(8)[3:]))  # back to back: the 40 MB source stays in L2
-    # cold L2: before each timed launch, write a 256 MB buffer (twice the L2) on the stream the
-    # launch waits for; only the linearization kernel is inside the events
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    for i in range(8):
-        flush.fill_(float(i))
-        plant.launch_timed(i)
-    t_ms = float(np.median(plant.kernel_ms(8)[3:]))
-    del flush
+    t_ms, t_warm = terrain_times(plant)
+    box = mt[tgt].info(0)["capacity"]
     out["terrain"] = {"workload": "terrain: 1M-pt scan vs 20M-pt map (0.25 m, one level), unary factor",
                       "pair_points": wt.n_pair_points, "kernel": plant.opts()["kernel"],
                       "kernel_ms": t_ms, "kernel_ms_note": "cold L2 (256 MB written before each launch)",
                       "kernel_ms_back_to_back": t_warm, "points_per_s": wt.n_pair_points / (t_ms / 1e3),
                       "e2e_plan_linearize_ms": med(lambda: plant.linearize(wt.poses), reps=10),
-                      "voxels": mt[int(wt.pairs[0, 1])].info(0)["n_voxels"],
-                      "dense_grid": bool(mt[int(wt.pairs[0, 1])].is_dense(0))}
+                      "voxels": mt[tgt].info(0)["n_voxels"], "grid_cells": box,
+                      "grid_gb": box * 48 / 1e9, "dense_grid": bool(mt[tgt].is_dense(0))}
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6400.0)
     n_t = wt.n_pair_points
     alg_gbs = BYTES_PER_POINT * n_t / (t_ms / 1e3) / 1e9
+    t_touched = touched_voxels(G, ctx, ft, mt, wt.pairs, wt.poses)
+    t_full = BYTES_PER_POINT * n_t + BYTES_PER_TOUCHED_VOXEL * t_touched + BYTES_OUT_PER_PAIR * len(wt.pairs)
     t_bpp, t_src = captured_traffic("terrain")
     dram_gbs = None if t_bpp is None else t_bpp * n_t / (t_ms / 1e3) / 1e9
     out["terrain"]["roofline"] = {
         "bound": "hbm", "achieved": alg_gbs, "peak": hbm, "unit": "GB/s", "frac": alg_gbs / hbm,
+        "frac_full": t_full / (t_ms / 1e3) / 1e9 / hbm,
+        "full_bytes": t_full, "touched_voxels": t_touched,
         "traffic": None if t_bpp is None else t_bpp * n_t, "traffic_source": t_src, "dram_achieved": dram_gbs,
         "dram_frac": None if dram_gbs is None else dram_gbs / hbm,
-        "note": "achieved: 40 B of source stream per point over the cold-L2 launch time; traffic: ncu DRAM bytes "
-                "of this launch (the grid gathered from HBM)",
+        "traffic_over_full": None if t_bpp is None else t_bpp * n_t / t_full,
+        "note": "achieved: 40 B of source stream per point over the cold-L2 launch time; frac_full adds 56 B per "
+                "distinct voxel hit and the outputs; traffic: ncu DRAM bytes of this launch (the grid gathered "
+                "from HBM: a hit or an empty cell inside the grid's box reads the sectors of its record)",
         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk else "fallback"}
-    del ft, mt, plant
+    plant.close()
+    # the same batch on hashed voxel blocks (the map's 5.9 M voxels in 2 x 2 x 2 blocks)
+    mth = [None if m is None else G.VoxelMap(ctx, ft[i].pts4, ft[i].cov6, wt.resolutions, layout="hash")
+           for i, m in enumerate(mt)]
+    planh = G.Plan(ctx, ft, mth, wt.pairs)
+    planh.set_poses(wt.poses)
+    h_ms, h_warm = terrain_times(planh)
+    out["terrain"]["hash_layout"] = {"kernel": planh.opts()["kernel"], "kernel_ms": h_ms,
+                                     "kernel_ms_back_to_back": h_warm,
+                                     "cell_records_gb": mth[tgt].info(0)["capacity"] * 48 / 1e9}
+    planh.close()
+    for m in mth:
+        if m is not None:
+            m.free()
+    del ft, mt, plant, planh, mth
     poses = gn10()
     D = np.linalg.inv(np.vstack([wb.poses_true[0], [0, 0, 0, 1]])) @ np.vstack([poses[0], [0, 0, 0, 1]])
     ang = float(np.degrees(np.arccos(min(1.0, (np.trace(D[:3, :3]) - 1) / 2))))
