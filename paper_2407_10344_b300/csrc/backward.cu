@@ -23,7 +23,7 @@
 #include <algorithm>
 #include <cstring>
 
-#include "plan.cuh"
+#include "lin_kernel.cuh"
 
 namespace {
 
@@ -41,6 +41,8 @@ struct BwdArgs {
   const PairDev* pairs;
   const FrameDev* frames;
   const MapDev* maps;
+  const DenseMapDev* dmaps;  // per map, when every target level is a dense grid
+  const HashMapDev* hmaps;   // per map, when every target level is hashed
   const PoseF* pose;
   const int32_t* src_list;
   const int64_t* frame_off;
@@ -187,6 +189,9 @@ __device__ __forceinline__ void backward_item(const BwdArgs& a, int g, PairView&
       if (a.dw) a.dw[base + k] = pacc[r].w;
     }
   }
+  // the queue's next item index (written by thread 0 during this item) is read after this
+  // barrier: an item of a frame that is the source of no pair has no other barrier
+  __syncthreads();
 }
 
 // Persistent blocks over the item queue (the next item fetched one item ahead).
@@ -203,6 +208,269 @@ __global__ void __launch_bounds__(BWD_BLOCK) k_backward_items(const BwdArgs a) {
     backward_item(a, cur, V, s_red);  // ends with a barrier
     cur = s_item[b];
   }
+}
+
+// ---------------------------------------------------------------- pipelined form
+// Batches whose target maps are all dense grids, or all hashed voxel blocks, take the
+// per-lane form of the linearization kernels: a block of BWL_BLOCK threads, BWL_PPT points
+// per thread and pair (the same 1024-point tiles), the records of a (pair, point) read one
+// round ahead of its arithmetic (lane_fetch, or hash_fetch then hash_resolve), across the
+// pairs of the group too.  The per-pair constants of the group (at most BWL_VMAX pairs) are
+// built once per gradient call in the order of the pairs by source frame (k_backward_views)
+// and copied into shared memory once per item, so a pair starts without a wait; each warp
+// keeps its 9 pose sums of every pair in shared memory and the block sums them once at the
+// end of the item (FP32 warp trees, warps in FP64, fixed order).  A point's dE/dmu and dE/dw,
+// summed over the pairs, stay in shared memory (one float4 per point of the tile).
+constexpr int BWL_BLOCK = 128;
+constexpr int BWL_PPT = BWD_TILE / BWL_BLOCK;
+constexpr int BWL_VMAX = 16;  // pairs per group at most (bwd_prepare splits larger groups)
+static_assert(BWL_PPT % 2 == 0, "the rounds alternate two fetch buffers");
+
+template <bool HASH>
+using BwlView = LaneView<typename std::conditional<HASH, HashMapDev, DenseMapDev>::type>;
+static_assert(sizeof(BwlView<false>) % 16 == 0 && sizeof(BwlView<true>) % 16 == 0, "views are copied as float4");
+
+template <int LMAX, bool HASH, class View>
+__device__ __forceinline__ void bwl_fetch(const View& V, const float4* pts, int k, int last, int validate,
+                                          LaneFetch<LMAX>& F) {
+  const int kk = min(k, last);
+  const float4 m = ldg4(pts + kk);
+  if constexpr (HASH) {
+    HashFetch<LMAX> h;
+    hash_fetch<LMAX, false>(V, m, k <= last, validate, kk, h);
+    hash_resolve<LMAX, false>(V, h, F);
+  } else {
+    lane_fetch<LMAX, false>(V, m, k <= last, validate, kk, F);
+  }
+}
+
+// One (pair, point) from its fetched records: the same terms as point_gradient.
+template <int LMAX, class View>
+__device__ __forceinline__ void bwl_point(const View& V, const LaneFetch<LMAX>& F, int full, float (&acc)[9],
+                                          float4& pg) {
+  const float4 R0 = V.Rt[0], R1 = V.Rt[1], R2 = V.Rt[2];
+  const float3 q = F.q;
+  const float c00 = F.ca.x, c01 = F.ca.y, c02 = F.cb.x, c11 = F.cb.y, c12 = F.cc.x, c22 = F.cc.y;
+  const float w00 = R0.x * c00 + R0.y * c01 + R0.z * c02;
+  const float w01 = R0.x * c01 + R0.y * c11 + R0.z * c12;
+  const float w02 = R0.x * c02 + R0.y * c12 + R0.z * c22;
+  const float w10 = R1.x * c00 + R1.y * c01 + R1.z * c02;
+  const float w11 = R1.x * c01 + R1.y * c11 + R1.z * c12;
+  const float w12 = R1.x * c02 + R1.y * c12 + R1.z * c22;
+  const float w20 = R2.x * c00 + R2.y * c01 + R2.z * c02;
+  const float w21 = R2.x * c01 + R2.y * c11 + R2.z * c12;
+  const float w22 = R2.x * c02 + R2.y * c12 + R2.z * c22;
+  const float r00 = w00 * R0.x + w01 * R0.y + w02 * R0.z;
+  const float r01 = w00 * R1.x + w01 * R1.y + w02 * R1.z;
+  const float r02 = w00 * R2.x + w01 * R2.y + w02 * R2.z;
+  const float r11 = w10 * R1.x + w11 * R1.y + w12 * R1.z;
+  const float r12 = w10 * R2.x + w11 * R2.y + w12 * R2.z;
+  const float r22 = w20 * R2.x + w21 * R2.y + w22 * R2.z;
+  float Y0 = 0.f, Y1 = 0.f, Y2 = 0.f, E = 0.f, av0 = 0.f, av1 = 0.f, av2 = 0.f;
+#pragma unroll
+  for (int l = 0; l < LMAX; ++l) {
+    const float4 v0 = F.s0[l], v1 = F.s1[l], v2 = F.s2[l];
+    const bool hit = __float_as_int(v0.x) >= 0;  // occupied cell
+    const float sa = v1.w + r00, sb = v2.x + r01, sc = v2.y + r02, sd = v2.z + r11, se = v2.w + r12, sf = v0.y + r22;
+    const float A00 = sd * sf - se * se, A01 = sc * se - sb * sf, A02 = sb * se - sc * sd;
+    const float A11 = sa * sf - sc * sc, A12 = sb * sc - sa * se, A22 = sa * sd - sb * sb;
+    const float det = sa * A00 + sb * A01 + sc * A02;
+    const bool ok = hit && det > 0.f && det < INFINITY;
+    const float id = __frcp_rn(det);
+    const float O00 = A00 * id, O01 = A01 * id, O02 = A02 * id, O11 = A11 * id, O12 = A12 * id, O22 = A22 * id;
+    const float d0 = v1.x - q.x, d1 = v1.y - q.y, d2 = v1.z - q.z;
+    const float y0 = O00 * d0 + O01 * d1 + O02 * d2;
+    const float y1 = O01 * d0 + O11 * d1 + O12 * d2;
+    const float y2 = O02 * d0 + O12 * d1 + O22 * d2;
+    const float el = d0 * y0 + d1 * y1 + d2 * y2;
+    // a term that is a miss or not positive definite adds nothing (selected, not multiplied:
+    // its values need not be finite)
+    Y0 += ok ? y0 : 0.f;
+    Y1 += ok ? y1 : 0.f;
+    Y2 += ok ? y2 : 0.f;
+    E += ok ? el : 0.f;
+    if (full) {
+      const float z0 = R0.x * y0 + R1.x * y1 + R2.x * y2;  // R^T y
+      const float z1 = R0.y * y0 + R1.y * y1 + R2.y * y2;
+      const float z2 = R0.z * y0 + R1.z * y1 + R2.z * y2;
+      const float Cz0 = c00 * z0 + c01 * z1 + c02 * z2;
+      const float Cz1 = c01 * z0 + c11 * z1 + c12 * z2;
+      const float Cz2 = c02 * z0 + c12 * z1 + c22 * z2;
+      av0 += ok ? z1 * Cz2 - z2 * Cz1 : 0.f;
+      av1 += ok ? z2 * Cz0 - z0 * Cz2 : 0.f;
+      av2 += ok ? z0 * Cz1 - z1 * Cz0 : 0.f;
+    }
+  }
+  const float w = F.w;
+  // dE/dmu = -2 w R^T Y, dE/dw = E
+  pg.x += -2.f * w * (R0.x * Y0 + R1.x * Y1 + R2.x * Y2);
+  pg.y += -2.f * w * (R0.y * Y0 + R1.y * Y1 + R2.y * Y2);
+  pg.z += -2.f * w * (R0.z * Y0 + R1.z * Y1 + R2.z * Y2);
+  pg.w += E;
+  const float ux = q.x - R0.w, uy = q.y - R1.w, uz = q.z - R2.w;
+  const float wy0 = w * Y0, wy1 = w * Y1, wy2 = w * Y2;
+  acc[0] += uy * wy2 - uz * wy1;
+  acc[1] += uz * wy0 - ux * wy2;
+  acc[2] += ux * wy1 - uy * wy0;
+  acc[3] += wy0;
+  acc[4] += wy1;
+  acc[5] += wy2;
+  acc[6] += 2.f * w * av0;
+  acc[7] += 2.f * w * av1;
+  acc[8] += 2.f * w * av2;
+}
+
+// The constants of every pair, in the order of the pairs by source frame (src_list), for the
+// poses of this gradient call.
+template <bool HASH>
+__global__ void k_backward_views(const BwdArgs a, int npairs, BwlView<HASH>* __restrict__ views) {
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= npairs) return;
+  const int p = a.src_list[pos];
+  const PairDev pd = a.pairs[p];
+  const PoseF pf = a.pose[p];
+  BwlView<HASH> V;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) V.Rt[r] = make_float4(pf.R[3 * r], pf.R[3 * r + 1], pf.R[3 * r + 2], pf.t[r]);
+  V.v = make_float4(pf.v[0], pf.v[1], pf.v[2], 0.f);
+  const FrameDev F = a.frames[pd.src];
+  V.pts = F.pts;
+  V.cov = F.cov;
+  V.nrm = F.nrm;
+  if constexpr (HASH) V.M = a.hmaps[pd.map];
+  else V.M = a.dmaps[pd.map];
+  V.end = 0;  // unused: the item knows its tile
+  V.pad = 0;
+  views[pos] = V;
+}
+
+template <int LMAX, bool HASH>
+__device__ __forceinline__ void bwl_item(const BwdArgs& a, const BwlView<HASH>* __restrict__ views, int g,
+                                         BwlView<HASH> (&Vs)[BWL_VMAX], float (&s_red)[BWL_VMAX][BWL_BLOCK / 32][9],
+                                         float4 (&s_pg)[BWL_PPT][BWL_BLOCK]) {
+  const int4 it = a.items[g];
+  const int f = it.x;
+  const int start = it.y;
+  const int pb = it.z, npf = it.w;
+  const int64_t slot0 = a.item_slot[g];
+  const int end = int(min(int64_t(start) + BWD_TILE, a.frames[f].n));
+  const int last = end - 1;  // items are never empty
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int r = 0; r < BWL_PPT; ++r) s_pg[r][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+  {  // the group's views (a frame that is the source of no pair has items with none)
+    constexpr int W = int(sizeof(BwlView<HASH>) / 16);
+    const float4* src = reinterpret_cast<const float4*>(views + pb);
+    float4* dst = reinterpret_cast<float4*>(Vs);
+    for (int i = tid; i < npf * W; i += BWL_BLOCK) dst[i] = __ldg(src + i);
+  }
+  __syncthreads();
+  const float4* pts = a.frames[f].pts;
+  LaneFetch<LMAX> fa, fb;
+  if (npf > 0) bwl_fetch<LMAX, HASH>(Vs[0], pts, start + tid, last, a.validate, fa);
+#pragma unroll 1
+  for (int j = 0; j < npf; ++j) {
+    const auto& V = Vs[j];
+    const bool more = j + 1 < npf;
+    float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // two rounds per iteration (the buffers alternate); not unrolled further, so that the
+    // code of a pair stays small enough for the instruction cache
+#pragma unroll 1
+    for (int r = 0; r < BWL_PPT; r += 2) {
+      bwl_fetch<LMAX, HASH>(V, pts, start + (r + 1) * BWL_BLOCK + tid, last, a.validate, fb);
+      bwl_point<LMAX>(V, fa, a.full, acc, s_pg[r][tid]);
+      // round r + 2 of this pair, or the first round of the next pair
+      const bool in_pair = r + 2 < BWL_PPT;
+      if (in_pair || more)
+        bwl_fetch<LMAX, HASH>(Vs[in_pair ? j : j + 1], pts, start + (in_pair ? r + 2 : 0) * BWL_BLOCK + tid, last,
+                              a.validate, fa);
+      bwl_point<LMAX>(V, fb, a.full, acc, s_pg[r + 1][tid]);
+    }
+    // this warp's pose sums of pair j (FP32 tree)
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      float v = acc[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) s_red[j][warp][i] = v;
+    }
+  }
+  __syncthreads();
+  // the pairs' pose sums over the warps in FP64, in warp order
+  for (int t = tid; t < npf * 9; t += BWL_BLOCK) {
+    const int j = t / 9, i = t - 9 * j;
+    double sum = 0.0;
+#pragma unroll
+    for (int w = 0; w < BWL_BLOCK / 32; ++w) sum += double(s_red[j][w][i]);
+    a.part[(slot0 + j) * BSTRIDE + i] = sum;
+  }
+  const int64_t base = a.frame_off[f];
+#pragma unroll
+  for (int r = 0; r < BWL_PPT; ++r) {
+    const int64_t k = start + r * BWL_BLOCK + tid;
+    const float4 pg = s_pg[r][tid];
+    if (k < end && a.pp) {
+      a.pp[int64_t(a.item_grp[g]) * a.ntot + base + k] = pg;
+    } else if (k < end) {
+      if (a.dmu) {
+        a.dmu[3 * (base + k)] = pg.x;
+        a.dmu[3 * (base + k) + 1] = pg.y;
+        a.dmu[3 * (base + k) + 2] = pg.z;
+      }
+      if (a.dw) a.dw[base + k] = pg.w;
+    }
+  }
+  // the queue's next item index (written by thread 0 during this item) is read after this
+  // barrier, and the views and pose sums are rewritten by the next item
+  __syncthreads();
+}
+
+template <int LMAX, bool HASH>
+__global__ void __launch_bounds__(BWL_BLOCK, 4) k_backward_lane(const BwdArgs a, const BwlView<HASH>* views) {
+  __shared__ BwlView<HASH> Vs[BWL_VMAX];
+  __shared__ float s_red[BWL_VMAX][BWL_BLOCK / 32][9];
+  __shared__ float4 s_pg[BWL_PPT][BWL_BLOCK];
+  __shared__ int s_item[2];
+  if (threadIdx.x == 0) s_item[0] = atomicAdd(a.head, 1);
+  __syncthreads();
+  int cur = s_item[0];
+  for (int b = 1;; b ^= 1) {
+    if (cur >= a.nitems) break;
+    if (threadIdx.x == 0) s_item[b] = atomicAdd(a.head, 1);
+    bwl_item<LMAX, HASH>(a, views, cur, Vs, s_red, s_pg);  // ends with a barrier
+    cur = s_item[b];
+  }
+}
+
+// Launch of the pipelined gradient pass for a plan whose target maps are all dense grids or
+// all hashed, with 1 to 4 levels: the views, then the items.  false: the general kernel runs.
+template <bool HASH>
+bool launch_backward_lane_t(const glim_plan* p, const BwdScratch& sc, const BwdArgs& a, cudaStream_t st) {
+  auto* views = reinterpret_cast<BwlView<HASH>*>(sc.views);
+  if (p->npairs > 0) k_backward_views<HASH><<<ceil_div_i(p->npairs, 128), 128, 0, st>>>(a, p->npairs, views);
+  switch (p->lmax) {
+    case 1: k_backward_lane<1, HASH><<<sc.grid_lane, BWL_BLOCK, 0, st>>>(a, views); return true;
+    case 2: k_backward_lane<2, HASH><<<sc.grid_lane, BWL_BLOCK, 0, st>>>(a, views); return true;
+    case 3: k_backward_lane<3, HASH><<<sc.grid_lane, BWL_BLOCK, 0, st>>>(a, views); return true;
+    case 4: k_backward_lane<4, HASH><<<sc.grid_lane, BWL_BLOCK, 0, st>>>(a, views); return true;
+  }
+  return false;
+}
+
+// Blocks per SM of the pipelined kernel for a plan, or 0 when the plan takes the general one.
+int backward_lane_occupancy(const glim_plan* p) {
+  const bool dense = p->d_dmaps != nullptr, hash = p->d_hmaps != nullptr;
+  if ((!dense && !hash) || p->lmax < 1 || p->lmax > 4) return 0;
+  const void* fn = nullptr;
+  switch (p->lmax) {
+    case 1: fn = dense ? reinterpret_cast<const void*>(k_backward_lane<1, false>) : reinterpret_cast<const void*>(k_backward_lane<1, true>); break;
+    case 2: fn = dense ? reinterpret_cast<const void*>(k_backward_lane<2, false>) : reinterpret_cast<const void*>(k_backward_lane<2, true>); break;
+    case 3: fn = dense ? reinterpret_cast<const void*>(k_backward_lane<3, false>) : reinterpret_cast<const void*>(k_backward_lane<3, true>); break;
+    default: fn = dense ? reinterpret_cast<const void*>(k_backward_lane<4, false>) : reinterpret_cast<const void*>(k_backward_lane<4, true>); break;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BWL_BLOCK, 0) != cudaSuccess) return 0;
+  return std::max(per_sm, 1);
 }
 
 // per pair: dxi_pair (12) = 2 Lift^T g + [a; 0; -R a; 0], g and a summed over the items of
@@ -314,10 +582,13 @@ glim_status bwd_prepare(glim_plan* p, BwdScratch& sc) {
   std::vector<int32_t> pair_item0(std::max(npairs, 1), 0), pair_nitems(std::max(npairs, 1), 0),
       pair_jj(std::max(npairs, 1), 0);
   int64_t nslots = 0;
+  int Gmax = 1;
   for (int f = 0; f < nframes; ++f) {
     const int npf = src_begin[f + 1] - src_begin[f];
-    const int Gf = std::max(1, std::min(G, npf));
+    // at most BWL_VMAX pairs per group: the pipelined kernel stages a group's pairs at once
+    const int Gf = std::max({1, std::min(G, npf), (npf + BWL_VMAX - 1) / BWL_VMAX});
     frame_groups[f] = Gf;
+    Gmax = std::max(Gmax, Gf);
     for (int g = 0; g < Gf; ++g) {
       const int jb = int(int64_t(g) * npf / Gf), je = int(int64_t(g + 1) * npf / Gf);
       const int32_t it0 = int32_t(items.size());
@@ -345,11 +616,14 @@ glim_status bwd_prepare(glim_plan* p, BwdScratch& sc) {
   }
   sc.ntot = frame_off[nframes];
   sc.nslots = nslots;
-  sc.groups = G;
+  sc.groups = Gmax;
   int per_sm = 1;
   GLIM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_items, BWD_BLOCK, 0));
   sc.grid = std::max(1, std::min(std::max(per_sm, 1) * ctx->num_sms, std::max(sc.nitems, 1)));
-  const size_t npp = G > 1 ? size_t(G) * size_t(std::max<int64_t>(sc.ntot, 1)) : 0;
+  if (const int per_sm_lane = backward_lane_occupancy(p))
+    sc.grid_lane = std::max(1, std::min(per_sm_lane * ctx->num_sms, std::max(sc.nitems, 1)));
+  const size_t npp = Gmax > 1 ? size_t(Gmax) * size_t(std::max<int64_t>(sc.ntot, 1)) : 0;
+  const size_t view_bytes = std::max(sizeof(BwlView<false>), sizeof(BwlView<true>));
   if (dmalloc(&sc.items, items.size() * sizeof(int4)) != cudaSuccess ||
       dmalloc(&sc.item_grp, item_grp.size() * sizeof(int32_t)) != cudaSuccess ||
       dmalloc(&sc.item_slot, item_slot.size() * sizeof(int64_t)) != cudaSuccess ||
@@ -364,7 +638,8 @@ glim_status bwd_prepare(glim_plan* p, BwdScratch& sc) {
       (npp > 0 && dmalloc(&sc.pp, npp * sizeof(float4)) != cudaSuccess) ||
       dmalloc(&sc.part, size_t(std::max<int64_t>(nslots, 1)) * BSTRIDE * sizeof(double)) != cudaSuccess ||
       dmalloc(&sc.pair_grad, size_t(std::max(npairs, 1)) * 12 * sizeof(double)) != cudaSuccess ||
-      dmalloc(&sc.head, sizeof(int)) != cudaSuccess) {
+      dmalloc(&sc.head, sizeof(int)) != cudaSuccess ||
+      (sc.grid_lane > 0 && dmalloc(&sc.views, size_t(std::max(npairs, 1)) * view_bytes) != cudaSuccess)) {
     sc.release();
     return set_error(ctx, GLIM_ENOMEM, "backward: scratch allocation failed");
   }
@@ -404,6 +679,8 @@ glim_status bwd_run(glim_plan* p, const BwdScratch& sc, int32_t omega_grad_full,
     a.pairs = p->d_pairs;
     a.frames = p->d_frames;
     a.maps = p->d_maps;
+    a.dmaps = p->d_dmaps;
+    a.hmaps = p->d_hmaps;
     a.pose = p->in_pose32();
     a.src_list = sc.src_list;
     a.frame_off = sc.frame_off;
@@ -415,7 +692,12 @@ glim_status bwd_run(glim_plan* p, const BwdScratch& sc, int32_t omega_grad_full,
     a.dmu = dmu_out;
     a.dw = dw_out;
     GLIM_CUDA(ctx, cudaMemsetAsync(sc.head, 0, sizeof(int), ctx->stream));
-    k_backward_items<<<sc.grid, BWD_BLOCK, 0, ctx->stream>>>(a);
+    bool lane = false;
+    if (sc.grid_lane > 0)
+      lane = p->d_dmaps ? launch_backward_lane_t<false>(p, sc, a, ctx->stream)
+                        : launch_backward_lane_t<true>(p, sc, a, ctx->stream);
+    if (!lane) k_backward_items<<<sc.grid, BWD_BLOCK, 0, ctx->stream>>>(a);
+    else if (npairs > 0) ctx->launches++;  // the views
     GLIM_LAUNCHED(ctx);
   }
   if (sc.groups > 1 && sc.ntot > 0 && (dmu_out || dw_out)) {

@@ -117,7 +117,9 @@ struct BwdScratch {
   double* part = nullptr;              // nslots x 9
   double* pair_grad = nullptr;         // npairs x 12
   int* head = nullptr;                 // work-queue head
+  void* views = nullptr;               // npairs: per-pair constants of the pipelined kernel (in src_list order)
   int nitems = 0, grid = 0, groups = 1;
+  int grid_lane = 0;  // grid of the pipelined kernel (all-dense or all-hashed batches), else 0
   int64_t ntot = 0, nslots = 0;
   void release() {
     cudaFree(items);
@@ -135,6 +137,7 @@ struct BwdScratch {
     cudaFree(part);
     cudaFree(pair_grad);
     cudaFree(head);
+    cudaFree(views);
     *this = BwdScratch{};
   }
 };

@@ -124,6 +124,75 @@ def test_kernel_ids_at_the_edge_of_the_key_range(G, ctx, layout):
             _check_plan(G, ctx, gf, gm, pairs, poses, ref["ids"], kernel, ref=ref)
 
 
+# ---------------------------------------------------------------------------- probe chains
+def _home_slot(bx, by, bz, log2cap):
+    """Home slot of a block key in a hashed level's table, as the library lays the table out
+    (the top log2cap bits of the 32-bit linear hash of the block key)."""
+    h = (np.int64(bx) * 0xFFE6CC61 + np.int64(by) * 0xFC4A3B47 + np.int64(bz) * 0x27004D2D) & 0xFFFFFFFF
+    return int(h) >> (32 - log2cap)
+
+
+def test_kernel_ids_through_long_probe_chains(G, ctx):
+    """Hashed voxel blocks whose keys share one home slot, so that finding them takes probe
+    chains of up to nine entries, plus blocks absent from the map whose home slot is the same
+    one (their lookups walk the chain to the first empty entry) and empty cells of present
+    blocks: every kernel must resolve each (point, level) to the oracle's voxel or miss.  The
+    block keys are chosen on the host for the table size the build picks (load <= 1/16)."""
+    res = 1.0
+    s = synth.Stream(21, "probe-chains")
+    nblk = 12
+    log2cap = int(np.ceil(np.log2(16 * nblk)))  # 16 * 12 = 192 -> 256 entries
+    chain, absent, others = [], [], []
+    target = None
+    while len(chain) < 9 or len(absent) < 4 or len(others) < nblk - 9:
+        b = tuple(int(v) for v in s.integers(3, -40, 40))
+        if b in chain or b in absent or b in others:
+            continue
+        h = _home_slot(*b, log2cap)
+        if target is None:
+            target = h
+        if h == target and len(chain) < 9:
+            chain.append(b)
+        elif h == target and len(absent) < 4:
+            absent.append(b)
+        elif h in ((target + 1) % 256, (target + 2) % 256) and len(others) < nblk - 9:
+            others.append(b)  # present blocks whose home slots lie inside the chain
+    present = chain + others
+    # one voxel per present block, at a cell chosen by the stream; three points per voxel
+    tgt, src = [], []
+    for b in present:
+        loc = s.integers(3, 0, 2)
+        k = np.array(b) * 2 + loc
+        c = (k + 0.5) * res
+        tgt += [c + [0.1, 0.0, 0.0], c - [0.1, 0.0, 0.0], c + [0.0, 0.1, 0.05]]
+        src.append(c + [0.05, -0.05, 0.05])                       # hit
+        src.append((np.array(b) * 2 + (1 - loc) + 0.5) * res)  # empty cell of a present block
+    for b in absent:
+        src.append((np.array(b) * 2 + 0.5) * res)               # block not in the table
+    tgt = np.array(tgt, np.float32)
+    src = np.array(src, np.float32)
+    cov = lambda n: np.tile(np.array([0.02, 0.001, 0, 0.03, 0.002, 0.01], np.float32), (n, 1))
+    of = [O.Frame(O.as_pts4(src), cov(len(src))), O.Frame(O.as_pts4(tgt), cov(len(tgt)))]
+    om = [None, O.VMap(of[1].pts4, of[1].cov6, [res])]
+    poses = np.stack([np.eye(3, 4)] * 2)
+    pairs = np.array([[0, 1]], np.int32)
+    ref = O.linearize(of, om, pairs, poses, want_ids=True, want_comp=True)
+    ids = ref["ids"]
+    assert (ids[0::2][:len(present)] >= 0).all() and (ids[1:2 * len(present):2] < 0).all()
+    assert (ids[2 * len(present):] < 0).all()
+    gf = [G.FrameData(torch.as_tensor(f.pts4, device="cuda"), torch.as_tensor(f.cov6, device="cuda")) for f in of]
+    gm = [None, G.VoxelMap(ctx, gf[1].pts4, gf[1].cov6, [res], layout="hash")]
+    assert not gm[1].is_dense(0)
+    assert gm[1].info(0)["max_probe"] >= 9
+    seen = set()
+    for kernel, block, ppt in (("auto", 0, 0), ("general", 0, 0), ("auto", 128, 1)):
+        ran, _ = _check_plan(G, ctx, gf, gm, pairs, poses, ids, kernel, block=block, ppt=ppt, ref=ref)
+        seen.add(ran)
+    assert seen == {"hash", "general"}
+    got = G.correspondences(ctx, gf[0], gm[1], poses[0], poses[1]).cpu().numpy()
+    assert np.array_equal(got.reshape(ids.shape), ids)
+
+
 # ---------------------------------------------------------------------------- scenes
 @pytest.fixture(scope="module")
 def room(ctx):
