@@ -89,7 +89,7 @@ __device__ __forceinline__ void point_gradient(const PairView& V, int64_t k, int
     const float A11 = sa * sf - sc * sc, A12 = sb * sc - sa * se, A22 = sa * sd - sb * sb;
     const float det = sa * A00 + sb * A01 + sc * A02;
     if (!(det > 0.f) || !isfinite(det)) continue;
-    const float id = __frcp_rn(det);
+    const float id = __fdividef(1.f, det);
     const float O[3][3] = {{A00 * id, A01 * id, A02 * id}, {A01 * id, A11 * id, A12 * id},
                            {A02 * id, A12 * id, A22 * id}};
     const float d[3] = {v1.x - q.x, v1.y - q.y, v1.z - q.z};
@@ -276,7 +276,7 @@ __device__ __forceinline__ void bwl_point(const View& V, const LaneFetch<LMAX>& 
     const float A11 = sa * sf - sc * sc, A12 = sb * sc - sa * se, A22 = sa * sd - sb * sb;
     const float det = sa * A00 + sb * A01 + sc * A02;
     const bool ok = hit && det > 0.f && det < INFINITY;
-    const float id = __frcp_rn(det);
+    const float id = __fdividef(1.f, det);
     const float O00 = A00 * id, O01 = A01 * id, O02 = A02 * id, O11 = A11 * id, O12 = A12 * id, O22 = A22 * id;
     const float d0 = v1.x - q.x, d1 = v1.y - q.y, d2 = v1.z - q.z;
     const float y0 = O00 * d0 + O01 * d1 + O02 * d2;
