@@ -648,10 +648,7 @@ extern "C" void glim_plan_destroy(glim_plan* p) {
   cudaFree(p->d_dmaps);
   cudaFree(p->d_hmaps);
   cudaFree(p->d_empty_slots);
-  if (p->bwd) {
-    p->bwd->release();
-    delete p->bwd;
-  }
+  bwd_scratch_free(p->bwd);
   cudaFree(p->d_items);
   cudaFree(p->d_item_begin);
   cudaFree(p->d_part);

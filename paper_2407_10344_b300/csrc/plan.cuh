@@ -96,51 +96,10 @@ struct PairView {
   MapDev M;
 };
 
-// Scratch of the gradient pass of a plan, created at the first glim_plan_backward and kept by
-// the plan: the work list of (source frame, point tile, group of the frame's pairs) items, the
-// pairs grouped by source frame, one partial slot of 9 sums per (item, pair of its group), the
-// per-pair gradients, and (only when a frame's pairs are split into several groups) one
-// per-point gradient slot per group.
-struct BwdScratch {
-  int4* items = nullptr;               // nitems: (frame, first point, first pair of the group in src_list, pairs)
-  int32_t* item_grp = nullptr;         // nitems: the item's group
-  int64_t* item_slot = nullptr;        // nitems: first partial slot of the item
-  int32_t* src_begin = nullptr;        // nframes + 1: pairs grouped by source frame
-  int32_t* src_list = nullptr;
-  int32_t* pair_item0 = nullptr;       // npairs: first item of the pair's group
-  int32_t* pair_nitems = nullptr;      // npairs: items of that group (the frame's tiles)
-  int32_t* pair_jj = nullptr;          // npairs: position of the pair in its group
-  int32_t* tgt = nullptr;              // npairs: target frame
-  int64_t* frame_off = nullptr;        // nframes + 1: first point of each frame in the outputs
-  int32_t* frame_groups = nullptr;     // nframes: groups of the frame's pairs
-  float4* pp = nullptr;                // groups > 1: groups x ntot per-point (dE/dmu, dE/dw) slots
-  double* part = nullptr;              // nslots x 9
-  double* pair_grad = nullptr;         // npairs x 12
-  int* head = nullptr;                 // work-queue head
-  void* views = nullptr;               // npairs: per-pair constants of the pipelined kernel (in src_list order)
-  int nitems = 0, grid = 0, groups = 1;
-  int grid_lane = 0;  // grid of the pipelined kernel (all-dense or all-hashed batches), else 0
-  int64_t ntot = 0, nslots = 0;
-  void release() {
-    cudaFree(items);
-    cudaFree(item_grp);
-    cudaFree(item_slot);
-    cudaFree(src_begin);
-    cudaFree(src_list);
-    cudaFree(pair_item0);
-    cudaFree(pair_nitems);
-    cudaFree(pair_jj);
-    cudaFree(tgt);
-    cudaFree(frame_off);
-    cudaFree(frame_groups);
-    cudaFree(pp);
-    cudaFree(part);
-    cudaFree(pair_grad);
-    cudaFree(head);
-    cudaFree(views);
-    *this = BwdScratch{};
-  }
-};
+// Scratch of the gradient pass of a plan (defined with the gradient kernels); freed by
+// bwd_scratch_free.
+struct BwdScratch;
+void bwd_scratch_free(BwdScratch* sc);
 
 using LinKernel = void (*)(const LinArgs);
 struct LinKernelInfo {
