@@ -41,10 +41,16 @@ TRAFFIC_SUMMARIES = {"urban": "k_linearize_dense_urban40_ncu_full.md", "terrain"
 
 
 def kernel_digest():
+    """Digest of the kernel's sources with comments and blank space removed, so that it changes
+    with the code only."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2407_10344_b300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2407_10344_b300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -3,10 +3,10 @@
 // in lin_fp32.cu, lin_kahan.cu and lin_fp64.cu.
 //
 // Per point (FP32): the pinned transform q = R mu + t, u = R mu, the rotated covariance
-// R C R^T once for all levels; the first hash probe of every level is issued at once (the
-// 48-byte slot carries key and statistics, so one read resolves a probe), then per hit
-// S = C~ + R C R^T, Omega = S^-1 (adjugate / determinant), d = mu~ - q, y = Omega d,
-// e = d^T y, summed over levels as Omega_sum = sum w Omega, g_sum = sum w y, e_sum.
+// R C R^T once for all levels; the lookup of every level (a dense grid's cell, or a hashed
+// level's block-table entry then the cell) with the reads of all levels in flight together,
+// then per hit S = C~ + R C R^T, Omega = S^-1 (adjugate / determinant), d = mu~ - q,
+// y = Omega d, e = d^T y, summed over levels as Omega_sum = sum w Omega, g_sum = sum w y, e_sum.
 //
 // With G = [-(u)x, I] (3 x 6), the same for every level of a point, A_k = -G diag(R, R) and
 // B_k = G S_t (S_t = [[I, 0], [-(t)x, I]]), Eqs. (4)-(5).  A point therefore contributes
