@@ -6,7 +6,9 @@
   recomputed by the oracle one pair at a time on the same float32 inputs, and each sampled
   pair must match (inliers exactly, e / H / b within 1e-4, and the correspondence ids that the
   kernel's id-recording instantiation resolved, in the same launch configuration, bit for
-  bit).  The plain relative error of b, |b - b*| / |b*|, is bounded as well.
+  bit).  The plain relative error of b, |b - b*| / |b*|, is bounded as well.  The same step
+  on hashed voxel blocks gives the same bits for all 4000 pairs (e, H, b, ids and the gradient);
+  the gradient of the sampled pairs matches the oracle's analytic gradient.
 * Odometry window at its full size (30k-point frame, 10 keyframes, per-point weights): the
   gradient of the batch against the oracle's analytic gradient.
 """
@@ -72,6 +74,44 @@ def test_urban_global_step_full_size_sampled_pairs(G, ctx):
         worst = [max(worst[0], ee[0]), max(worst[1], eH[0]), max(worst[2], eb[0]), max(worst[3], ebp[0])]
     print("urban full size, worst over sampled pairs: e %.2e  H %.2e  b (P7) %.2e  b plain %.2e" % tuple(worst))
     assert max(worst) <= TOL, worst
+
+    # The same step on hashed voxel blocks, in the same launch configuration: the hash kernel
+    # resolves every (pair, point, level) to the same record as the dense-grid kernel and runs
+    # the same arithmetic, so all 4000 pairs' e, H and b are the same bits.
+    hmaps = [None if m is None else G.VoxelMap(ctx, frames[i].pts4, frames[i].cov6, w.resolutions, layout="hash")
+             for i, m in enumerate(maps)]
+    plan_h = G.Plan(ctx, frames, hmaps, w.pairs, accum_mode=G.ACC_FP64, block=128, pts_per_thread=64)
+    assert plan_h.opts()["kernel"] == "hash"
+    e_h, H_h, b_h, inl_h = [np.array(x) for x in plan_h.linearize(w.poses)]
+    assert np.array_equal(e_h, e) and np.array_equal(H_h, H) and np.array_equal(b_h, b)
+    assert np.array_equal(inl_h, inl)
+    ids_h, _ = plan_h.correspondence_ids(w.poses)
+    assert torch.equal(ids_h, ids)
+    # the gradient of the whole step is the same bits on both layouts (the pipelined gradient
+    # kernel, one fetch per layout), and the gradient of the sampled pairs alone matches the
+    # oracle's analytic gradient at these frame sizes
+    g_d = plan.backward(w.poses)
+    g_h = plan_h.backward(w.poses)
+    for a_, b_ in zip(g_d, g_h):
+        assert torch.equal(a_, b_)
+    plan_h.close()
+    for m in hmaps:
+        if m is not None:
+            m.free()
+    used = sorted(set(int(v) for v in w.pairs[sample].ravel()))
+    remap = {f: i for i, f in enumerate(used)}
+    sub_pairs = np.array([[remap[int(a_)], remap[int(b_)]] for a_, b_ in w.pairs[sample]], np.int32)
+    sub_frames = [frames[f] for f in used]
+    sub_maps = [maps[f] if f in set(int(t) for t in w.pairs[sample, 1]) else None for f in used]
+    sub_poses = np.stack([w.poses[f] for f in used])
+    dxi, dmu, dw = G.Plan(ctx, sub_frames, sub_maps, sub_pairs).backward(sub_poses)
+    ofr = [O.Frame(f.pts4.cpu().numpy(), f.cov6.cpu().numpy(), f.normal3.cpu().numpy()) for f in sub_frames]
+    omp = [None if m is None else O.VMap(ofr[i].pts4, ofr[i].cov6, w.resolutions) for i, m in enumerate(sub_maps)]
+    odxi, odmu, odw = O.gradient(ofr, omp, sub_pairs, sub_poses)
+    assert np.linalg.norm(dxi.cpu().numpy() - odxi) <= TOL * np.linalg.norm(odxi)
+    odmu_all, odw_all = np.concatenate(odmu), np.concatenate(odw)
+    assert np.linalg.norm(dmu.cpu().numpy() - odmu_all) <= TOL * np.linalg.norm(odmu_all)
+    assert np.linalg.norm(dw.cpu().numpy() - odw_all) <= TOL * np.linalg.norm(odw_all)
 
 
 def test_odometry_window_gradient_full_size(G, ctx):
