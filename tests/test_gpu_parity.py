@@ -493,6 +493,37 @@ def test_gauss_newton_recovers_pose(G, ctx):
     assert ee.max() <= TOL and eH.max() <= TOL and eb.max() <= TOL, (ee.max(), eH.max(), eb.max())
 
 
+def test_corridor_parity_after_gauss_newton(G, ctx, corridor):
+    """The odometry window after Gauss-Newton on the current frame (the keyframes fixed): the
+    frame's 6 x 6 system is the sum of the source blocks of its 10 binary factors, solved on
+    the device; at the optimum, where b is the difference of large cancelling terms, the batch
+    still matches the oracle (P7, b against the cancellation-free scale)."""
+    from gpu_helpers import rel_errors
+    P = corridor
+    w = P.w
+    assert (w.pairs[:, 0] == 0).all()
+    plan = G.Plan(ctx, P.gframes, P.gmaps, w.pairs)
+    poses = w.poses.copy()
+    e0 = None
+    for _ in range(6):
+        e, H, b, _ = plan.linearize(poses)
+        e0 = e.sum() if e0 is None else e0
+        Hs = torch.as_tensor(H.sum(axis=0)[None], device="cuda")
+        bs = torch.as_tensor(b.sum(axis=0)[None], device="cuda")
+        xi, st = G.gn_solve(ctx, Hs, bs, dim=6)
+        assert st.cpu().numpy()[0] == 0
+        poses[0] = O.retract(poses[0], xi.cpu().numpy()[0])
+    e, H, b, inl = plan.linearize(poses)
+    assert e.sum() < e0
+    ref = P.oracle(poses=poses)
+    ref0 = P.oracle()
+    # the frame's gradient has shrunk (its factors' source blocks largely cancel now)
+    assert np.linalg.norm(ref["b"][:, :6].sum(axis=0)) < 0.1 * np.linalg.norm(ref0["b"][:, :6].sum(axis=0))
+    ee, eH, eb = rel_errors(e, H, b, ref)
+    assert np.array_equal(np.asarray(inl), ref["inliers"])
+    assert ee.max() <= TOL and eH.max() <= TOL and eb.max() <= TOL, (ee.max(), eH.max(), eb.max())
+
+
 # ---------------------------------------------------------------------------- overlap
 def test_overlap_matches_oracle(G, ctx, corridor):
     w = corridor.w

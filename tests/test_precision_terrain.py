@@ -60,6 +60,24 @@ def test_terrain_precision_all_accumulation_modes():
                        "H_max_elementwise_rel": float(np.abs(H[0] - ref["H"][0]).max() / np.abs(ref["H"][0]).max())}
         assert np.array_equal(inl, ref["inliers"])
         assert ee.max() <= TOL and eH.max() <= TOL and eb.max() <= TOL, (name, table[name])
+    # after Gauss-Newton on the scan pose (unary factor: the map fixed, the 6 x 6 source block
+    # solved on the device), at the optimum where b cancels: the FP64-accumulation result
+    # against the oracle, b against the cancellation-free scale
+    poses = w.poses.copy()
+    for _ in range(4):
+        e, H, b, _ = G.linearize(ctx, frames, [None, vm], w.pairs, poses, accum_mode=G.ACC_FP64)
+        xi, st = G.gn_solve(ctx, torch.as_tensor(np.asarray(H), device=dev), torch.as_tensor(np.asarray(b), device=dev),
+                            dim=6)
+        assert st.cpu().numpy()[0] == 0
+        poses[0] = O.retract(poses[0], xi.cpu().numpy()[0])
+    e, H, b, inl = G.linearize(ctx, frames, [None, vm], w.pairs, poses, accum_mode=G.ACC_FP64)
+    ref_gn = O.linearize(of, [None, om], w.pairs, poses, want_comp=True)
+    assert np.linalg.norm(ref_gn["b"][0, :6]) < 0.1 * np.linalg.norm(ref["b"][0, :6])
+    assert np.array_equal(inl, ref_gn["inliers"])
+    ee, eH, eb = rel_errors(e, H, b, ref_gn)
+    table["fp64_after_gauss_newton"] = {"e": float(ee[0]), "H": float(eH[0]), "b": float(eb[0]),
+                                        "b_plain": float(b_rel_plain(b, ref_gn)[0]), "inliers": int(inl[0])}
+    assert ee.max() <= TOL and eH.max() <= TOL and eb.max() <= TOL, table["fp64_after_gauss_newton"]
     oe = abs(ref["e"][0] - ref["comp_e"][0]) / ref["e"][0]
     oH = np.linalg.norm(ref["H"][0] - ref["comp_H"][0]) / np.linalg.norm(ref["comp_H"][0])
     table["oracle_fp64_vs_long_double"] = {"e": float(oe), "H": float(oH)}
