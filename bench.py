@@ -317,10 +317,12 @@ def small_workloads(G, ctx, dev):
     w = synth.corridor()
     frames, maps = prep(w)
     plan = G.Plan(ctx, frames, maps, w.pairs)
+    o_tuned = plan.autotune(w.poses)
     plan.set_poses(w.poses)
     out["odometry_window"] = {
         "workload": "corridor: 30k-pt frame vs 10 keyframes of 15k-40k pts, 0.5 m, 10 binary factors",
         "pair_points": w.n_pair_points,
+        "launch": {"block": o_tuned["block"], "pts_per_thread": o_tuned["pts_per_thread"], "autotuned": True},
         "graph_launch_ms": med(plan.launch),
         "e2e_plan_linearize_ms": med(lambda: plan.linearize(w.poses)),
         "plain_per_factor_ms": med(lambda: G.linearize(ctx, frames, maps, w.pairs, w.poses, plain=True), reps=10),
@@ -461,7 +463,11 @@ def small_workloads(G, ctx, dev):
         del flush
         return cold, warm
 
+    # the default launch shape (256 threads, 16 points per thread: 245 items, one wave): the
+    # autotuner times back-to-back launches, whose warm L2 favours fewer, longer items than a
+    # cold launch does
     plant = G.Plan(ctx, ft, mt, wt.pairs)
+    t_opts = plant.opts()
     plant.set_poses(wt.poses)
     t_ms, t_warm = terrain_times(plant)
     box = mt[tgt].info(0)["capacity"]
@@ -470,6 +476,8 @@ def small_workloads(G, ctx, dev):
                       "kernel_ms": t_ms, "kernel_ms_note": "cold L2 (256 MB written before each launch)",
                       "kernel_ms_back_to_back": t_warm, "points_per_s": wt.n_pair_points / (t_ms / 1e3),
                       "e2e_plan_linearize_ms": med(lambda: plant.linearize(wt.poses), reps=10),
+                      "launch": {"block": t_opts["block"], "pts_per_thread": t_opts["pts_per_thread"],
+                                 "autotuned": False},
                       "voxels": mt[tgt].info(0)["n_voxels"], "grid_cells": box,
                       "grid_gb": box * 48 / 1e9, "dense_grid": bool(mt[tgt].is_dense(0))}
     pk = peaks()

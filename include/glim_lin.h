@@ -370,7 +370,9 @@ glim_status glim_plan_launch_timed(glim_plan* plan, int32_t slot);
  * milliseconds to ms_out (host array of nslots floats). */
 glim_status glim_plan_kernel_ms(glim_plan* plan, int32_t nslots, float* ms_out);
 /* Autotuner: time every (block, pts_per_thread) candidate of the persistent kernel on this
- * plan's batch at poses12 with CUDA events (`iters` timed launches each, after one warm-up),
+ * plan's batch at poses12 with CUDA events (`iters` timed launches each, after one warm-up):
+ * block 128 or 256 with 4, 8, 16, 32 or 64 points per thread, and per block size the points
+ * per thread that make the batch's tiles about one resident wave of blocks;
  * keep the fastest in the plan, and write it to best_out (may be NULL).  On an error the
  * plan returns to its original configuration where that succeeds, and otherwise keeps the
  * last configuration that did: it stays launchable either way. */

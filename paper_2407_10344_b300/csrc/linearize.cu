@@ -913,12 +913,28 @@ extern "C" glim_status glim_plan_autotune(glim_plan* p, const double* poses12, i
     cudaEventDestroy(e0);
     return set_error(ctx, GLIM_ECUDA, "plan_autotune: cudaEventCreate failed");
   }
-  const int blocks[] = {128, 256};
-  const int ppts[] = {8, 16, 32, 64};
-  for (int c = 0; c < 8 && st == GLIM_OK; ++c) {
+  // candidates: block 128 or 256 with 4 to 64 points per thread, plus per block size the
+  // points per thread that make the batch's tiles one resident wave of the persistent kernel
+  // (small batches: an under-filled or ragged last wave decides their time)
+  int64_t total = 0;
+  for (int q = 0; q < p->npairs; ++q) total += p->frames[p->pairs[q].src_frame].n;
+  std::vector<std::pair<int, int>> cand;
+  for (int b : {128, 256}) {
+    for (int t : {4, 8, 16, 32, 64}) cand.emplace_back(b, t);
+    const int lane = base.kernel == 1 ? 0 : (p->d_dmaps ? 1 : (p->d_hmaps ? 2 : 0));
+    const LinKernelInfo ki = pick_kernel(b, base.accum_mode, p->lmax, lane);
+    int per_sm = 0;
+    if (ki.fn && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki.fn, b, ki.smem) == cudaSuccess &&
+        per_sm > 0) {
+      const int64_t slots = int64_t(per_sm) * ctx->num_sms * b;
+      const int fill = int(std::min<int64_t>(256, std::max<int64_t>(1, (total + slots - 1) / slots)));
+      if (fill != 4 && fill != 8 && fill != 16 && fill != 32 && fill != 64) cand.emplace_back(b, fill);
+    }
+  }
+  for (size_t c = 0; c < cand.size() && st == GLIM_OK; ++c) {
     glim_lin_opts o = base;
-    o.block = blocks[c / 4];
-    o.pts_per_thread = ppts[c % 4];
+    o.block = cand[c].first;
+    o.pts_per_thread = cand[c].second;
     o.persistent = 1;
     o.blocks_per_sm = 0;
     st = plan_configure(p, o);
@@ -952,7 +968,12 @@ extern "C" glim_status glim_plan_autotune(glim_plan* p, const double* poses12, i
     return st;
   }
   st = plan_configure(p, best);
-  if (st != GLIM_OK) return st;
+  if (st != GLIM_OK) {  // the plan still holds the last candidate: back to the original one
+    const std::string msg = ctx->err;
+    plan_configure(p, base);
+    ctx->err = msg;
+    return st;
+  }
   if (best_out) *best_out = best;
   if (best_ms_out) *best_ms_out = best_ms;
   return GLIM_OK;
