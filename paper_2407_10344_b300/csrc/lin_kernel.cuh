@@ -482,8 +482,9 @@ static_assert(sizeof(DenseLevelDev) == 32 && sizeof(HashLevelDev) == 32 && offse
               "lane-kernel descriptors must sit on 16-byte boundaries");
 
 // What a lane has read for one point: the transformed point, its weight and covariance, and
-// the voxel records of every level (for a hash table the home slot).  Split from the
-// arithmetic so that one point's reads can be in flight while the previous point is computed.
+// the voxel records of every level (on hashed levels, once hash_resolve has found the cell).
+// Split from the arithmetic so that one point's reads can be in flight while the previous
+// point is computed.
 template <int LMAX>
 struct LaneFetch {
   float3 q;
