@@ -430,14 +430,16 @@ def test_backward_matches_oracle_gradient(G, ctx, full, layout):
     assert np.linalg.norm(dw.cpu().numpy() - odw_all) <= 1e-4 * np.linalg.norm(odw_all)
 
 
-@pytest.mark.parametrize("full", [True, False])
-def test_backward_pipelined_and_general_kernels_agree(G, ctx, full):
+@pytest.mark.parametrize("full,n_kf,n_cur", [(True, 4, 6000), (False, 4, 6000), (True, 18, 1_300_000)])
+def test_backward_pipelined_and_general_kernels_agree(G, ctx, full, n_kf, n_cur):
     """The gradient pass of a batch whose target maps are all dense grids, or all hashed, runs
     the pipelined per-lane kernel; a batch that mixes the layouts runs the general kernel.  On
     the same voxels (the maps of one batch built in both layouts) the three give the same
-    gradient up to FP32 rounding, with three levels and surface validation."""
+    gradient up to FP32 rounding, with three levels and surface validation.  With 18 keyframes
+    and a 1.3M-point current frame the batch has enough tiles for one group per frame, which
+    the 16-pair limit of a group splits in two."""
     from gpu_helpers import Prepared
-    w = synth.corridor(n_cur=6000, kf_range=(3000, 5000), n_kf=4, weights=True)
+    w = synth.corridor(n_cur=n_cur, kf_range=(3000, 5000), n_kf=n_kf, weights=True)
     w.resolutions = [0.5, 1.0, 2.0]
     P = Prepared(ctx, w)
     targets = sorted(set(int(t) for t in w.pairs[:, 1]))
