@@ -333,11 +333,11 @@ __device__ __forceinline__ void bwl_point(const View& V, const LaneFetch<LMAX>& 
     const float det = sa * A00 + sb * A01 + sc * A02;
     const bool ok = hit && det > 0.f && det < INFINITY;
     const float id = __fdividef(1.f, det);
-    const float O00 = A00 * id, O01 = A01 * id, O02 = A02 * id, O11 = A11 * id, O12 = A12 * id, O22 = A22 * id;
     const float d0 = v1.x - q.x, d1 = v1.y - q.y, d2 = v1.z - q.z;
-    const float y0 = O00 * d0 + O01 * d1 + O02 * d2;
-    const float y1 = O01 * d0 + O11 * d1 + O12 * d2;
-    const float y2 = O02 * d0 + O12 * d1 + O22 * d2;
+    // y = Omega d = adj(S) d / det (Omega itself is not needed here)
+    const float y0 = (A00 * d0 + A01 * d1 + A02 * d2) * id;
+    const float y1 = (A01 * d0 + A11 * d1 + A12 * d2) * id;
+    const float y2 = (A02 * d0 + A12 * d1 + A22 * d2) * id;
     const float el = d0 * y0 + d1 * y1 + d2 * y2;
     // a term that is a miss or not positive definite adds nothing: its additions are
     // predicated on `ok` (its values need not be finite, so it is not multiplied by zero);
