@@ -539,7 +539,10 @@ int backward_lane_occupancy(const glim_plan* p) {
     default: fn = dense ? reinterpret_cast<const void*>(k_backward_lane<4, false>) : reinterpret_cast<const void*>(k_backward_lane<4, true>); break;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BWL_BLOCK, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BWL_BLOCK, 0) != cudaSuccess) {
+    cudaGetLastError();  // the general kernel runs instead
+    return 0;
+  }
   return std::max(per_sm, 1);
 }
 

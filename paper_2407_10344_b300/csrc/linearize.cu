@@ -924,8 +924,11 @@ extern "C" glim_status glim_plan_autotune(glim_plan* p, const double* poses12, i
     const int lane = base.kernel == 1 ? 0 : (p->d_dmaps ? 1 : (p->d_hmaps ? 2 : 0));
     const LinKernelInfo ki = pick_kernel(b, base.accum_mode, p->lmax, lane);
     int per_sm = 0;
-    if (ki.fn && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki.fn, b, ki.smem) == cudaSuccess &&
-        per_sm > 0) {
+    if (ki.fn && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki.fn, b, ki.smem) != cudaSuccess) {
+      cudaGetLastError();  // a failed query only drops this candidate
+      per_sm = 0;
+    }
+    if (per_sm > 0) {
       const int64_t slots = int64_t(per_sm) * ctx->num_sms * b;
       const int fill = int(std::min<int64_t>(256, std::max<int64_t>(1, (total + slots - 1) / slots)));
       if (fill != 4 && fill != 8 && fill != 16 && fill != 32 && fill != 64) cand.emplace_back(b, fill);
