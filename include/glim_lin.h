@@ -414,6 +414,23 @@ glim_status glim_plan_backward(glim_plan* plan, const double* poses12, int32_t o
 
 /* ---------------------------------------------------------------- Gauss-Newton step */
 
+/* Gauss-Newton on the device for one frame with every other frame fixed (Sec. III-C: the
+ * quadratic factors' Gauss-Newton step, xi = -H^-1 b, and the pose update T <- T Exp(xi)):
+ * starting from poses12 (host, nframes x 12 doubles), `iters` times linearize the plan's
+ * batch, sum the 6 x 6 systems of `frame` over the pairs in pair order (the source block
+ * H[0:6, 0:6], b[0:6] of the pairs whose source it is, the target block H[6:12, 6:12],
+ * b[6:12] of the pairs whose target it is), solve by Cholesky in FP64 and update the frame's
+ * pose on the device, T <- T Exp(xi), xi = [omega; v], Exp(xi) = [Exp(omega) | V v]
+ * (Rodrigues; V the left Jacobian of SO(3)).  No host round trip between iterations.
+ * Writes the final poses to poses12_out (host, nframes x 12), the batch's total cost at each
+ * linearization to cost_out (host, iters doubles, may be NULL) and GLIM_OK, or GLIM_ENOTPD
+ * when a system was not positive definite (that iteration takes no step), to *status_out
+ * (may be NULL).  The plan's device poses are the final ones afterwards; its outputs hold
+ * the last linearization (at the poses before the last step).  Synchronizes.  GLIM_EINVAL
+ * for a bad frame index, iters < 1 or a plan whose maps changed. */
+glim_status glim_plan_gauss_newton(glim_plan* plan, const double* poses12, int32_t frame, int32_t iters,
+                                   double* poses12_out, double* cost_out, int32_t* status_out);
+
 /* Solve `count` systems H xi = -b by Cholesky in FP64 on the device (Sec. III-C: the
  * Gauss-Newton step of the quadratic factor).  System i uses the dim x dim block
  * H[i * stride_H + r * ldh + c] and b[i * stride_b + r]; xi_out is count x dim; status_out

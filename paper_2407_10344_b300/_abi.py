@@ -81,6 +81,7 @@ SIGNATURES = {
     "glim_backward": (_i32, [_vp, C.POINTER(Frame), _i32, C.POINTER(Pair), _i32, _vp, _i32, _i32, _vp, _vp,
                              _vp]),
     "glim_plan_backward": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
+    "glim_plan_gauss_newton": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp]),
     "glim_gn_solve": (_i32, [_vp, _vp, _i32, _i64, _vp, _i64, _i32, _i64, _vp, _vp]),
     "glim_graph_step": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _i32, _f64, _vp, _vp, _vp]),
 }

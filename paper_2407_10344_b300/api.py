@@ -470,6 +470,20 @@ class Plan:
                       _ptr(dxi), _ptr(dmu), _ptr(dw))
         return dxi, dmu, dw
 
+    def gauss_newton(self, poses, frame, iters=10):
+        """Gauss-Newton on the device for `frame` with the other frames fixed: `iters`
+        linearizations and steps without a host round trip.  Returns the final poses
+        (nframes, 3, 4), the batch's total cost at each linearization (iters,) and the status
+        (0, or the code for a system that was not positive definite)."""
+        self._maps_alive()
+        Pz = _poses(poses, self.nframes)
+        out = np.empty_like(Pz)
+        cost = np.empty(int(iters), np.float64)
+        st = C.c_int32(0)
+        self.ctx.call("plan_gauss_newton", self.ctx.lib.glim_plan_gauss_newton, self.h, _ptr(Pz), int(frame),
+                      int(iters), _ptr(out), _ptr(cost), C.byref(st))
+        return out.reshape(-1, 3, 4), cost, int(st.value)
+
     def launch(self):
         self._maps_alive()
         self.ctx.call("plan_launch", self.ctx.lib.glim_plan_launch, self.h)

@@ -194,6 +194,8 @@ void drop_graphs(glim_plan* p) {
   if (p->g_full) cudaGraphExecDestroy(p->g_full);
   if (p->g_dev) cudaGraphExecDestroy(p->g_dev);
   p->g_full = p->g_dev = nullptr;
+  gn_graph_free(p->gn);
+  p->gn = nullptr;
 }
 
 }  // namespace
@@ -670,6 +672,231 @@ extern "C" glim_status glim_plan_set_poses(glim_plan* p, const double* poses12) 
   // the pinned block may still be read by an earlier upload
   GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return plan_upload_poses(p, poses12);
+}
+
+namespace {
+
+// ---------------------------------------------------------------- Gauss-Newton on the device
+// S9 (Sec. III-C, "Linearization" and the Gauss-Newton step it feeds): the 6 x 6 system of one
+// frame with every other frame fixed, summed over the pairs in pair order (the source block
+// of the pairs whose source it is, the target block of the pairs whose target it is), and the
+// batch's total cost; FP64.
+__global__ void k_gn_frame_system(const double* __restrict__ e, const double* __restrict__ H,
+                                  const double* __restrict__ b, const int2* __restrict__ pair_frames, int npairs,
+                                  int frame, double* __restrict__ sys, double* __restrict__ cost) {
+  const int i = threadIdx.x;  // 0..35: H (row-major), 36..41: b, 42: the cost
+  if (i > 42) return;
+  double s = 0.0;
+  for (int q = 0; q < npairs; ++q) {
+    const int2 f = pair_frames[q];
+    if (i == 42) {
+      s += e[q];
+      continue;
+    }
+    for (int side = 0; side < 2; ++side) {  // source block, then target block
+      if ((side == 0 ? f.x : f.y) != frame) continue;
+      const int o = 6 * side;
+      s += i < 36 ? H[144 * int64_t(q) + 12 * (o + i / 6) + o + i % 6] : b[12 * int64_t(q) + o + i - 36];
+    }
+  }
+  if (i == 42) *cost = s;
+  else sys[i] = s;
+}
+
+// xi = -H^-1 b by Cholesky (a system that is not positive definite takes no step and sets
+// *status), then T_frame <- T_frame Exp(xi) with Exp(xi) = [Exp(omega) | V v] (Rodrigues; V the
+// left Jacobian of SO(3)), in FP64.
+__global__ void k_gn_frame_step(const double* __restrict__ sys, double* __restrict__ T, int32_t* __restrict__ status) {
+  double L[6][6], x[6];
+  bool ok = true;
+  for (int j = 0; j < 6 && ok; ++j) {
+    double d = sys[6 * j + j];
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    if (!(d > 0.0) || !isfinite(d)) {
+      ok = false;
+      break;
+    }
+    L[j][j] = sqrt(d);
+    for (int i = j + 1; i < 6; ++i) {
+      double v = sys[6 * i + j];
+      for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+      L[i][j] = v / L[j][j];
+    }
+  }
+  if (!ok) {
+    *status = GLIM_ENOTPD;
+    return;
+  }
+  double y[6];
+  for (int i = 0; i < 6; ++i) {  // L y = -b
+    double v = -sys[36 + i];
+    for (int k = 0; k < i; ++k) v -= L[i][k] * y[k];
+    y[i] = v / L[i][i];
+  }
+  for (int i = 5; i >= 0; --i) {  // L^T x = y
+    double v = y[i];
+    for (int k = i + 1; k < 6; ++k) v -= L[k][i] * x[k];
+    x[i] = v / L[i][i];
+  }
+  const double w[3] = {x[0], x[1], x[2]}, u[3] = {x[3], x[4], x[5]};
+  const double th = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  const double K[3][3] = {{0.0, -w[2], w[1]}, {w[2], 0.0, -w[0]}, {-w[1], w[0], 0.0}};
+  double K2[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) K2[r][c] = K[r][0] * K[0][c] + K[r][1] * K[1][c] + K[r][2] * K[2][c];
+  double a, bb, cc;  // Exp(omega) = I + a K + bb K^2, V = I + bb K + cc K^2
+  if (th < 1e-12) {
+    a = 1.0;
+    bb = 0.5;
+    cc = 1.0 / 6.0;
+  } else {
+    a = sin(th) / th;
+    bb = (1.0 - cos(th)) / (th * th);
+    cc = (th - sin(th)) / (th * th * th);
+  }
+  double E[3][3], Vv[3];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) E[r][c] = (r == c ? 1.0 : 0.0) + a * K[r][c] + bb * K2[r][c];
+    double v = u[r];
+    for (int c = 0; c < 3; ++c) v += (bb * K[r][c] + cc * K2[r][c]) * u[c];
+    Vv[r] = v;
+  }
+  double Rn[3][3], tn[3];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) Rn[r][c] = T[4 * r] * E[0][c] + T[4 * r + 1] * E[1][c] + T[4 * r + 2] * E[2][c];
+    tn[r] = T[4 * r] * Vv[0] + T[4 * r + 1] * Vv[1] + T[4 * r + 2] * Vv[2] + T[4 * r + 3];
+  }
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) T[4 * r + c] = Rn[r][c];
+    T[4 * r + 3] = tn[r];
+  }
+}
+
+}  // namespace
+
+namespace glim_detail {
+
+struct GnGraph {
+  cudaGraphExec_t exec = nullptr;
+  int frame = -1, iters = 0;
+  double* sys = nullptr;   // device: the frame's 6 x 6 system and b
+  double* cost = nullptr;  // device: the batch's cost per iteration
+  int32_t* st = nullptr;   // device: status
+  double* h_cost = nullptr;  // pinned: the costs read back by the graph
+  int32_t* h_st = nullptr;   // pinned: the status read back by the graph
+};
+
+void gn_graph_free(GnGraph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  cudaFree(g->sys);
+  cudaFree(g->cost);
+  cudaFree(g->st);
+  cudaFreeHost(g->h_cost);
+  cudaFreeHost(g->h_st);
+  delete g;
+}
+
+}  // namespace glim_detail
+
+namespace {
+
+// The device loop of glim_plan_gauss_newton on ctx->stream: reset, the upload of the staged
+// frame poses, `iters` x (pair poses, linearization, the frame's system, step), the final pair
+// poses, and the read-back of the poses (into the plan's pinned staging block), costs and status.
+glim_status gn_enqueue(glim_plan* p, const GnGraph& g) {
+  glim_ctx* ctx = p->ctx;
+  GLIM_CUDA(ctx, cudaMemsetAsync(g.st, 0, sizeof(int32_t), ctx->stream));
+  GLIM_CUDA(ctx, cudaMemsetAsync(g.cost, 0, size_t(g.iters) * sizeof(double), ctx->stream));
+  GLIM_CUDA(ctx, cudaMemcpyAsync(p->d_fposes, p->h_fposes, size_t(p->nframes) * 12 * sizeof(double),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+  for (int it = 0; it <= g.iters; ++it) {
+    if (p->npairs > 0) {  // the last packing makes the pairs' device poses follow the final frame poses
+      k_pack_poses<<<ceil_div_i(p->npairs, 128), 128, 0, ctx->stream>>>(p->d_fposes, p->d_pair_frames, p->npairs,
+                                                                         p->in_pose32(), p->in_pose64());
+      GLIM_LAUNCHED(ctx);
+    }
+    if (it == g.iters) break;
+    glim_status s = plan_enqueue_kernels(p);
+    if (s != GLIM_OK) return s;
+    k_gn_frame_system<<<1, 64, 0, ctx->stream>>>(p->out_e(), p->out_H(), p->out_b(), p->d_pair_frames, p->npairs,
+                                                 g.frame, g.sys, g.cost + it);
+    GLIM_LAUNCHED(ctx);
+    k_gn_frame_step<<<1, 1, 0, ctx->stream>>>(g.sys, p->d_fposes + 12 * int64_t(g.frame), g.st);
+    GLIM_LAUNCHED(ctx);
+  }
+  GLIM_CUDA(ctx, cudaMemcpyAsync(p->h_fposes, p->d_fposes, size_t(p->nframes) * 12 * sizeof(double),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+  GLIM_CUDA(ctx, cudaMemcpyAsync(g.h_cost, g.cost, size_t(g.iters) * sizeof(double), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  GLIM_CUDA(ctx, cudaMemcpyAsync(g.h_st, g.st, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  return GLIM_OK;
+}
+
+}  // namespace
+
+extern "C" glim_status glim_plan_gauss_newton(glim_plan* p, const double* poses12, int32_t frame, int32_t iters,
+                                              double* poses12_out, double* cost_out, int32_t* status_out) {
+  GLIM_RANGE("glim_plan_gauss_newton");
+  if (!p || !poses12 || !poses12_out) return GLIM_EINVAL;
+  glim_ctx* ctx = p->ctx;
+  if (frame < 0 || frame >= p->nframes || iters < 1)
+    return set_error(ctx, GLIM_EINVAL, "plan_gauss_newton: bad frame %d or iterations %d", frame, iters);
+  if (maps_current(p) != GLIM_OK) return GLIM_EINVAL;
+  DeviceGuard device_guard;
+  GLIM_CUDA(ctx, device_guard.set(ctx->device));
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the pinned staging block may be in use
+  if (p->gn && (p->gn->frame != frame || p->gn->iters != iters)) {
+    gn_graph_free(p->gn);
+    p->gn = nullptr;
+  }
+  if (!p->gn) {
+    GnGraph* g = new GnGraph;
+    g->frame = frame;
+    g->iters = iters;
+    if (dmalloc(&g->sys, 42 * sizeof(double)) != cudaSuccess ||
+        dmalloc(&g->cost, size_t(iters) * sizeof(double)) != cudaSuccess ||
+        dmalloc(&g->st, sizeof(int32_t)) != cudaSuccess ||
+        hmalloc(&g->h_cost, size_t(iters) * sizeof(double)) != cudaSuccess ||
+        hmalloc(&g->h_st, sizeof(int32_t)) != cudaSuccess) {
+      gn_graph_free(g);
+      return set_error(ctx, GLIM_ENOMEM, "plan_gauss_newton: allocation failed");
+    }
+    if (p->use_graph) {  // the loop as one graph, captured once per (frame, iterations)
+      cudaGraph_t graph = nullptr;
+      cudaError_t ce = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+      if (ce != cudaSuccess) {
+        gn_graph_free(g);
+        return cuda_check(ctx, ce, "plan_gauss_newton: begin capture");
+      }
+      const glim_status st = gn_enqueue(p, *g);
+      ce = cudaStreamEndCapture(ctx->stream, &graph);
+      if (st == GLIM_OK && ce == cudaSuccess) ce = cudaGraphInstantiate(&g->exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (st != GLIM_OK || ce != cudaSuccess) {
+        gn_graph_free(g);
+        return st != GLIM_OK ? st : cuda_check(ctx, ce, "plan_gauss_newton: graph");
+      }
+    }
+    p->gn = g;
+  }
+  plan_stage_poses(p, poses12);
+  if (p->gn->exec) {
+    GLIM_CUDA(ctx, cudaGraphLaunch(p->gn->exec, ctx->stream));
+    ctx->launches += (p->npairs > 0 ? iters + 1 : 0) + iters * (2 + glim_plan_kernels_per_launch(p));
+  } else {
+    const glim_status st = gn_enqueue(p, *p->gn);
+    if (st != GLIM_OK) return st;
+  }
+  GLIM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  // h_fposes now holds the final poses, which the device pose block also holds (its outputs:
+  // the last linearization, at the poses before the last step)
+  std::memcpy(poses12_out, p->h_fposes, size_t(p->nframes) * 12 * sizeof(double));
+  p->fposes_on_device = true;
+  if (cost_out) std::memcpy(cost_out, p->gn->h_cost, size_t(iters) * sizeof(double));
+  if (status_out) *status_out = *p->gn->h_st;
+  ctx->err.clear();
+  return GLIM_OK;
 }
 
 extern "C" glim_status glim_plan_relative_poses(glim_plan* p, double* rt64_out, float* pose32_out) {

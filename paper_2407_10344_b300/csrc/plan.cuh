@@ -100,6 +100,10 @@ struct PairView {
 // bwd_scratch_free.
 struct BwdScratch;
 void bwd_scratch_free(BwdScratch* sc);
+// The captured device Gauss-Newton loop of a plan (one frame, a number of iterations) and
+// its buffers; freed by gn_graph_free.
+struct GnGraph;
+void gn_graph_free(GnGraph* g);
 
 using LinKernel = void (*)(const LinArgs);
 struct LinKernelInfo {
@@ -164,6 +168,7 @@ struct glim_plan {
   bool use_graph = true;
   cudaGraphExec_t g_full = nullptr;  // upload + kernels + download
   cudaGraphExec_t g_dev = nullptr;   // kernels only
+  GnGraph* gn = nullptr;             // glim_plan_gauss_newton's captured loop
   BwdScratch* bwd = nullptr;         // gradient pass scratch (glim_plan_backward)
 
   PoseF* in_pose32() const { return reinterpret_cast<PoseF*>(d_in); }

@@ -142,13 +142,24 @@ def run_all(G, batch):
     plan.close()
     plan_b.close()
 
+    # the device Gauss-Newton loop's buffers and graph: a failure leaves the plan as it was
+    plan_g = G.Plan(ctx, frames, maps, w.pairs)
+    ref_g = [np.asarray(x).copy() for x in plan_g.linearize(w.poses)]
+
+    def gn_plan_unchanged():
+        for a, b in zip(plan_g.linearize(w.poses), ref_g):
+            assert np.array_equal(np.asarray(a), b)
+
+    counts["gauss_newton"] = sweep(G, lambda: plan_g.gauss_newton(w.poses, 0, 2), gn_plan_unchanged)
+    plan_g.close()
+
     e, H, b, _ = G.linearize(ctx, frames, maps, w.pairs, w.poses, out="cuda")
     counts["graph_step"] = sweep(G, lambda: G.graph_step(ctx, w.pairs, len(frames), H, b), same_as_before)
     counts["gn_solve"] = sweep(G, lambda: G.gn_solve(ctx, H, b), same_as_before)
 
     # every operation that allocates reached its failure paths at least once
     for name in ("context", "covariances", "voxelmap_auto", "voxelmap_hash", "insert", "plan", "one_shot",
-                 "backward", "plan_backward", "autotune", "graph_step"):
+                 "backward", "plan_backward", "autotune", "gauss_newton", "graph_step"):
         assert counts[name] >= 1, (name, counts)
     same_as_before()
     return counts

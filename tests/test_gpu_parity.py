@@ -526,6 +526,51 @@ def test_corridor_parity_after_gauss_newton(G, ctx, corridor):
     assert ee.max() <= TOL and eH.max() <= TOL and eb.max() <= TOL, (ee.max(), eH.max(), eb.max())
 
 
+def test_gauss_newton_on_the_device_matches_the_host_loop(G, ctx, corridor):
+    """glim_plan_gauss_newton (linearize, per-frame 6 x 6 system, Cholesky, T <- T Exp(xi),
+    all on the device) against the same iterations driven from the host (device Cholesky,
+    pose update in FP64 on the host): the box room's unary factor and the odometry window's
+    current frame against 10 fixed keyframes.  The poses agree to FP64 rounding (the update's
+    sine and cosine come from different libraries), the costs to 1e-9; a frame of no pair has
+    a zero system and takes no step."""
+    from gpu_helpers import Prepared
+    P = Prepared(ctx, synth.box_room(sigma=0.0))
+    for prep, iters in ((P, 10), (corridor, 6)):
+        w = prep.w
+        plan = G.Plan(ctx, prep.gframes, prep.gmaps, w.pairs)
+        poses = w.poses.copy()
+        costs = []
+        for _ in range(iters):
+            e, H, b, _ = plan.linearize(poses)
+            costs.append(float(np.sum(e)))
+            Hs = torch.as_tensor(H[w.pairs[:, 0] == 0].sum(axis=0)[None], device="cuda")
+            bs = torch.as_tensor(b[w.pairs[:, 0] == 0].sum(axis=0)[None], device="cuda")
+            xi, st = G.gn_solve(ctx, Hs, bs, dim=6)
+            poses[0] = O.retract(poses[0], xi.cpu().numpy()[0])
+        out, cost, status = plan.gauss_newton(w.poses, 0, iters)
+        assert status == 0
+        out2, cost2, _ = plan.gauss_newton(w.poses, 0, iters)  # the cached loop, replayed
+        assert np.array_equal(out2, out) and np.array_equal(cost2, cost)
+        assert np.abs(out - poses).max() <= 1e-9, np.abs(out - poses).max()
+        assert np.array_equal(out[1:], w.poses[1:])
+        np.testing.assert_allclose(cost, costs, rtol=1e-9)
+        # the plan's device poses are the final ones: a gradient at those poses uploads nothing
+        # and equals the one-shot gradient there
+        g_plan = plan.backward(out)
+        g_one = G.backward(ctx, prep.gframes, prep.gmaps, w.pairs, out)
+        for a, b_ in zip(g_plan, g_one):
+            assert torch.equal(a, b_)
+        plan.close()
+    # a frame that is in no pair: its system is zero, no step is taken
+    w = P.w
+    frames = P.gframes + [P.gframes[0]]
+    plan = G.Plan(ctx, frames, P.gmaps + [None], w.pairs)
+    poses = np.concatenate([w.poses, w.poses[:1]])
+    out, cost, status = plan.gauss_newton(poses, 2, 2)
+    assert status == -6 and np.array_equal(out, poses)  # GLIM_ENOTPD
+    plan.close()
+
+
 # ---------------------------------------------------------------------------- overlap
 def test_overlap_matches_oracle(G, ctx, corridor):
     w = corridor.w
