@@ -329,6 +329,9 @@ def small_workloads(G, ctx, dev):
     }
     out["odometry_window"]["speedup_vs_plain"] = (out["odometry_window"]["plain_per_factor_ms"] /
                                                   out["odometry_window"]["e2e_plan_linearize_ms"])
+    # odometry: Gauss-Newton on the current frame against the fixed keyframes, on the device
+    out["odometry_window"]["gauss_newton_6_iterations_device_ms"] = med(lambda: plan.gauss_newton(w.poses, 0, 6),
+                                                                        reps=10)
     # differentiable cost on the odometry window (with per-point weights)
     ww = synth.corridor(weights=True)
     fr2, mp2 = prep(ww)
