@@ -380,6 +380,11 @@ def test_invalid_arguments(G, ctx, room):
         G.linearize(ctx, room.gframes, room.gmaps, [[0, 1]], room.w.poses, block=96)
     with pytest.raises(ValueError):
         G.linearize(ctx, room.gframes, room.gmaps, [[0, 0]], room.w.poses)  # frame 0 has no voxelmap
+    plan = G.Plan(ctx, room.gframes, room.gmaps, room.w.pairs)
+    for frame, iters in ((-1, 2), (len(room.gframes), 2), (0, 0)):
+        with pytest.raises(G.GlimError, match="EINVAL"):
+            plan.gauss_newton(room.w.poses, frame, iters)
+    plan.close()
 
 
 # ---------------------------------------------------------------------------- covariances
