@@ -345,6 +345,36 @@ def test_lane_kernels_mixed_levels_ragged_and_nonfinite(G, ctx, layout):
             assert ee.max() <= TOL and eH.max() <= TOL and eb.max() <= TOL, (kernel, block, ppt)
 
 
+@pytest.mark.parametrize("layout", ["dense", "hash"])
+def test_four_level_maps(G, ctx, layout):
+    """Maps of four levels (0.25 / 0.5 / 1 / 2 m; the kernels' largest level count): the
+    per-lane and general linearization, their correspondence ids, and the gradient (the
+    pipelined per-lane kernel) against the oracle, with surface validation."""
+    from gpu_helpers import rel_errors
+    w = synth.corridor(n_kf=3, n_cur=8000, kf_range=(5000, 7000), weights=True)
+    w.resolutions = [0.25, 0.5, 1.0, 2.0]
+    from gpu_helpers import Prepared
+    P = Prepared(ctx, w, layout=layout)
+    assert all(P.gmaps[t].levels == 4 for t in set(int(t) for t in w.pairs[:, 1]))
+    ref = P.oracle(validate=True, want_ids=True)
+    for kernel in ("auto", "general"):
+        plan = G.Plan(ctx, P.gframes, P.gmaps, w.pairs, kernel=kernel, validate_surface=True)
+        e, H, b, inl = [np.array(x) for x in plan.linearize(w.poses)]
+        assert np.array_equal(inl, ref["inliers"])
+        ee, eH, eb = rel_errors(e, H, b, ref)
+        assert ee.max() <= TOL and eH.max() <= TOL and eb.max() <= TOL, (kernel, ee.max(), eH.max(), eb.max())
+        ids, _ = plan.correspondence_ids(w.poses)
+        assert np.array_equal(ids.cpu().numpy(), ref["ids"])
+        if kernel == "auto":
+            assert plan.opts()["kernel"] == layout
+            dxi, dmu, dw = plan.backward(w.poses)
+            odxi, odmu, odw = O.gradient(P.oframes, P.omaps, w.pairs, w.poses, validate=True)
+            assert np.linalg.norm(dxi.cpu().numpy() - odxi) <= TOL * np.linalg.norm(odxi)
+            odmu_all = np.concatenate(odmu)
+            assert np.linalg.norm(dmu.cpu().numpy() - odmu_all) <= TOL * np.linalg.norm(odmu_all)
+        plan.close()
+
+
 @pytest.mark.parametrize("validate", [False, True])
 def test_hash_kernel_and_general_kernel_on_hash_maps(G, ctx, room, validate):
     """Hash-table maps: the per-lane hash kernel (chosen automatically) and the general kernel
