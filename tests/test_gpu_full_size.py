@@ -8,7 +8,8 @@
   kernel's id-recording instantiation resolved, in the same launch configuration, bit for
   bit).  The plain relative error of b, |b - b*| / |b*|, is bounded as well.  The same step
   on hashed voxel blocks gives the same bits for all 4000 pairs (e, H, b, ids and the gradient);
-  the gradient of the sampled pairs matches the oracle's analytic gradient.
+  the gradient of the sampled pairs matches the oracle's analytic gradient; with surface
+  validation, sampled pairs match the oracle too.
 * Odometry window at its full size (30k-point frame, 10 keyframes, per-point weights): the
   gradient of the batch against the oracle's analytic gradient.
 """
@@ -98,6 +99,23 @@ def test_urban_global_step_full_size_sampled_pairs(G, ctx):
     for m in hmaps:
         if m is not None:
             m.free()
+    # the same step with surface validation (S3), sampled pairs against the oracle
+    plan_v = G.Plan(ctx, frames, maps, w.pairs, accum_mode=G.ACC_FP64, block=128, pts_per_thread=64,
+                    validate_surface=True)
+    e_v, H_v, b_v, inl_v = [np.array(x) for x in plan_v.linearize(w.poses)]
+    ids_v, _ = plan_v.correspondence_ids(w.poses)
+    for q in sample[:4]:
+        s, t = int(w.pairs[q, 0]), int(w.pairs[q, 1])
+        fs = O.Frame(frames[s].pts4.cpu().numpy(), frames[s].cov6.cpu().numpy(), frames[s].normal3.cpu().numpy())
+        ft = O.Frame(frames[t].pts4.cpu().numpy(), frames[t].cov6.cpu().numpy())
+        vm = O.VMap(ft.pts4, ft.cov6, w.resolutions)
+        ref = O.linearize([fs, ft], [None, vm], np.array([[0, 1]], np.int32), np.stack([w.poses[s], w.poses[t]]),
+                          validate=True, want_comp=True, want_ids=True)
+        assert inl_v[q] == ref["inliers"][0] and inl_v[q] < inl[q]
+        assert np.array_equal(ids_v[int(off[q]):int(off[q + 1])].cpu().numpy(), ref["ids"])
+        ee, eH, eb = rel_errors(e_v[q:q + 1], H_v[q:q + 1], b_v[q:q + 1], ref)
+        assert max(ee[0], eH[0], eb[0]) <= TOL
+    plan_v.close()
     used = sorted(set(int(v) for v in w.pairs[sample].ravel()))
     remap = {f: i for i, f in enumerate(used)}
     sub_pairs = np.array([[remap[int(a_)], remap[int(b_)]] for a_, b_ in w.pairs[sample]], np.int32)
