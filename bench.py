@@ -687,7 +687,7 @@ def run_ours(args):
     acc = {"fp32": G.ACC_FP32, "kahan": G.ACC_KAHAN, "fp64": G.ACC_FP64}[args.accum]
     block, ppt = args.block, args.ppt
     if sharded and block == 0 and ppt == 0:
-        block, ppt = 128, 64  # every rank uses the same tiles, so records are the single-GPU bits
+        block, ppt = 64, 64  # every rank uses the same tiles, so records are the single-GPU bits
     plan = G.Plan(ctx, frames, maps, w.pairs, accum_mode=acc, block=block, pts_per_thread=ppt)
     tuned = plan.autotune(w.poses, iters=2) if (args.autotune and not sharded) else None
     opts = plan.opts()

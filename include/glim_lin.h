@@ -99,7 +99,8 @@ typedef struct {
 /* Launch options of the linearization kernels.  Zero fields take defaults.
  *   validate_surface  1 = apply the surface-orientation test.
  *   accum_mode        GLIM_ACC_*.
- *   block             threads per block (128 or 256; default 256).
+ *   block             threads per block (64, 128 or 256, 64 for the per-lane dense-grid and
+ *                     hash kernels only; default 256).
  *   pts_per_thread    points per thread per work item (1..256; default 16);
  *                     a work item (tile) covers block * pts_per_thread points of one pair.
  *   blocks_per_sm     resident blocks per SM of the persistent kernel (default: occupancy).

@@ -171,7 +171,7 @@ void fill_defaults(glim_lin_opts& o) {
 }
 
 bool opts_valid(const glim_lin_opts& o) {
-  return (o.block == 128 || o.block == 256) &&
+  return (o.block == 64 || o.block == 128 || o.block == 256) &&
          (o.pts_per_thread >= 1 && o.pts_per_thread <= 256) &&
          (o.accum_mode >= 0 && o.accum_mode <= 2) && (o.persistent == 1 || o.persistent == 2) &&
          o.blocks_per_sm >= 0 && o.blocks_per_sm <= 32 && o.kernel >= 0 && o.kernel <= 3;
@@ -1146,9 +1146,10 @@ extern "C" glim_status glim_plan_autotune(glim_plan* p, const double* poses12, i
   int64_t total = 0;
   for (int q = 0; q < p->npairs; ++q) total += p->frames[p->pairs[q].src_frame].n;
   std::vector<std::pair<int, int>> cand;
-  for (int b : {128, 256}) {
+  const int lane = base.kernel == 1 ? 0 : (p->d_dmaps ? 1 : (p->d_hmaps ? 2 : 0));
+  for (int b : {64, 128, 256}) {
+    if (b == 64 && lane == 0) continue;  // 64-thread blocks: the per-lane kernels only
     for (int t : {4, 8, 16, 32, 64}) cand.emplace_back(b, t);
-    const int lane = base.kernel == 1 ? 0 : (p->d_dmaps ? 1 : (p->d_hmaps ? 2 : 0));
     const LinKernelInfo ki = pick_kernel(b, base.accum_mode, p->lmax, lane);
     int per_sm = 0;
     if (ki.fn && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ki.fn, b, ki.smem) != cudaSuccess) {

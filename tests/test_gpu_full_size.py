@@ -1,7 +1,7 @@
 """Parity at the benchmark's full sizes, in the launch configuration the benchmark times.
 
 * Urban global step (400 submaps of log-U[50k, 200k] points, 4000 pairs, 0.5 / 1 / 2 m): the
-  whole batch runs as one plan (dense-grid kernel, block 128, 64 points per thread, FP64
+  whole batch runs as one plan (dense-grid kernel, block 64, 64 points per thread, FP64
   cross-block sums, Z-ordered points, persistent work queue); a seeded sample of pairs is
   recomputed by the oracle one pair at a time on the same float32 inputs, and each sampled
   pair must match (inliers exactly, e / H / b within 1e-4, and the correspondence ids that the
@@ -50,7 +50,7 @@ def test_urban_global_step_full_size_sampled_pairs(G, ctx):
         frames.append(G.FrameData(p4, cov, nrm))
         if i in targets:
             maps[i] = G.VoxelMap(ctx, p4, cov, w.resolutions)
-    plan = G.Plan(ctx, frames, maps, w.pairs, accum_mode=G.ACC_FP64, block=128, pts_per_thread=64)
+    plan = G.Plan(ctx, frames, maps, w.pairs, accum_mode=G.ACC_FP64, block=64, pts_per_thread=64)
     assert plan.opts()["kernel"] == "dense"
     e, H, b, inl = [np.array(x) for x in plan.linearize(w.poses)]
     assert np.isfinite(e).all() and np.isfinite(H).all() and np.isfinite(b).all()
@@ -81,7 +81,7 @@ def test_urban_global_step_full_size_sampled_pairs(G, ctx):
     # the same arithmetic, so all 4000 pairs' e, H and b are the same bits.
     hmaps = [None if m is None else G.VoxelMap(ctx, frames[i].pts4, frames[i].cov6, w.resolutions, layout="hash")
              for i, m in enumerate(maps)]
-    plan_h = G.Plan(ctx, frames, hmaps, w.pairs, accum_mode=G.ACC_FP64, block=128, pts_per_thread=64)
+    plan_h = G.Plan(ctx, frames, hmaps, w.pairs, accum_mode=G.ACC_FP64, block=64, pts_per_thread=64)
     assert plan_h.opts()["kernel"] == "hash"
     e_h, H_h, b_h, inl_h = [np.array(x) for x in plan_h.linearize(w.poses)]
     assert np.array_equal(e_h, e) and np.array_equal(H_h, H) and np.array_equal(b_h, b)
@@ -100,7 +100,7 @@ def test_urban_global_step_full_size_sampled_pairs(G, ctx):
         if m is not None:
             m.free()
     # the same step with surface validation (S3), sampled pairs against the oracle
-    plan_v = G.Plan(ctx, frames, maps, w.pairs, accum_mode=G.ACC_FP64, block=128, pts_per_thread=64,
+    plan_v = G.Plan(ctx, frames, maps, w.pairs, accum_mode=G.ACC_FP64, block=64, pts_per_thread=64,
                     validate_surface=True)
     e_v, H_v, b_v, inl_v = [np.array(x) for x in plan_v.linearize(w.poses)]
     ids_v, _ = plan_v.correspondence_ids(w.poses)

@@ -182,7 +182,7 @@ def test_linearize_grid_variant_and_autotune(G, ctx, urban_small):
     _check(res, ref)
     plan = G.Plan(ctx, urban_small.gframes, urban_small.gmaps, w.pairs)
     best = plan.autotune(w.poses, iters=2)
-    assert best["block"] in (128, 256) and 1 <= best["pts_per_thread"] <= 256 and best["ms"] > 0
+    assert best["block"] in (64, 128, 256) and 1 <= best["pts_per_thread"] <= 256 and best["ms"] > 0
     _check(plan.linearize(w.poses), ref)
 
 
