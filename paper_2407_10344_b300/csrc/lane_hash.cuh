@@ -31,13 +31,13 @@ __device__ __forceinline__ void hash_fetch(const HashView& V, const float4 m, bo
                                            HashFetch<LMAX>& H) {
   if constexpr (IDS) H.idx = live ? kk : -1;
   const float3 q = lane_transform(V, m, live, validate, kk, H.ca, H.cb, H.cc);
-  const float4 irq = *reinterpret_cast<const float4*>(V.M.inv_r);
-  const float irv[4] = {irq.x, irq.y, irq.z, irq.w};
+  // level-0 keys, shifted on the coarser levels (resolutions doubling per level, as in lane_fetch)
+  const int k0x = __float2int_rd(__fmul_rn(q.x, V.M.inv_r[0]));
+  const int k0y = __float2int_rd(__fmul_rn(q.y, V.M.inv_r[0]));
+  const int k0z = __float2int_rd(__fmul_rn(q.z, V.M.inv_r[0]));
 #pragma unroll
   for (int l = 0; l < LMAX; ++l) {
-    const int kx = __float2int_rd(__fmul_rn(q.x, irv[l]));
-    const int ky = __float2int_rd(__fmul_rn(q.y, irv[l]));
-    const int kz = __float2int_rd(__fmul_rn(q.z, irv[l]));
+    const int kx = k0x >> l, ky = k0y >> l, kz = k0z >> l;
     H.kx[l] = kx;
     H.ky[l] = ky;
     H.kz[l] = kz;

@@ -206,9 +206,11 @@ glim_status plan_configure(glim_plan* p, const glim_lin_opts& o) {
   // a failed reconfiguration (an autotuner candidate that meets an out-of-memory condition)
   // leaves a plan that still launches its previous configuration.
   if (o.kernel == 2 && !p->d_dmaps)
-    return set_error(ctx, GLIM_EINVAL, "the dense-grid kernel needs every target level to be a dense grid");
+    return set_error(ctx, GLIM_EINVAL,
+                     "the dense-grid kernel needs every target level to be a dense grid and resolutions doubling per level");
   if (o.kernel == 3 && !p->d_hmaps)
-    return set_error(ctx, GLIM_EINVAL, "the hash kernel needs every target level to be a hash table");
+    return set_error(ctx, GLIM_EINVAL,
+                     "the hash kernel needs every target level to be a hash table and resolutions doubling per level");
   const int lane = o.kernel == 1 ? 0 : (p->d_dmaps ? 1 : (p->d_hmaps ? 2 : 0));
   const LinKernelInfo ki = pick_kernel(o.block, o.accum_mode, p->lmax, lane);
   if (!ki.fn) return set_error(ctx, GLIM_EINVAL, "no kernel for block=%d ppt=%d acc=%d", o.block, o.pts_per_thread, o.accum_mode);
@@ -320,16 +322,26 @@ glim_status plan_enqueue_kernels(glim_plan* p, int slot = -1) {
 
 LinKernelInfo pick_lin_kernel(int block, int acc, int lmax, int lane) { return pick_kernel(block, acc, lmax, lane); }
 
+// The per-lane kernels take the key of level l as the level-0 key shifted right by l, which
+// is floor(q * inv_r_l) exactly when inv_r_l = inv_r_0 2^-l (a power-of-two scaling of an
+// FP32 product is exact, and floor(floor(x) / 2^l) = floor(x / 2^l)); maps whose resolutions
+// do not double from level to level run the general kernel.
+static bool map_pow2(const glim_vmap* m) {
+  for (int l = 1; l < m->levels; ++l)
+    if (m->inv_r[l] != std::ldexp(m->inv_r[0], -l)) return false;
+  return true;
+}
+
 bool map_all_dense(const glim_vmap* m) {
   for (int l = 0; l < m->levels; ++l)
     if (!m->dense[l] || !m->slots[l]) return false;
-  return true;
+  return map_pow2(m);
 }
 
 bool map_all_hash(const glim_vmap* m) {
   for (int l = 0; l < m->levels; ++l)
     if (m->dense[l] || !m->slots[l] || !m->btab[l] || m->max_probe[l] < 1) return false;
-  return true;
+  return map_pow2(m);
 }
 
 void fill_dense_map(const glim_vmap* m, DenseMapDev& d) {

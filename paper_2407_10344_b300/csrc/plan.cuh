@@ -193,8 +193,8 @@ inline glim_status plan_upload_poses(glim_plan* p, const double* poses12) {
 }
 // false once a target map was freed or had its tables replaced since the plan was created
 bool plan_maps_current(glim_plan* p);
-bool map_all_dense(const glim_vmap* m);     // every level a dense grid
-bool map_all_hash(const glim_vmap* m);      // every level a hash table
+bool map_all_dense(const glim_vmap* m);     // every level a dense grid, resolutions doubling per level
+bool map_all_hash(const glim_vmap* m);      // every level a hash table, resolutions doubling per level
 void fill_dense_map(const glim_vmap* m, DenseMapDev& d);
 void fill_hash_map(const glim_vmap* m, const VoxSlot* empty16, HashMapDev& d);  // empty16: 16 empty slots
 // the kernel for an options' accumulation mode and block size, the deepest map's levels and
