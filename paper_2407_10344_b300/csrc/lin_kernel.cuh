@@ -632,17 +632,20 @@ __device__ __forceinline__ void lane_levels(const LaneView<typename std::conditi
     const float A00 = d * f - e * e, A01 = c * e - b * f, A02 = b * e - c * d;
     const float A11 = a * f - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
     const float det = a * A00 + b * A01 + c * A02;
-    const bool ok = hit[l] && det > 0.f && det < INFINITY;
     const float id = __fdividef(w, det);
     // A d and d^T A d; the term enters the sums as w/det times these, by fused multiply-adds
-    // predicated on `ok` (a masked term's adj(S) need not be finite, so it is not multiplied
-    // by zero: its instructions do not execute), and counts as an inlier
+    // predicated on the term's validity, an occupied record (id >= 0) and 0 < det(S) < inf,
+    // which the asm forms itself from det and the id word (three compares, no select); a
+    // masked term's adj(S) need not be finite, so it is not multiplied by zero: its
+    // instructions do not execute.  A valid term counts as an inlier.
     const float a0 = A00 * dx + A01 * dy + A02 * dz;
     const float a1 = A01 * dx + A11 * dy + A12 * dz;
     const float a2 = A02 * dx + A12 * dy + A22 * dz;
     const float el = dx * a0 + dy * a1 + dz * a2;
     asm("{\n\t.reg .pred p;\n\t"
-        "setp.ne.u32 p, %11, 0;\n\t"
+        "setp.gt.f32 p, %11, 0f00000000;\n\t"
+        "setp.lt.and.f32 p, %11, 0f7F800000, p;\n\t"
+        "setp.ge.and.s32 p, %23, 0, p;\n\t"
         "@p fma.rn.f32 %0, %13, %12, %0;\n\t"
         "@p fma.rn.f32 %1, %14, %12, %1;\n\t"
         "@p fma.rn.f32 %2, %15, %12, %2;\n\t"
@@ -656,8 +659,8 @@ __device__ __forceinline__ void lane_levels(const LaneView<typename std::conditi
         "@p add.s32 %10, %10, 1;\n\t}"
         : "+f"(O00), "+f"(O01), "+f"(O02), "+f"(O11), "+f"(O12), "+f"(O22), "+f"(g0), "+f"(g1), "+f"(g2),
           "+f"(es), "+r"(inl)
-        : "r"(ok ? 1u : 0u), "f"(id), "f"(A00), "f"(A01), "f"(A02), "f"(A11), "f"(A12), "f"(A22), "f"(a0), "f"(a1),
-          "f"(a2), "f"(el));
+        : "f"(det), "f"(id), "f"(A00), "f"(A01), "f"(A02), "f"(A11), "f"(A12), "f"(A22), "f"(a0), "f"(a1),
+          "f"(a2), "f"(el), "r"(__float_as_int(s0[l].x)));
   }
   S.O00 = O00;
   S.O01 = O01;

@@ -375,6 +375,27 @@ def test_four_level_maps(G, ctx, layout):
         plan.close()
 
 
+@pytest.mark.parametrize("layout", ["dense", "hash"])
+def test_resolutions_not_doubling_run_the_general_kernel(G, ctx, layout):
+    """The per-lane kernels take a coarser level's key as the level-0 key shifted right, which
+    is exact only when the resolutions double per level.  Maps of 0.5 / 0.75 / 1.6 m run the
+    general kernel (which forms every level's key by its own product), forcing a per-lane
+    kernel is refused, and the result matches the oracle, correspondence ids included."""
+    from gpu_helpers import Prepared
+    w = synth.corridor(n_kf=3, n_cur=8000, kf_range=(5000, 7000))
+    w.resolutions = [0.5, 0.75, 1.6]
+    P = Prepared(ctx, w, layout=layout)
+    ref = P.oracle(validate=True, want_ids=True)
+    plan = G.Plan(ctx, P.gframes, P.gmaps, w.pairs, validate_surface=True)
+    assert plan.opts()["kernel"] == "general"
+    _check(plan.linearize(w.poses), ref)
+    ids, _ = plan.correspondence_ids(w.poses)
+    assert np.array_equal(ids.cpu().numpy(), ref["ids"])
+    plan.close()
+    with pytest.raises(G.GlimError, match="EINVAL"):
+        G.linearize(ctx, P.gframes, P.gmaps, w.pairs, w.poses, kernel=layout)
+
+
 @pytest.mark.parametrize("validate", [False, True])
 def test_hash_kernel_and_general_kernel_on_hash_maps(G, ctx, room, validate):
     """Hash-table maps: the per-lane hash kernel (chosen automatically) and the general kernel
