@@ -111,7 +111,12 @@ typedef struct {
  *                     one is a hash table, else the general kernel; 1 = the general kernel
  *                     (any mix of dense grids and hash tables); 2 = the dense-grid kernel,
  *                     3 = the hash kernel (GLIM_EINVAL if a target level has the other
- *                     layout).  All give the same results up to FP32 rounding order.
+ *                     layout).  The per-lane kernels form a coarser level's key as the
+ *                     level-0 key shifted right, so they also need every target map's
+ *                     resolutions to double from level to level (r_l = r_0 2^l, the paper's
+ *                     multi-resolution maps); other maps take the general kernel by default
+ *                     and GLIM_EINVAL with 2 or 3.  All give the same results up to FP32
+ *                     rounding order.
  *   reserved          must be 0. */
 typedef struct {
   int32_t validate_surface;
